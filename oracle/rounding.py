@@ -1,0 +1,222 @@
+"""TT-rounding algorithms of the paper, written step by step in FP64 (numpy / LAPACK).
+
+TEST INFRASTRUCTURE ONLY: this is the CPU oracle the CUDA path is checked against.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may use it.
+It shares no code with the CUDA path; both sides only share the seeded input generators.
+
+Contents (paper sections / algorithms):
+* ``partial_contractions_rl``  - Algorithm 3 (KRP-PartialContractionsRL), Eqs. (3.1)-(3.3)
+* ``tt_round_fixed``           - Algorithm 4 (fixed-rank Rand-Orth with KRP), Sec. 3.2
+* ``residual_sketch``          - Algorithm 5 (GenerateResidualSketch), Eqs. (3.4)-(3.5)
+* ``tt_round_adaptive``        - Algorithm 6 (adaptive-rank Rand-Orth with KRP), Sec. 3.3
+* ``norm_estimate``            - Remark 3.1, Eq. (3.6)
+* ``svd_pass_rl``              - Remark 3.2 (the "Adap-R" compression pass, right to left)
+* ``tt_round_deterministic``   - Algorithm 1 (TT-Rounding, Oseledets)
+
+Library primitives used as single steps: matrix product, Householder QR (numpy.linalg.qr)
+and the SVD (numpy.linalg.svd).  Readings of points where the paper is silent or garbled:
+  R1  W_k(a, j) = sum_{i,c} X_k(a,i,c) W_{k+1}(c,j) Omega_k(i,j): the KRP rows are ordered
+      (i, c) with c fastest, matching the columns of H(X_k) (Eq. (3.3) read by index).
+  R2  Omega_k(i, j) depends only on (seed, k, i, j) for a global column index j; extending W
+      (Algorithm 5) appends columns col(W)..col(Q)+b-1 of that one stream (the printed size
+      "n_j x (b - col(W_{k+1}))" is read as col(Q) + b - col(W_{k+1}) columns).
+  R3  Block sizes: block > 0 gives b_init = b_inc = block; otherwise b = ceil(f * rbar_k)
+      with f_init, f_inc as in Sec. 3.3 (a 1e-9 guard makes ceil exact for products like
+      30*0.1); every block is clamped to [1, rbar_k].
+  R4  The adaptive loop also stops once col(Q_k) = rbar_k (stated in the text of Sec. 3.3,
+      missing from the while condition of Algorithm 6); the last block is clamped to
+      rbar_k - col(Q_k).
+  R5  Initial sketch width w0 = ceil(f_init * max_k r_k) (Algorithm 6, first line), or
+      ``block`` in block mode; Eq. (3.6) divides by w0.
+  R6  Fixed rank: l_k is clamped to min(l_k, l_{k-1} n_k, r_k, prod_{j>k} n_j) so that the
+      sketch has no more columns than the rank it can have.
+  R7  The tau-truncated SVD keeps the smallest rank whose discarded tail is <= tau (see
+      ``oracle.tt.truncation_rank``); the Adap-R pass reuses tau (Remark 3.2) unless
+      ``adap_r_tau`` is given.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .philox import omega
+from .tt import H, V, modes, orthogonalize_rl, ranks, truncation_rank
+
+
+def block_size(rbar: int, block: int, frac: float) -> int:
+    """Reading R3: block > 0 wins, else ceil(frac * rbar); clamped to [1, rbar]."""
+    b = block if block > 0 else int(math.ceil(rbar * frac - 1e-9))
+    return max(1, min(rbar, b))
+
+
+def partial_contractions_rl(cores, seed: int, col0: int, col1: int, t: int = 2):
+    """Algorithm 3 on sketch columns [col0, col1): {W_k(:, col0:col1)} for k = d..t (1-based k).
+
+    W_d = H(X_d) Omega_d and W_k = H(X_k) [W_{k+1} (KRP) Omega_k]   (Eqs. (3.1)-(3.3), R1).
+    """
+    d = len(cores)
+    n = modes(cores)
+    W = {}
+    W[d] = H(cores[d - 1]) @ omega(seed, d, n[d - 1], col0, col1)
+    for k in range(d - 1, t - 1, -1):
+        om = omega(seed, k, n[k - 1], col0, col1)                 # n_k x w
+        wn = W[k + 1]                                              # r_k x w
+        krp = (om[:, None, :] * wn[None, :, :]).reshape(-1, wn.shape[1])   # rows (i, c), c fastest
+        W[k] = H(cores[k - 1]) @ krp
+    return W
+
+
+def norm_estimate(core1: np.ndarray, W2: np.ndarray) -> float:
+    """Remark 3.1, Eq. (3.6): ||X|| ~ ||V(X_1) W_2||_F / sqrt(#columns of W_2)."""
+    return float(np.linalg.norm(V(core1) @ W2) / math.sqrt(W2.shape[1]))
+
+
+def tt_round_fixed(cores, ell, seed: int):
+    """Algorithm 4: fixed-rank randomize-then-orthogonalize with KRP sketches.
+
+    ``ell`` is one target rank or a list (l_1..l_{d-1}).  Returns (Y cores, info).
+    """
+    d = len(cores)
+    r, n = ranks(cores), modes(cores)
+    ell_k = [int(ell)] * (d - 1) if np.isscalar(ell) else [int(v) for v in ell]
+    lmax = max(ell_k)
+    W = partial_contractions_rl(cores, seed, 0, lmax)              # line: {W_k} = KRP-PartialContractionsRL
+    Y = [None] * d
+    Yk = cores[0].copy()                                           # Y_1 = X_1
+    out_ranks = [1]
+    for k in range(1, d):                                          # paper k = 1..d-1
+        Z = V(Yk)                                                  # (l_{k-1} n_k) x r_k
+        right = int(np.prod(n[k:]))
+        lk = min(ell_k[k - 1], Z.shape[0], Z.shape[1], right)      # R6
+        S = Z @ W[k + 1][:, :lk]                                   # S_k = V(Y_k) W_{k+1}(:, 1:l_k)
+        Q, _ = np.linalg.qr(S)                                     # thin QR
+        M = Q.T @ Z                                                # M_k = Q_k^T V(Y_k)
+        Y[k - 1] = Q.reshape(out_ranks[-1], n[k - 1], lk)          # V(Y_k) = Q_k
+        Yk = (M @ H(cores[k])).reshape(lk, n[k], r[k + 1])         # H(Y_{k+1}) = M_k H(X_{k+1})
+        out_ranks.append(lk)
+    Y[d - 1] = Yk
+    out_ranks.append(1)
+    return Y, {"ranks": out_ranks, "width": lmax}
+
+
+class _Sketches:
+    """The growing partial contractions W_{k+1..d} of Algorithm 6 (all share one width)."""
+
+    def __init__(self, cores, seed: int, w0: int):
+        self.cores, self.seed = cores, seed
+        self.W = partial_contractions_rl(cores, seed, 0, w0)
+        self.width = w0
+        self.extensions = 0
+
+    def ensure(self, k: int, need: int):
+        """Algorithm 5, first branch: if col(W_{k+1}) < need, append columns for j = k+1..d (R2)."""
+        if self.width >= need:
+            return
+        new = partial_contractions_rl(self.cores, self.seed, self.width, need, t=k + 1)
+        for j, wj in new.items():
+            self.W[j] = np.concatenate([self.W[j], wj], axis=1)
+        self.width = need
+        self.extensions += 1
+
+
+def residual_sketch(sk: _Sketches, Z: np.ndarray, Q: np.ndarray, k: int, b: int) -> np.ndarray:
+    """Algorithm 5 (GenerateResidualSketch): S = Z W_{k+1}(:, col(Q)+1 : col(Q)+b), then S - Q(Q^T S)."""
+    c = Q.shape[1]
+    sk.ensure(k, c + b)
+    S = Z @ sk.W[k + 1][:, c:c + b]                                # Eq. (3.4)
+    return S - Q @ (Q.T @ S)                                       # Eq. (3.5)
+
+
+def tt_round_adaptive(cores, tol: float, seed: int, block: int = 0, f_init: float = 0.1,
+                      f_inc: float = 0.05, nrmx: float | None = None, adap_r: bool = False,
+                      adap_r_tau: float | None = None):
+    """Algorithm 6: adaptive-rank randomize-then-orthogonalize with KRP sketches.
+
+    ``nrmx`` is ||X|| if known; otherwise Eq. (3.6) estimates it (Remark 3.1).  ``adap_r``
+    appends the right-to-left compression pass of Remark 3.2.  Returns (Y cores, info).
+    """
+    d = len(cores)
+    r, n = ranks(cores), modes(cores)
+    w0 = block if block > 0 else int(math.ceil(max(r[1:d]) * f_init - 1e-9))   # R5
+    w0 = max(1, w0)
+    sk = _Sketches(cores, seed, w0)                                # Omega_2..Omega_d, W_2..W_d
+    if nrmx is None:
+        nrmx = norm_estimate(cores[0], sk.W[2][:, :w0])
+    tau = tol * nrmx / math.sqrt(d - 1)
+    Y = [None] * d
+    Yk = cores[0].copy()                                           # Y_1 = X_1
+    out_ranks, ests = [1], []
+    for k in range(1, d):
+        Z = V(Yk)
+        rbar = min(Z.shape)
+        b_init = block_size(rbar, block, f_init)
+        sk.ensure(k, b_init)
+        S = Z @ sk.W[k + 1][:, :b_init]                            # phase 1 sketch
+        Q, _ = np.linalg.qr(S)
+        Hn = (Q.T @ Z) @ H(cores[k])                               # H(Y_{k+1}) = M_k H(X_{k+1})
+        b_inc = block_size(rbar, block, f_inc)
+        est_k = []
+        while Q.shape[1] < rbar:                                   # R4
+            S = residual_sketch(sk, Z, Q, k, b_inc)
+            est = float(np.linalg.norm(S) / math.sqrt(b_inc))
+            est_k.append(est)
+            if not est > tau:
+                break
+            bb = min(b_inc, rbar - Q.shape[1])                     # R4: last block clamped
+            Qn, _ = np.linalg.qr(S[:, :bb])
+            Qn, _ = np.linalg.qr(Qn - Q @ (Q.T @ Qn))              # re-orthogonalization
+            Q = np.concatenate([Q, Qn], axis=1)
+            Hn = np.concatenate([Hn, (Qn.T @ Z) @ H(cores[k])], axis=0)   # append rows
+        lk = Q.shape[1]
+        Y[k - 1] = Q.reshape(out_ranks[-1], n[k - 1], lk)          # V(Y_k) = Q_k
+        Yk = Hn.reshape(lk, n[k], r[k + 1])
+        out_ranks.append(lk)
+        ests.append(est_k)
+    Y[d - 1] = Yk
+    out_ranks.append(1)
+    info = {"ranks": out_ranks, "tau": tau, "nrmx": nrmx, "estimates": ests,
+            "width": sk.width, "extensions": sk.extensions, "w0": w0}
+    if adap_r:
+        Y = svd_pass_rl(Y, tau if adap_r_tau is None else adap_r_tau)
+        info["ranks_before_adap_r"] = out_ranks
+        info["ranks"] = ranks(Y)
+    return Y, info
+
+
+def svd_pass_rl(cores, tau: float | None = None, max_rank=None):
+    """Remark 3.2: right-to-left truncation of a left-orthonormal TT (k = d..2).
+
+    For each k: [Q, R] = QR(H(Y_k)^T); [U, s, Vt] = SVD(R^T) truncated at ``tau`` (R7) and/or
+    at ``max_rank``; H(Y_k) = Vt Q^T (orthonormal rows); V(Y_{k-1}) = V(Y_{k-1}) U diag(s).
+    """
+    Y = [c.copy() for c in cores]
+    d = len(Y)
+    for k in range(d - 1, 0, -1):
+        r0, nk, r1 = Y[k].shape
+        Q, R = np.linalg.qr(H(Y[k]).T)                             # (n r1) x m, m x r0
+        U, s, Vt = np.linalg.svd(R.T, full_matrices=False)        # r0 x p, p, p x m
+        rp = len(s) if tau is None else truncation_rank(s, tau)
+        if max_rank is not None:
+            mr = max_rank if np.isscalar(max_rank) else max_rank[k - 1]
+            rp = min(rp, int(mr))
+        Y[k] = (Vt[:rp] @ Q.T).reshape(rp, nk, r1)
+        p0, pn, _ = Y[k - 1].shape
+        Y[k - 1] = (V(Y[k - 1]) @ (U[:, :rp] * s[:rp])).reshape(p0, pn, rp)
+    return Y
+
+
+def tt_round_deterministic(cores, tol: float):
+    """Algorithm 1 (TT-Rounding): orthogonalize right to left, then tau-truncated SVDs left to right."""
+    d = len(cores)
+    Y = orthogonalize_rl(cores)                                    # OrthogonalizeRL
+    tau = float(np.linalg.norm(Y[0])) * tol / math.sqrt(d - 1)     # tau = ||Y_1|| eps / sqrt(d-1)
+    for k in range(d - 1):
+        r0, nk, r1 = Y[k].shape
+        Q, R = np.linalg.qr(V(Y[k]))                               # [V(Y_k), R] = QR(V(Y_k))
+        U, s, Vt = np.linalg.svd(R, full_matrices=False)
+        rp = truncation_rank(s, tau)
+        Y[k] = (Q @ U[:, :rp]).reshape(r0, nk, rp)                 # V(Y_k) = V(Y_k) U
+        q0, qn, q1 = Y[k + 1].shape
+        Y[k + 1] = ((s[:rp, None] * Vt[:rp]) @ H(Y[k + 1])).reshape(rp, qn, q1)   # H(Y_{k+1}) = S V^T H(Y_{k+1})
+    return Y, {"ranks": ranks(Y), "tau": tau}
