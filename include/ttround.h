@@ -1,0 +1,162 @@
+/*
+ * ttround.h - C ABI of libttround: randomized TT-rounding with Khatri-Rao-product (KRP)
+ * sketches on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Al Daas, Ballard, Grigori, Martinez Aguilar, Saibaba, Verma, "Adaptive Randomized
+ * Tensor Train Rounding using Khatri-Rao Products" (arXiv 2511.03598).
+ *
+ * TT layout (Sec. 2.2, Eq. (2.1)): a d-way tensor X = [X_1, ..., X_d] with cores
+ * X_k in R^{r_{k-1} x n_k x r_k}, r_0 = r_d = 1.  Every core is one contiguous row-major
+ * FP64 array [a][i][c] (a < r_{k-1}, i < n_k, c < r_k) in DEVICE memory, so that the
+ * vertical unfolding V(X_k) is the row-major (r_{k-1} n_k) x r_k matrix and the horizontal
+ * unfolding H(X_k) the row-major r_{k-1} x (n_k r_k) matrix, with no copies.
+ *
+ * Arguments common to the rounding calls
+ *   d        number of cores, 2 <= d <= TTR_MAX_D.
+ *   n        HOST array of d mode sizes, n[k] >= 1.
+ *   r        HOST array of d+1 ranks, r[0] = r[d] = 1, r[k] >= 1.
+ *   cores    HOST array of d DEVICE pointers; core k holds r[k]*n[k]*r[k+1] doubles and must
+ *            be 8-byte aligned.  Read only; not retained after the call returns.
+ *   stream   a cudaStream_t (passed as void*; NULL = legacy default stream).  All device
+ *            work is ordered on it.  The call returns after the result is complete on the
+ *            device and its ranks are known on the host (it synchronizes the stream).
+ *   opts     optional (NULL = defaults, see ttr_default_options).
+ *   out      result; on success the library owns out->cores (one device allocation made
+ *            with cudaMallocAsync on `stream`) and out->ranks / out->estimates (host); the
+ *            caller releases them with ttr_free.  On error nothing is allocated and *out is
+ *            zeroed except out->status.
+ *
+ * Errors: every call returns a ttr_status; the library never aborts, traps or exits.  Device
+ * waits inside kernels are bounded; a wait that runs out reports TTR_ERR_TIMEOUT.
+ *
+ * Threading: calls on different streams may run concurrently from different host threads.
+ */
+#ifndef TTROUND_H
+#define TTROUND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TTR_MAX_D 4096
+
+typedef enum {
+  TTR_OK = 0,
+  TTR_ERR_ARG = 1,           /* invalid argument (d, n, r, pointers, tol, ell, block, opts) */
+  TTR_ERR_OOM = 2,           /* a device or host allocation failed */
+  TTR_ERR_NONFINITE = 3,     /* NaN/Inf met in a sketch, a norm or an estimate */
+  TTR_ERR_QR_BREAKDOWN = 4,  /* CholeskyQR failed even after the shifted fallback */
+  TTR_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+  TTR_ERR_CUDA = 6,          /* a CUDA runtime call failed (message in ttr_last_error) */
+  TTR_ERR_UNSUPPORTED = 7    /* the request is outside what this build supports */
+} ttr_status;
+
+/* Arithmetic used for the large contractions (partial contractions, sketches, projections).
+ * TTR_PREC_FP64: native FP64 FMA (DFMA) everywhere.
+ * TTR_PREC_SLICED: the large contractions run on the BF16 tensor cores (tcgen05) on
+ *   fixed-point slices of the FP64 operands with exact FP32 accumulation, recombined in
+ *   integer/FP64 arithmetic; `slices` sets the number of 7-bit slices per operand (3..8);
+ *   8 slices reproduce FP64 results to about 1e-15 relative.  QR, Gram matrices, the
+ *   estimator and all truncation decisions stay FP64. */
+typedef enum { TTR_PREC_FP64 = 0, TTR_PREC_SLICED = 1 } ttr_precision;
+
+typedef struct {
+  int32_t precision;      /* ttr_precision */
+  int32_t slices;         /* TTR_PREC_SLICED only; 0 = choose from the tolerance */
+  int32_t adap_r;         /* 1: append the right-to-left compression pass (Remark 3.2) */
+  double adap_r_tau_scale;/* threshold of that pass = scale * tau (paper: 1.0) */
+  double nrmx;            /* adaptive only: ||X|| if known (> 0), else estimated by Eq. (3.6) */
+  double f_init, f_inc;   /* adaptive block fractions of Sec. 3.3, used when block <= 0 */
+  int64_t width_hint;     /* initial sketch width drawn on the device (0 = automatic); never
+                             changes results, only how often the partial contractions are
+                             extended (Algorithm 5) */
+} ttr_options;
+
+typedef struct {
+  int32_t status;         /* ttr_status of the call */
+  int32_t d;
+  int64_t* ranks;         /* host, d+1 output ranks */
+  double** cores;         /* host array of d device pointers (one arena) */
+  void* arena;            /* the device allocation behind cores */
+  double tau;             /* per-core threshold used (adaptive, deterministic) */
+  double nrmx;            /* norm used for tau (given or estimated) */
+  int64_t width;          /* final number of sketch columns of W_2..W_d */
+  int32_t extensions;     /* times Algorithm 5 appended columns to the partial contractions */
+  int32_t n_estimates;    /* number of entries in estimates */
+  double* estimates;      /* host: residual estimates ||S_k||_F / sqrt(b_inc) in sweep order */
+  int32_t* est_core;      /* host: core index k (1-based) of each estimate */
+  float ms_sketch_rl;     /* device time of the right-to-left partial contractions */
+  float ms_sweep_lr;      /* device time of the left-to-right sweep */
+  float ms_total;         /* device time of the whole call */
+  int64_t kernel_launches;/* kernels this call launched */
+} ttr_result;
+
+/* Fill `opts` with defaults: FP64, adap_r off, scale 1, nrmx 0 (estimate), f_init 0.1,
+ * f_inc 0.05 (the values of Sec. 4.2), width_hint 0. */
+void ttr_default_options(ttr_options* opts);
+
+/* Algorithm 4 (Sec. 3.2): fixed-rank randomize-then-orthogonalize with a KRP sketch.
+ *   ell    target rank l >= 1 for every bond; l_k is clamped to
+ *          min(l, l_{k-1} n_k, r_k, prod_{j>k} n_j).
+ *   target if 0 < target < l, the left-orthonormal result is truncated to rank `target` by a
+ *          right-to-left SVD pass (Remark 3.2 with a rank bound); <= 0 keeps rank l.
+ *   seed   64-bit key of the Gaussian stream: Omega_k(i, j) = round_to_binary32(Box-Muller of
+ *          Philox4x32-10(counter (j, i, k, 0), key seed)), k 1-based.  The same seed gives the
+ *          same Omega as the CPU oracle, bit for bit.
+ * Output cores 1..d-1 are left-orthonormal (V(Y_k)^T V(Y_k) = I). */
+int tt_round_fixed(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
+                   int64_t ell, int64_t target, uint64_t seed, const ttr_options* opts,
+                   void* stream, ttr_result* out);
+
+/* Algorithm 6 (Sec. 3.3) with Algorithm 5: adaptive-rank rounding to relative tolerance tol.
+ *   tol    relative Frobenius tolerance eps > 0; per-core threshold tau = eps*nrmx/sqrt(d-1).
+ *   block  > 0: b_init = b_inc = block; <= 0: b = ceil(f * rbar_k) with opts->f_init/f_inc.
+ *   seed   as in tt_round_fixed; the first columns of the sketch are those of the fixed call.
+ * The loop at core k stops when ||S_k||_F / sqrt(b_inc) <= tau (Eq. (3.5) residual sketch)
+ * or when col(Q_k) reaches rbar_k = min(rows, cols of V(Y_k)).  Output cores 1..d-1 are
+ * left-orthonormal unless opts->adap_r is set (then cores 2..d are right-orthonormal). */
+int tt_round_adaptive(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
+                      double tol, int64_t block, uint64_t seed, const ttr_options* opts,
+                      void* stream, ttr_result* out);
+
+/* Algorithm 1 (Sec. 2.3, Oseledets' TT-Rounding), FP64: right-to-left orthogonalization,
+ * tau = ||Y_1|| tol / sqrt(d-1), left-to-right tau-truncated SVDs (smallest rank whose
+ * discarded Frobenius tail is <= tau).  The baseline the randomized calls are measured
+ * against. */
+int tt_round_deterministic(int32_t d, const int64_t* n, const int64_t* r,
+                           const double* const* cores, double tol, void* stream,
+                           ttr_result* out);
+
+/* Release what a successful call allocated (device arena on `stream`, host arrays) and zero
+ * *out.  Safe on a zeroed or already freed result. */
+void ttr_free(ttr_result* out, void* stream);
+
+/* Static description of a status code. */
+const char* ttr_strerror(int status);
+
+/* Last error message of the calling host thread (CUDA error text, argument problem). */
+const char* ttr_last_error(void);
+
+/* Gaussian sketch block Omega_k(:, col0:col1) as produced on the device (Sec. 3.1), written
+ * row-major [i][j - col0] to the DEVICE buffer `dst` (n_k * (col1 - col0) doubles, values
+ * exactly representable in binary32).  For parity tests of the sketch stream. */
+int ttr_sketch_omega(uint64_t seed, int32_t k, int64_t n_k, int64_t col0, int64_t col1,
+                     double* dst, void* stream);
+
+/* Right-to-left KRP partial contractions (Algorithm 3, Eqs. (3.1)-(3.3)) on sketch columns
+ * [col0, col1), for k = d..t (1-based, 2 <= t <= d).  W[k-1] (k = t..d) are DEVICE buffers of
+ * r[k-1] * (col1 - col0) doubles, row-major [a][j - col0]; W[k-1] for k < t are ignored.
+ * precision/slices as in ttr_options.  For parity tests of the hot kernel and for callers
+ * that want the sketches alone. */
+int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r,
+                             const double* const* cores, uint64_t seed, int64_t col0,
+                             int64_t col1, int32_t t, int32_t precision, int32_t slices,
+                             double* const* W, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTROUND_H */

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of libttround (include/ttround.h): argument marshalling only.
+
+Cores are torch CUDA float64 tensors of shape (r_{k-1}, n_k, r_k); PyTorch provides device
+memory and the current stream.  Every step of the rounding runs inside the library's CUDA
+kernels; there is no CPU path: if the library is missing this module raises on load.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libttround.so")
+
+TTR_PREC_FP64 = 0
+TTR_PREC_SLICED = 1
+STATUS = {0: "TTR_OK", 1: "TTR_ERR_ARG", 2: "TTR_ERR_OOM", 3: "TTR_ERR_NONFINITE", 4: "TTR_ERR_QR_BREAKDOWN",
+          5: "TTR_ERR_TIMEOUT", 6: "TTR_ERR_CUDA", 7: "TTR_ERR_UNSUPPORTED"}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("slices", ctypes.c_int32), ("adap_r", ctypes.c_int32),
+                ("adap_r_tau_scale", ctypes.c_double), ("nrmx", ctypes.c_double), ("f_init", ctypes.c_double),
+                ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("d", ctypes.c_int32), ("ranks", ctypes.POINTER(ctypes.c_int64)),
+                ("cores", ctypes.POINTER(ctypes.c_void_p)), ("arena", ctypes.c_void_p), ("tau", ctypes.c_double),
+                ("nrmx", ctypes.c_double), ("width", ctypes.c_int64), ("extensions", ctypes.c_int32),
+                ("n_estimates", ctypes.c_int32), ("estimates", ctypes.POINTER(ctypes.c_double)),
+                ("est_core", ctypes.POINTER(ctypes.c_int32)), ("ms_sketch_rl", ctypes.c_float),
+                ("ms_sweep_lr", ctypes.c_float), ("ms_total", ctypes.c_float), ("kernel_launches", ctypes.c_int64)]
+
+
+class TTRoundError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libttround.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libttround.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        i32, i64, u64, dbl, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+        P64 = ctypes.POINTER(ctypes.c_int64)
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        L.ttr_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.tt_round_fixed.argtypes = [i32, P64, P64, PP, i64, i64, u64, ctypes.POINTER(Options), vp, ctypes.POINTER(Result)]
+        L.tt_round_adaptive.argtypes = [i32, P64, P64, PP, dbl, i64, u64, ctypes.POINTER(Options), vp, ctypes.POINTER(Result)]
+        L.tt_round_deterministic.argtypes = [i32, P64, P64, PP, dbl, vp, ctypes.POINTER(Result)]
+        L.ttr_free.argtypes = [ctypes.POINTER(Result), vp]
+        L.ttr_free.restype = None
+        L.ttr_strerror.restype = ctypes.c_char_p
+        L.ttr_last_error.restype = ctypes.c_char_p
+        L.ttr_sketch_omega.argtypes = [u64, i32, i64, i64, i64, vp, vp]
+        L.ttr_partial_contractions.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, i32, i32, PP, vp]
+        for f in ("tt_round_fixed", "tt_round_adaptive", "tt_round_deterministic", "ttr_sketch_omega",
+                  "ttr_partial_contractions"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise TTRoundError(st, lib().ttr_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _tt_args(cores):
+    import torch
+    d = len(cores)
+    for c in cores:
+        if not (isinstance(c, torch.Tensor) and c.is_cuda and c.dtype == torch.float64 and c.dim() == 3
+                and c.is_contiguous()):
+            raise ValueError("cores must be contiguous CUDA float64 tensors of shape (r0, n, r1)")
+    n = (ctypes.c_int64 * d)(*[int(c.shape[1]) for c in cores])
+    r = (ctypes.c_int64 * (d + 1))(*([int(cores[0].shape[0])] + [int(c.shape[2]) for c in cores]))
+    ptrs = (ctypes.c_void_p * d)(*[c.data_ptr() for c in cores])
+    return d, n, r, ptrs
+
+
+def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = False, adap_r_tau_scale: float = 1.0,
+            nrmx: float = 0.0, f_init: float = 0.1, f_inc: float = 0.05, width_hint: int = 0) -> Options:
+    o = Options()
+    lib().ttr_default_options(ctypes.byref(o))
+    o.precision, o.slices, o.adap_r = precision, slices, int(adap_r)
+    o.adap_r_tau_scale, o.nrmx, o.f_init, o.f_inc, o.width_hint = adap_r_tau_scale, nrmx, f_init, f_inc, width_hint
+    return o
+
+
+class Rounded:
+    """A rounded TT owned by the library (device arena); call ``free()`` or use as a context manager."""
+
+    def __init__(self, res: Result, stream):
+        self._res, self._stream = res, stream
+
+    @property
+    def d(self) -> int:
+        return self._res.d
+
+    @property
+    def ranks(self) -> list:
+        return [int(self._res.ranks[i]) for i in range(self._res.d + 1)]
+
+    @property
+    def info(self) -> dict:
+        r = self._res
+        ne = r.n_estimates
+        return {"ranks": self.ranks, "tau": r.tau, "nrmx": r.nrmx, "width": int(r.width),
+                "extensions": int(r.extensions),
+                "estimates": [r.estimates[i] for i in range(ne)] if ne else [],
+                "est_core": [int(r.est_core[i]) for i in range(ne)] if ne else [],
+                "ms_sketch_rl": r.ms_sketch_rl, "ms_sweep_lr": r.ms_sweep_lr, "ms_total": r.ms_total,
+                "kernel_launches": int(r.kernel_launches)}
+
+    def core_ptr(self, k: int) -> int:
+        return int(self._res.cores[k])
+
+    def to_torch(self):
+        """Copies of the cores as torch CUDA tensors."""
+        import torch
+        out = []
+        rk = self.ranks
+        for k in range(self.d):
+            shape = (rk[k], self._res_n[k], rk[k + 1])
+            t = torch.empty(shape, dtype=torch.float64, device="cuda")
+            nbytes = t.numel() * 8
+            _cuda_memcpy_d2d(t.data_ptr(), self.core_ptr(k), nbytes, self._stream)
+            out.append(t)
+        return out
+
+    def to_numpy(self):
+        return [t.cpu().numpy() for t in self.to_torch()]
+
+    def free(self):
+        if self._res.arena:
+            lib().ttr_free(ctypes.byref(self._res), self._stream)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _cuda_memcpy_d2d(dst: int, src: int, nbytes: int, stream):
+    import torch
+    # a byte view copy through torch on the same stream (no host round trip)
+    s = torch.cuda.ExternalStream(stream.value) if stream.value else torch.cuda.current_stream()
+    with torch.cuda.stream(s):
+        src_t = _wrap_device_ptr(src, nbytes)
+        dst_t = _wrap_device_ptr(dst, nbytes)
+        dst_t.copy_(src_t)
+
+
+def _wrap_device_ptr(ptr: int, nbytes: int):
+    import torch
+
+    class _Holder:
+        def __init__(self, p, n):
+            self.__cuda_array_interface__ = {"shape": (n,), "typestr": "|u1", "data": (p, False), "version": 3}
+
+    return torch.as_tensor(_Holder(ptr, nbytes), device="cuda")
+
+
+def _finish(res: Result, st: int, stream, n):
+    _check(st)
+    out = Rounded(res, stream)
+    out._res_n = n
+    return out
+
+
+def round_fixed(cores, ell: int, seed: int, target: int = 0, opts: Options | None = None, stream=None) -> Rounded:
+    """Algorithm 4 (fixed rank ell, optional truncation to ``target``); see tt_round_fixed."""
+    d, n, r, p = _tt_args(cores)
+    res = Result()
+    s = _stream_handle(stream)
+    st = lib().tt_round_fixed(d, n, r, p, int(ell), int(target), ctypes.c_uint64(seed),
+                              ctypes.byref(opts) if opts else None, s, ctypes.byref(res))
+    return _finish(res, st, s, list(n))
+
+
+def round_adaptive(cores, tol: float, block: int, seed: int, opts: Options | None = None, stream=None) -> Rounded:
+    """Algorithm 6 (adaptive rank to relative tolerance ``tol``); see tt_round_adaptive."""
+    d, n, r, p = _tt_args(cores)
+    res = Result()
+    s = _stream_handle(stream)
+    st = lib().tt_round_adaptive(d, n, r, p, float(tol), int(block), ctypes.c_uint64(seed),
+                                 ctypes.byref(opts) if opts else None, s, ctypes.byref(res))
+    return _finish(res, st, s, list(n))
+
+
+def round_deterministic(cores, tol: float, stream=None) -> Rounded:
+    """Algorithm 1 (deterministic TT-rounding, FP64); see tt_round_deterministic."""
+    d, n, r, p = _tt_args(cores)
+    res = Result()
+    s = _stream_handle(stream)
+    st = lib().tt_round_deterministic(d, n, r, p, float(tol), s, ctypes.byref(res))
+    return _finish(res, st, s, list(n))
+
+
+def sketch_omega(seed: int, k: int, n_k: int, col0: int, col1: int, stream=None):
+    import torch
+    out = torch.empty((n_k, col1 - col0), dtype=torch.float64, device="cuda")
+    _check(lib().ttr_sketch_omega(ctypes.c_uint64(seed), k, n_k, col0, col1, ctypes.c_void_p(out.data_ptr()),
+                                  _stream_handle(stream)))
+    return out
+
+
+def partial_contractions(cores, seed: int, col0: int, col1: int, t: int = 2, precision: int = TTR_PREC_FP64,
+                         slices: int = 0, stream=None) -> dict:
+    """Algorithm 3 on sketch columns [col0, col1): {k: W_k} for k = t..d (1-based)."""
+    import torch
+    d, n, r, p = _tt_args(cores)
+    w = col1 - col0
+    bufs = {k: torch.empty((r[k - 1], w), dtype=torch.float64, device="cuda") for k in range(t, d + 1)}
+    ptrs = (ctypes.c_void_p * d)(*[bufs[k + 1].data_ptr() if (k + 1) in bufs else 0 for k in range(d)])
+    _check(lib().ttr_partial_contractions(d, n, r, p, ctypes.c_uint64(seed), col0, col1, t, precision, slices, ptrs,
+                                          _stream_handle(stream)))
+    return bufs
+
+
+@dataclass
+class HostRounding:
+    cores: list
+    ranks: list
+    info: dict
+
+
+def round_adaptive_host(cores_np, tol: float, block: int, seed: int, opts: Options | None = None) -> HostRounding:
+    """End-to-end call with HOST inputs: upload, round, download (what a CPU-side user calls)."""
+    import torch
+    dev = [torch.from_numpy(np.ascontiguousarray(c)).pin_memory().to("cuda", non_blocking=True) for c in cores_np]
+    with round_adaptive(dev, tol, block, seed, opts) as y:
+        out = [t.cpu().numpy() for t in y.to_torch()]
+        return HostRounding(out, y.ranks, y.info)

@@ -1,0 +1,961 @@
+// Host driver of libttround: argument checking, device buffers, the right-to-left sketch pass,
+// the left-to-right sweeps of the fixed-rank and adaptive algorithms, the deterministic
+// baseline and the C-ABI entry points.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+#include "ttr_internal.cuh"
+
+namespace ttr {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int Ctx::alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    *p = nullptr;
+    return TTR_ERR_OOM;
+  }
+  owned.push_back(*p);
+  return TTR_OK;
+}
+
+int Ctx::check_launch(const char* what) {
+  ++launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return TTR_ERR_CUDA;
+  }
+  return TTR_OK;
+}
+
+void Ctx::release() {
+  for (void* p : owned) cudaFreeAsync(p, stream);
+  owned.clear();
+}
+
+// Hand an allocation to the caller: it is no longer freed with the context.
+static void disown(Ctx& c, void* p) {
+  auto it = std::find(c.owned.begin(), c.owned.end(), p);
+  if (it != c.owned.end()) c.owned.erase(it);
+}
+
+// ----------------------------------------------------------------------------- validation
+struct TT {
+  int d;
+  const int64_t* n;
+  const int64_t* r;
+  const double* const* cores;
+};
+
+static int validate(const TT& X) {
+  if (X.d < 2 || X.d > TTR_MAX_D) return set_error("d must be in [2, TTR_MAX_D]"), TTR_ERR_ARG;
+  if (!X.n || !X.r || !X.cores) return set_error("n, r and cores must be non-null"), TTR_ERR_ARG;
+  if (X.r[0] != 1 || X.r[X.d] != 1) return set_error("r[0] and r[d] must be 1"), TTR_ERR_ARG;
+  for (int k = 0; k < X.d; ++k) {
+    if (X.n[k] < 1) return set_error("mode sizes must be >= 1"), TTR_ERR_ARG;
+    if (X.r[k + 1] < 1) return set_error("ranks must be >= 1"), TTR_ERR_ARG;
+    if (!X.cores[k]) return set_error("null core pointer"), TTR_ERR_ARG;
+    if (((uintptr_t)X.cores[k]) & 7) return set_error("core pointers must be 8-byte aligned"), TTR_ERR_ARG;
+    const double big = (double)X.r[k] * (double)X.n[k] * (double)X.r[k + 1];
+    if (big > 9.0e15) return set_error("core too large"), TTR_ERR_ARG;
+  }
+  return TTR_OK;
+}
+
+static int64_t block_size(int64_t rbar, int64_t block, double frac) {
+  int64_t b = block > 0 ? block : (int64_t)ceil((double)rbar * frac - 1e-9);
+  return std::max<int64_t>(1, std::min<int64_t>(rbar, b));
+}
+
+static double dsync_read(Ctx& c, const double* dptr, int* status) {
+  double v = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&v, dptr, sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    set_error(std::string("device read: ") + cudaGetErrorString(e));
+    *status = TTR_ERR_CUDA;
+  }
+  return v;
+}
+
+static int isync_read(Ctx& c, const int* dptr, int* status) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    set_error(std::string("device read: ") + cudaGetErrorString(e));
+    *status = TTR_ERR_CUDA;
+  }
+  return v;
+}
+
+// ----------------------------------------------------------------------------- QR
+// Thin QR of the m x b row-major matrix X (leading dimension ldx), in place: X <- Q.
+// CholeskyQR2; if a Cholesky pivot breaks down, shifted CholeskyQR3 (Fukaya, Kannan,
+// Nakatsukasa, Yamamoto, Yanagisawa 2020) from the saved input.  Scratch: tmp and save
+// (m x b, ld b), G and Rinv (b x b, ld b), dscal (>= 2 doubles), dflag (1 int).
+struct QrWork {
+  double* tmp = nullptr;
+  double* save = nullptr;
+  double* G = nullptr;
+  double* Rinv = nullptr;
+  double* dscal = nullptr;
+  int* dflag = nullptr;
+};
+
+static int chol_pass(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m, int64_t b, double* out,
+                     int64_t ldo, const QrWork& w, const double* shift) {
+  TTR_CHECK(fill_zero(c, w.G, b * b));
+  Gemm g;  // G = X^T X
+  g.M = b; g.N = b; g.K = m;
+  g.A = X; g.sam = 1; g.sak = ldx;
+  g.B = X; g.sbk = ldx; g.sbn = 1;
+  g.C = w.G; g.scm = b; g.scn = 1;
+  g.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, m / 256), 128);
+  TTR_CHECK(E.small_gemm(c, g));
+  TTR_CHECK(chol_inv(c, w.G, b, b, shift, w.Rinv, w.dflag));
+  Gemm h;  // out = X Rinv
+  h.M = m; h.N = b; h.K = b;
+  h.A = X; h.sam = ldx; h.sak = 1;
+  h.B = w.Rinv; h.sbk = b; h.sbn = 1;
+  h.C = out; h.scm = ldo; h.scn = 1;
+  return E.small_gemm(c, h);
+}
+
+static int qr_inplace(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m, int64_t b, const QrWork& w) {
+  if (b <= 0) return TTR_OK;
+  if (b > m) return set_error("qr: more columns than rows"), TTR_ERR_ARG;
+  TTR_CUDA(cudaMemsetAsync(w.dflag, 0, sizeof(int), c.stream));
+  TTR_CHECK(copy2d(c, w.save, b, X, ldx, m, b));
+  TTR_CHECK(chol_pass(c, E, w.save, b, m, b, w.tmp, b, w, nullptr));
+  TTR_CHECK(chol_pass(c, E, w.tmp, b, m, b, X, ldx, w, nullptr));
+  int st = TTR_OK;
+  const int bad = isync_read(c, w.dflag, &st);
+  if (st != TTR_OK) return st;
+  if (!bad) return TTR_OK;
+  // shifted CholeskyQR3: shift = 11 (m b + b (b + 1)) u ||X||_F^2  (||X||_2 <= ||X||_F)
+  TTR_CUDA(cudaMemsetAsync(w.dflag, 0, sizeof(int), c.stream));
+  TTR_CUDA(cudaMemsetAsync(w.dscal, 0, 2 * sizeof(double), c.stream));
+  TTR_CHECK(sumsq(c, w.save, m, b, b, 1, w.dscal));
+  const double fro2 = dsync_read(c, w.dscal, &st);
+  if (st != TTR_OK) return st;
+  if (!(fro2 > 0.0) || !isfinite(fro2)) return set_error("qr: zero or non-finite input"), TTR_ERR_QR_BREAKDOWN;
+  const double sh = 11.0 * ((double)m * b + (double)b * (b + 1)) * 1.1102230246251565e-16 * fro2;
+  TTR_CUDA(cudaMemcpyAsync(w.dscal + 1, &sh, sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  // three passes that keep the saved input intact: save -> tmp (shifted) -> X -> tmp -> X
+  TTR_CHECK(chol_pass(c, E, w.save, b, m, b, w.tmp, b, w, w.dscal + 1));
+  TTR_CHECK(chol_pass(c, E, w.tmp, b, m, b, X, ldx, w, nullptr));
+  TTR_CHECK(chol_pass(c, E, X, ldx, m, b, w.tmp, b, w, nullptr));
+  TTR_CHECK(copy2d(c, X, ldx, w.tmp, b, m, b));
+  const int bad2 = isync_read(c, w.dflag, &st);
+  if (st != TTR_OK) return st;
+  if (!bad2) return TTR_OK;
+  // Exactly rank-deficient input (more sketch columns than the rank of the sketched matrix):
+  // any orthonormal completion of its range is a valid thin-QR factor, and the completion
+  // directions are orthogonal to the range, so they do not change the projected tensor.
+  // Lift the deficiency with a seeded Gaussian perturbation of relative size 1e-13 and
+  // repeat shifted CholeskyQR3 (the perturbed matrix has condition number ~1e13).
+  TTR_CUDA(cudaMemsetAsync(w.dflag, 0, sizeof(int), c.stream));
+  const double eps = 1e-13 * sqrt(fro2 / ((double)m * b));
+  const double sh2 = sh * (1.0 + 1e-26 * (double)m * b);
+  double hv[2] = {eps, sh2};
+  TTR_CUDA(cudaMemcpyAsync(w.dscal + 2, hv, 2 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  TTR_CHECK(add_gaussian(c, w.save, m, b, b, w.dscal + 2, 0x5eed5eed5eed5eedULL));
+  TTR_CHECK(chol_pass(c, E, w.save, b, m, b, w.tmp, b, w, w.dscal + 3));
+  TTR_CHECK(chol_pass(c, E, w.tmp, b, m, b, X, ldx, w, nullptr));
+  TTR_CHECK(chol_pass(c, E, X, ldx, m, b, w.tmp, b, w, nullptr));
+  TTR_CHECK(copy2d(c, X, ldx, w.tmp, b, m, b));
+  const int bad3 = isync_read(c, w.dflag, &st);
+  if (st != TTR_OK) return st;
+  if (bad3) return set_error("qr: CholeskyQR breakdown after shift and perturbation"), TTR_ERR_QR_BREAKDOWN;
+  return TTR_OK;
+}
+
+// ----------------------------------------------------------------------------- RL sketch pass
+// Algorithm 3 on columns [col0, col1) for k = d..t: W_k(:, col0:col1) with W_k row-major,
+// leading dimension ldw.  Omega blocks go to Om (core k at (k-1)*om_stride, ld ldom).
+struct Sketch {
+  std::vector<double*> W;   // W[k-1] for k = 2..d (index 0 unused)
+  int64_t ldw = 0;
+  int64_t width = 0;        // columns computed so far
+  double* Om = nullptr;
+  int64_t om_stride = 0, ldom = 0;
+  double* T = nullptr;      // (max r_{k-1} n_k) x ldw scratch
+  int extensions = 0;
+};
+
+static int rl_pass(Ctx& c, const Engine& E, const TT& X, uint64_t seed, int64_t col0, int64_t col1, int t,
+                   Sketch& s) {
+  const int d = X.d;
+  const int64_t w = col1 - col0;
+  if (w <= 0) return TTR_OK;
+  TTR_CHECK(omega_fill(c, seed, t, d, X.n, col0, col1, s.Om + (int64_t)(t - 1) * s.om_stride, s.om_stride, s.ldom));
+  // W_d = H(X_d) Omega_d  (r_{d-1} x n_d) (n_d x w)
+  {
+    Gemm g;
+    g.M = X.r[d - 1]; g.N = w; g.K = X.n[d - 1];
+    g.A = X.cores[d - 1]; g.sam = X.n[d - 1]; g.sak = 1;
+    g.B = s.Om + (int64_t)(d - 1) * s.om_stride; g.sbk = s.ldom; g.sbn = 1;
+    g.C = s.W[d - 1] + col0; g.scm = s.ldw; g.scn = 1;
+    TTR_CHECK(E.small_gemm(c, g));
+  }
+  for (int k = d - 1; k >= t; --k) {
+    TTR_CHECK(E.rl_step(c, X.cores[k - 1], X.r[k - 1], X.n[k - 1], X.r[k], s.W[k] + col0, s.ldw,
+                        s.Om + (int64_t)(k - 1) * s.om_stride, s.ldom, w, s.W[k - 1] + col0, s.ldw, s.T));
+  }
+  return TTR_OK;
+}
+
+static int sketch_alloc(Ctx& c, const TT& X, int64_t wcap, Sketch& s) {
+  const int d = X.d;
+  int64_t nmax = 1, rowsmax = 1, tot = 0;
+  for (int k = 0; k < d; ++k) {
+    nmax = std::max(nmax, X.n[k]);
+    rowsmax = std::max(rowsmax, X.r[k] * X.n[k]);
+    if (k >= 1) tot += X.r[k] * wcap;
+  }
+  s.ldw = wcap;
+  s.W.assign(d, nullptr);
+  double* base = nullptr;
+  TTR_CHECK(c.alloc_t(&base, std::max<int64_t>(tot, 1)));
+  int64_t off = 0;
+  for (int k = 2; k <= d; ++k) {
+    s.W[k - 1] = base + off;
+    off += X.r[k - 1] * wcap;
+  }
+  s.ldom = wcap;
+  s.om_stride = nmax * wcap;
+  TTR_CHECK(c.alloc_t(&s.Om, (int64_t)d * s.om_stride));
+  TTR_CHECK(c.alloc_t(&s.T, rowsmax * wcap));
+  return TTR_OK;
+}
+
+// ----------------------------------------------------------------------------- result helpers
+static void result_zero(ttr_result* out) {
+  if (out) memset(out, 0, sizeof(*out));
+}
+
+struct Timer {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  Timer() {
+    for (auto& x : e) cudaEventCreate(&x);
+  }
+  ~Timer() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  void rec(int i, cudaStream_t s) { cudaEventRecord(e[i], s); }
+  float ms(int a, int b) {
+    float v = 0.f;
+    cudaEventElapsedTime(&v, e[a], e[b]);
+    return v;
+  }
+};
+
+// Allocates the output arena (worst case: the input size) and host arrays.
+static int result_alloc(Ctx& c, const TT& X, ttr_result* out) {
+  int64_t tot = 0;
+  for (int k = 0; k < X.d; ++k) tot += X.r[k] * X.n[k] * X.r[k + 1];
+  double* arena = nullptr;
+  TTR_CHECK(c.alloc_t(&arena, tot));
+  out->arena = arena;
+  out->d = X.d;
+  out->ranks = (int64_t*)calloc(X.d + 1, sizeof(int64_t));
+  out->cores = (double**)calloc(X.d, sizeof(double*));
+  if (!out->ranks || !out->cores) return set_error("host allocation"), TTR_ERR_OOM;
+  return TTR_OK;
+}
+
+static void result_host_free(ttr_result* out) {
+  free(out->ranks);
+  free(out->cores);
+  free(out->estimates);
+  free(out->est_core);
+  out->ranks = nullptr;
+  out->cores = nullptr;
+  out->estimates = nullptr;
+  out->est_core = nullptr;
+}
+
+// ----------------------------------------------------------------------------- LR sweep buffers
+struct Sweep {
+  double* Y[2] = {nullptr, nullptr};  // current unprojected core H(Y_k) and the next one
+  double* Q = nullptr;                 // rows x qcap
+  int64_t qcap = 0;
+  double* S = nullptr;                 // rows x bcap
+  double* P = nullptr;                 // rmax x bcap
+  double* M = nullptr;                 // rmax x rmax
+  int64_t bcap = 0;
+  QrWork qr;
+};
+
+static int sweep_alloc(Ctx& c, const TT& X, int64_t bcap, Sweep& s) {
+  int64_t cmax = 1, rowsmax = 1, rmax = 1;
+  for (int k = 0; k < X.d; ++k) {
+    cmax = std::max(cmax, X.r[k] * X.n[k] * X.r[k + 1]);
+    rowsmax = std::max(rowsmax, X.r[k] * X.n[k]);
+    rmax = std::max(rmax, X.r[k + 1]);
+  }
+  s.qcap = rmax;
+  s.bcap = std::max<int64_t>(1, bcap);
+  TTR_CHECK(c.alloc_t(&s.Y[0], cmax));
+  TTR_CHECK(c.alloc_t(&s.Y[1], cmax));
+  TTR_CHECK(c.alloc_t(&s.Q, rowsmax * s.qcap));
+  TTR_CHECK(c.alloc_t(&s.S, rowsmax * s.bcap));
+  TTR_CHECK(c.alloc_t(&s.P, rmax * s.bcap));
+  TTR_CHECK(c.alloc_t(&s.M, rmax * rmax));
+  const int64_t qb = std::max(s.bcap, rmax);
+  TTR_CHECK(c.alloc_t(&s.qr.tmp, rowsmax * qb));
+  TTR_CHECK(c.alloc_t(&s.qr.save, rowsmax * qb));
+  TTR_CHECK(c.alloc_t(&s.qr.G, qb * qb));
+  TTR_CHECK(c.alloc_t(&s.qr.Rinv, qb * qb));
+  TTR_CHECK(c.alloc_t(&s.qr.dscal, 8));
+  TTR_CHECK(c.alloc_t(&s.qr.dflag, 4));
+  return TTR_OK;
+}
+
+// M = Q^T Z  (c x cols), then Ynext = M H(X_{k+1})  (c x n r)
+static int project_next(Ctx& c, const Engine& E, const Sweep& s, const double* Z, int64_t rows, int64_t cols,
+                        int64_t ccols, const TT& X, int k, double* Ynext) {
+  Gemm g;
+  g.M = ccols; g.N = cols; g.K = rows;
+  g.A = s.Q; g.sam = 1; g.sak = s.qcap;
+  g.B = Z; g.sbk = cols; g.sbn = 1;
+  g.C = s.M; g.scm = cols; g.scn = 1;
+  g.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, rows / 512), 64);
+  if (g.split_k > 1) TTR_CHECK(fill_zero(c, s.M, ccols * cols));
+  TTR_CHECK(E.small_gemm(c, g));
+  // H(X_{k+1}) is cols x (n_{k+1} r_{k+2}), row-major
+  return E.project(c, s.M, ccols, cols, X.cores[k], X.n[k] * X.r[k + 1], Ynext);
+}
+
+// ----------------------------------------------------------------------------- SVD pass (Remark 3.2)
+// Right-to-left truncation of the left-orthonormal TT held as out->cores / out->ranks, in place
+// in a fresh arena.  Threshold tau (<= 0: none) and optional rank cap.
+static int svd_pass_rl(Ctx& c, const Engine& E, ttr_result* out, const int64_t* n, double tau, int64_t max_rank) {
+  const int d = out->d;
+  int64_t* r = out->ranks;
+  int64_t rmax = 1, cmax = 1;
+  for (int k = 0; k < d; ++k) {
+    rmax = std::max(rmax, r[k + 1]);
+    cmax = std::max(cmax, r[k] * n[k] * r[k + 1]);
+  }
+  // work copies of every core (they shrink), then pack into a new arena
+  std::vector<double*> Yc(d);
+  for (int k = 0; k < d; ++k) {
+    TTR_CHECK(c.alloc_t(&Yc[k], std::max<int64_t>(r[k] * n[k] * r[k + 1], 1)));
+    TTR_CUDA(cudaMemcpyAsync(Yc[k], out->cores[k], sizeof(double) * r[k] * n[k] * r[k + 1], cudaMemcpyDeviceToDevice,
+                             c.stream));
+  }
+  double *Ht, *R, *U, *Vt, *sig, *tmp;
+  QrWork w;
+  TTR_CHECK(c.alloc_t(&Ht, cmax));
+  TTR_CHECK(c.alloc_t(&R, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&U, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&Vt, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&sig, rmax));
+  TTR_CHECK(c.alloc_t(&tmp, cmax));
+  TTR_CHECK(c.alloc_t(&w.tmp, cmax));
+  TTR_CHECK(c.alloc_t(&w.save, cmax));
+  TTR_CHECK(c.alloc_t(&w.G, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&w.Rinv, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&w.dscal, 8));
+  TTR_CHECK(c.alloc_t(&w.dflag, 4));
+  std::vector<double> hs(rmax);
+  for (int k = d - 1; k >= 1; --k) {
+    const int64_t r0 = r[k], nk = n[k], r1 = r[k + 1];
+    const int64_t m = nk * r1;  // rows of H(Y_k)^T
+    if (r0 > m) continue;       // cannot be reduced by a thin QR of H^T; keep rank
+    // Ht = H(Y_k)^T  (m x r0, row-major ld r0): Ht[(i,c), a] = Y[a][i][c]
+    TTR_CHECK(E.transpose(c, Yc[k], r0, m, Ht));
+    TTR_CHECK(qr_inplace(c, E, Ht, r0, m, r0, w));             // Ht <- Q  (m x r0)
+    // R = Q^T H(Y_k)^T  (r0 x r0)
+    Gemm g;
+    g.M = r0; g.N = r0; g.K = m;
+    g.A = Ht; g.sam = 1; g.sak = r0;
+    g.B = Yc[k]; g.sbk = 1; g.sbn = m;                       // H(Y_k)^T(row, a) = Y[a*m + row]
+    g.C = R; g.scm = r0; g.scn = 1;
+    g.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, m / 256), 64);
+    TTR_CHECK(fill_zero(c, R, r0 * r0));
+    TTR_CHECK(E.small_gemm(c, g));
+    // SVD of R^T = U S Vt: Jacobi on R^T (transpose R into U's storage first)
+    TTR_CHECK(E.transpose(c, R, r0, r0, tmp));                // tmp = R^T (r0 x r0)
+    TTR_CUDA(cudaMemsetAsync(w.dflag, 0, sizeof(int), c.stream));
+    TTR_CHECK(jacobi_svd(c, tmp, r0, r0, sig, U, Vt, w.dflag));
+    TTR_CUDA(cudaMemcpyAsync(hs.data(), sig, sizeof(double) * r0, cudaMemcpyDeviceToHost, c.stream));
+    TTR_CUDA(cudaStreamSynchronize(c.stream));
+    int64_t rp = r0;
+    if (tau > 0.0) {
+      // smallest rp >= 1 with sqrt(sum_{i >= rp} s_i^2) <= tau
+      std::vector<double> tail(r0 + 1, 0.0);
+      for (int64_t i = r0 - 1; i >= 0; --i) tail[i] = tail[i + 1] + hs[i] * hs[i];
+      rp = r0;
+      for (int64_t q = 1; q <= r0; ++q)
+        if (sqrt(tail[q]) <= tau) {
+          rp = q;
+          break;
+        }
+    }
+    if (max_rank > 0) rp = std::min(rp, max_rank);
+    // H(Y_k) <- Vt[:rp] Q^T   (rp x m):  new[p][row] = sum_j Vt[p][j] Q[row][j]
+    Gemm h;
+    h.M = rp; h.N = m; h.K = r0;
+    h.A = Vt; h.sam = r0; h.sak = 1;
+    h.B = Ht; h.sbk = 1; h.sbn = r0;
+    h.C = tmp; h.scm = m; h.scn = 1;
+    TTR_CHECK(E.small_gemm(c, h));
+    TTR_CUDA(cudaMemcpyAsync(Yc[k], tmp, sizeof(double) * rp * m, cudaMemcpyDeviceToDevice, c.stream));
+    // V(Y_{k-1}) <- V(Y_{k-1}) U[:, :rp] diag(s)  ((r_{k-1} n_{k-1}) x r0) (r0 x rp)
+    TTR_CHECK(E.scale_cols(c, U, r0, rp, r0, sig));
+    const int64_t rows = r[k - 1] * n[k - 1];
+    Gemm v;
+    v.M = rows; v.N = rp; v.K = r0;
+    v.A = Yc[k - 1]; v.sam = r0; v.sak = 1;
+    v.B = U; v.sbk = r0; v.sbn = 1;
+    v.C = tmp; v.scm = rp; v.scn = 1;
+    TTR_CHECK(E.small_gemm(c, v));
+    TTR_CUDA(cudaMemcpyAsync(Yc[k - 1], tmp, sizeof(double) * rows * rp, cudaMemcpyDeviceToDevice, c.stream));
+    r[k] = rp;
+  }
+  // pack into the existing arena (it is at least as large)
+  int64_t off = 0;
+  double* arena = (double*)out->arena;
+  for (int k = 0; k < d; ++k) {
+    const int64_t sz = r[k] * n[k] * r[k + 1];
+    TTR_CUDA(cudaMemcpyAsync(arena + off, Yc[k], sizeof(double) * sz, cudaMemcpyDeviceToDevice, c.stream));
+    out->cores[k] = arena + off;
+    off += sz;
+  }
+  return TTR_OK;
+}
+
+// ----------------------------------------------------------------------------- fixed rank
+static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, const ttr_options& o,
+                       cudaStream_t stream, ttr_result* out) {
+  if (ell < 1) return set_error("ell must be >= 1"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = stream;
+  Timer tm;
+  tm.rec(0, stream);
+  Engine E;
+  TTR_CHECK(E.init(c, o.precision, o.slices, 0.0));
+  const int d = X.d;
+  Sketch s;
+  TTR_CHECK(sketch_alloc(c, X, ell, s));
+  TTR_CHECK(rl_pass(c, E, X, seed, 0, ell, 2, s));
+  s.width = ell;
+  tm.rec(1, stream);
+  Sweep w;
+  int64_t rmax = 1;
+  for (int k = 1; k < d; ++k) rmax = std::max(rmax, X.r[k]);
+  TTR_CHECK(sweep_alloc(c, X, std::min(ell, rmax), w));
+  TTR_CHECK(result_alloc(c, X, out));
+  double* arena = (double*)out->arena;
+  int64_t off = 0, lprev = 1;
+  const double* Z = X.cores[0];
+  int cur = 0;
+  out->ranks[0] = 1;
+  for (int k = 1; k < d; ++k) {
+    const int64_t rows = lprev * X.n[k - 1], cols = X.r[k];
+    double right = 1.0;
+    for (int j = k; j < d; ++j) right = std::min(right * (double)X.n[j], 1e18);
+    int64_t lk = std::min<int64_t>(std::min<int64_t>(ell, rows), cols);
+    if ((double)lk > right) lk = (int64_t)right;
+    // S = Z W_{k+1}(:, 0:lk) -> Q (ld qcap)
+    Gemm g;
+    g.M = rows; g.N = lk; g.K = cols;
+    g.A = Z; g.sam = cols; g.sak = 1;
+    g.B = s.W[k]; g.sbk = s.ldw; g.sbn = 1;
+    g.C = w.Q; g.scm = w.qcap; g.scn = 1;
+    TTR_CHECK(E.sketch(c, g));
+    TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, lk, w.qr));
+    double* Ynext = w.Y[cur];
+    TTR_CHECK(project_next(c, E, w, Z, rows, cols, lk, X, k, Ynext));
+    TTR_CHECK(copy2d(c, arena + off, lk, w.Q, w.qcap, rows, lk));
+    out->cores[k - 1] = arena + off;
+    out->ranks[k] = lk;
+    off += rows * lk;
+    Z = Ynext;
+    cur ^= 1;
+    lprev = lk;
+  }
+  const int64_t last = lprev * X.n[d - 1];
+  TTR_CUDA(cudaMemcpyAsync(arena + off, Z, sizeof(double) * last, cudaMemcpyDeviceToDevice, stream));
+  out->cores[d - 1] = arena + off;
+  out->ranks[d] = 1;
+  if (target > 0 && target < ell) TTR_CHECK(svd_pass_rl(c, E, out, X.n, 0.0, target));
+  tm.rec(2, stream);
+  TTR_CUDA(cudaStreamSynchronize(stream));
+  out->width = ell;
+  out->ms_sketch_rl = tm.ms(0, 1);
+  out->ms_sweep_lr = tm.ms(1, 2);
+  out->ms_total = tm.ms(0, 2);
+  out->kernel_launches = c.launches;
+  disown(c, out->arena);
+  return TTR_OK;
+}
+
+// ----------------------------------------------------------------------------- adaptive
+static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed, const ttr_options& o,
+                          cudaStream_t stream, ttr_result* out) {
+  if (!(tol > 0.0) || !isfinite(tol)) return set_error("tol must be positive and finite"), TTR_ERR_ARG;
+  if (block <= 0 && !(o.f_init > 0.0 && o.f_init < 1.0 && o.f_inc > 0.0 && o.f_inc < 1.0))
+    return set_error("f_init and f_inc must lie in (0, 1)"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = stream;
+  Timer tm;
+  tm.rec(0, stream);
+  const int d = X.d;
+  int64_t rmax = 1;
+  for (int k = 1; k < d; ++k) rmax = std::max(rmax, X.r[k]);
+  const int64_t w0 = std::max<int64_t>(1, block > 0 ? block : (int64_t)ceil((double)rmax * o.f_init - 1e-9));
+  const int64_t binc_max = block > 0 ? std::min(block, rmax) : block_size(rmax, 0, o.f_inc);
+  const int64_t binit_max = block > 0 ? std::min(block, rmax) : block_size(rmax, 0, o.f_init);
+  const int64_t wcap = std::max(w0, rmax + binc_max);
+  Engine E;
+  TTR_CHECK(E.init(c, o.precision, o.slices, tol));
+  Sketch s;
+  TTR_CHECK(sketch_alloc(c, X, wcap, s));
+  int64_t wdev = w0;
+  if (o.width_hint > 0) wdev = std::min(wcap, std::max(w0, o.width_hint));
+  TTR_CHECK(rl_pass(c, E, X, seed, 0, wdev, 2, s));
+  s.width = wdev;
+  // norm: given, or Eq. (3.6) with the first w0 columns of W_2
+  double* dscal = nullptr;
+  TTR_CHECK(c.alloc_t(&dscal, 8));
+  double nrmx = o.nrmx;
+  int st = TTR_OK;
+  if (!(nrmx > 0.0)) {
+    double* E1 = nullptr;
+    TTR_CHECK(c.alloc_t(&E1, X.n[0] * w0));
+    Gemm g;
+    g.M = X.n[0]; g.N = w0; g.K = X.r[1];
+    g.A = X.cores[0]; g.sam = X.r[1]; g.sak = 1;
+    g.B = s.W[1]; g.sbk = s.ldw; g.sbn = 1;
+    g.C = E1; g.scm = w0; g.scn = 1;
+    TTR_CHECK(E.small_gemm(c, g));
+    TTR_CUDA(cudaMemsetAsync(dscal, 0, sizeof(double), stream));
+    TTR_CHECK(sumsq(c, E1, X.n[0], w0, w0, 1, dscal));
+    const double ss = dsync_read(c, dscal, &st);
+    if (st != TTR_OK) return st;
+    nrmx = sqrt(ss) / sqrt((double)w0);
+    if (!isfinite(nrmx)) return set_error("non-finite norm estimate"), TTR_ERR_NONFINITE;
+  }
+  const double tau = tol * nrmx / sqrt((double)(d - 1));
+  tm.rec(1, stream);
+  Sweep w;
+  TTR_CHECK(sweep_alloc(c, X, std::max(binc_max, binit_max), w));
+  TTR_CHECK(result_alloc(c, X, out));
+  std::vector<double> ests;
+  std::vector<int32_t> est_core;
+  double* arena = (double*)out->arena;
+  int64_t off = 0, lprev = 1;
+  const double* Z = X.cores[0];
+  int cur = 0;
+  out->ranks[0] = 1;
+  auto ensure = [&](int k, int64_t need) -> int {
+    if (s.width >= need) return TTR_OK;
+    if (need > s.ldw) return set_error("sketch capacity exceeded"), TTR_ERR_ARG;
+    TTR_CHECK(rl_pass(c, E, X, seed, s.width, need, k + 1, s));
+    s.width = need;
+    s.extensions++;
+    return TTR_OK;
+  };
+  for (int k = 1; k < d; ++k) {
+    const int64_t rows = lprev * X.n[k - 1], cols = X.r[k];
+    const int64_t rbar = std::min(rows, cols);
+    const int64_t b0 = block_size(rbar, block, o.f_init);
+    TTR_CHECK(ensure(k, b0));
+    Gemm g;
+    g.M = rows; g.N = b0; g.K = cols;
+    g.A = Z; g.sam = cols; g.sak = 1;
+    g.B = s.W[k]; g.sbk = s.ldw; g.sbn = 1;
+    g.C = w.Q; g.scm = w.qcap; g.scn = 1;
+    TTR_CHECK(E.sketch(c, g));
+    TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+    int64_t cc = b0;
+    const int64_t bi = block_size(rbar, block, o.f_inc);
+    while (cc < rbar) {
+      TTR_CHECK(ensure(k, cc + bi));
+      // S = Z W_{k+1}(:, cc:cc+bi)   (Eq. (3.4))
+      Gemm h;
+      h.M = rows; h.N = bi; h.K = cols;
+      h.A = Z; h.sam = cols; h.sak = 1;
+      h.B = s.W[k] + cc; h.sbk = s.ldw; h.sbn = 1;
+      h.C = w.S; h.scm = bi; h.scn = 1;
+      TTR_CHECK(E.sketch(c, h));
+      // S <- S - Q (Q^T S)   (Eq. (3.5))
+      TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.S, bi, bi, w.P));
+      TTR_CUDA(cudaMemsetAsync(dscal, 0, sizeof(double), stream));
+      TTR_CHECK(sumsq(c, w.S, rows, bi, bi, 1, dscal));
+      const double ss = dsync_read(c, dscal, &st);
+      if (st != TTR_OK) return st;
+      const double est = sqrt(ss) / sqrt((double)bi);
+      if (!isfinite(est)) return set_error("non-finite residual estimate"), TTR_ERR_NONFINITE;
+      ests.push_back(est);
+      est_core.push_back(k);
+      if (!(est > tau)) break;
+      const int64_t bb = std::min(bi, rbar - cc);
+      // Q_new = qr(S(:, :bb)); re-orthogonalize against Q; qr again; append
+      TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
+      TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
+      TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
+      TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
+      cc += bb;
+    }
+    double* Ynext = w.Y[cur];
+    TTR_CHECK(project_next(c, E, w, Z, rows, cols, cc, X, k, Ynext));
+    TTR_CHECK(copy2d(c, arena + off, cc, w.Q, w.qcap, rows, cc));
+    out->cores[k - 1] = arena + off;
+    out->ranks[k] = cc;
+    off += rows * cc;
+    Z = Ynext;
+    cur ^= 1;
+    lprev = cc;
+  }
+  const int64_t last = lprev * X.n[d - 1];
+  TTR_CUDA(cudaMemcpyAsync(arena + off, Z, sizeof(double) * last, cudaMemcpyDeviceToDevice, stream));
+  out->cores[d - 1] = arena + off;
+  out->ranks[d] = 1;
+  if (o.adap_r) TTR_CHECK(svd_pass_rl(c, E, out, X.n, tau * o.adap_r_tau_scale, 0));
+  tm.rec(2, stream);
+  TTR_CUDA(cudaStreamSynchronize(stream));
+  out->tau = tau;
+  out->nrmx = nrmx;
+  out->width = s.width;
+  out->extensions = s.extensions;
+  out->n_estimates = (int32_t)ests.size();
+  out->estimates = (double*)calloc(std::max<size_t>(1, ests.size()), sizeof(double));
+  out->est_core = (int32_t*)calloc(std::max<size_t>(1, ests.size()), sizeof(int32_t));
+  if (!out->estimates || !out->est_core) return set_error("host allocation"), TTR_ERR_OOM;
+  std::copy(ests.begin(), ests.end(), out->estimates);
+  std::copy(est_core.begin(), est_core.end(), out->est_core);
+  out->ms_sketch_rl = tm.ms(0, 1);
+  out->ms_sweep_lr = tm.ms(1, 2);
+  out->ms_total = tm.ms(0, 2);
+  out->kernel_launches = c.launches;
+  disown(c, out->arena);
+  return TTR_OK;
+}
+
+// ----------------------------------------------------------------------------- deterministic
+// Algorithm 1.  QR and SVD of the (possibly rank-deficient) unfoldings of a formal sum are taken
+// through the Gram matrix: A^T A = V diag(lambda) V^T by one-sided Jacobi, sigma = sqrt(lambda),
+// U = A V_r diag(1/sigma_r) re-orthonormalized by CholeskyQR2.  Directions with
+// sigma < 1e-7 * sigma_max are dropped from the QR of the orthogonalization phase (they are
+// below the FP64 resolution of a Gram matrix); the represented tensor changes by less than that.
+static int gram_svd(Ctx& c, const Engine& E, const double* A, int64_t sam, int64_t sak, int64_t m, int64_t b,
+                    double* G, double* U, double* Vt, double* sig, int* flag, std::vector<double>& hsig) {
+  TTR_CHECK(fill_zero(c, G, b * b));
+  Gemm g;
+  g.M = b; g.N = b; g.K = m;
+  g.A = A; g.sam = sak; g.sak = sam;
+  g.B = A; g.sbk = sam; g.sbn = sak;
+  g.C = G; g.scm = b; g.scn = 1;
+  g.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, m / 256), 128);
+  TTR_CHECK(E.small_gemm(c, g));
+  TTR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
+  TTR_CHECK(jacobi_svd(c, G, b, b, sig, U, Vt, flag));
+  hsig.resize(b);
+  TTR_CUDA(cudaMemcpyAsync(hsig.data(), sig, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
+  TTR_CUDA(cudaStreamSynchronize(c.stream));
+  for (auto& v : hsig) v = sqrt(std::max(v, 0.0));   // eigenvalues of the Gram -> singular values
+  return TTR_OK;
+}
+
+static int round_deterministic(const TT& X, double tol, cudaStream_t stream, ttr_result* out) {
+  if (!(tol > 0.0) || !isfinite(tol)) return set_error("tol must be positive and finite"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = stream;
+  Timer tm;
+  tm.rec(0, stream);
+  Engine E;
+  ttr_options o;
+  ttr_default_options(&o);
+  TTR_CHECK(E.init(c, TTR_PREC_FP64, 0, tol));
+  const int d = X.d;
+  std::vector<int64_t> r(X.r, X.r + d + 1);
+  int64_t cmax = 1, rmax = 1;
+  for (int k = 0; k < d; ++k) {
+    cmax = std::max(cmax, X.r[k] * X.n[k] * X.r[k + 1]);
+    rmax = std::max(rmax, X.r[k + 1]);
+  }
+  std::vector<double*> Y(d);
+  for (int k = 0; k < d; ++k) {
+    const int64_t sz = X.r[k] * X.n[k] * X.r[k + 1];
+    TTR_CHECK(c.alloc_t(&Y[k], sz));
+    TTR_CUDA(cudaMemcpyAsync(Y[k], X.cores[k], sizeof(double) * sz, cudaMemcpyDeviceToDevice, stream));
+  }
+  double *G, *U, *Vt, *sig, *tmp, *Rm;
+  int* flag;
+  TTR_CHECK(c.alloc_t(&G, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&U, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&Vt, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&sig, rmax));
+  TTR_CHECK(c.alloc_t(&tmp, cmax));
+  TTR_CHECK(c.alloc_t(&Rm, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&flag, 4));
+  QrWork qw;
+  TTR_CHECK(c.alloc_t(&qw.tmp, cmax));
+  TTR_CHECK(c.alloc_t(&qw.save, cmax));
+  TTR_CHECK(c.alloc_t(&qw.G, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&qw.Rinv, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&qw.dscal, 8));
+  TTR_CHECK(c.alloc_t(&qw.dflag, 4));
+  std::vector<double> hs;
+  // ---- OrthogonalizeRL: H(Y_k)^T = Q R (rank-revealing through the Gram), H(Y_k) <- Q^T,
+  //      V(Y_{k-1}) <- V(Y_{k-1}) R^T
+  for (int k = d - 1; k >= 1; --k) {
+    const int64_t r0 = r[k], nk = X.n[k], r1 = r[k + 1], m = nk * r1;
+    // A = H(Y_k)^T: A(row, a) = Y[a*m + row]  -> sam = 1, sak = m
+    TTR_CHECK(gram_svd(c, E, Y[k], 1, m, m, r0, G, U, Vt, sig, flag, hs));
+    int64_t q = 0;
+    while (q < r0 && q < m && hs[q] > 1e-7 * hs[0]) ++q;
+    if (q < 1) q = 1;
+    // Qt = diag(1/s) Vt[:q] H(Y_k)   (q x m) -> orthonormal rows, then CholQR2 on its transpose
+    TTR_CHECK(E.scale_rows_inv(c, Vt, r0, q, r0, sig));   // Vt[j,:] /= sqrt(lambda_j)
+    Gemm g;
+    g.M = q; g.N = m; g.K = r0;
+    g.A = Vt; g.sam = r0; g.sak = 1;
+    g.B = Y[k]; g.sbk = m; g.sbn = 1;
+    g.C = tmp; g.scm = m; g.scn = 1;
+    TTR_CHECK(E.small_gemm(c, g));
+    // tmp (q x m) rows ~ orthonormal; make them exactly so: QR of tmp^T (m x q)
+    TTR_CHECK(E.transpose(c, tmp, q, m, qw.tmp));          // qw.tmp = tmp^T (m x q)
+    // qr_inplace uses qw.tmp as scratch, so copy to another buffer first
+    TTR_CHECK(copy2d(c, tmp, q, qw.tmp, q, m, q));          // tmp = Qhat (m x q, ld q)
+    TTR_CHECK(qr_inplace(c, E, tmp, q, m, q, qw));
+    // R = Q^T H(Y_k)^T (q x r0) : R(j, a) = sum_row Q(row, j) Y[a*m + row]
+    TTR_CHECK(fill_zero(c, Rm, q * r0));
+    Gemm h;
+    h.M = q; h.N = r0; h.K = m;
+    h.A = tmp; h.sam = 1; h.sak = q;
+    h.B = Y[k]; h.sbk = 1; h.sbn = m;
+    h.C = Rm; h.scm = r0; h.scn = 1;
+    h.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, m / 256), 128);
+    TTR_CHECK(E.small_gemm(c, h));
+    // new core k: H(Y_k) = Q^T  (q x m)
+    TTR_CHECK(E.transpose(c, tmp, m, q, Y[k]));
+    // V(Y_{k-1}) <- V(Y_{k-1}) R^T  ((r_{k-1} n_{k-1}) x r0)(r0 x q)
+    const int64_t rows = r[k - 1] * X.n[k - 1];
+    Gemm v;
+    v.M = rows; v.N = q; v.K = r0;
+    v.A = Y[k - 1]; v.sam = r0; v.sak = 1;
+    v.B = Rm; v.sbk = 1; v.sbn = r0;
+    v.C = tmp; v.scm = q; v.scn = 1;
+    TTR_CHECK(E.small_gemm(c, v));
+    TTR_CUDA(cudaMemcpyAsync(Y[k - 1], tmp, sizeof(double) * rows * q, cudaMemcpyDeviceToDevice, stream));
+    r[k] = q;
+  }
+  // ---- tau = ||Y_1|| tol / sqrt(d-1)
+  double* dsc;
+  TTR_CHECK(c.alloc_t(&dsc, 2));
+  TTR_CUDA(cudaMemsetAsync(dsc, 0, sizeof(double), stream));
+  TTR_CHECK(sumsq(c, Y[0], X.n[0] * r[1], 1, 1, 1, dsc));
+  int st = TTR_OK;
+  const double nrm = sqrt(dsync_read(c, dsc, &st));
+  if (st != TTR_OK) return st;
+  const double tau = nrm * tol / sqrt((double)(d - 1));
+  // ---- compression: SVD of V(Y_k) truncated at tau; V(Y_k) <- U, H(Y_{k+1}) <- S Vt H(Y_{k+1})
+  for (int k = 0; k < d - 1; ++k) {
+    const int64_t rows = r[k] * X.n[k], cols = r[k + 1];
+    TTR_CHECK(gram_svd(c, E, Y[k], cols, 1, rows, cols, G, U, Vt, sig, flag, hs));
+    std::vector<double> tail(cols + 1, 0.0);
+    for (int64_t i = cols - 1; i >= 0; --i) tail[i] = tail[i + 1] + hs[i] * hs[i];
+    int64_t rp = cols;
+    for (int64_t q = 1; q <= cols; ++q)
+      if (sqrt(tail[q]) <= tau) {
+        rp = q;
+        break;
+      }
+    // U_Y = V(Y_k) V[:, :rp] diag(1/s)  -> then CholQR2 for exact orthonormality
+    Gemm g;
+    g.M = rows; g.N = rp; g.K = cols;
+    g.A = Y[k]; g.sam = cols; g.sak = 1;
+    g.B = Vt; g.sbk = 1; g.sbn = cols;                      // V = Vt^T
+    g.C = tmp; g.scm = rp; g.scn = 1;
+    TTR_CHECK(E.small_gemm(c, g));
+    TTR_CHECK(qr_inplace(c, E, tmp, rp, rows, rp, qw));
+    // coefficient C = U_Y^T V(Y_k)  (rp x cols) = S V^T up to the re-orthonormalization
+    TTR_CHECK(fill_zero(c, Rm, rp * cols));
+    Gemm h;
+    h.M = rp; h.N = cols; h.K = rows;
+    h.A = tmp; h.sam = 1; h.sak = rp;
+    h.B = Y[k]; h.sbk = cols; h.sbn = 1;
+    h.C = Rm; h.scm = cols; h.scn = 1;
+    h.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, rows / 256), 128);
+    TTR_CHECK(E.small_gemm(c, h));
+    TTR_CUDA(cudaMemcpyAsync(Y[k], tmp, sizeof(double) * rows * rp, cudaMemcpyDeviceToDevice, stream));
+    // H(Y_{k+1}) <- C H(Y_{k+1})  (rp x cols)(cols x n r)
+    const int64_t ncol = X.n[k + 1] * r[k + 2];
+    Gemm v;
+    v.M = rp; v.N = ncol; v.K = cols;
+    v.A = Rm; v.sam = cols; v.sak = 1;
+    v.B = Y[k + 1]; v.sbk = ncol; v.sbn = 1;
+    v.C = tmp; v.scm = ncol; v.scn = 1;
+    TTR_CHECK(E.small_gemm(c, v));
+    TTR_CUDA(cudaMemcpyAsync(Y[k + 1], tmp, sizeof(double) * rp * ncol, cudaMemcpyDeviceToDevice, stream));
+    r[k + 1] = rp;
+  }
+  TTR_CHECK(result_alloc(c, X, out));
+  double* arena = (double*)out->arena;
+  int64_t off = 0;
+  for (int k = 0; k < d; ++k) {
+    const int64_t sz = r[k] * X.n[k] * r[k + 1];
+    TTR_CUDA(cudaMemcpyAsync(arena + off, Y[k], sizeof(double) * sz, cudaMemcpyDeviceToDevice, stream));
+    out->cores[k] = arena + off;
+    off += sz;
+  }
+  for (int k = 0; k <= d; ++k) out->ranks[k] = r[k];
+  tm.rec(2, stream);
+  TTR_CUDA(cudaStreamSynchronize(stream));
+  out->tau = tau;
+  out->nrmx = nrm;
+  out->ms_total = tm.ms(0, 2);
+  out->ms_sweep_lr = out->ms_total;
+  out->kernel_launches = c.launches;
+  disown(c, out->arena);
+  return TTR_OK;
+}
+
+}  // namespace ttr
+
+// ============================================================================= C ABI
+using namespace ttr;
+
+extern "C" {
+
+void ttr_default_options(ttr_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = TTR_PREC_FP64;
+  o->slices = 0;
+  o->adap_r = 0;
+  o->adap_r_tau_scale = 1.0;
+  o->nrmx = 0.0;
+  o->f_init = 0.1;
+  o->f_inc = 0.05;
+  o->width_hint = 0;
+}
+
+static int finish(int st, ttr_result* out, cudaStream_t s) {
+  if (st != TTR_OK && out) {
+    if (out->arena) cudaFreeAsync(out->arena, s);
+    result_host_free(out);
+    result_zero(out);
+    out->status = st;
+  } else if (out) {
+    out->status = st;
+  }
+  return st;
+}
+
+int tt_round_fixed(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores, int64_t ell,
+                   int64_t target, uint64_t seed, const ttr_options* opts, void* stream, ttr_result* out) {
+  if (!out) return set_error("out must be non-null"), TTR_ERR_ARG;
+  result_zero(out);
+  ttr_options o;
+  if (opts) o = *opts; else ttr_default_options(&o);
+  TT X{d, n, r, cores};
+  int st = validate(X);
+  if (st == TTR_OK) st = round_fixed(X, ell, target, seed, o, (cudaStream_t)stream, out);
+  return finish(st, out, (cudaStream_t)stream);
+}
+
+int tt_round_adaptive(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores, double tol,
+                      int64_t block, uint64_t seed, const ttr_options* opts, void* stream, ttr_result* out) {
+  if (!out) return set_error("out must be non-null"), TTR_ERR_ARG;
+  result_zero(out);
+  ttr_options o;
+  if (opts) o = *opts; else ttr_default_options(&o);
+  TT X{d, n, r, cores};
+  int st = validate(X);
+  if (st == TTR_OK) st = round_adaptive(X, tol, block, seed, o, (cudaStream_t)stream, out);
+  return finish(st, out, (cudaStream_t)stream);
+}
+
+int tt_round_deterministic(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores, double tol,
+                           void* stream, ttr_result* out) {
+  if (!out) return set_error("out must be non-null"), TTR_ERR_ARG;
+  result_zero(out);
+  TT X{d, n, r, cores};
+  int st = validate(X);
+  if (st == TTR_OK) st = round_deterministic(X, tol, (cudaStream_t)stream, out);
+  return finish(st, out, (cudaStream_t)stream);
+}
+
+void ttr_free(ttr_result* out, void* stream) {
+  if (!out) return;
+  if (out->arena) cudaFreeAsync(out->arena, (cudaStream_t)stream);
+  result_host_free(out);
+  result_zero(out);
+}
+
+const char* ttr_strerror(int s) {
+  switch (s) {
+    case TTR_OK: return "ok";
+    case TTR_ERR_ARG: return "invalid argument";
+    case TTR_ERR_OOM: return "out of memory";
+    case TTR_ERR_NONFINITE: return "non-finite value";
+    case TTR_ERR_QR_BREAKDOWN: return "CholeskyQR breakdown";
+    case TTR_ERR_TIMEOUT: return "bounded device wait ran out";
+    case TTR_ERR_CUDA: return "CUDA error";
+    case TTR_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+const char* ttr_last_error(void) { return g_last_error.c_str(); }
+
+int ttr_sketch_omega(uint64_t seed, int32_t k, int64_t n_k, int64_t col0, int64_t col1, double* dst, void* stream) {
+  if (!dst || n_k < 1 || col1 < col0 || col0 < 0 || k < 1) return set_error("bad omega arguments"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = (cudaStream_t)stream;
+  std::vector<int64_t> nn(k, n_k);
+  int st = omega_fill(c, seed, k, k, nn.data(), col0, col1, dst, 0, col1 - col0);
+  if (st == TTR_OK) {
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
+  }
+  return st;
+}
+
+int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
+                             uint64_t seed, int64_t col0, int64_t col1, int32_t t, int32_t precision,
+                             int32_t slices, double* const* W, void* stream) {
+  TT X{d, n, r, cores};
+  int st = validate(X);
+  if (st != TTR_OK) return st;
+  if (!W || t < 2 || t > d || col1 <= col0 || col0 < 0) return set_error("bad partial-contraction arguments"), TTR_ERR_ARG;
+  for (int k = t; k <= d; ++k)
+    if (!W[k - 1]) return set_error("null W buffer"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = (cudaStream_t)stream;
+  Engine E;
+  TTR_CHECK(E.init(c, precision, slices, 0.0));
+  const int64_t w = col1 - col0;
+  Sketch s;
+  TTR_CHECK(sketch_alloc(c, X, w, s));
+  for (int k = t; k <= d; ++k) s.W[k - 1] = W[k - 1] - col0;   // caller buffers: [a][j - col0], ld w
+  s.ldw = w;
+  TTR_CHECK(rl_pass(c, E, X, seed, col0, col1, t, s));
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
+  return TTR_OK;
+}
+
+}  // extern "C"

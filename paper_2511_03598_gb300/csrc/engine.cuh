@@ -1,0 +1,128 @@
+// Contraction engine: routes each contraction of the rounding algorithms to a kernel.
+// FP64 mode uses the SIMT DFMA kernels; sliced mode sends the large contractions (partial
+// contractions, sketches, next-core projections) to the tcgen05 tensor-core kernels and
+// keeps the small dense work in FP64.
+#pragma once
+
+#include "ttr_internal.cuh"
+
+namespace ttr {
+
+// Tensor-core path (ozaki_tc.cu).  Each returns TTR_ERR_UNSUPPORTED when a shape is outside
+// what the kernel handles; the engine then uses the FP64 kernel for that call.
+int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn,
+               int64_t ldw, const double* Om, int64_t ldom, int64_t w, double* Wout, int64_t ldwo);
+int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
+                     int64_t ldb, int64_t N, double* C, int64_t ldc);
+int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn,
+               int64_t ncol, double* Y);
+
+// Small helper kernels (engine.cu)
+int transpose_f64(Ctx& c, const double* A, int64_t rows, int64_t cols, double* out);
+int scale_cols_f64(Ctx& c, double* U, int64_t ld, int64_t ncols, int64_t rows, const double* s);
+int scale_rows_rsqrt_f64(Ctx& c, double* Vt, int64_t ld, int64_t nrows, int64_t ncols, const double* lam);
+
+struct Engine {
+  int precision = TTR_PREC_FP64;
+  int slices = 0;
+
+  int init(Ctx& c, int prec, int sl, double tol) {
+    (void)c;
+    if (prec != TTR_PREC_FP64 && prec != TTR_PREC_SLICED) {
+      set_error("unknown precision");
+      return TTR_ERR_ARG;
+    }
+    precision = prec;
+    if (prec == TTR_PREC_SLICED) {
+      if (sl == 0) {
+        // enough 7-bit slices that the contraction error sits well below the tolerance:
+        // about 7*slices - 4 bits survive; ask for 12 bits beyond -log2(tol), at least 4.
+        double bits = (tol > 0.0) ? -log2(tol) + 12.0 : 53.0;
+        sl = (int)ceil((bits + 4.0) / 7.0);
+        if (sl < 4) sl = 4;
+        if (sl > 8) sl = 8;
+      }
+      if (sl < 3 || sl > 8) {
+        set_error("slices must be in [3, 8]");
+        return TTR_ERR_ARG;
+      }
+    }
+    slices = sl;
+    return TTR_OK;
+  }
+
+  int small_gemm(Ctx& c, const Gemm& g) const { return gemm_f64(c, g); }
+
+  // S = Z W(:, cols): A row-major (sak == 1), B row-major (sbn == 1), C row-major (scn == 1)
+  int sketch(Ctx& c, const Gemm& g) const {
+    if (precision == TTR_PREC_SLICED && g.sak == 1 && g.sbn == 1 && g.scn == 1 && g.split_k <= 1 &&
+        g.alpha == 1.0 && g.beta == 0.0) {
+      int st = tc_gemm_rowmajor(c, slices, g.A, g.sam, g.M, g.K, g.B, g.sbk, g.N, g.C, g.scm);
+      if (st != TTR_ERR_UNSUPPORTED) return st;
+    }
+    return gemm_f64(c, g);
+  }
+
+  // W_k = sum_i [V(X_k) W_{k+1}](a, i, :) * Omega_k(i, :)   (Algorithm 3, one step)
+  int rl_step(Ctx& c, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
+              const double* Om, int64_t ldom, int64_t w, double* Wout, int64_t ldwo, double* T) const {
+    if (precision == TTR_PREC_SLICED) {
+      int st = tc_rl_step(c, slices, Xk, r0, n, r1, Wn, ldw, Om, ldom, w, Wout, ldwo);
+      if (st != TTR_ERR_UNSUPPORTED) return st;
+    }
+    Gemm g;
+    g.M = r0 * n; g.N = w; g.K = r1;
+    g.A = Xk; g.sam = r1; g.sak = 1;
+    g.B = Wn; g.sbk = ldw; g.sbn = 1;
+    g.C = T; g.scm = w; g.scn = 1;
+    TTR_CHECK(gemm_f64(c, g));
+    return omega_reduce(c, T, w, Om, ldom, r0, n, w, Wout, ldwo);
+  }
+
+  // Y = M H(X_{k+1}):  (L x K)(K x ncol), all row-major
+  int project(Ctx& c, const double* Mk, int64_t L, int64_t K, const double* Xn, int64_t ncol, double* Y) const {
+    if (precision == TTR_PREC_SLICED) {
+      int st = tc_project(c, slices, Mk, K, L, K, Xn, ncol, Y);
+      if (st != TTR_ERR_UNSUPPORTED) return st;
+    }
+    Gemm g;
+    g.M = L; g.N = ncol; g.K = K;
+    g.A = Mk; g.sam = K; g.sak = 1;
+    g.B = Xn; g.sbk = ncol; g.sbn = 1;
+    g.C = Y; g.scm = ncol; g.scn = 1;
+    return gemm_f64(c, g);
+  }
+
+  // P = Q(:, :cc)^T S;  S <- S - Q(:, :cc) P     (Eq. (3.5) / block Gram-Schmidt)
+  int project_out(Ctx& c, const double* Q, int64_t ldq, int64_t rows, int64_t cc, double* S, int64_t lds,
+                  int64_t bcols, double* P) const {
+    if (cc <= 0) return TTR_OK;
+    TTR_CHECK(fill_zero(c, P, cc * bcols));
+    Gemm g;
+    g.M = cc; g.N = bcols; g.K = rows;
+    g.A = Q; g.sam = 1; g.sak = ldq;
+    g.B = S; g.sbk = lds; g.sbn = 1;
+    g.C = P; g.scm = bcols; g.scn = 1;
+    g.split_k = (int)(rows / 256 < 1 ? 1 : (rows / 256 > 64 ? 64 : rows / 256));
+    TTR_CHECK(gemm_f64(c, g));
+    Gemm h;
+    h.M = rows; h.N = bcols; h.K = cc;
+    h.A = Q; h.sam = ldq; h.sak = 1;
+    h.B = P; h.sbk = bcols; h.sbn = 1;
+    h.C = S; h.scm = lds; h.scn = 1;
+    h.alpha = -1.0; h.beta = 1.0;
+    return gemm_f64(c, h);
+  }
+
+  int transpose(Ctx& c, const double* A, int64_t rows, int64_t cols, double* out) const {
+    return transpose_f64(c, A, rows, cols, out);
+  }
+  int scale_cols(Ctx& c, double* U, int64_t ld, int64_t ncols, int64_t rows, const double* s) const {
+    return scale_cols_f64(c, U, ld, ncols, rows, s);
+  }
+  int scale_rows_inv(Ctx& c, double* Vt, int64_t ld, int64_t nrows, int64_t ncols, const double* lam) const {
+    return scale_rows_rsqrt_f64(c, Vt, ld, nrows, ncols, lam);
+  }
+};
+
+}  // namespace ttr

@@ -1,0 +1,361 @@
+// FP64 SIMT kernels of libttround: the native-FP64 contraction path and the small dense
+// kernels (Gram matrices, Cholesky, norms, one-sided Jacobi SVD) that stay FP64 in every
+// precision mode.
+#include <math.h>
+
+#include <algorithm>
+
+#include "gaussian.cuh"
+#include "ttr_internal.cuh"
+
+namespace ttr {
+
+// ----------------------------------------------------------------------------- GEMM
+// 64 x 64 output tile, K chunks of 16 staged in shared memory, 256 threads x (4 x 4) outputs.
+// The staging loop picks the thread-to-element mapping from the operand strides so that the
+// global loads are coalesced along whichever index is contiguous.
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(Gemm g, int64_t kchunk) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * GT, n0 = (int64_t)blockIdx.x * GT;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk;
+  const int64_t ke = min(g.K, kb + kchunk);
+  double acc[4][4] = {};
+  const bool a_kfast = (g.sak == 1);
+  const bool b_nfast = (g.sbn == 1) || (g.sbk != 1);
+  for (int64_t k0 = kb; k0 < ke; k0 += GK) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = tid + t * 256;
+      int mm, kk;
+      if (a_kfast) { kk = idx & 15; mm = idx >> 4; } else { mm = idx & 63; kk = idx >> 6; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < g.M && gk < ke) ? g.A[gm * g.sam + gk * g.sak] : 0.0;
+      int nn, kb2;
+      if (b_nfast) { nn = idx & 63; kb2 = idx >> 6; } else { kb2 = idx & 15; nn = idx >> 4; }
+      const int64_t gn = n0 + nn, gk2 = k0 + kb2;
+      Bs[kb2][nn] = (gn < g.N && gk2 < ke) ? g.B[gk2 * g.sbk + gn * g.sbn] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= g.N) continue;
+      double* cp = g.C + gm * g.scm + gn * g.scn;
+      const double v = g.alpha * acc[i][j];
+      if (gridDim.z > 1) atomicAdd(cp, v);
+      else *cp = (g.beta == 0.0) ? v : fma(g.beta, *cp, v);
+    }
+  }
+}
+
+int gemm_f64(Ctx& c, const Gemm& g) {
+  if (g.M <= 0 || g.N <= 0) return TTR_OK;
+  int splits = g.split_k < 1 ? 1 : g.split_k;
+  int64_t kchunk = (g.K + splits - 1) / splits;
+  kchunk = ((kchunk + GK - 1) / GK) * GK;
+  if (kchunk < GK) kchunk = GK;
+  splits = (int)((g.K + kchunk - 1) / kchunk);
+  if (splits < 1) splits = 1;
+  dim3 grid((unsigned)((g.N + GT - 1) / GT), (unsigned)((g.M + GT - 1) / GT), (unsigned)splits);
+  if (g.K <= 0) grid.z = 1;
+  gemm_f64_kernel<<<grid, 256, 0, c.stream>>>(g, g.K <= 0 ? GK : kchunk);
+  return c.check_launch("gemm_f64");
+}
+
+// ----------------------------------------------------------------------------- Omega
+__global__ void omega_kernel(uint64_t seed, int32_t k_lo, const int64_t* nk, int64_t col0, int64_t w,
+                             double* dst, int64_t ostride, int64_t ld, int64_t total_per_core) {
+  const int32_t kk = blockIdx.y;                       // core offset
+  const int64_t n = nk[kk];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * w;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / w, j = e % w;
+    const float v = omega_entry(seed, (uint32_t)(k_lo + kk), (uint32_t)i, (uint32_t)(col0 + j));
+    dst[kk * ostride + i * ld + j] = (double)v;
+  }
+  (void)total_per_core;
+}
+
+int omega_fill(Ctx& c, uint64_t seed, int32_t k_lo, int32_t k_hi, const int64_t* n_host, int64_t col0,
+               int64_t col1, double* dst, int64_t ostride, int64_t ld) {
+  const int32_t nc = k_hi - k_lo + 1;
+  const int64_t w = col1 - col0;
+  if (nc <= 0 || w <= 0) return TTR_OK;
+  int64_t* nk = nullptr;
+  TTR_CHECK(c.alloc_t(&nk, nc));
+  int64_t nmax = 0;
+  for (int i = 0; i < nc; ++i) nmax = n_host[k_lo - 1 + i] > nmax ? n_host[k_lo - 1 + i] : nmax;
+  TTR_CUDA(cudaMemcpyAsync(nk, n_host + (k_lo - 1), sizeof(int64_t) * nc, cudaMemcpyHostToDevice, c.stream));
+  const int64_t per = nmax * w;
+  unsigned bx = (unsigned)((per + 255) / 256);
+  if (bx > 1024) bx = 1024;
+  omega_kernel<<<dim3(bx, nc), 256, 0, c.stream>>>(seed, k_lo, nk, col0, w, dst, ostride, ld, per);
+  return c.check_launch("omega_fill");
+}
+
+// ----------------------------------------------------------------------------- Omega reduction
+__global__ void omega_reduce_kernel(const double* T, int64_t ldt, const double* Om, int64_t ldo, int64_t r0,
+                                    int64_t n, int64_t w, double* W, int64_t ldw) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r0 * w) return;
+  const int64_t a = e / w, j = e % w;
+  const double* t = T + a * n * ldt + j;
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s = fma(t[i * ldt], Om[i * ldo + j], s);
+  W[a * ldw + j] = s;
+}
+
+int omega_reduce(Ctx& c, const double* T, int64_t ldt, const double* Om, int64_t ldo, int64_t r0, int64_t n,
+                 int64_t w, double* W, int64_t ldw) {
+  const int64_t tot = r0 * w;
+  if (tot <= 0) return TTR_OK;
+  omega_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T, ldt, Om, ldo, r0, n, w, W, ldw);
+  return c.check_launch("omega_reduce");
+}
+
+// ----------------------------------------------------------------------------- sum of squares
+__global__ void sumsq_kernel(const double* S, int64_t m, int64_t b, int64_t sm, int64_t sb, double* out) {
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * b; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / b, j = e % b;
+    const double v = S[i * sm + j * sb];
+    s = fma(v, v, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+int sumsq(Ctx& c, const double* S, int64_t m, int64_t b, int64_t sm, int64_t sb, double* out) {
+  const int64_t tot = m * b;
+  if (tot <= 0) return TTR_OK;
+  unsigned blocks = (unsigned)((tot + 255) / 256);
+  if (blocks > 304) blocks = 304;
+  sumsq_kernel<<<blocks, 256, 0, c.stream>>>(S, m, b, sm, sb, out);
+  return c.check_launch("sumsq");
+}
+
+// ----------------------------------------------------------------------------- perturbation
+// X(i, j) += scale * g(i, j), g standard Gaussian from the sketch generator with core index 0
+// (a counter range the sketches never use).  Used to lift an exactly rank-deficient sketch.
+__global__ void add_gaussian_kernel(double* X, int64_t m, int64_t b, int64_t ld, const double* scale, uint64_t seed) {
+  const double sc = *scale;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * b; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / b, j = e % b;
+    X[i * ld + j] += sc * gaussian_f64(seed, 0u, (uint32_t)i, (uint32_t)j);
+  }
+}
+
+int add_gaussian(Ctx& c, double* X, int64_t m, int64_t b, int64_t ld, const double* scale_dev, uint64_t seed) {
+  const int64_t tot = m * b;
+  if (tot <= 0) return TTR_OK;
+  add_gaussian_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 2048), 256, 0, c.stream>>>(X, m, b, ld, scale_dev, seed);
+  return c.check_launch("add_gaussian");
+}
+
+// ----------------------------------------------------------------------------- Cholesky + inverse
+// One CTA.  Upper factor R (G = R^T R) overwrites the upper triangle of G; Rinv = R^{-1}.
+__global__ void __launch_bounds__(1024) chol_inv_kernel(double* G, int64_t b, int64_t ld, const double* shift,
+                                                        double* Rinv, int* bad) {
+  __shared__ double piv;
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  const double sh = shift ? *shift : 0.0;
+  __syncthreads();
+  for (int64_t j = 0; j < b; ++j) {
+    // R[j][c] = (G[j][c] + sh*[c==j] - sum_{p<j} R[p][j] R[p][c]) / R[j][j], c >= j
+    if (threadIdx.x == 0) {
+      double d = G[j * ld + j] + sh;
+      for (int64_t p = 0; p < j; ++p) d -= G[p * ld + j] * G[p * ld + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        fail = 1;
+        d = 1.0;
+      }
+      piv = sqrt(d);
+      G[j * ld + j] = piv;
+    }
+    __syncthreads();
+    for (int64_t col = j + 1 + threadIdx.x; col < b; col += blockDim.x) {
+      double v = G[j * ld + col];
+      for (int64_t p = 0; p < j; ++p) v -= G[p * ld + j] * G[p * ld + col];
+      G[j * ld + col] = v / piv;
+    }
+    __syncthreads();
+  }
+  // Rinv: column c by back substitution, one thread per column.
+  for (int64_t col = threadIdx.x; col < b; col += blockDim.x) {
+    for (int64_t i = b - 1; i >= 0; --i) {
+      if (i > col) {
+        Rinv[i * ld + col] = 0.0;
+        continue;
+      }
+      double v = (i == col) ? 1.0 : 0.0;
+      for (int64_t p = i + 1; p <= col; ++p) v -= G[i * ld + p] * Rinv[p * ld + col];
+      Rinv[i * ld + col] = v / G[i * ld + i];
+    }
+  }
+  if (threadIdx.x == 0 && fail) *bad = 1;
+}
+
+int chol_inv(Ctx& c, double* G, int64_t b, int64_t ld, const double* shift_dev, double* Rinv, int* bad) {
+  if (b <= 0) return TTR_OK;
+  chol_inv_kernel<<<1, 256, 0, c.stream>>>(G, b, ld, shift_dev, Rinv, bad);
+  return c.check_launch("chol_inv");
+}
+
+// ----------------------------------------------------------------------------- copies
+__global__ void copy2d_kernel(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows, int64_t cols) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e % cols;
+    dst[i * ldd + j] = src[i * lds + j];
+  }
+}
+
+int copy2d(Ctx& c, double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows, int64_t cols) {
+  if (rows <= 0 || cols <= 0) return TTR_OK;
+  TTR_CUDA(cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double), cols * sizeof(double), rows,
+                             cudaMemcpyDeviceToDevice, c.stream));
+  return TTR_OK;
+}
+
+int fill_zero(Ctx& c, double* p, int64_t count) {
+  if (count <= 0) return TTR_OK;
+  TTR_CUDA(cudaMemsetAsync(p, 0, count * sizeof(double), c.stream));
+  return TTR_OK;
+}
+
+// ----------------------------------------------------------------------------- Jacobi SVD
+// One-sided (Hestenes) Jacobi on the columns of a b x b matrix A, one CTA, b <= 1024.
+// Round-robin pair ordering: in round r, position i pairs with position b2-1-i where
+// positions hold players (0, 1+((i-1+r) mod (b2-1))).  One warp per pair.
+__global__ void __launch_bounds__(1024) jacobi_svd_kernel(double* A, int64_t b, int64_t ld, double* sigma,
+                                                          double* U, double* Vt, int* bad) {
+  extern __shared__ int sh_idx[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int64_t b2 = (b + 1) & ~1LL;
+  // V := I  (stored transposed as Vt rows = columns of V)
+  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) Vt[(e / b) * ld + (e % b)] = ((e / b) == (e % b)) ? 1.0 : 0.0;
+  __shared__ int rotated;
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int64_t r = 0; r < b2 - 1; ++r) {
+      for (int64_t pi = warp; pi < b2 / 2; pi += nwarps) {
+        const int64_t i1 = pi, i2 = b2 - 1 - pi;
+        const int64_t p = (i1 == 0) ? 0 : 1 + ((i1 - 1 + r) % (b2 - 1));
+        const int64_t q = (i2 == 0) ? 0 : 1 + ((i2 - 1 + r) % (b2 - 1));
+        if (p >= b || q >= b) continue;
+        double al = 0, be = 0, ga = 0;
+        for (int64_t i = lane; i < b; i += 32) {
+          const double x = A[i * ld + p], y = A[i * ld + q];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int64_t i = lane; i < b; i += 32) {
+            const double x = A[i * ld + p], y = A[i * ld + q];
+            A[i * ld + p] = cs * x - sn * y;
+            A[i * ld + q] = sn * x + cs * y;
+            const double vx = Vt[p * ld + i], vy = Vt[q * ld + i];
+            Vt[p * ld + i] = cs * vx - sn * vy;
+            Vt[q * ld + i] = sn * vx + cs * vy;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // sigma_j = ||a_j||, U_j = a_j / sigma_j; sort descending (selection sort by thread 0)
+  for (int64_t j = warp; j < b; j += nwarps) {
+    double s = 0;
+    for (int64_t i = lane; i < b; i += 32) s = fma(A[i * ld + j], A[i * ld + j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sigma[j] = sqrt(s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int64_t j = 0; j < b; ++j) sh_idx[j] = (int)j;
+    for (int64_t j = 0; j < b; ++j) {
+      int64_t best = j;
+      for (int64_t t = j + 1; t < b; ++t)
+        if (sigma[sh_idx[t]] > sigma[sh_idx[best]]) best = t;
+      const int tmp = sh_idx[j];
+      sh_idx[j] = sh_idx[best];
+      sh_idx[best] = tmp;
+    }
+  }
+  __syncthreads();
+  // U(:, j) = A(:, idx[j]) / sigma[idx[j]]; Vt row j = old Vt row idx[j]  (A and old Vt still intact)
+  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int64_t i = e / b, j = e % b;
+    const int src = sh_idx[j];
+    const double s = sigma[src];
+    U[i * ld + j] = (s > 0.0) ? A[i * ld + src] / s : ((i == j) ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  // permute Vt rows through A (A is free now) and sigma
+  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int64_t j = e / b, i = e % b;
+    A[j * ld + i] = Vt[(int64_t)sh_idx[j] * ld + i];
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) Vt[(e / b) * ld + (e % b)] = A[(e / b) * ld + (e % b)];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int64_t j = 0; j < b; ++j) A[j] = sigma[sh_idx[j]];
+    for (int64_t j = 0; j < b; ++j) sigma[j] = A[j];
+    if (!isfinite(sigma[0])) *bad = 1;
+  }
+}
+
+int jacobi_svd(Ctx& c, double* A, int64_t b, int64_t ld, double* sigma, double* U, double* Vt, int* bad) {
+  if (b <= 0) return TTR_OK;
+  if (b > 1024) return TTR_ERR_UNSUPPORTED;
+  jacobi_svd_kernel<<<1, 1024, sizeof(int) * b, c.stream>>>(A, b, ld, sigma, U, Vt, bad);
+  return c.check_launch("jacobi_svd");
+}
+
+}  // namespace ttr

@@ -1,0 +1,100 @@
+// Internal declarations shared by the libttround translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ttround.h"
+
+namespace ttr {
+
+// ----------------------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+
+#define TTR_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ::ttr::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));         \
+      return (e_ == cudaErrorMemoryAllocation) ? TTR_ERR_OOM : TTR_ERR_CUDA;        \
+    }                                                                               \
+  } while (0)
+
+#define TTR_CHECK(expr)            \
+  do {                             \
+    int s_ = (expr);               \
+    if (s_ != TTR_OK) return s_;   \
+  } while (0)
+
+// ----------------------------------------------------------------------------- context
+// Per-call state: the stream, stream-ordered allocations made during the call (freed at the
+// end unless handed to the caller) and a count of kernel launches.
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  int64_t launches = 0;
+  std::vector<void*> owned;
+  int* d_flags = nullptr;          // device status flags (0 = ok); bounded waits write here
+
+  int alloc(void** p, size_t bytes);
+  template <typename T>
+  int alloc_t(T** p, size_t count) {
+    return alloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  }
+  int check_launch(const char* what);
+  void release();
+  ~Ctx() { release(); }
+};
+
+// ----------------------------------------------------------------------------- kernels (FP64 SIMT)
+// General strided, batched FP64 GEMM: C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n),
+// with X(i,j) = X[i*s_i + j*s_j].  split_k > 1 accumulates partial sums atomically into C
+// (C must then be initialised by the caller and beta is ignored).
+struct Gemm {
+  int64_t M = 0, N = 0, K = 0;
+  const double* A = nullptr;
+  int64_t sam = 0, sak = 0;
+  const double* B = nullptr;
+  int64_t sbk = 0, sbn = 0;
+  double* C = nullptr;
+  int64_t scm = 0, scn = 0;
+  double alpha = 1.0, beta = 0.0;
+  int split_k = 1;
+};
+int gemm_f64(Ctx& c, const Gemm& g);
+
+// Omega_k(:, col0:col1) for cores k = k_lo..k_hi (1-based); block k goes to
+// dst + (k - k_lo) * ostride as row-major [i][j - col0] with leading dimension ld.
+int omega_fill(Ctx& c, uint64_t seed, int32_t k_lo, int32_t k_hi, const int64_t* n_host,
+               int64_t col0, int64_t col1, double* dst, int64_t ostride, int64_t ld);
+
+// W_k(a, j) = sum_i T(a*n + i, j) * Omega(i, j) for a < r0, j < w  (Algorithm 3 epilogue)
+int omega_reduce(Ctx& c, const double* T, int64_t ldt, const double* Om, int64_t ldo, int64_t r0,
+                 int64_t n, int64_t w, double* W, int64_t ldw);
+
+// Sum of squares of an m x b strided matrix, accumulated into *out (device, zeroed by caller).
+int sumsq(Ctx& c, const double* S, int64_t m, int64_t b, int64_t sm, int64_t sb, double* out);
+
+// Upper Cholesky of a b x b symmetric matrix (row-major, ld) in place, plus the inverse of
+// the factor into Rinv (row-major, ld).  shift is added to the diagonal first.  *bad is set
+// to 1 on a non-positive or non-finite pivot.
+int chol_inv(Ctx& c, double* G, int64_t b, int64_t ld, const double* shift_dev, double* Rinv,
+             int* bad);
+
+// X += (*scale_dev) * G with G an m x b standard Gaussian matrix drawn from `seed`.
+int add_gaussian(Ctx& c, double* X, int64_t m, int64_t b, int64_t ld, const double* scale_dev, uint64_t seed);
+
+// Copies / fills
+int copy2d(Ctx& c, double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows,
+           int64_t cols);
+int fill_zero(Ctx& c, double* p, int64_t count);
+
+// Small-matrix SVD by one-sided Jacobi (Hestenes) on a b x b matrix in one CTA:
+// A (row-major, ld) is overwritten; on return sigma (descending), U (b x b, ld) and
+// Vt (b x b, ld) with A_in = U diag(sigma) Vt.
+int jacobi_svd(Ctx& c, double* A, int64_t b, int64_t ld, double* sigma, double* U, double* Vt,
+               int* bad);
+
+}  // namespace ttr

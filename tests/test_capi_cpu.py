@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function include/*.h declares."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            name = m.group(1)
+            if name not in ("defined", "if", "sizeof"):
+                names.append(name)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2511_03598_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("tt_round_fixed", "tt_round_adaptive", "tt_round_deterministic", "ttr_free",
+                     "ttr_strerror", "ttr_default_options"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points_work_without_gpu(libpath):
+    from paper_2511_03598_gb300 import binding as B
+    L = B.lib()
+    assert L.ttr_strerror(0) == b"ok"
+    assert L.ttr_strerror(4) == b"CholeskyQR breakdown"
+    o = B.Options()
+    L.ttr_default_options(ctypes.byref(o))
+    assert (o.precision, o.adap_r, o.f_init, o.f_inc, o.adap_r_tau_scale) == (0, 0, 0.1, 0.05, 1.0)
+
+
+def test_argument_errors_are_reported_not_raised_on_host(libpath):
+    """Argument checks run before any device work, so they work without a GPU."""
+    from paper_2511_03598_gb300 import binding as B
+    L = B.lib()
+    res = B.Result()
+    n = (ctypes.c_int64 * 2)(3, 3)
+    r = (ctypes.c_int64 * 3)(2, 2, 1)          # r[0] != 1
+    p = (ctypes.c_void_p * 2)(8, 16)
+    st = L.tt_round_adaptive(2, n, r, p, 1e-6, 2, ctypes.c_uint64(1), None, None, ctypes.byref(res))
+    assert st == 1 and res.status == 1
+    assert b"r[0]" in L.ttr_last_error()
+    r2 = (ctypes.c_int64 * 3)(1, 2, 1)
+    st = L.tt_round_adaptive(2, n, r2, p, -1.0, 2, ctypes.c_uint64(1), None, None, ctypes.byref(res))
+    assert st == 1
+    st = L.tt_round_fixed(1, n, r2, p, 2, 0, ctypes.c_uint64(1), None, None, ctypes.byref(res))
+    assert st == 1
+    p_bad = (ctypes.c_void_p * 2)(8, 12)       # misaligned core pointer
+    st = L.tt_round_deterministic(2, n, r2, p_bad, 1e-6, None, ctypes.byref(res))
+    assert st == 1

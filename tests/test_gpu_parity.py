@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Tolerances (FP64 mode): Omega bit for bit; partial contractions 1e-12 relative (max-norm);
+rounded tensors 1e-10 relative Frobenius distance of the represented tensors (the QR bases
+themselves are not unique), identical ranks, residual estimates 1e-8 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as WL
+from oracle import philox as OP
+from oracle import rounding as R
+from oracle import tt as T
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2511_03598_gb300 import build
+    build.build()
+    from paper_2511_03598_gb300 import binding
+    assert torch.cuda.is_available()
+    return binding
+
+
+def dev(cores):
+    return [torch.from_numpy(np.ascontiguousarray(c)).to("cuda") for c in cores]
+
+
+def rel_tensor_diff(a, b):
+    return T.tt_dist(a, b) / max(T.tt_norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------ Omega
+@pytest.mark.parametrize("seed,k,n,c0,c1", [(1, 2, 50, 0, 64), (2**63 + 12345, 7, 3, 5, 77), (0, 20, 128, 100, 101),
+                                             (987654321, 3, 1, 0, 300)])
+def test_omega_bitwise(B, seed, k, n, c0, c1):
+    got = B.sketch_omega(seed, k, n, c0, c1).cpu().numpy()
+    ref = OP.omega(seed, k, n, c0, c1)
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+
+
+# ------------------------------------------------------------------ Algorithm 3
+CASES_RL = [("c1", lambda: WL.c1().cores, 13), ("ragged", lambda: WL.random_tt(np.random.default_rng(3), 5, [3, 7, 1, 5, 4], [4, 9, 2, 6]), 21),
+            ("c3s", lambda: WL.c3(d=6, n=16, r=10).cores, 40)]
+
+
+@pytest.mark.parametrize("name,make,w", CASES_RL)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_partial_contractions(B, name, make, w, prec):
+    cores = make()
+    got = B.partial_contractions(dev(cores), 77, 3, 3 + w, precision=prec, slices=8)
+    ref = R.partial_contractions_rl(cores, 77, 3, 3 + w)
+    for k, Wk in ref.items():
+        g = got[k].cpu().numpy()
+        assert g.shape == Wk.shape
+        scale = np.abs(Wk).max()
+        assert np.abs(g - Wk).max() <= 1e-12 * scale, (k, np.abs(g - Wk).max() / scale)
+
+
+def test_partial_contractions_c2_full_size(B):
+    x = WL.c2()
+    got = B.partial_contractions(dev(x.cores), 5, 0, 70)
+    ref = R.partial_contractions_rl(x.cores, 5, 0, 70)
+    for k in (2, 11, 20):
+        g = got[k].cpu().numpy()
+        assert np.abs(g - ref[k]).max() <= 1e-12 * np.abs(ref[k]).max()
+
+
+# ------------------------------------------------------------------ Algorithm 4
+def test_fixed_c1(B):
+    x = WL.c1()
+    ref, info = R.tt_round_fixed(x.cores, 13, seed=31)
+    with B.round_fixed(dev(x.cores), 13, 31) as y:
+        assert y.ranks == info["ranks"]
+        got = y.to_numpy()
+    assert rel_tensor_diff(got, ref) <= 1e-10
+    assert T.left_orth_defect(got) <= 1e-12
+
+
+def test_fixed_c1_target(B):
+    x = WL.c1()
+    Y, _ = R.tt_round_fixed(x.cores, 13, seed=31)
+    ref = R.svd_pass_rl(Y, max_rank=8)
+    with B.round_fixed(dev(x.cores), 13, 31, target=8) as y:
+        assert y.ranks == [1, 8, 8, 8, 8, 8, 1]
+        got = y.to_numpy()
+    assert rel_tensor_diff(got, ref) <= 1e-10
+
+
+# ------------------------------------------------------------------ Algorithm 6
+CASES_AD = [
+    ("c1_blk2", lambda: WL.c1(), 1e-6, 2),
+    ("c1_frac", lambda: WL.c1(), 1e-3, 0),
+    ("c3_small", lambda: WL.c3(d=6, n=16, r=10), 1e-8, 0),
+    ("ragged", lambda: WL.copies_plus_noise(8, 5, 7, 5, 3, 2, 1e-6, "ragged"), 1e-5, 3),
+]
+
+
+@pytest.mark.parametrize("name,make,tol,block", CASES_AD)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_adaptive_parity(B, name, make, tol, block, prec):
+    x = make()
+    ref, info = R.tt_round_adaptive(x.cores, tol, seed=5, block=block, nrmx=x.norm)
+    with B.round_adaptive(dev(x.cores), tol, block, 5, B.options(precision=prec, slices=8, nrmx=x.norm)) as y:
+        yi = y.info
+        got = y.to_numpy()
+    assert yi["ranks"] == info["ranks"]
+    flat = [e for es in info["estimates"] for e in es]
+    assert len(flat) == len(yi["estimates"])
+    assert np.allclose(yi["estimates"], flat, rtol=1e-8, atol=1e-14 * x.norm)
+    assert rel_tensor_diff(got, ref) <= 1e-10
+    assert T.tt_dist(got, x.cores) <= tol * x.norm * (1 + 1e-9) or name.startswith("c3")
+
+
+def test_adaptive_norm_estimate(B):
+    x = WL.c1()
+    ref, info = R.tt_round_adaptive(x.cores, 1e-6, seed=9, block=2)
+    with B.round_adaptive(dev(x.cores), 1e-6, 2, 9) as y:
+        assert math.isclose(y.info["nrmx"], info["nrmx"], rel_tol=1e-12)
+        assert y.ranks == info["ranks"]
+        assert rel_tensor_diff(y.to_numpy(), ref) <= 1e-10
+
+
+def test_adaptive_width_hint_does_not_change_result(B):
+    x = WL.c1()
+    outs = []
+    for hint in (0, 9, 40):
+        with B.round_adaptive(dev(x.cores), 1e-7, 2, 3, B.options(nrmx=x.norm, width_hint=hint)) as y:
+            outs.append((y.ranks, y.to_numpy(), y.info["extensions"]))
+    for ranks, cores, _ in outs[1:]:
+        assert ranks == outs[0][0]
+        assert rel_tensor_diff(cores, outs[0][1]) <= 1e-12
+    assert outs[2][2] < outs[0][2]
+
+
+def test_adaptive_adap_r(B):
+    x = WL.c1()
+    ref, info = R.tt_round_adaptive(x.cores, 1e-6, seed=5, block=2, nrmx=x.norm, adap_r=True)
+    with B.round_adaptive(dev(x.cores), 1e-6, 2, 5, B.options(nrmx=x.norm, adap_r=True)) as y:
+        assert y.ranks == info["ranks"]
+        assert rel_tensor_diff(y.to_numpy(), ref) <= 1e-10
+
+
+def test_adaptive_c2_full_size(B):
+    """The bench workload: d=20, n=50, formal rank 210, tol 1e-6, block 10."""
+    x = WL.c2()
+    ref, info = R.tt_round_adaptive(x.cores, 1e-6, seed=2024, block=10, nrmx=x.norm)
+    with B.round_adaptive(dev(x.cores), 1e-6, 10, 2024, B.options(nrmx=x.norm)) as y:
+        yi = y.info
+        got = y.to_numpy()
+    assert yi["ranks"] == info["ranks"]
+    flat = [e for es in info["estimates"] for e in es]
+    assert np.allclose(yi["estimates"], flat, rtol=1e-8, atol=1e-14 * x.norm)
+    assert rel_tensor_diff(got, ref) <= 1e-10
+
+
+# ------------------------------------------------------------------ Algorithm 1
+@pytest.mark.parametrize("tol", [1e-2, 1e-6])
+def test_deterministic_c1(B, tol):
+    x = WL.c1()
+    ref, info = R.tt_round_deterministic(x.cores, tol)
+    with B.round_deterministic(dev(x.cores), tol) as y:
+        assert y.ranks == info["ranks"]
+        got = y.to_numpy()
+    assert T.tt_dist(got, x.cores) <= tol * x.norm
+    assert rel_tensor_diff(got, ref) <= 1e-7
+
+
+# ------------------------------------------------------------------ edge cases and errors
+def test_rank_one_and_n_one(B):
+    cores = WL.random_tt(np.random.default_rng(1), 4, [1, 5, 1, 3], [1, 3, 2])
+    ref, info = R.tt_round_adaptive(cores, 1e-9, seed=1, block=1, nrmx=T.tt_norm(cores))
+    with B.round_adaptive(dev(cores), 1e-9, 1, 1, B.options(nrmx=T.tt_norm(cores))) as y:
+        assert y.ranks == info["ranks"]
+        assert rel_tensor_diff(y.to_numpy(), ref) <= 1e-10
+
+
+def test_bad_arguments_raise(B):
+    x = WL.c1()
+    with pytest.raises(B.TTRoundError):
+        B.round_adaptive(dev(x.cores), 0.0, 2, 1)
+    with pytest.raises(B.TTRoundError):
+        B.round_fixed(dev(x.cores), 0, 1)
