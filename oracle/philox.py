@@ -30,6 +30,9 @@ element and never fuse a multiply with an add.
 """
 from __future__ import annotations
 
+import math
+from fractions import Fraction
+
 import numpy as np
 
 _M0 = np.uint64(0xD2511F53)
@@ -122,10 +125,8 @@ def _sin_poly(x, x2):
 
 
 def _inv_fact(n: int) -> float:
-    f = 1
-    for i in range(2, n + 1):
-        f *= i
-    return 1.0 / f     # correctly rounded: exact integer f converted once, one division
+    """1/n! rounded once to the nearest double (exact rational first; n! > 2^53 for n > 18)."""
+    return float(Fraction(1, math.factorial(n)))
 
 
 def own_cos2pi(t: np.ndarray) -> np.ndarray:
