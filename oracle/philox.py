@@ -21,9 +21,11 @@ append columns, Algorithm 4, without changing earlier ones).
   using only correctly rounded IEEE-754 double +, -, *, / and sqrt, in a fixed order.  The
   CUDA side evaluates the same operation sequence with explicitly rounded intrinsics, so the
   two agree bit for bit.
-* The sketch entry is the Gaussian rounded to binary32 (round to nearest even).  The CUDA
-  contraction kernels multiply by these entries in exact FP32 two-product form, which is
-  why the entries carry 24 significant bits.
+* The sketch entry is the Gaussian rounded to the fixed-point grid 2^-20 (round half to
+  even): Omega = rint(g * 2^20) * 2^-20, so |Omega| * 2^20 is an integer below 2^24.  The
+  CUDA partial-contraction kernel multiplies by these entries and sums over the mode index
+  in exact integer arithmetic, which needs a common scale; the grid changes E[Omega^2] by
+  2^-40/12 and leaves the Gaussian sketch properties of Sec. 3.4 intact.
 
 Everything is vectorised over numpy arrays; numpy float64 ufuncs are IEEE-correct per
 element and never fuse a multiply with an add.
@@ -167,7 +169,7 @@ def gaussian_f64(seed: int, k, i, j) -> np.ndarray:
 
 
 def omega(seed: int, k: int, n_k: int, col0: int, col1: int) -> np.ndarray:
-    """Sketch block Omega_k(:, col0:col1) in R^{n_k x (col1-col0)} (values exactly binary32, stored as float64).
+    """Sketch block Omega_k(:, col0:col1) in R^{n_k x (col1-col0)} (values on the 2^-20 grid, float64).
 
     ``k`` is the 1-based core index of Sec. 3.1 (Omega_2 .. Omega_d are used); columns use the
     global column index j so that a column never depends on how many columns were drawn.
@@ -175,4 +177,7 @@ def omega(seed: int, k: int, n_k: int, col0: int, col1: int) -> np.ndarray:
     i = np.arange(n_k, dtype=np.uint64)[:, None]
     j = np.arange(col0, col1, dtype=np.uint64)[None, :]
     g = gaussian_f64(seed, np.uint64(k), i, j)
-    return g.astype(np.float32).astype(np.float64)
+    return np.rint(g * OMEGA_SCALE) / OMEGA_SCALE
+
+
+OMEGA_SCALE = 2.0 ** 20     # sketch entries live on the grid 2^-20 (see module docstring)
