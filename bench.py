@@ -158,6 +158,7 @@ def main():
     ap.add_argument("--precision", default="sliced", choices=["fp64", "sliced"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--det-steps", type=int, default=2)
+    ap.add_argument("--only-main", action="store_true", help="timed rounding loop only (for profiler runs)")
     args = ap.parse_args()
 
     import workloads as WL
@@ -214,6 +215,11 @@ def main():
     total_ms = float(tmax.item())
     value = world * args.steps / (total_ms / 1e3)
 
+    if args.only_main:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "roundings/s", "ms_per_step": total_ms / args.steps,
+                              "gpu_launches": int(launches), "only_main": True}), flush=True)
+        return
     # ---- dominant kernel: right-to-left partial contractions at the final sketch width
     w = int(info["width"])
     reps = 10

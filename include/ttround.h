@@ -103,9 +103,9 @@ void ttr_default_options(ttr_options* opts);
  *          min(l, l_{k-1} n_k, r_k, prod_{j>k} n_j).
  *   target if 0 < target < l, the left-orthonormal result is truncated to rank `target` by a
  *          right-to-left SVD pass (Remark 3.2 with a rank bound); <= 0 keeps rank l.
- *   seed   64-bit key of the Gaussian stream: Omega_k(i, j) = round_to_binary32(Box-Muller of
- *          Philox4x32-10(counter (j, i, k, 0), key seed)), k 1-based.  The same seed gives the
- *          same Omega as the CPU oracle, bit for bit.
+ *   seed   64-bit key of the Gaussian stream: Omega_k(i, j) = rint(2^20 g) / 2^20 with g the
+ *          Box-Muller Gaussian of Philox4x32-10(counter (j, i, k, 0), key seed), k 1-based.  The
+ *          same seed gives the same Omega as the CPU oracle, bit for bit.
  * Output cores 1..d-1 are left-orthonormal (V(Y_k)^T V(Y_k) = I). */
 int tt_round_fixed(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
                    int64_t ell, int64_t target, uint64_t seed, const ttr_options* opts,
@@ -141,8 +141,8 @@ const char* ttr_strerror(int status);
 const char* ttr_last_error(void);
 
 /* Gaussian sketch block Omega_k(:, col0:col1) as produced on the device (Sec. 3.1), written
- * row-major [i][j - col0] to the DEVICE buffer `dst` (n_k * (col1 - col0) doubles, values
- * exactly representable in binary32).  For parity tests of the sketch stream. */
+ * row-major [i][j - col0] to the DEVICE buffer `dst` (n_k * (col1 - col0) doubles, values on
+ * the grid 2^-20).  For parity tests of the sketch stream. */
 int ttr_sketch_omega(uint64_t seed, int32_t k, int64_t n_k, int64_t col0, int64_t col1,
                      double* dst, void* stream);
 

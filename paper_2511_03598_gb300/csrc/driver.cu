@@ -103,6 +103,16 @@ static int isync_read(Ctx& c, const int* dptr, int* status) {
   return v;
 }
 
+// Device-side bounded waits record failures in c.d_flags; report them once per call.
+static int check_device_flags(Ctx& c) {
+  if (!c.d_flags) return TTR_OK;
+  int st = TTR_OK;
+  const int v = isync_read(c, c.d_flags, &st);
+  if (st != TTR_OK) return st;
+  if (v) return set_error("a bounded device wait ran out"), TTR_ERR_TIMEOUT;
+  return TTR_OK;
+}
+
 // ----------------------------------------------------------------------------- QR
 // Thin QR of the m x b row-major matrix X (leading dimension ldx), in place: X <- Q.
 // CholeskyQR2; if a Cholesky pivot breaks down, shifted CholeskyQR3 (Fukaya, Kannan,
@@ -119,21 +129,10 @@ struct QrWork {
 
 static int chol_pass(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m, int64_t b, double* out,
                      int64_t ldo, const QrWork& w, const double* shift) {
-  TTR_CHECK(fill_zero(c, w.G, b * b));
-  Gemm g;  // G = X^T X
-  g.M = b; g.N = b; g.K = m;
-  g.A = X; g.sam = 1; g.sak = ldx;
-  g.B = X; g.sbk = ldx; g.sbn = 1;
-  g.C = w.G; g.scm = b; g.scn = 1;
-  g.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, m / 256), 128);
-  TTR_CHECK(E.small_gemm(c, g));
+  (void)E;
+  TTR_CHECK(gram_tn(c, X, ldx, X, ldx, m, b, b, w.G, b));                 // G = X^T X
   TTR_CHECK(chol_inv(c, w.G, b, b, shift, w.Rinv, w.dflag));
-  Gemm h;  // out = X Rinv
-  h.M = m; h.N = b; h.K = b;
-  h.A = X; h.sam = ldx; h.sak = 1;
-  h.B = w.Rinv; h.sbk = b; h.sbn = 1;
-  h.C = out; h.scm = ldo; h.scn = 1;
-  return E.small_gemm(c, h);
+  return gemm_nn_small(c, X, ldx, w.Rinv, b, m, b, b, out, ldo, 1.0, 0.0);  // out = X R^{-1}
 }
 
 static int qr_inplace(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m, int64_t b, const QrWork& w) {
@@ -193,6 +192,7 @@ struct Sketch {
   int64_t ldw = 0;
   int64_t width = 0;        // columns computed so far
   double* Om = nullptr;
+  int* Omi = nullptr;        // 2^20 * Omega as integers, same layout as Om
   int64_t om_stride = 0, ldom = 0;
   double* T = nullptr;      // (max r_{k-1} n_k) x ldw scratch
   int extensions = 0;
@@ -203,7 +203,8 @@ static int rl_pass(Ctx& c, const Engine& E, const TT& X, uint64_t seed, int64_t 
   const int d = X.d;
   const int64_t w = col1 - col0;
   if (w <= 0) return TTR_OK;
-  TTR_CHECK(omega_fill(c, seed, t, d, X.n, col0, col1, s.Om + (int64_t)(t - 1) * s.om_stride, s.om_stride, s.ldom));
+  TTR_CHECK(omega_fill(c, seed, t, d, X.n, col0, col1, s.Om + (int64_t)(t - 1) * s.om_stride,
+                       s.Omi + (int64_t)(t - 1) * s.om_stride, s.om_stride, s.ldom));
   // W_d = H(X_d) Omega_d  (r_{d-1} x n_d) (n_d x w)
   {
     Gemm g;
@@ -215,7 +216,8 @@ static int rl_pass(Ctx& c, const Engine& E, const TT& X, uint64_t seed, int64_t 
   }
   for (int k = d - 1; k >= t; --k) {
     TTR_CHECK(E.rl_step(c, X.cores[k - 1], X.r[k - 1], X.n[k - 1], X.r[k], s.W[k] + col0, s.ldw,
-                        s.Om + (int64_t)(k - 1) * s.om_stride, s.ldom, w, s.W[k - 1] + col0, s.ldw, s.T));
+                        s.Om + (int64_t)(k - 1) * s.om_stride, s.Omi + (int64_t)(k - 1) * s.om_stride, s.ldom, w,
+                        s.W[k - 1] + col0, s.ldw, s.T));
   }
   return TTR_OK;
 }
@@ -240,6 +242,7 @@ static int sketch_alloc(Ctx& c, const TT& X, int64_t wcap, Sketch& s) {
   s.ldom = wcap;
   s.om_stride = nmax * wcap;
   TTR_CHECK(c.alloc_t(&s.Om, (int64_t)d * s.om_stride));
+  TTR_CHECK(c.alloc_t(&s.Omi, (int64_t)d * s.om_stride));
   TTR_CHECK(c.alloc_t(&s.T, rowsmax * wcap));
   return TTR_OK;
 }
@@ -331,14 +334,7 @@ static int sweep_alloc(Ctx& c, const TT& X, int64_t bcap, Sweep& s) {
 // M = Q^T Z  (c x cols), then Ynext = M H(X_{k+1})  (c x n r)
 static int project_next(Ctx& c, const Engine& E, const Sweep& s, const double* Z, int64_t rows, int64_t cols,
                         int64_t ccols, const TT& X, int k, double* Ynext) {
-  Gemm g;
-  g.M = ccols; g.N = cols; g.K = rows;
-  g.A = s.Q; g.sam = 1; g.sak = s.qcap;
-  g.B = Z; g.sbk = cols; g.sbn = 1;
-  g.C = s.M; g.scm = cols; g.scn = 1;
-  g.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, rows / 512), 64);
-  if (g.split_k > 1) TTR_CHECK(fill_zero(c, s.M, ccols * cols));
-  TTR_CHECK(E.small_gemm(c, g));
+  TTR_CHECK(E.left_project(c, s.Q, s.qcap, Z, rows, cols, ccols, s.M));
   // H(X_{k+1}) is cols x (n_{k+1} r_{k+2}), row-major
   return E.project(c, s.M, ccols, cols, X.cores[k], X.n[k] * X.r[k + 1], Ynext);
 }
@@ -500,6 +496,7 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   if (target > 0 && target < ell) TTR_CHECK(svd_pass_rl(c, E, out, X.n, 0.0, target));
   tm.rec(2, stream);
   TTR_CUDA(cudaStreamSynchronize(stream));
+  TTR_CHECK(check_device_flags(c));
   out->width = ell;
   out->ms_sketch_rl = tm.ms(0, 1);
   out->ms_sweep_lr = tm.ms(1, 2);
@@ -530,7 +527,10 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   TTR_CHECK(E.init(c, o.precision, o.slices, tol));
   Sketch s;
   TTR_CHECK(sketch_alloc(c, X, wcap, s));
-  int64_t wdev = w0;
+  // Columns of W are a prefix of one counter-based stream, so how many are drawn up front (and how
+  // the rest are appended) never changes a result; draw one tensor-core tile width up front and
+  // grow geometrically, which keeps the number of right-to-left passes small.
+  int64_t wdev = std::min(wcap, std::max<int64_t>(w0, 64));
   if (o.width_hint > 0) wdev = std::min(wcap, std::max(w0, o.width_hint));
   TTR_CHECK(rl_pass(c, E, X, seed, 0, wdev, 2, s));
   s.width = wdev;
@@ -560,6 +560,16 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   Sweep w;
   TTR_CHECK(sweep_alloc(c, X, std::max(binc_max, binit_max), w));
   TTR_CHECK(result_alloc(c, X, out));
+  int64_t rowsmax = 1;
+  for (int k = 0; k < d; ++k) rowsmax = std::max(rowsmax, X.r[k] * X.n[k]);
+  double* Sall = nullptr;                       // Z W_{k+1}(:, 0:width): every sketch column of core k
+  TTR_CHECK(c.alloc_t(&Sall, rowsmax * wcap));
+  struct Probe {
+    double ss;
+    int flag;
+  };
+  Probe* dprobe = nullptr;                      // residual sum of squares + QR breakdown flag
+  TTR_CHECK(c.alloc(reinterpret_cast<void**>(&dprobe), sizeof(Probe)));
   std::vector<double> ests;
   std::vector<int32_t> est_core;
   double* arena = (double*)out->arena;
@@ -567,55 +577,100 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   const double* Z = X.cores[0];
   int cur = 0;
   out->ranks[0] = 1;
-  auto ensure = [&](int k, int64_t need) -> int {
-    if (s.width >= need) return TTR_OK;
-    if (need > s.ldw) return set_error("sketch capacity exceeded"), TTR_ERR_ARG;
-    TTR_CHECK(rl_pass(c, E, X, seed, s.width, need, k + 1, s));
-    s.width = need;
-    s.extensions++;
+  int64_t sk_cols = 0;                          // columns of Sall computed for the current core
+  auto sketch_cols = [&](int k, int64_t rows, int64_t cols, int64_t c0, int64_t c1) -> int {
+    if (c1 <= c0) return TTR_OK;
+    Gemm g;
+    g.M = rows; g.N = c1 - c0; g.K = cols;
+    g.A = Z; g.sam = cols; g.sak = 1;
+    g.B = s.W[k] + c0; g.sbk = s.ldw; g.sbn = 1;
+    g.C = Sall + c0; g.scm = wcap; g.scn = 1;
+    return E.sketch(c, g);
+  };
+  auto ensure = [&](int k, int64_t need, int64_t rows, int64_t cols) -> int {
+    if (s.width < need) {
+      if (need > s.ldw) return set_error("sketch capacity exceeded"), TTR_ERR_ARG;
+      const int64_t target = std::min(s.ldw, std::max(need, s.width + std::max(binc_max, s.width / 2)));
+      TTR_CHECK(rl_pass(c, E, X, seed, s.width, target, k + 1, s));   // Algorithm 5: append columns
+      s.width = target;
+      s.extensions++;
+    }
+    if (sk_cols < s.width) {
+      TTR_CHECK(sketch_cols(k, rows, cols, sk_cols, s.width));
+      sk_cols = s.width;
+    }
     return TTR_OK;
+  };
+  // CholeskyQR2 without a host round trip; a breakdown only raises dprobe->flag.
+  auto qr_try = [&](double* Xq, int64_t ldx, int64_t m, int64_t b) -> int {
+    TTR_CHECK(copy2d(c, w.qr.save, b, Xq, ldx, m, b));
+    QrWork q2 = w.qr;
+    q2.dflag = &dprobe->flag;
+    TTR_CHECK(chol_pass(c, E, w.qr.save, b, m, b, w.qr.tmp, b, q2, nullptr));
+    return chol_pass(c, E, w.qr.tmp, b, m, b, Xq, ldx, q2, nullptr);
   };
   for (int k = 1; k < d; ++k) {
     const int64_t rows = lprev * X.n[k - 1], cols = X.r[k];
     const int64_t rbar = std::min(rows, cols);
     const int64_t b0 = block_size(rbar, block, o.f_init);
-    TTR_CHECK(ensure(k, b0));
-    Gemm g;
-    g.M = rows; g.N = b0; g.K = cols;
-    g.A = Z; g.sam = cols; g.sak = 1;
-    g.B = s.W[k]; g.sbk = s.ldw; g.sbn = 1;
-    g.C = w.Q; g.scm = w.qcap; g.scn = 1;
-    TTR_CHECK(E.sketch(c, g));
-    TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
-    int64_t cc = b0;
     const int64_t bi = block_size(rbar, block, o.f_inc);
+    sk_cols = 0;
+    TTR_CHECK(ensure(k, b0, rows, cols));
+    // phase 1: Q = qr(S(:, 1:b_init))
+    TTR_CUDA(cudaMemsetAsync(dprobe, 0, sizeof(Probe), stream));
+    TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
+    TTR_CHECK(qr_try(w.Q, w.qcap, rows, b0));
+    bool phase1_checked = false;
+    int64_t cc = b0;
     while (cc < rbar) {
-      TTR_CHECK(ensure(k, cc + bi));
-      // S = Z W_{k+1}(:, cc:cc+bi)   (Eq. (3.4))
-      Gemm h;
-      h.M = rows; h.N = bi; h.K = cols;
-      h.A = Z; h.sam = cols; h.sak = 1;
-      h.B = s.W[k] + cc; h.sbk = s.ldw; h.sbn = 1;
-      h.C = w.S; h.scm = bi; h.scn = 1;
-      TTR_CHECK(E.sketch(c, h));
-      // S <- S - Q (Q^T S)   (Eq. (3.5))
+      TTR_CHECK(ensure(k, cc + bi, rows, cols));
+      // residual sketch S = (I - Q Q^T) Z W_{k+1}(:, cc:cc+bi)   (Eqs. (3.4)-(3.5))
+      TTR_CHECK(copy2d(c, w.S, bi, Sall + cc, wcap, rows, bi));
       TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.S, bi, bi, w.P));
-      TTR_CUDA(cudaMemsetAsync(dscal, 0, sizeof(double), stream));
-      TTR_CHECK(sumsq(c, w.S, rows, bi, bi, 1, dscal));
-      const double ss = dsync_read(c, dscal, &st);
-      if (st != TTR_OK) return st;
-      const double est = sqrt(ss) / sqrt((double)bi);
+      TTR_CUDA(cudaMemsetAsync(&dprobe->ss, 0, sizeof(double), stream));
+      TTR_CHECK(sumsq(c, w.S, rows, bi, bi, 1, &dprobe->ss));
+      // speculative next block: Q_new = qr(S(:, :bb)), re-orthogonalized against Q, qr again
+      const int64_t bb = std::min(bi, rbar - cc);
+      TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
+      TTR_CHECK(qr_try(w.Q + cc, w.qcap, rows, bb));
+      TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
+      TTR_CHECK(qr_try(w.Q + cc, w.qcap, rows, bb));
+      Probe hp;
+      TTR_CUDA(cudaMemcpyAsync(&hp, dprobe, sizeof(Probe), cudaMemcpyDeviceToHost, stream));
+      TTR_CUDA(cudaStreamSynchronize(stream));
+      if (hp.flag && !phase1_checked) {
+        // the phase-1 factor may be the broken one: redo it robustly, then this iteration
+        TTR_CUDA(cudaMemsetAsync(dprobe, 0, sizeof(Probe), stream));
+        TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
+        TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+        phase1_checked = true;
+        continue;
+      }
+      phase1_checked = true;
+      const double est = sqrt(hp.ss) / sqrt((double)bi);
       if (!isfinite(est)) return set_error("non-finite residual estimate"), TTR_ERR_NONFINITE;
       ests.push_back(est);
       est_core.push_back(k);
-      if (!(est > tau)) break;
-      const int64_t bb = std::min(bi, rbar - cc);
-      // Q_new = qr(S(:, :bb)); re-orthogonalize against Q; qr again; append
-      TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
-      TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
-      TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
-      TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
+      if (!(est > tau)) break;                   // the speculative block is dropped
+      if (hp.flag) {
+        // CholeskyQR broke down on the new block: redo it with the robust fallbacks
+        TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
+        TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
+        TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
+        TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
+      }
+      TTR_CUDA(cudaMemsetAsync(&dprobe->flag, 0, sizeof(int), stream));
       cc += bb;
+    }
+    if (!phase1_checked) {
+      // the loop never ran (b_init already reached rbar): check the phase-1 factorization
+      Probe hp;
+      TTR_CUDA(cudaMemcpyAsync(&hp, dprobe, sizeof(Probe), cudaMemcpyDeviceToHost, stream));
+      TTR_CUDA(cudaStreamSynchronize(stream));
+      if (hp.flag) {
+        TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
+        TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+      }
     }
     double* Ynext = w.Y[cur];
     TTR_CHECK(project_next(c, E, w, Z, rows, cols, cc, X, k, Ynext));
@@ -634,6 +689,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   if (o.adap_r) TTR_CHECK(svd_pass_rl(c, E, out, X.n, tau * o.adap_r_tau_scale, 0));
   tm.rec(2, stream);
   TTR_CUDA(cudaStreamSynchronize(stream));
+  TTR_CHECK(check_device_flags(c));
   out->tau = tau;
   out->nrmx = nrmx;
   out->width = s.width;
@@ -926,7 +982,7 @@ int ttr_sketch_omega(uint64_t seed, int32_t k, int64_t n_k, int64_t col0, int64_
   Ctx c;
   c.stream = (cudaStream_t)stream;
   std::vector<int64_t> nn(k, n_k);
-  int st = omega_fill(c, seed, k, k, nn.data(), col0, col1, dst, 0, col1 - col0);
+  int st = omega_fill(c, seed, k, k, nn.data(), col0, col1, dst, nullptr, 0, col1 - col0);
   if (st == TTR_OK) {
     cudaError_t e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
@@ -955,7 +1011,7 @@ int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r, cons
   TTR_CHECK(rl_pass(c, E, X, seed, col0, col1, t, s));
   cudaError_t e = cudaStreamSynchronize(c.stream);
   if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
-  return TTR_OK;
+  return check_device_flags(c);
 }
 
 }  // extern "C"

@@ -11,7 +11,9 @@ namespace ttr {
 // Tensor-core path (ozaki_tc.cu).  Each returns TTR_ERR_UNSUPPORTED when a shape is outside
 // what the kernel handles; the engine then uses the FP64 kernel for that call.
 int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn,
-               int64_t ldw, const double* Om, int64_t ldom, int64_t w, double* Wout, int64_t ldwo);
+               int64_t ldw, const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo);
+int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int64_t a_cols, const double* Y,
+               int64_t ldy, int64_t b_cols, double* C, int64_t scm, int64_t scn);
 int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
                      int64_t ldb, int64_t N, double* C, int64_t ldc);
 int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn,
@@ -65,9 +67,9 @@ struct Engine {
 
   // W_k = sum_i [V(X_k) W_{k+1}](a, i, :) * Omega_k(i, :)   (Algorithm 3, one step)
   int rl_step(Ctx& c, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
-              const double* Om, int64_t ldom, int64_t w, double* Wout, int64_t ldwo, double* T) const {
+              const double* Om, const int* Omi, int64_t ldom, int64_t w, double* Wout, int64_t ldwo, double* T) const {
     if (precision == TTR_PREC_SLICED) {
-      int st = tc_rl_step(c, slices, Xk, r0, n, r1, Wn, ldw, Om, ldom, w, Wout, ldwo);
+      int st = tc_rl_step(c, slices, Xk, r0, n, r1, Wn, ldw, Omi, ldom, w, Wout, ldwo);
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
     Gemm g;
@@ -93,25 +95,23 @@ struct Engine {
     return gemm_f64(c, g);
   }
 
-  // P = Q(:, :cc)^T S;  S <- S - Q(:, :cc) P     (Eq. (3.5) / block Gram-Schmidt)
+  // P = Q(:, :cc)^T S;  S <- S - Q(:, :cc) P     (Eq. (3.5) / block Gram-Schmidt), FP64
   int project_out(Ctx& c, const double* Q, int64_t ldq, int64_t rows, int64_t cc, double* S, int64_t lds,
                   int64_t bcols, double* P) const {
     if (cc <= 0) return TTR_OK;
-    TTR_CHECK(fill_zero(c, P, cc * bcols));
-    Gemm g;
-    g.M = cc; g.N = bcols; g.K = rows;
-    g.A = Q; g.sam = 1; g.sak = ldq;
-    g.B = S; g.sbk = lds; g.sbn = 1;
-    g.C = P; g.scm = bcols; g.scn = 1;
-    g.split_k = (int)(rows / 256 < 1 ? 1 : (rows / 256 > 64 ? 64 : rows / 256));
-    TTR_CHECK(gemm_f64(c, g));
-    Gemm h;
-    h.M = rows; h.N = bcols; h.K = cc;
-    h.A = Q; h.sam = ldq; h.sak = 1;
-    h.B = P; h.sbk = bcols; h.sbn = 1;
-    h.C = S; h.scm = lds; h.scn = 1;
-    h.alpha = -1.0; h.beta = 1.0;
-    return gemm_f64(c, h);
+    TTR_CHECK(gram_tn(c, Q, ldq, S, lds, rows, cc, bcols, P, bcols));
+    return gemm_nn_small(c, Q, ldq, P, bcols, rows, cc, bcols, S, lds, -1.0, 1.0);
+  }
+
+  // M (ccols x cols, ld cols) = Q(:, :ccols)^T Z   (M_k = Q_k^T V(Y_k))
+  int left_project(Ctx& c, const double* Q, int64_t ldq, const double* Z, int64_t rows, int64_t cols, int64_t ccols,
+                   double* M) const {
+    if (precision == TTR_PREC_SLICED) {
+      // M^T = Z^T Q: big operand Z^T (column-major view), rows split over CTAs
+      int st = tc_gemm_tn(c, slices, Z, cols, rows, cols, Q, ldq, ccols, M, 1, cols);
+      if (st != TTR_ERR_UNSUPPORTED) return st;
+    }
+    return gram_tn(c, Q, ldq, Z, cols, rows, ccols, cols, M, cols);
   }
 
   int transpose(Ctx& c, const double* A, int64_t rows, int64_t cols, double* out) const {

@@ -1,6 +1,6 @@
 // Counter-based Gaussian sketch entries (Sec. 3.1: Omega_k with iid N(0,1) entries).
 //
-// Omega_k(i, j) = round_to_binary32( sqrt(-2 ln u1) * cos(2 pi u2) ), where (u1, u2) are two
+// Omega_k(i, j) = rint(2^20 * sqrt(-2 ln u1) * cos(2 pi u2)) / 2^20, where (u1, u2) are two
 // 53-bit uniforms from one Philox4x32-10 block (Salmon et al., SC'11) with counter
 // (j, i, k, 0) and key (seed mod 2^32, seed div 2^32); u1 in (0, 1], u2 in [0, 1).
 // ln and cos are evaluated here from their series (atanh series after an exact binary
@@ -87,9 +87,15 @@ __device__ __forceinline__ double gaussian_f64(uint64_t seed, uint32_t k, uint32
   return __dmul_rn(rad, series_cos2pi(u2));
 }
 
-// The sketch entry: the Gaussian rounded to binary32.
-__device__ __forceinline__ float omega_entry(uint64_t seed, uint32_t k, uint32_t i, uint32_t j) {
-  return __double2float_rn(gaussian_f64(seed, k, i, j));
+// The sketch entry: the Gaussian rounded (half to even) to the fixed-point grid 2^-20, so that
+// entry * 2^20 is an integer of magnitude below 2^24 (|g| <= sqrt(2*53*ln 2) < 8.6).  The
+// integer is what the tensor-core partial-contraction epilogue multiplies by.
+constexpr double kOmegaScale = 1048576.0;   // 2^20
+__device__ __forceinline__ int32_t omega_int(uint64_t seed, uint32_t k, uint32_t i, uint32_t j) {
+  return (int32_t)rint(__dmul_rn(gaussian_f64(seed, k, i, j), kOmegaScale));
+}
+__device__ __forceinline__ double omega_entry(uint64_t seed, uint32_t k, uint32_t i, uint32_t j) {
+  return (double)omega_int(seed, k, i, j) * (1.0 / kOmegaScale);
 }
 
 }  // namespace ttr

@@ -85,22 +85,97 @@ int gemm_f64(Ctx& c, const Gemm& g) {
   return c.check_launch("gemm_f64");
 }
 
+// ----------------------------------------------------------------------------- tall-skinny products
+// C (a x b, row-major ldc) += X^T Y over rows [0, m): X(r, i) = X[r*ldx + i], Y(r, j) = Y[r*ldy + j].
+// Each CTA takes a block of rows; every thread owns output elements (i, j) and accumulates
+// over the block's rows, then adds its partial sum atomically (C is zeroed by the caller).
+// FP64 work is exactly 2 m a b: no padding of the small dimensions.
+__global__ void __launch_bounds__(256) gram_tn_kernel(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                                                       int64_t m, int64_t a, int64_t b, int64_t rows_per_block,
+                                                       double* C, int64_t ldc) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min(m, r0 + rows_per_block);
+  for (int64_t o = threadIdx.x; o < a * b; o += blockDim.x) {
+    const int64_t i = o / b, j = o % b;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t r = r0;
+    for (; r + 3 < r1; r += 4) {
+      s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
+      s1 = fma(X[(r + 1) * ldx + i], Y[(r + 1) * ldy + j], s1);
+      s2 = fma(X[(r + 2) * ldx + i], Y[(r + 2) * ldy + j], s2);
+      s3 = fma(X[(r + 3) * ldx + i], Y[(r + 3) * ldy + j], s3);
+    }
+    for (; r < r1; ++r) s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
+    atomicAdd(C + i * ldc + j, (s0 + s1) + (s2 + s3));
+  }
+}
+
+int gram_tn(Ctx& c, const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t a, int64_t b,
+            double* C, int64_t ldc) {
+  if (a <= 0 || b <= 0) return TTR_OK;
+  TTR_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, b * sizeof(double), a, c.stream));
+  if (m <= 0) return TTR_OK;
+  // enough row blocks to cover the GPU twice, at least 16 rows each
+  int64_t blocks = std::min<int64_t>(304, std::max<int64_t>(1, m / 16));
+  const int64_t rpb = (m + blocks - 1) / blocks;
+  blocks = (m + rpb - 1) / rpb;
+  gram_tn_kernel<<<(unsigned)blocks, 256, 0, c.stream>>>(X, ldx, Y, ldy, m, a, b, rpb, C, ldc);
+  return c.check_launch("gram_tn");
+}
+
+// C (m x n, ldc) = alpha * X (m x k, ldx) P (k x n, ldp) + beta * C, for small k and n: one
+// thread per output element, P staged in shared memory (k*n <= 4096).
+__global__ void __launch_bounds__(256) gemm_nn_small_kernel(const double* X, int64_t ldx, const double* P, int64_t ldp,
+                                                             int64_t m, int64_t k, int64_t n, double* C, int64_t ldc,
+                                                             double alpha, double beta) {
+  __shared__ double Ps[4096];
+  for (int64_t e = threadIdx.x; e < k * n; e += blockDim.x) Ps[e] = P[(e / n) * ldp + (e % n)];
+  __syncthreads();
+  const int64_t tot = m * n;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < tot; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = o / n, j = o % n;
+    const double* xr = X + r * ldx;
+    double s = 0.0;
+    for (int64_t q = 0; q < k; ++q) s = fma(xr[q], Ps[q * n + j], s);
+    double* cp = C + r * ldc + j;
+    *cp = (beta == 0.0) ? alpha * s : fma(beta, *cp, alpha * s);
+  }
+}
+
+int gemm_nn_small(Ctx& c, const double* X, int64_t ldx, const double* P, int64_t ldp, int64_t m, int64_t k, int64_t n,
+                  double* C, int64_t ldc, double alpha, double beta) {
+  if (m <= 0 || n <= 0) return TTR_OK;
+  if (k * n > 4096) {
+    Gemm g;
+    g.M = m; g.N = n; g.K = k;
+    g.A = X; g.sam = ldx; g.sak = 1;
+    g.B = P; g.sbk = ldp; g.sbn = 1;
+    g.C = C; g.scm = ldc; g.scn = 1;
+    g.alpha = alpha; g.beta = beta;
+    return gemm_f64(c, g);
+  }
+  const int64_t tot = m * n;
+  const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 1216);
+  gemm_nn_small_kernel<<<blocks, 256, 0, c.stream>>>(X, ldx, P, ldp, m, k, n, C, ldc, alpha, beta);
+  return c.check_launch("gemm_nn_small");
+}
+
 // ----------------------------------------------------------------------------- Omega
 __global__ void omega_kernel(uint64_t seed, int32_t k_lo, const int64_t* nk, int64_t col0, int64_t w,
-                             double* dst, int64_t ostride, int64_t ld, int64_t total_per_core) {
+                             double* dst, int* dst_int, int64_t ostride, int64_t ld) {
   const int32_t kk = blockIdx.y;                       // core offset
   const int64_t n = nk[kk];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * w;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / w, j = e % w;
-    const float v = omega_entry(seed, (uint32_t)(k_lo + kk), (uint32_t)i, (uint32_t)(col0 + j));
-    dst[kk * ostride + i * ld + j] = (double)v;
+    const int32_t q = omega_int(seed, (uint32_t)(k_lo + kk), (uint32_t)i, (uint32_t)(col0 + j));
+    dst[kk * ostride + i * ld + j] = (double)q * (1.0 / kOmegaScale);
+    if (dst_int) dst_int[kk * ostride + i * ld + j] = q;
   }
-  (void)total_per_core;
 }
 
 int omega_fill(Ctx& c, uint64_t seed, int32_t k_lo, int32_t k_hi, const int64_t* n_host, int64_t col0,
-               int64_t col1, double* dst, int64_t ostride, int64_t ld) {
+               int64_t col1, double* dst, int* dst_int, int64_t ostride, int64_t ld) {
   const int32_t nc = k_hi - k_lo + 1;
   const int64_t w = col1 - col0;
   if (nc <= 0 || w <= 0) return TTR_OK;
@@ -112,7 +187,7 @@ int omega_fill(Ctx& c, uint64_t seed, int32_t k_lo, int32_t k_hi, const int64_t*
   const int64_t per = nmax * w;
   unsigned bx = (unsigned)((per + 255) / 256);
   if (bx > 1024) bx = 1024;
-  omega_kernel<<<dim3(bx, nc), 256, 0, c.stream>>>(seed, k_lo, nk, col0, w, dst, ostride, ld, per);
+  omega_kernel<<<dim3(bx, nc), 256, 0, c.stream>>>(seed, k_lo, nk, col0, w, dst, dst_int, ostride, ld);
   return c.check_launch("omega_fill");
 }
 
@@ -191,11 +266,18 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(double* G, int64_t b, in
   if (threadIdx.x == 0) fail = 0;
   const double sh = shift ? *shift : 0.0;
   __syncthreads();
+  __shared__ double red[32];
   for (int64_t j = 0; j < b; ++j) {
     // R[j][c] = (G[j][c] + sh*[c==j] - sum_{p<j} R[p][j] R[p][c]) / R[j][j], c >= j
+    double part = 0.0;
+    for (int64_t p = threadIdx.x; p < j; p += blockDim.x) part = fma(G[p * ld + j], G[p * ld + j], part);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double d = G[j * ld + j] + sh;
-      for (int64_t p = 0; p < j; ++p) d -= G[p * ld + j] * G[p * ld + j];
+      double ssum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ssum += red[w];
+      double d = G[j * ld + j] + sh - ssum;
       if (!(d > 0.0) || !isfinite(d)) {
         fail = 1;
         d = 1.0;

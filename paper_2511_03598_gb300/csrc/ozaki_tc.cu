@@ -1,19 +1,563 @@
-// Tensor-core (tcgen05) sliced contractions.  Placeholder until the kernels land: every entry
-// reports TTR_ERR_UNSUPPORTED so the engine uses the FP64 kernels.
+// FP64-accurate contractions on the BF16 tensor cores (tcgen05, sm_103a).
+//
+// GB300 runs FP64 FMA at ~1.2 TFLOP/s but BF16 MMA at ~2 PFLOP/s, so the large contractions of
+// the rounding (the right-to-left partial contractions of Algorithm 3, the sketches
+// S_k = V(Y_k) W_{k+1} and the next-core projections M_k H(X_{k+1})) are computed from
+// fixed-point slices of the FP64 operands, in the manner of the Ozaki splitting scheme
+// (Ozaki, Ogita, Oishi, "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer. Algorithms 2012):
+//
+//  * every row m of A (or, for partial contractions, every mode slab X_k(a, :, :)) gets the
+//    scale 2^(Emax_m - 1022) of its largest entry; each entry becomes a 7*s-bit integer
+//    v = floor(|a| 2^(7s - Emax_m + 1022)) cut into s base-128 digits (sign attached), each
+//    exactly representable in BF16; columns of B get digits the same way;
+//  * digit products a_p b_q with p + q = t are accumulated on the tensor cores into one FP32
+//    TMEM accumulator per "diagonal" t < s.  With |digit| <= 127 and at most 256 K-terms per
+//    accumulation, diagonals t <= 3 stay below 2^24 (exact integers); higher diagonals carry
+//    weights <= 2^-28 relative, so their FP32 rounding is below 2^-52 of the result;
+//  * the epilogue converts the accumulators to integers and forms
+//    V = sum_t acc_t 2^(7(s-1-t)) in 128-bit integer arithmetic, and only then scales to FP64
+//    (or, for partial contractions, weights by the integer sketch entries 2^20*Omega and sums
+//    over the mode index exactly before the single conversion).  No FP64 arithmetic runs per
+//    element, which matters on this FP64-starved part.
+//
+// Truncating the digits and the diagonals at s leaves a relative error of about s*2^(1-7s)
+// of the row/column scales: 8 slices reach FP64 accuracy, 5 slices ~1e-10.
+//
+// Operands are staged by the CTA's threads into shared memory in the canonical K-major,
+// no-swizzle UMMA layout (8x16-byte core matrices; the leading byte offset steps along K,
+// the stride byte offset along M/N), double-buffered across K-chunks of 32; one thread issues
+// the tcgen05.mma instructions and commits them to an mbarrier; accumulators live in TMEM
+// and come back through tcgen05.ld.  All device waits are bounded.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+
 #include "engine.cuh"
 
 namespace ttr {
+namespace tc {
 
-int tc_rl_step(Ctx&, int, const double*, int64_t, int64_t, int64_t, const double*, int64_t, const double*, int64_t,
-               int64_t, double*, int64_t) {
-  return TTR_ERR_UNSUPPORTED;
+constexpr int TM = 128;               // rows per tile = UMMA M
+constexpr int TN = 64;                // columns per tile = UMMA N
+constexpr int KC = 32;                // K per shared-memory chunk (two UMMA K-steps of 16)
+constexpr int KSEG = 256;             // K per CTA: bound for exact FP32 accumulation
+constexpr int MAXS = 8;               // slices per operand
+constexpr int PLANE_A = TM * KC;      // bf16 per A digit plane per chunk (8 KB)
+constexpr int PLANE_B = TN * KC;      // bf16 per B digit plane per chunk (4 KB)
+constexpr int NT = 128;               // threads per CTA (one per TMEM lane in the epilogue)
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+
+enum Mode { PLAIN = 0, ATOMIC = 1, RLM = 2 };
+
+struct Args {
+  const double* A;
+  int64_t M, K, sam, sak;
+  const uint4* Bp;                    // digit planes [nchunk][kchunk][s][PLANE_B]
+  const int* Fmax;                    // biased exponent scale of each B column [nchunks*TN]
+  int64_t N;
+  int kchunks;                        // ceil(K / KC)
+  int s;
+  double* C;
+  int64_t scm, scn;
+  // partial-contraction epilogue
+  const int* Omint;                   // 2^20 * Omega(i, j), [i * ldo + j]
+  int64_t ldo;
+  int64_t nmode;                      // n_k: rows per slab
+  int g;                              // slabs per tile
+  int64_t slabs;                      // r_{k-1}
+  double* W;
+  int64_t ldw;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
-int tc_gemm_rowmajor(Ctx&, int, const double*, int64_t, int64_t, int64_t, const double*, int64_t, int64_t, double*,
-                     int64_t) {
-  return TTR_ERR_UNSUPPORTED;
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  const long long t0 = clock64();
+  uint32_t done = 0;
+  while (true) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
 }
-int tc_project(Ctx&, int, const double*, int64_t, int64_t, int64_t, const double*, int64_t, double*) {
-  return TTR_ERR_UNSUPPORTED;
+
+// s base-128 digits (BF16 bit patterns) of 8 values sharing the biased exponent scale E.
+__device__ __forceinline__ void slice8(const double* v, int E, int s, uint32_t (&w)[MAXS][4]) {
+#pragma unroll
+  for (int p = 0; p < MAXS; ++p)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) w[p][h] = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(v[q]);
+    const uint32_t neg = (uint32_t)(bits >> 63);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
+    const int e = ef ? ef : 1;
+    const int sh = 53 - 7 * s + (E - e);
+    const uint64_t fx = (sh >= 64) ? 0ull : (sh >= 0 ? (mant >> sh) : (mant << (-sh)));
+#pragma unroll
+    for (int p = 0; p < MAXS; ++p) {
+      if (p < s) {
+        const uint32_t dg = (uint32_t)(fx >> (7 * (s - 1 - p))) & 127u;
+        const float f = __uint_as_float(0x4B000000u | dg) - 8388608.0f;   // exact: dg < 2^23
+        const uint32_t b16 = (__float_as_uint(f) >> 16) | (neg << 15);
+        w[p][q >> 1] |= b16 << (16 * (q & 1));
+      }
+    }
+  }
+}
+
+// V * 2^X as a double (round to nearest even; underflow to zero).
+__device__ __forceinline__ double i128_to_double(__int128 V, int X) {
+  if (V == 0) return 0.0;
+  const uint64_t sign = V < 0 ? (1ull << 63) : 0ull;
+  unsigned __int128 u = V < 0 ? (unsigned __int128)(-V) : (unsigned __int128)V;
+  const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  u <<= lz;                                                  // top bit at position 127
+  uint64_t mant = (uint64_t)(u >> 75);                       // 53 bits
+  const unsigned __int128 rest = u & (((unsigned __int128)1 << 75) - 1);
+  const unsigned __int128 half = (unsigned __int128)1 << 74;
+  int e = 127 - lz + X;                                      // value = mant/2^52 * 2^e
+  if (rest > half || (rest == half && (mant & 1ull))) {
+    ++mant;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  const int field = e + 1023;
+  if (field <= 0) return __longlong_as_double((long long)sign);
+  if (field >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((uint64_t)field << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)(((uint64_t)__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+template <int MODE, bool AKFAST>
+__global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int rowE[TM];
+  __shared__ int slabE[TM];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s = a.s;
+  const int nc = blockIdx.y;
+  const int64_t kseg0 = (int64_t)blockIdx.z * KSEG;
+  const int kseg_len = (int)(a.K - kseg0 < (int64_t)KSEG ? a.K - kseg0 : (int64_t)KSEG);
+  const int nchunk = (kseg_len + KC - 1) / KC;
+  const int kc0 = (int)(kseg0 / KC);
+  // rows of this tile
+  int64_t m0;
+  int rows;
+  if (MODE == RLM) {
+    const int64_t a0 = (int64_t)blockIdx.x * a.g;
+    const int64_t na = (a.slabs - a0 < (int64_t)a.g) ? a.slabs - a0 : (int64_t)a.g;
+    m0 = a0 * a.nmode;
+    rows = (int)(na * a.nmode);
+  } else {
+    m0 = (int64_t)blockIdx.x * TM;
+    rows = (int)(a.M - m0 < (int64_t)TM ? a.M - m0 : (int64_t)TM);
+  }
+  const uint32_t tcols = (s <= 4) ? 256u : 512u;
+  const size_t buf_bytes = (size_t)s * (PLANE_A + PLANE_B) * 2;
+  unsigned char* bufs[2] = {smem, smem + buf_bytes};
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (tid < TM) slabE[tid] = 1;
+
+  // ---- pass 1: exponent scale of every row over this K segment (many loads in flight)
+  if (AKFAST) {
+    int em[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) em[r] = 1;
+    for (int k = lane; k < kseg_len; k += 32) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const int row = warp * 32 + r;
+        if (row < rows) em[r] = max(em[r], exp_field(__ldg(a.A + (m0 + row) * a.sam + kseg0 + k)));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int e = __reduce_max_sync(0xffffffffu, em[r]);
+      if (lane == 0) rowE[warp * 32 + r] = e;
+    }
+  } else {
+    int e0 = 1, e1 = 1, e2 = 1, e3 = 1;
+    if (tid < rows) {
+      const double* colp = a.A + (m0 + tid) * a.sam + kseg0 * a.sak;
+      int k = 0;
+      for (; k + 3 < kseg_len; k += 4) {
+        e0 = max(e0, exp_field(__ldg(colp + (int64_t)k * a.sak)));
+        e1 = max(e1, exp_field(__ldg(colp + (int64_t)(k + 1) * a.sak)));
+        e2 = max(e2, exp_field(__ldg(colp + (int64_t)(k + 2) * a.sak)));
+        e3 = max(e3, exp_field(__ldg(colp + (int64_t)(k + 3) * a.sak)));
+      }
+      for (; k < kseg_len; ++k) e0 = max(e0, exp_field(__ldg(colp + (int64_t)k * a.sak)));
+    }
+    rowE[tid] = max(max(e0, e1), max(e2, e3));
+  }
+  __syncthreads();
+  if (MODE == RLM) {
+    if (tid < rows) atomicMax(&slabE[tid / a.nmode], rowE[tid]);
+    __syncthreads();
+    if (tid < rows) rowE[tid] = slabE[tid / a.nmode];
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  bool ok = true;
+
+  // ---- K loop over chunks of 32, double buffered
+  for (int c = 0; c < nchunk && ok; ++c) {
+    const int b = c & 1;
+    if (c >= 2) ok = mbar_wait(smem_u32(&mbar[b]), (uint32_t)(((c - 2) >> 1) & 1), a.err);
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    uint16_t* Ap = (uint16_t*)bufs[b];
+    uint16_t* Bpl = Ap + (size_t)s * PLANE_A;
+    // A digits: 128 rows x 4 groups of 8 consecutive k; all 32 loads of a thread issued first
+    {
+      double v[4][8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = AKFAST ? ((tid + NT * i) >> 2) : tid;
+        const int grp = AKFAST ? ((tid + NT * i) & 3) : i;
+        const int kl = c * KC + grp * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int kk = kl + q;
+          v[i][q] = (row < rows && kk < kseg_len) ? __ldg(a.A + (m0 + row) * a.sam + (kseg0 + kk) * a.sak) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = AKFAST ? ((tid + NT * i) >> 2) : tid;
+        const int grp = AKFAST ? ((tid + NT * i) & 3) : i;
+        uint32_t w[MAXS][4];
+        slice8(v[i], rowE[row], s, w);
+        const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
+#pragma unroll
+        for (int p = 0; p < MAXS; ++p)
+          if (p < s)
+            *reinterpret_cast<uint4*>(Ap + (size_t)p * PLANE_A + idx) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      }
+    }
+    // B digit planes of this chunk: a straight copy of s * 4 KB
+    {
+      const uint4* src = a.Bp + ((size_t)nc * a.kchunks + (kc0 + c)) * (size_t)s * (PLANE_B / 8);
+      uint4* dst = reinterpret_cast<uint4*>(Bpl);
+#pragma unroll 4
+      for (int e = tid; e < s * (PLANE_B / 8); e += NT) dst[e] = __ldg(src + e);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      const uint32_t abase = smem_u32(Ap), bbase = smem_u32(Bpl);
+#pragma unroll 1
+      for (int ks = 0; ks < KC / 16; ++ks) {
+#pragma unroll 1
+        for (int t = 0; t < s; ++t) {
+#pragma unroll 1
+          for (int p = 0; p <= t; ++p) {
+            const int q = t - p;
+            const uint64_t da = umma_desc(abase + p * PLANE_A * 2 + ks * 2 * (TM / 8) * 128, (TM / 8) * 128, 128);
+            const uint64_t db = umma_desc(bbase + q * PLANE_B * 2 + ks * 2 * (TN / 8) * 128, (TN / 8) * 128, 128);
+            const uint32_t accum = (c == 0 && ks == 0 && p == 0) ? 0u : 1u;
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(t * TN)),
+                         "l"(da), "l"(db), "r"(idesc), "r"(accum));
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar[b])));
+    }
+  }
+  if (ok && nchunk > 0) {
+    const int c = nchunk - 1;
+    ok = mbar_wait(smem_u32(&mbar[c & 1]), (uint32_t)((c >> 1) & 1), a.err);
+  }
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+
+  // ---- epilogue: 16 columns at a time
+  if (ok && nchunk > 0) {
+    __int128* P = reinterpret_cast<__int128*>(smem);           // [TM][16] for the slab sums
+    const int row = tid;
+    for (int cg = 0; cg < TN / 16; ++cg) {
+      __int128 V[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) V[j] = 0;
+#pragma unroll 1
+      for (int t = 0; t < s; ++t) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * TN + cg * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int shift = 7 * (s - 1 - t);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) V[j] += (__int128)__float2ll_rn(__uint_as_float(r[j])) << shift;
+      }
+      const int64_t n0 = (int64_t)nc * TN + cg * 16;
+      if (MODE != RLM) {
+        if (row < rows) {
+          const int e_row = rowE[row];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t n = n0 + j;
+            if (n < a.N) {
+              const double out = i128_to_double(V[j], e_row + a.Fmax[n] - 2044 - 7 * s - 7);
+              double* cp = a.C + (m0 + row) * a.scm + n * a.scn;
+              if (MODE == ATOMIC) atomicAdd(cp, out);
+              else *cp = out;
+            }
+          }
+        }
+      } else {
+        // weight by 2^20*Omega(i, n) and sum over i inside each slab, exactly
+        const int i = row % (int)a.nmode;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t n = n0 + j;
+          const int om = (row < rows && n < a.N) ? a.Omint[i * a.ldo + n] : 0;
+          P[row * 16 + j] = V[j] * (__int128)om;
+        }
+        __syncthreads();
+        const int nslab = rows / (int)a.nmode;
+        for (int task = tid; task < nslab * 16; task += NT) {
+          const int sl = task >> 4, j = task & 15;
+          const int64_t n = n0 + j;
+          if (n >= a.N) continue;
+          __int128 acc = 0;
+          for (int ii = 0; ii < (int)a.nmode; ++ii) acc += P[(sl * (int)a.nmode + ii) * 16 + j];
+          const int e_slab = rowE[sl * (int)a.nmode];
+          const int64_t aidx = (int64_t)blockIdx.x * a.g + sl;
+          a.W[aidx * a.ldw + n] = i128_to_double(acc, e_slab + a.Fmax[n] - 2044 - 7 * s - 7 - 20);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+}
+
+// ---- B operand preparation: column exponent scales, then digit planes in the shared-memory
+// image.  B(k, n) = B[k*sbk + n*sbn], K x N.
+__global__ void __launch_bounds__(256) colmax_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
+                                                       int* Fmax) {
+  // grid (N-chunks, K-splits); Fmax pre-set to 1
+  const int nc = blockIdx.x, tid = threadIdx.x;
+  const int j = tid % TN, ph = tid / TN, nph = blockDim.x / TN;
+  const int64_t n = (int64_t)nc * TN + j;
+  const int64_t kb = (int64_t)blockIdx.y * 1024, ke = min(K, kb + 1024);
+  int e = 1;
+  if (n < N) {
+#pragma unroll 8
+    for (int64_t k = kb + ph; k < ke; k += nph) e = max(e, exp_field(B[k * sbk + n * sbn]));
+  }
+  atomicMax(&Fmax[nc * TN + j], e);
+}
+
+// One CTA per (64-column chunk, 32-row K chunk): 256 tasks (column, group of 8 k).
+__global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
+                                                      int s, int kchunks, const int* Fmax, uint4* planes) {
+  const int nc = blockIdx.x, kcn = blockIdx.y, u = threadIdx.x;
+  const int j = u % TN, grp = u / TN;
+  const int64_t n = (int64_t)nc * TN + j;
+  double v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t k = (int64_t)kcn * KC + grp * 8 + q;
+    v[q] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0;
+  }
+  uint32_t w[MAXS][4];
+  slice8(v, Fmax[nc * TN + j], s, w);
+  uint4* blk = planes + ((size_t)nc * kchunks + kcn) * (size_t)s * (PLANE_B / 8);
+  const int idx = ((grp * (TN / 8)) + (j >> 3)) * 8 + (j & 7);        // uint4 index in a plane
+  for (int p = 0; p < s; ++p) blk[(size_t)p * (PLANE_B / 8) + idx] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+
+__global__ void fill_int_kernel(int* p, int64_t n, int v) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) p[e] = v;
+}
+
+static size_t smem_bytes(int s) {
+  size_t need = 2 * (size_t)s * (PLANE_A + PLANE_B) * 2;
+  const size_t epi = (size_t)TM * 16 * sizeof(__int128);
+  need = std::max(need, epi);
+  if (s <= 4) need = std::max<size_t>(need, 100 * 1024);   // at most 2 CTAs per SM: 2 x 256 TMEM columns
+  return need + 1024;
+}
+
+template <int MODE, bool AKFAST>
+static int launch(Ctx& c, const Args& a, dim3 grid) {
+  const size_t sm = smem_bytes(a.s);
+  auto kern = sliced_kernel<MODE, AKFAST>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
+  kern<<<grid, NT, sm, c.stream>>>(a);
+  return c.check_launch("sliced_kernel");
+}
+
+struct BPrep {
+  uint4* planes = nullptr;
+  int* Fmax = nullptr;
+  int nchunks = 0, kchunks = 0;
+};
+
+static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int s, BPrep& p) {
+  p.nchunks = (int)((N + TN - 1) / TN);
+  p.kchunks = (int)((K + KC - 1) / KC);
+  TTR_CHECK(c.alloc(reinterpret_cast<void**>(&p.planes), (size_t)p.nchunks * p.kchunks * s * PLANE_B * 2));
+  TTR_CHECK(c.alloc_t(&p.Fmax, (size_t)p.nchunks * TN));
+  fill_int_kernel<<<1, 256, 0, c.stream>>>(p.Fmax, (int64_t)p.nchunks * TN, 1);
+  TTR_CHECK(c.check_launch("fill_int"));
+  colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)((K + 1023) / 1024)), 256, 0, c.stream>>>(B, sbk, sbn, K, N,
+                                                                                                  p.Fmax);
+  TTR_CHECK(c.check_launch("colmax_b"));
+  slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, s, p.kchunks,
+                                                                                     p.Fmax, p.planes);
+  return c.check_launch("slice_b");
+}
+
+static int ensure_err(Ctx& c) {
+  if (!c.d_flags) {
+    TTR_CHECK(c.alloc_t(&c.d_flags, 4));
+    TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
+  }
+  return TTR_OK;
+}
+
+// Zero the a x b region C(i, j) = C[i*scm + j*scn] where one of the strides is 1.
+static int zero_region(Ctx& c, double* C, int64_t a, int64_t b, int64_t scm, int64_t scn) {
+  if (scn == 1) {
+    TTR_CUDA(cudaMemset2DAsync(C, scm * sizeof(double), 0, b * sizeof(double), a, c.stream));
+  } else {
+    TTR_CUDA(cudaMemset2DAsync(C, scn * sizeof(double), 0, a * sizeof(double), b, c.stream));
+  }
+  return TTR_OK;
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+// C(i, j) = sum_r X(r, i) Y(r, j) (i < a, j < b) stored at C[i*scm + j*scn]; X, Y row-major m x a, m x b.
+// The big operand X^T is read column-major; the row dimension m is split over CTAs in segments
+// of 256 and partial results are added atomically.
+int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int64_t a_cols, const double* Y, int64_t ldy,
+               int64_t b_cols, double* C, int64_t scm, int64_t scn) {
+  if (slices < 3 || slices > MAXS || m <= 0 || a_cols <= 0 || b_cols <= 0) return TTR_ERR_UNSUPPORTED;
+  if (scm != 1 && scn != 1) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b(c, Y, ldy, 1, m, b_cols, slices, bp));
+  Args a{};
+  a.A = X; a.M = a_cols; a.K = m; a.sam = 1; a.sak = ldx;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = b_cols; a.kchunks = bp.kchunks; a.s = slices;
+  a.C = C; a.scm = scm; a.scn = scn; a.err = c.d_flags;
+  const unsigned ksplit = (unsigned)((m + KSEG - 1) / KSEG);
+  dim3 grid((unsigned)((a_cols + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
+  if (ksplit > 1) {
+    TTR_CHECK(zero_region(c, C, a_cols, b_cols, scm, scn));
+    return launch<ATOMIC, false>(c, a, grid);
+  }
+  return launch<PLAIN, false>(c, a, grid);
+}
+
+int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
+               const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo) {
+  if (n > TM || r1 > KSEG || slices < 3 || slices > MAXS || !Omi) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b(c, Wn, ldw, 1, r1, w, slices, bp));
+  Args a{};
+  a.A = Xk; a.M = r0 * n; a.K = r1; a.sam = r1; a.sak = 1;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = w; a.kchunks = bp.kchunks; a.s = slices;
+  a.Omint = Omi; a.ldo = ldoi; a.nmode = n; a.g = (int)(TM / n); a.slabs = r0; a.W = Wout; a.ldw = ldwo;
+  a.err = c.d_flags;
+  dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, 1);
+  return launch<RLM, true>(c, a, grid);
+}
+
+int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
+                     int64_t ldb, int64_t N, double* C, int64_t ldc) {
+  if (slices < 3 || slices > MAXS || M <= 0 || N <= 0 || K <= 0) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b(c, B, ldb, 1, K, N, slices, bp));
+  Args a{};
+  a.A = A; a.M = M; a.K = K; a.sam = lda; a.sak = 1;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = N; a.kchunks = bp.kchunks; a.s = slices;
+  a.C = C; a.scm = ldc; a.scn = 1; a.err = c.d_flags;
+  const unsigned ksplit = (unsigned)((K + KSEG - 1) / KSEG);
+  dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
+  if (ksplit > 1) {
+    TTR_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, N * sizeof(double), M, c.stream));
+    return launch<ATOMIC, true>(c, a, grid);
+  }
+  return launch<PLAIN, true>(c, a, grid);
+}
+
+// Y = Mk (L x K, row-major ldm) @ H(X_{k+1}) (K x ncol, row-major), computed as
+// Y^T = H(X_{k+1})^T Mk^T so that the big operand is the M side (column-major).
+int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn, int64_t ncol,
+               double* Y) {
+  if (slices < 3 || slices > MAXS || L <= 0 || ncol <= 0 || K <= 0) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b(c, Mk, 1, ldm, K, L, slices, bp));
+  Args a{};
+  a.A = Xn; a.M = ncol; a.K = K; a.sam = 1; a.sak = ncol;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = L; a.kchunks = bp.kchunks; a.s = slices;
+  a.C = Y; a.scm = 1; a.scn = ncol; a.err = c.d_flags;
+  const unsigned ksplit = (unsigned)((K + KSEG - 1) / KSEG);
+  dim3 grid((unsigned)((ncol + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
+  if (ksplit > 1) {
+    TTR_CUDA(cudaMemsetAsync(Y, 0, (size_t)L * ncol * sizeof(double), c.stream));
+    return launch<ATOMIC, false>(c, a, grid);
+  }
+  return launch<PLAIN, false>(c, a, grid);
 }
 
 }  // namespace ttr

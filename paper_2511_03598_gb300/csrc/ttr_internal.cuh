@@ -65,10 +65,18 @@ struct Gemm {
 };
 int gemm_f64(Ctx& c, const Gemm& g);
 
+// C (a x b) = X^T Y over m rows (row-major operands; FP64; C zeroed here).
+int gram_tn(Ctx& c, const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t a, int64_t b,
+            double* C, int64_t ldc);
+// C = alpha X P + beta C with X m x k, P k x n (small k, n), row-major.
+int gemm_nn_small(Ctx& c, const double* X, int64_t ldx, const double* P, int64_t ldp, int64_t m, int64_t k, int64_t n,
+                  double* C, int64_t ldc, double alpha, double beta);
+
 // Omega_k(:, col0:col1) for cores k = k_lo..k_hi (1-based); block k goes to
 // dst + (k - k_lo) * ostride as row-major [i][j - col0] with leading dimension ld.
+// dst_int (optional) receives 2^20 * Omega as integers in the same layout.
 int omega_fill(Ctx& c, uint64_t seed, int32_t k_lo, int32_t k_hi, const int64_t* n_host,
-               int64_t col0, int64_t col1, double* dst, int64_t ostride, int64_t ld);
+               int64_t col0, int64_t col1, double* dst, int* dst_int, int64_t ostride, int64_t ld);
 
 // W_k(a, j) = sum_i T(a*n + i, j) * Omega(i, j) for a < r0, j < w  (Algorithm 3 epilogue)
 int omega_reduce(Ctx& c, const double* T, int64_t ldt, const double* Om, int64_t ldo, int64_t r0,

@@ -130,13 +130,13 @@ def test_adaptive_norm_estimate(B):
 def test_adaptive_width_hint_does_not_change_result(B):
     x = WL.c1()
     outs = []
-    for hint in (0, 9, 40):
+    for hint in (2, 9, 40):          # width 2 forces Algorithm 5 to append columns repeatedly
         with B.round_adaptive(dev(x.cores), 1e-7, 2, 3, B.options(nrmx=x.norm, width_hint=hint)) as y:
             outs.append((y.ranks, y.to_numpy(), y.info["extensions"]))
     for ranks, cores, _ in outs[1:]:
         assert ranks == outs[0][0]
         assert rel_tensor_diff(cores, outs[0][1]) <= 1e-12
-    assert outs[2][2] < outs[0][2]
+    assert outs[2][2] < outs[0][2] and outs[0][2] > 0
 
 
 def test_adaptive_adap_r(B):
