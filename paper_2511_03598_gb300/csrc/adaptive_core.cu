@@ -1,0 +1,421 @@
+// The adaptive block loop of one core (Algorithm 6 with Algorithm 5's residual sketch) as one
+// persistent cooperative kernel.
+//
+// Given the sketch S_all = V(Y_k) W_{k+1}(:, 0:width) (computed on the tensor cores), the loop
+//   Q = qr(S_all(:, 0:b_init))
+//   repeat: S = S_all(:, c:c+b_inc) - Q (Q^T S_all(:, c:c+b_inc))          (Eqs. (3.4)-(3.5))
+//           est = ||S||_F / sqrt(b_inc); stop if est <= tau or c = rbar
+//           Q_new = qr(S(:, 1:bb)); Q_new = qr(Q_new - Q (Q^T Q_new)); Q = [Q, Q_new]
+// is a chain of small dependent FP64 steps.  On GB300 FP64 runs at ~1.2 TFLOP/s, so every step is
+// spread over all SMs (each CTA owns a block of rows) and the steps are separated by a grid
+// barrier instead of kernel launches; the stopping decision is taken on the device, and the
+// host synchronizes once per core.
+//
+// Reductions over rows (Gram matrices, Q^T S) go through per-CTA partials: small ones (b x b) are
+// summed redundantly by every CTA (no second barrier); larger ones (c x b) are summed in slices,
+// one slice per CTA, then read back by all.  CholeskyQR2 needs one barrier per pass.
+//
+// The grid barrier is a counter/generation pair with a bounded spin: a wait that runs out sets
+// the error flag and the kernel returns (the host reports TTR_ERR_TIMEOUT).
+#include <math.h>
+#include <stdint.h>
+
+#include "engine.cuh"
+
+namespace ttr {
+namespace ac {
+
+constexpr int NT = 256;
+constexpr int BMAX = 32;                          // largest block handled here
+constexpr long long BAR_CYCLES = 4000000000LL;   // ~2 s
+
+enum Status { ST_DONE = 0, ST_EXTEND = 1, ST_BREAKDOWN = 2, ST_TIMEOUT = 3 };
+
+struct Args {
+  const double* Sall;   // m x width sketch, leading dimension lds
+  int64_t lds;
+  double* Q;            // m x qcap basis, leading dimension ldq
+  int64_t ldq;
+  double* S;            // m x bi work (leading dimension bi)
+  double* acc;          // 3 x ACC accumulation buffers (zero on entry)
+  int acc_used;         // entries any reduction touches
+  int64_t m;
+  int64_t qcols;        // columns of Q kept per row in shared memory (>= rbar)
+  int rpc;              // rows per CTA
+  int b0, bi, rbar, width;
+  int cc0;              // columns of Q already final on entry (0: phase 1 still to do)
+  double tau;
+  unsigned* bar;        // [0] arrival counter, [1] generation
+  int* err;
+  // outputs
+  double* est_out;      // estimates in order
+  int* io;              // [0] status, [1] cc, [2] number of estimates
+};
+
+constexpr int ACC = 8192;                         // doubles per accumulation buffer (>= rbar * BMAX)
+
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
+  __syncthreads();
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    ok_s = 1;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > BAR_CYCLES) {
+          atomicExch(err, 1);
+          ok_s = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__device__ __forceinline__ void my_rows(int64_t m, int64_t& lo, int64_t& hi) {
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  lo = min(m, (int64_t)blockIdx.x * per);
+  hi = min(m, lo + per);
+}
+
+// Cross-CTA sums go through three rotating accumulation buffers in global memory: for reduction i
+// every CTA adds its partial sums into buffer i%3 with FP64 atomics, passes the grid barrier and
+// reads the totals (through L2).  Right after barrier i, CTA 0 zeroes buffer (i+2)%3: its last
+// readers (reduction i-1) finished before barrier i, and its next writers (reduction i+2) start
+// only after barrier i+1.  The totals are the same in every CTA, so all CTAs take the same branch.
+struct Red {
+  double* base;     // 3 x ACC doubles, zero on entry
+  int i;            // index of the next reduction
+  int used;         // entries to clear per buffer
+};
+
+__device__ __forceinline__ double* red_buf(const Red& r) { return r.base + (int64_t)(r.i % 3) * ACC; }
+
+// after the barrier of the current reduction: clear the buffer two reductions ahead, advance
+__device__ __forceinline__ void red_advance(Red& r) {
+  if (blockIdx.x == 0) {
+    double* z = r.base + (int64_t)((r.i + 2) % 3) * ACC;
+    for (int o = threadIdx.x; o < r.used; o += NT) z[o] = 0.0;
+  }
+  r.i++;
+}
+
+// Each CTA keeps its own rows resident in shared memory:
+//   Qs  [nr][ldq]  rows of Q,    Ss [nr][ldw] rows of the sketch S_all,   Rs [nr][bi] residual block.
+// buf[i*b + j] += sum_{own rows} X(r, i) Y(r, j), i < a, j < b   (X, Y in shared memory)
+__device__ void gram_acc(const double* X, int ldx, const double* Y, int ldy, int a, int b, int nr, double* buf) {
+  for (int o = threadIdx.x; o < a * b; o += NT) {
+    const int i = o / b, j = o % b;
+    double s0 = 0.0, s1 = 0.0;
+    int r = 0;
+    for (; r + 1 < nr; r += 2) {
+      s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
+      s1 = fma(X[(r + 1) * ldx + i], Y[(r + 1) * ldy + j], s1);
+    }
+    if (r < nr) s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
+    if (nr > 0) atomicAdd(buf + o, s0 + s1);
+  }
+}
+
+// buf[0] += sum of squares of the own rows of X (b columns, shared memory)
+__device__ void sumsq_acc(const double* X, int ldx, int b, int nr, double* buf) {
+  __shared__ double red[NT / 32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < nr * b; e += NT) {
+    const double v = X[(e / b) * ldx + e % b];
+    s = fma(v, v, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
+    atomicAdd(buf, t);
+  }
+  __syncthreads();
+}
+
+// shared-memory copy of the first n totals of buf (written by other CTAs: read through L2)
+__device__ void read_totals(const double* buf, int n, double* dst) {
+  for (int o = threadIdx.x; o < n; o += NT) dst[o] = __ldcg(buf + o);
+  __syncthreads();
+}
+
+// In shared memory: G (b x b) -> upper R (G = R^T R) and 1/diag(R), by warp 0 (lane = column).
+// Every CTA computes the same factor from the same data, so all take the same branch.
+__device__ bool chol_small(double* G, int b, double* invd, double* Ri) {
+  __shared__ int fail;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int bad = 0;
+    for (int j = 0; j < b; ++j) {
+      double v = (lane >= j && lane < b) ? G[j * b + lane] : 0.0;
+      for (int p = 0; p < j; ++p) v -= G[p * b + j] * ((lane < b) ? G[p * b + lane] : 0.0);
+      const double dj = __shfl_sync(0xffffffffu, v, j);
+      const double dd = (dj > 0.0 && isfinite(dj)) ? dj : 1.0;
+      bad |= !(dj > 0.0 && isfinite(dj));
+      // 1/sqrt(dd): binary32 seed (~23 bits) and two Newton steps r <- r (3 - dd r^2) / 2 in FP64
+      // (quadratic convergence: ~46, then ~92 bits), instead of FP64 sqrt and divide, which are
+      // long dependent instruction sequences on this part.
+      // (dd is first split as mnt * 2^e with e even and mnt in [0.5, 2), so the binary32 seed never
+      // under- or overflows whatever the scale of the input)
+      int ex = 0;
+      double mnt = frexp(dd, &ex);
+      if (ex & 1) {
+        mnt *= 2.0;
+        ex -= 1;
+      }
+      double inv = (double)rsqrtf((float)mnt);
+      inv = inv * fma(-0.5 * mnt, inv * inv, 1.5);
+      inv = inv * fma(-0.5 * mnt, inv * inv, 1.5);
+      inv = ldexp(inv, -ex / 2);
+      const double piv = dd * inv;
+      if (lane == j) {
+        G[j * b + j] = piv;
+        invd[j] = inv;
+      } else if (lane > j && lane < b) {
+        G[j * b + lane] = v * inv;
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+    // R^{-1} (upper) by back substitution, lane j computes column j:
+    //   Ri[j][j] = 1/R_jj;  Ri[i][j] = -(sum_{p=i+1..j} R[i][p] Ri[p][j]) / R_ii for i < j
+    if (lane < b) {
+      const int j = lane;
+      for (int i = 0; i < b; ++i) Ri[i * b + j] = 0.0;
+      Ri[j * b + j] = invd[j];
+      for (int i = j - 1; i >= 0; --i) {
+        double v = 0.0;
+        for (int p2 = i + 1; p2 <= j; ++p2) v = fma(G[i * b + p2], Ri[p2 * b + j], v);
+        Ri[i * b + j] = -v * invd[i];
+      }
+    }
+    if (lane == 0) fail = bad;
+  }
+  __syncthreads();
+  return fail == 0;
+}
+
+// own rows of X (b columns, shared memory) <- X R^{-1}, one thread per (row, column):
+// out(r, j) = sum_{i <= j} X(r, i) Ri(i, j), staged through T and written back after a barrier.
+__device__ void apply_rinv(double* X, int ldx, int b, const double* Ri, int nr, double* T) {
+  for (int e = threadIdx.x; e < nr * b; e += NT) {
+    const int r = e / b, j = e % b;
+    const double* xr = X + r * ldx;
+    double v = 0.0;
+    for (int i = 0; i <= j; ++i) v = fma(xr[i], Ri[i * b + j], v);
+    T[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * b; e += NT) X[(e / b) * ldx + e % b] = T[e];
+  __syncthreads();
+}
+
+// CholeskyQR of the own rows of X (shared memory, b columns), npass passes, one barrier each.
+// If pre_gram is given, the first pass's Gram matrix is already summed there (its barrier and
+// buffer rotation have been done by the caller).
+__device__ bool cholqr(double* X, int ldx, int b, int nr, int npass, Red& rd, unsigned* bar, int* err, bool* timeout,
+                       double* T, const double* pre_gram = nullptr) {
+  __shared__ double G[BMAX * BMAX];
+  __shared__ double Ri[BMAX * BMAX];
+  __shared__ double invd[BMAX];
+  for (int pass = 0; pass < npass; ++pass) {
+    if (pass == 0 && pre_gram) {
+      read_totals(pre_gram, b * b, G);
+    } else {
+      double* buf = red_buf(rd);
+      gram_acc(X, ldx, X, ldx, b, b, nr, buf);
+      if (!grid_sync(bar, err)) {
+        *timeout = true;
+        return false;
+      }
+      red_advance(rd);
+      read_totals(buf, b * b, G);
+    }
+    if (!chol_small(G, b, invd, Ri)) return false;
+    apply_rinv(X, ldx, b, Ri, nr, T);
+  }
+  return true;
+}
+
+// own rows: X(:, 0:b) -= Q(:, 0:c) P with P = Q(:, 0:c)^T X(:, 0:b) summed over all rows.
+__device__ bool project_out(const double* Q, int ldq, int c, double* X, int ldx, int b, int nr, Red& rd,
+                            unsigned* bar, int* err) {
+  if (c <= 0) return true;
+  double* buf = red_buf(rd);
+  gram_acc(Q, ldq, X, ldx, c, b, nr, buf);
+  if (!grid_sync(bar, err)) return false;
+  red_advance(rd);
+  __shared__ double Ps[ACC / 4];
+  const bool in_smem = c * b <= ACC / 4;
+  if (in_smem) read_totals(buf, c * b, Ps);
+  for (int e = threadIdx.x; e < nr * b; e += NT) {
+    const int r = e / b, j = e % b;
+    const double* qr = Q + r * ldq;
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    if (in_smem) {
+      for (; i + 1 < c; i += 2) {
+        s0 = fma(qr[i], Ps[i * b + j], s0);
+        s1 = fma(qr[i + 1], Ps[(i + 1) * b + j], s1);
+      }
+      if (i < c) s0 = fma(qr[i], Ps[i * b + j], s0);
+    } else {
+      for (; i < c; ++i) s0 = fma(qr[i], __ldcg(buf + i * b + j), s0);
+    }
+    X[r * ldx + j] -= s0 + s1;
+  }
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
+  extern __shared__ __align__(16) double sm[];
+  int64_t lo, hi;
+  my_rows(a.m, lo, hi);
+  const int nr = (int)(hi - lo);
+  const int ldq = (int)a.qcols, ldw = a.width;
+  double* Qs = sm;                                   // [rpc][ldq]
+  double* Ss = Qs + (size_t)a.rpc * ldq;             // [rpc][ldw]
+  double* Rs = Ss + (size_t)a.rpc * ldw;             // [rpc][bi]
+  double* Tb = Rs + (size_t)a.rpc * a.bi;            // [rpc][BMAX] staging for X R^{-1}
+  bool timeout = false;
+  int cc = a.cc0;
+  int nest = 0;
+  Red rd{a.acc, 0, a.acc_used};
+  // stage the own rows: sketch columns, and the part of Q that is already final
+  for (int e = threadIdx.x; e < nr * ldw; e += NT) Ss[e] = a.Sall[(lo + e / ldw) * a.lds + e % ldw];
+  for (int e = threadIdx.x; e < nr * cc; e += NT) Qs[(e / cc) * ldq + e % cc] = a.Q[(lo + e / cc) * a.ldq + e % cc];
+  __syncthreads();
+  auto finish = [&](int status) {
+    // write back Q(:, 0:cc) (plus the residual block, which the host needs after a breakdown)
+    for (int e = threadIdx.x; e < nr * cc; e += NT) a.Q[(lo + e / cc) * a.ldq + e % cc] = Qs[(e / cc) * ldq + e % cc];
+    for (int e = threadIdx.x; e < nr * a.bi; e += NT) a.S[(lo + e / a.bi) * a.bi + e % a.bi] = Rs[e];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.io[0] = timeout ? ST_TIMEOUT : status;
+      a.io[1] = cc;
+      a.io[2] = nest;
+    }
+  };
+  if (cc == 0) {
+    // phase 1: Q(:, 0:b0) = qr(S_all(:, 0:b0))
+    for (int e = threadIdx.x; e < nr * a.b0; e += NT) Qs[(e / a.b0) * ldq + e % a.b0] = Ss[(e / a.b0) * ldw + e % a.b0];
+    __syncthreads();
+    if (!cholqr(Qs, ldq, a.b0, nr, 2, rd, a.bar, a.err, &timeout, Tb)) return finish(ST_BREAKDOWN);
+    cc = a.b0;
+  }
+  __shared__ double est_s;
+  while (cc < a.rbar) {
+    if (cc + a.bi > a.width) return finish(ST_EXTEND);
+    // residual sketch of the next block (Eqs. (3.4)-(3.5)) and its norm
+    for (int e = threadIdx.x; e < nr * a.bi; e += NT) Rs[e] = Ss[(e / a.bi) * ldw + cc + e % a.bi];
+    __syncthreads();
+    if (!project_out(Qs, ldq, cc, Rs, a.bi, a.bi, nr, rd, a.bar, a.err)) {
+      timeout = true;
+      return finish(ST_TIMEOUT);
+    }
+    // one reduction for both the residual norm and the Gram matrix of the candidate block
+    // S(:, 0:bb), which is the first CholeskyQR pass of Q_new if the loop continues
+    const int bb = min(a.bi, a.rbar - cc);
+    double* eb = red_buf(rd);
+    sumsq_acc(Rs, a.bi, a.bi, nr, eb);
+    gram_acc(Rs, a.bi, Rs, a.bi, bb, bb, nr, eb + 1);
+    if (!grid_sync(a.bar, a.err)) {
+      timeout = true;
+      return finish(ST_TIMEOUT);
+    }
+    red_advance(rd);
+    if (threadIdx.x == 0) est_s = __ldcg(eb);
+    __syncthreads();
+    const double ss = est_s;                               // ||S||_F^2
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.est_out[nest] = ss;   // the host takes sqrt(ss / b_inc)
+    ++nest;
+    // est = sqrt(ss / b_inc) > tau  <=>  ss > tau^2 b_inc  (the square root is left to the host)
+    if (!(ss > a.tau * a.tau * (double)a.bi)) return finish(ST_DONE);
+    // new directions: Q_new = qr(S(:, 0:bb)) (one CholeskyQR pass), re-orthogonalized against Q,
+    // then CholeskyQR2 for an orthonormal basis
+    double* Qn = Qs + cc;
+    for (int e = threadIdx.x; e < nr * bb; e += NT) Qn[(e / bb) * ldq + e % bb] = Rs[(e / bb) * a.bi + e % bb];
+    __syncthreads();
+    if (!cholqr(Qn, ldq, bb, nr, 1, rd, a.bar, a.err, &timeout, Tb, eb + 1)) return finish(ST_BREAKDOWN);
+    if (!project_out(Qs, ldq, cc, Qn, ldq, bb, nr, rd, a.bar, a.err)) {
+      timeout = true;
+      return finish(ST_TIMEOUT);
+    }
+    if (!cholqr(Qn, ldq, bb, nr, 2, rd, a.bar, a.err, &timeout, Tb)) return finish(ST_BREAKDOWN);
+    cc += bb;
+  }
+  finish(ST_DONE);
+}
+
+}  // namespace ac
+
+// Host side: runs the adaptive loop of one core on the device.  Returns TTR_OK with *status set
+// (ST_DONE, ST_EXTEND: more sketch columns are needed, ST_BREAKDOWN: a CholeskyQR pivot failed
+// at column *cc), or TTR_ERR_UNSUPPORTED when this path does not apply.
+int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
+                  int bi, int rbar, int width, int cc0, double tau, double* est_out, int* status, int* cc, int* nest) {
+  if (b0 > ac::BMAX || bi > ac::BMAX || (int64_t)rbar * bi > ac::ACC || m <= 0) return TTR_ERR_UNSUPPORTED;
+  int dev = 0;
+  TTR_CUDA(cudaGetDevice(&dev));
+  int nsm = 0, coop = 0, smem_optin = 0;
+  TTR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  TTR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  TTR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (!coop) return TTR_ERR_UNSUPPORTED;
+  // no more CTAs than rows; each CTA keeps its rows of Q, of the sketch and of the residual block
+  const int nblocks = (int)std::min<int64_t>(nsm, m);
+  const int rpc = (int)((m + nblocks - 1) / nblocks);
+  const int64_t qcols = rbar;
+  const size_t dyn = sizeof(double) * (size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX);
+  const size_t static_bytes = 36 * 1024;   // G, R^{-1}, invd, P staging, reductions (about 33 KB)
+  if (dyn + static_bytes > (size_t)smem_optin) return TTR_ERR_UNSUPPORTED;
+  TTR_CUDA(cudaFuncSetAttribute(ac::adaptive_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  int per_sm = 0;
+  TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ac::adaptive_core_kernel, ac::NT, dyn));
+  if (per_sm < 1) return TTR_ERR_UNSUPPORTED;
+  if (!c.ac_part) {
+    TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * ac::ACC));
+    TTR_CHECK(c.alloc_t(&c.ac_bar, 4));
+    TTR_CHECK(c.alloc_t(&c.ac_io, 4));
+    TTR_CUDA(cudaMemsetAsync(c.ac_bar, 0, 4 * sizeof(unsigned), c.stream));
+  }
+  if (!c.d_flags) {
+    TTR_CHECK(c.alloc_t(&c.d_flags, 4));
+    TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
+  }
+  const int used = std::max(std::max(b0 * b0, bi * bi + 1), rbar * bi) + 1;
+  TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * ac::ACC, c.stream));
+  ac::Args a{};
+  a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;
+  a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.rbar = rbar; a.width = width; a.cc0 = cc0; a.tau = tau;
+  a.bar = c.ac_bar; a.err = c.d_flags; a.est_out = est_out; a.io = c.ac_io;
+  void* params[] = {&a};
+  TTR_CUDA(cudaLaunchCooperativeKernel((const void*)ac::adaptive_core_kernel, dim3(nblocks), dim3(ac::NT), params, dyn,
+                                       c.stream));
+  TTR_CHECK(c.check_launch("adaptive_core"));
+  int io[4] = {0, 0, 0, 0};
+  TTR_CUDA(cudaMemcpyAsync(io, c.ac_io, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  TTR_CUDA(cudaStreamSynchronize(c.stream));
+  if (io[0] == ac::ST_TIMEOUT) return set_error("adaptive loop: grid barrier wait ran out"), TTR_ERR_TIMEOUT;
+  *status = io[0];
+  *cc = io[1];
+  *nest = io[2];
+  return TTR_OK;
+}
+
+}  // namespace ttr

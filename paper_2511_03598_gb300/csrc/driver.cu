@@ -32,13 +32,72 @@ int Ctx::alloc(void** p, size_t bytes) {
   return TTR_OK;
 }
 
+void Ctx::prof_begin() {
+  const char* env = getenv("TTR_PROFILE");
+  profiling = env && env[0] == '1';
+  if (profiling) {
+    cudaEventCreate(&prof_start);
+    cudaEventRecord(prof_start, stream);
+  }
+}
+
+void Ctx::prof_report() {
+  if (!profiling || prof.empty()) return;
+  cudaStreamSynchronize(stream);
+  struct Acc {
+    int n = 0;
+    double ms = 0.0;
+  };
+  std::vector<std::pair<std::string, Acc>> acc;
+  cudaEvent_t prev = prof_start;
+  double total = 0.0;
+  for (auto& pe : prof) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, prev, pe.second);
+    total += ms;
+    auto it = std::find_if(acc.begin(), acc.end(), [&](const std::pair<std::string, Acc>& a) { return a.first == pe.first; });
+    if (it == acc.end()) {
+      acc.push_back({pe.first, Acc{}});
+      it = acc.end() - 1;
+    }
+    it->second.n++;
+    it->second.ms += ms;
+    prev = pe.second;
+  }
+  std::sort(acc.begin(), acc.end(), [](const std::pair<std::string, Acc>& a, const std::pair<std::string, Acc>& b) {
+    return a.second.ms > b.second.ms;
+  });
+  fprintf(stderr, "[ttr profile] %zu launches, %.3f ms between first and last launch\n", prof.size(), total);
+  for (auto& a : acc)
+    fprintf(stderr, "[ttr profile] %-22s n=%5d  %9.3f ms  %5.1f%%  %8.2f us/launch\n", a.first.c_str(), a.second.n,
+            a.second.ms, 100.0 * a.second.ms / std::max(total, 1e-9), 1e3 * a.second.ms / a.second.n);
+  for (auto& pe : prof) cudaEventDestroy(pe.second);
+  cudaEventDestroy(prof_start);
+  prof.clear();
+  profiling = false;
+}
+
 int Ctx::check_launch(const char* what) {
   ++launches;
+  if (profiling) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, stream);
+    prof.push_back({what, e});
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return TTR_ERR_CUDA;
   }
+  return TTR_OK;
+}
+
+int Ctx::workspace() {
+  if (ws) return TTR_OK;
+  TTR_CHECK(alloc_t(&ws, 128 * 1024));
+  TTR_CHECK(alloc_t(&ws_ticket, 4));
+  TTR_CUDA(cudaMemsetAsync(ws_ticket, 0, 4 * sizeof(unsigned), stream));
   return TTR_OK;
 }
 
@@ -130,6 +189,12 @@ struct QrWork {
 static int chol_pass(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m, int64_t b, double* out,
                      int64_t ldo, const QrWork& w, const double* shift) {
   (void)E;
+  if (b <= 32) {
+    // Gram, Cholesky and 1/diag in one kernel (w.G holds R, w.Rinv the inverse diagonal), then
+    // a row-parallel triangular solve
+    TTR_CHECK(gram_reduce(c, X, ldx, X, ldx, m, b, b, nullptr, 0, 1, shift, w.G, w.Rinv, w.dflag, nullptr));
+    return tri_solve(c, X, ldx, m, b, w.G, w.Rinv, out, ldo);
+  }
   TTR_CHECK(gram_tn(c, X, ldx, X, ldx, m, b, b, w.G, b));                 // G = X^T X
   TTR_CHECK(chol_inv(c, w.G, b, b, shift, w.Rinv, w.dflag));
   return gemm_nn_small(c, X, ldx, w.Rinv, b, m, b, b, out, ldo, 1.0, 0.0);  // out = X R^{-1}
@@ -445,6 +510,7 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   if (ell < 1) return set_error("ell must be >= 1"), TTR_ERR_ARG;
   Ctx c;
   c.stream = stream;
+  c.prof_begin();
   Timer tm;
   tm.rec(0, stream);
   Engine E;
@@ -514,6 +580,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
     return set_error("f_init and f_inc must lie in (0, 1)"), TTR_ERR_ARG;
   Ctx c;
   c.stream = stream;
+  c.prof_begin();
   Timer tm;
   tm.rec(0, stream);
   const int d = X.d;
@@ -603,32 +670,81 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   };
   // CholeskyQR2 without a host round trip; a breakdown only raises dprobe->flag.
   auto qr_try = [&](double* Xq, int64_t ldx, int64_t m, int64_t b) -> int {
-    TTR_CHECK(copy2d(c, w.qr.save, b, Xq, ldx, m, b));
     QrWork q2 = w.qr;
     q2.dflag = &dprobe->flag;
-    TTR_CHECK(chol_pass(c, E, w.qr.save, b, m, b, w.qr.tmp, b, q2, nullptr));
+    TTR_CHECK(chol_pass(c, E, Xq, ldx, m, b, w.qr.tmp, b, q2, nullptr));
     return chol_pass(c, E, w.qr.tmp, b, m, b, Xq, ldx, q2, nullptr);
   };
+  // estimates of one core land here (the device loop writes them, the host copies them out)
+  double* dest = nullptr;
+  TTR_CHECK(c.alloc_t(&dest, rmax + 8));
+  const bool device_loop = getenv("TTR_HOST_LOOP") == nullptr;
   for (int k = 1; k < d; ++k) {
     const int64_t rows = lprev * X.n[k - 1], cols = X.r[k];
     const int64_t rbar = std::min(rows, cols);
     const int64_t b0 = block_size(rbar, block, o.f_init);
     const int64_t bi = block_size(rbar, block, o.f_inc);
     sk_cols = 0;
-    TTR_CHECK(ensure(k, b0, rows, cols));
-    // phase 1: Q = qr(S(:, 1:b_init))
+    TTR_CHECK(ensure(k, std::min(rbar, b0) + bi, rows, cols));
+    int64_t cc = 0;
+    bool done = false;
+    if (device_loop) {
+      // the whole block loop on the device; the host steps in only to append sketch columns or to
+      // redo a block whose CholeskyQR broke down
+      int guard = 0;
+      while (!done) {
+        if (++guard > 4 * (int)rbar + 16) return set_error("adaptive loop did not terminate"), TTR_ERR_TIMEOUT;
+        int status = 0, ccn = 0, nest = 0;
+        st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)b0, (int)bi, (int)rbar, (int)sk_cols, (int)cc, tau,
+                           dest, &status, &ccn, &nest);
+        if (st == TTR_ERR_UNSUPPORTED) break;
+        if (st != TTR_OK) return st;
+        if (nest > 0) {
+          std::vector<double> h(nest);
+          TTR_CUDA(cudaMemcpy(h.data(), dest, sizeof(double) * nest, cudaMemcpyDeviceToHost));
+          for (double ss : h) {
+            const double e = sqrt(ss) / sqrt((double)bi);      // the device returns ||S||_F^2
+            if (!isfinite(e)) return set_error("non-finite residual estimate"), TTR_ERR_NONFINITE;
+            ests.push_back(e);
+            est_core.push_back(k);
+          }
+        }
+        cc = ccn;
+        if (status == 0) {
+          done = true;
+        } else if (status == 1) {
+          TTR_CHECK(ensure(k, cc + bi, rows, cols));
+        } else {
+          // CholeskyQR breakdown: redo that factorization with the shifted/perturbed fallbacks
+          if (cc == 0) {
+            TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
+            TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+            cc = b0;
+          } else {
+            const int64_t bb = std::min(bi, rbar - cc);
+            TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
+            TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
+            TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
+            TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
+            cc += bb;
+          }
+          if (cc >= rbar) done = true;
+        }
+      }
+    }
+    if (!done) {
+    cc = 0;
+    // host-driven loop (blocks wider than the device loop supports)
     TTR_CUDA(cudaMemsetAsync(dprobe, 0, sizeof(Probe), stream));
     TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
     TTR_CHECK(qr_try(w.Q, w.qcap, rows, b0));
     bool phase1_checked = false;
-    int64_t cc = b0;
+    cc = b0;
     while (cc < rbar) {
       TTR_CHECK(ensure(k, cc + bi, rows, cols));
       // residual sketch S = (I - Q Q^T) Z W_{k+1}(:, cc:cc+bi)   (Eqs. (3.4)-(3.5))
       TTR_CHECK(copy2d(c, w.S, bi, Sall + cc, wcap, rows, bi));
-      TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.S, bi, bi, w.P));
-      TTR_CUDA(cudaMemsetAsync(&dprobe->ss, 0, sizeof(double), stream));
-      TTR_CHECK(sumsq(c, w.S, rows, bi, bi, 1, &dprobe->ss));
+      TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.S, bi, bi, w.P, &dprobe->ss));
       // speculative next block: Q_new = qr(S(:, :bb)), re-orthogonalized against Q, qr again
       const int64_t bb = std::min(bi, rbar - cc);
       TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
@@ -671,6 +787,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
         TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
         TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
       }
+    }
     }
     double* Ynext = w.Y[cur];
     TTR_CHECK(project_next(c, E, w, Z, rows, cols, cc, X, k, Ynext));
@@ -737,6 +854,7 @@ static int round_deterministic(const TT& X, double tol, cudaStream_t stream, ttr
   if (!(tol > 0.0) || !isfinite(tol)) return set_error("tol must be positive and finite"), TTR_ERR_ARG;
   Ctx c;
   c.stream = stream;
+  c.prof_begin();
   Timer tm;
   tm.rec(0, stream);
   Engine E;

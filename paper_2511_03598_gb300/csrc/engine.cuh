@@ -19,6 +19,11 @@ int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M
 int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn,
                int64_t ncol, double* Y);
 
+// Persistent cooperative kernel for the adaptive block loop of one core (adaptive_core.cu).
+// *status: 0 done, 1 needs more sketch columns, 2 CholeskyQR breakdown at column *cc.
+int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
+                  int bi, int rbar, int width, int cc0, double tau, double* est_out, int* status, int* cc, int* nest);
+
 // Small helper kernels (engine.cu)
 int transpose_f64(Ctx& c, const double* A, int64_t rows, int64_t cols, double* out);
 int scale_cols_f64(Ctx& c, double* U, int64_t ld, int64_t ncols, int64_t rows, const double* s);
@@ -96,11 +101,27 @@ struct Engine {
   }
 
   // P = Q(:, :cc)^T S;  S <- S - Q(:, :cc) P     (Eq. (3.5) / block Gram-Schmidt), FP64
+  // With sumsq_out, ||S||_F^2 of the result is accumulated there (it is zeroed in here first).
   int project_out(Ctx& c, const double* Q, int64_t ldq, int64_t rows, int64_t cc, double* S, int64_t lds,
-                  int64_t bcols, double* P) const {
-    if (cc <= 0) return TTR_OK;
-    TTR_CHECK(gram_tn(c, Q, ldq, S, lds, rows, cc, bcols, P, bcols));
-    return gemm_nn_small(c, Q, ldq, P, bcols, rows, cc, bcols, S, lds, -1.0, 1.0);
+                  int64_t bcols, double* P, double* sumsq_out = nullptr) const {
+    if (cc <= 0) {
+      if (!sumsq_out) return TTR_OK;
+      TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
+      return sumsq(c, S, rows, bcols, lds, 1, sumsq_out);
+    }
+    int st = gram_reduce(c, Q, ldq, S, lds, rows, cc, bcols, P, bcols, 0, nullptr, nullptr, nullptr, nullptr, sumsq_out);
+    if (st == TTR_ERR_UNSUPPORTED) {
+      TTR_CHECK(gram_tn(c, Q, ldq, S, lds, rows, cc, bcols, P, bcols));
+      if (sumsq_out) TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
+    } else if (st != TTR_OK) {
+      return st;
+    }
+    st = gemm_nn_small(c, Q, ldq, P, bcols, rows, cc, bcols, S, lds, -1.0, 1.0, sumsq_out);
+    if (st == TTR_ERR_UNSUPPORTED && sumsq_out) {
+      TTR_CHECK(gemm_nn_small(c, Q, ldq, P, bcols, rows, cc, bcols, S, lds, -1.0, 1.0, nullptr));
+      return sumsq(c, S, rows, bcols, lds, 1, sumsq_out);
+    }
+    return st;
   }
 
   // M (ccols x cols, ld cols) = Q(:, :ccols)^T Z   (M_k = Q_k^T V(Y_k))

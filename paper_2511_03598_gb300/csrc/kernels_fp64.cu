@@ -123,29 +123,198 @@ int gram_tn(Ctx& c, const double* X, int64_t ldx, const double* Y, int64_t ldy, 
   return c.check_launch("gram_tn");
 }
 
+// ---- Gram with in-kernel reduction: C (a x b) = X^T Y over m rows, a*b <= 1024.
+// Each CTA writes its partial to ws[blockIdx][a*b]; the last CTA to finish (ticket counter,
+// reset by that CTA) sums the partials.  Optionally that CTA then factors C + shift*I = R^T R
+// (upper Cholesky, in shared memory) and writes R, 1/diag(R) and a breakdown flag, and/or
+// zeroes *zero_out (an accumulator the next kernel adds into).
+constexpr int GRAM_MAX = 1024;
+
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                                                           int64_t m, int a, int b, int64_t rpb, double* ws,
+                                                           unsigned* ticket, double* C, int64_t ldc, int chol,
+                                                           const double* shift, double* R, double* invd, int* bad,
+                                                           double* zero_out) {
+  __shared__ double G[GRAM_MAX];
+  __shared__ int last;
+  const int ab = a * b;
+  const int64_t r0 = (int64_t)blockIdx.x * rpb;
+  const int64_t r1 = min(m, r0 + rpb);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // warps split the outputs (16 at a time), lanes split the rows of this block
+  for (int o0 = warp * 16; o0 < ab; o0 += nw * 16) {
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int64_t r = r0 + lane; r < r1; r += 32) {
+      const double* xr = X + r * ldx;
+      const double* yr = Y + r * ldy;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int o = o0 + q;
+        if (o < ab) acc[q] = fma(xr[o / b], yr[o % b], acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      double v = acc[q];
+      for (int sft = 16; sft > 0; sft >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sft);
+      if (lane == 0 && o0 + q < ab) ws[(int64_t)blockIdx.x * ab + o0 + q] = v;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int o = threadIdx.x; o < ab; o += blockDim.x) {
+    double t0 = 0.0, t1 = 0.0;
+    unsigned blk = 0;
+    for (; blk + 1 < gridDim.x; blk += 2) {
+      t0 += ws[(int64_t)blk * ab + o];
+      t1 += ws[(int64_t)(blk + 1) * ab + o];
+    }
+    if (blk < gridDim.x) t0 += ws[(int64_t)blk * ab + o];
+    const double v = t0 + t1;
+    G[o] = v;
+    if (C) C[(o / b) * ldc + (o % b)] = v;
+  }
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    if (zero_out) *zero_out = 0.0;
+  }
+  if (!chol) return;
+  __syncthreads();
+  // upper Cholesky in shared memory: G[j][c], c >= j, becomes R[j][c]
+  __shared__ double piv;
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  const double sh = shift ? *shift : 0.0;
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    if (threadIdx.x == 0) {
+      double dsum = G[j * b + j] + sh;
+      for (int p = 0; p < j; ++p) dsum -= G[p * b + j] * G[p * b + j];
+      if (!(dsum > 0.0) || !isfinite(dsum)) {
+        fail = 1;
+        dsum = 1.0;
+      }
+      piv = sqrt(dsum);
+      G[j * b + j] = piv;
+    }
+    __syncthreads();
+    for (int col = j + 1 + threadIdx.x; col < b; col += blockDim.x) {
+      double v = G[j * b + col];
+      for (int p = 0; p < j; ++p) v -= G[p * b + j] * G[p * b + col];
+      G[j * b + col] = v / piv;
+    }
+    __syncthreads();
+  }
+  for (int o = threadIdx.x; o < b * b; o += blockDim.x) {
+    const int i = o / b, j = o % b;
+    R[o] = (j >= i) ? G[o] : 0.0;
+    if (i == j) invd[i] = 1.0 / G[o];
+  }
+  if (threadIdx.x == 0 && fail) *bad = 1;
+}
+
+int gram_reduce(Ctx& c, const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t a, int64_t b,
+                double* C, int64_t ldc, int chol, const double* shift, double* R, double* invd, int* bad,
+                double* zero_out) {
+  if (a * b > GRAM_MAX || a <= 0 || b <= 0) return TTR_ERR_UNSUPPORTED;
+  if (chol && a != b) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(c.workspace());
+  // blocks of at least 64 rows, at most 128 blocks (bounds the final reduction)
+  int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(128, m / 64));
+  const int64_t rpb = (std::max<int64_t>(m, 1) + blocks - 1) / blocks;
+  blocks = std::max<int64_t>(1, (m + rpb - 1) / rpb);
+  gram_reduce_kernel<<<(unsigned)blocks, 256, 0, c.stream>>>(X, ldx, Y, ldy, m, (int)a, (int)b, rpb, c.ws, c.ws_ticket,
+                                                              C, ldc, chol, shift, R, invd, bad, zero_out);
+  return c.check_launch("gram_reduce");
+}
+
+// out (m x b) = X (m x b) R^{-1} for upper-triangular R (b x b, row-major) by forward
+// substitution along each row: q_j = (x_j - sum_{i<j} q_i R_ij) / R_jj.  Row-parallel; BMAX is
+// a compile-time bound so the row stays in registers.
+template <int BMAX>
+__global__ void __launch_bounds__(256) tri_solve_kernel(const double* X, int64_t ldx, int64_t m, int b, const double* R,
+                                                         const double* invd, double* out, int64_t ldo) {
+  __shared__ double Rs[BMAX * BMAX];
+  __shared__ double id[BMAX];
+  for (int o = threadIdx.x; o < BMAX * BMAX; o += blockDim.x) {
+    const int i = o / BMAX, j = o % BMAX;
+    Rs[o] = (i < b && j < b) ? R[i * b + j] : 0.0;
+  }
+  for (int o = threadIdx.x; o < BMAX; o += blockDim.x) id[o] = (o < b) ? invd[o] : 0.0;
+  __syncthreads();
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+    double q[BMAX];
+    const double* xr = X + r * ldx;
+#pragma unroll
+    for (int j = 0; j < BMAX; ++j) q[j] = (j < b) ? xr[j] : 0.0;
+#pragma unroll
+    for (int j = 0; j < BMAX; ++j) {
+      double v = q[j];
+#pragma unroll
+      for (int i = 0; i < j; ++i) v = fma(-q[i], Rs[i * BMAX + j], v);
+      q[j] = v * id[j];
+    }
+    double* orow = out + r * ldo;
+#pragma unroll
+    for (int j = 0; j < BMAX; ++j)
+      if (j < b) orow[j] = q[j];
+  }
+}
+
+int tri_solve(Ctx& c, const double* X, int64_t ldx, int64_t m, int64_t b, const double* R, const double* invd,
+              double* out, int64_t ldo) {
+  if (b > 32) return TTR_ERR_UNSUPPORTED;
+  if (m <= 0 || b <= 0) return TTR_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>((m + 255) / 256, 1216);
+  if (b <= 16) tri_solve_kernel<16><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo);
+  else tri_solve_kernel<32><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo);
+  return c.check_launch("tri_solve");
+}
+
 // C (m x n, ldc) = alpha * X (m x k, ldx) P (k x n, ldp) + beta * C, for small k and n: one
 // thread per output element, P staged in shared memory (k*n <= 4096).
 __global__ void __launch_bounds__(256) gemm_nn_small_kernel(const double* X, int64_t ldx, const double* P, int64_t ldp,
                                                              int64_t m, int64_t k, int64_t n, double* C, int64_t ldc,
-                                                             double alpha, double beta) {
+                                                             double alpha, double beta, double* sumsq_out) {
   __shared__ double Ps[4096];
+  __shared__ double red[8];
   for (int64_t e = threadIdx.x; e < k * n; e += blockDim.x) Ps[e] = P[(e / n) * ldp + (e % n)];
   __syncthreads();
   const int64_t tot = m * n;
+  double ss = 0.0;
   for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < tot; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = o / n, j = o % n;
     const double* xr = X + r * ldx;
     double s = 0.0;
     for (int64_t q = 0; q < k; ++q) s = fma(xr[q], Ps[q * n + j], s);
     double* cp = C + r * ldc + j;
-    *cp = (beta == 0.0) ? alpha * s : fma(beta, *cp, alpha * s);
+    const double v = (beta == 0.0) ? alpha * s : fma(beta, *cp, alpha * s);
+    *cp = v;
+    ss = fma(v, v, ss);
+  }
+  if (sumsq_out) {
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      atomicAdd(sumsq_out, t);
+    }
   }
 }
 
 int gemm_nn_small(Ctx& c, const double* X, int64_t ldx, const double* P, int64_t ldp, int64_t m, int64_t k, int64_t n,
-                  double* C, int64_t ldc, double alpha, double beta) {
+                  double* C, int64_t ldc, double alpha, double beta, double* sumsq_out) {
   if (m <= 0 || n <= 0) return TTR_OK;
   if (k * n > 4096) {
+    if (sumsq_out) return TTR_ERR_UNSUPPORTED;
     Gemm g;
     g.M = m; g.N = n; g.K = k;
     g.A = X; g.sam = ldx; g.sak = 1;
@@ -156,7 +325,7 @@ int gemm_nn_small(Ctx& c, const double* X, int64_t ldx, const double* P, int64_t
   }
   const int64_t tot = m * n;
   const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 1216);
-  gemm_nn_small_kernel<<<blocks, 256, 0, c.stream>>>(X, ldx, P, ldp, m, k, n, C, ldc, alpha, beta);
+  gemm_nn_small_kernel<<<blocks, 256, 0, c.stream>>>(X, ldx, P, ldp, m, k, n, C, ldc, alpha, beta, sumsq_out);
   return c.check_launch("gemm_nn_small");
 }
 

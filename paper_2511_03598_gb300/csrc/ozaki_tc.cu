@@ -46,7 +46,8 @@ constexpr int KSEG = 256;             // K per CTA: bound for exact FP32 accumul
 constexpr int MAXS = 8;               // slices per operand
 constexpr int PLANE_A = TM * KC;      // bf16 per A digit plane per chunk (8 KB)
 constexpr int PLANE_B = TN * KC;      // bf16 per B digit plane per chunk (4 KB)
-constexpr int NT = 128;               // threads per CTA (one per TMEM lane in the epilogue)
+constexpr int NT = 256;               // threads per CTA (two warps per TMEM lane quarter)
+constexpr int NW = NT / 32;           // warps per CTA
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 enum Mode { PLAIN = 0, ATOMIC = 1, RLM = 2 };
@@ -191,39 +192,45 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (tid < TM) slabE[tid] = 1;
+  if (tid < TM) {
+    slabE[tid] = 1;
+    rowE[tid] = 1;
+  }
+  __syncthreads();
 
   // ---- pass 1: exponent scale of every row over this K segment (many loads in flight)
   if (AKFAST) {
-    int em[32];
+    constexpr int RPW = TM / NW;              // rows per warp
+    int em[RPW];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) em[r] = 1;
+    for (int r = 0; r < RPW; ++r) em[r] = 1;
     for (int k = lane; k < kseg_len; k += 32) {
 #pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        const int row = warp * 32 + r;
+      for (int r = 0; r < RPW; ++r) {
+        const int row = warp * RPW + r;
         if (row < rows) em[r] = max(em[r], exp_field(__ldg(a.A + (m0 + row) * a.sam + kseg0 + k)));
       }
     }
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
+    for (int r = 0; r < RPW; ++r) {
       const int e = __reduce_max_sync(0xffffffffu, em[r]);
-      if (lane == 0) rowE[warp * 32 + r] = e;
+      if (lane == 0) rowE[warp * RPW + r] = e;
     }
   } else {
-    int e0 = 1, e1 = 1, e2 = 1, e3 = 1;
-    if (tid < rows) {
-      const double* colp = a.A + (m0 + tid) * a.sam + kseg0 * a.sak;
-      int k = 0;
-      for (; k + 3 < kseg_len; k += 4) {
+    // NT/TM threads per row, interleaved over k
+    const int row = tid % TM, part = tid / TM;
+    constexpr int PARTS = NT / TM;
+    int e0 = 1, e1 = 1;
+    if (row < rows) {
+      const double* colp = a.A + (m0 + row) * a.sam + kseg0 * a.sak;
+      int k = part;
+      for (; k + PARTS < kseg_len; k += 2 * PARTS) {
         e0 = max(e0, exp_field(__ldg(colp + (int64_t)k * a.sak)));
-        e1 = max(e1, exp_field(__ldg(colp + (int64_t)(k + 1) * a.sak)));
-        e2 = max(e2, exp_field(__ldg(colp + (int64_t)(k + 2) * a.sak)));
-        e3 = max(e3, exp_field(__ldg(colp + (int64_t)(k + 3) * a.sak)));
+        e1 = max(e1, exp_field(__ldg(colp + (int64_t)(k + PARTS) * a.sak)));
       }
-      for (; k < kseg_len; ++k) e0 = max(e0, exp_field(__ldg(colp + (int64_t)k * a.sak)));
+      if (k < kseg_len) e0 = max(e0, exp_field(__ldg(colp + (int64_t)k * a.sak)));
     }
-    rowE[tid] = max(max(e0, e1), max(e2, e3));
+    atomicMax(&rowE[row], max(e0, e1));
   }
   __syncthreads();
   if (MODE == RLM) {
@@ -247,13 +254,15 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
     if (!ok) break;
     uint16_t* Ap = (uint16_t*)bufs[b];
     uint16_t* Bpl = Ap + (size_t)s * PLANE_A;
-    // A digits: 128 rows x 4 groups of 8 consecutive k; all 32 loads of a thread issued first
+    // A digits: 128 rows x 4 groups of 8 consecutive k = 512 tasks, TASKS per thread, all loads first
     {
-      double v[4][8];
+      constexpr int TASKS = (TM * (KC / 8)) / NT;
+      double v[TASKS][8];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int row = AKFAST ? ((tid + NT * i) >> 2) : tid;
-        const int grp = AKFAST ? ((tid + NT * i) & 3) : i;
+      for (int i = 0; i < TASKS; ++i) {
+        const int u = tid + NT * i;
+        const int row = AKFAST ? (u >> 2) : (u % TM);
+        const int grp = AKFAST ? (u & 3) : (u / TM);
         const int kl = c * KC + grp * 8;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -262,9 +271,10 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
         }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int row = AKFAST ? ((tid + NT * i) >> 2) : tid;
-        const int grp = AKFAST ? ((tid + NT * i) & 3) : i;
+      for (int i = 0; i < TASKS; ++i) {
+        const int u = tid + NT * i;
+        const int row = AKFAST ? (u >> 2) : (u % TM);
+        const int grp = AKFAST ? (u & 3) : (u / TM);
         uint32_t w[MAXS][4];
         slice8(v[i], rowE[row], s, w);
         const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
@@ -314,18 +324,20 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;");
 
-  // ---- epilogue: 16 columns at a time
+  // ---- epilogue: warp w reads TMEM lane quarter (w % 4) and column half (w / 4)
   if (ok && nchunk > 0) {
-    __int128* P = reinterpret_cast<__int128*>(smem);           // [TM][16] for the slab sums
-    const int row = tid;
-    for (int cg = 0; cg < TN / 16; ++cg) {
+    __int128* P = reinterpret_cast<__int128*>(smem);           // [TM][TN] for the slab sums
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    for (int cgi = 0; cgi < (TN / 16) / (NW / 4); ++cgi) {
+      const int cg = half * ((TN / 16) / (NW / 4)) + cgi;
       __int128 V[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) V[j] = 0;
 #pragma unroll 1
       for (int t = 0; t < s; ++t) {
         uint32_t r[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * TN + cg * 16);
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * TN + cg * 16);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -344,7 +356,7 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
           for (int j = 0; j < 16; ++j) {
             const int64_t n = n0 + j;
             if (n < a.N) {
-              const double out = i128_to_double(V[j], e_row + a.Fmax[n] - 2044 - 7 * s - 7);
+              const double out = i128_to_double(V[j], e_row + max(1, a.Fmax[n]) - 2044 - 7 * s - 7);
               double* cp = a.C + (m0 + row) * a.scm + n * a.scn;
               if (MODE == ATOMIC) atomicAdd(cp, out);
               else *cp = out;
@@ -352,27 +364,28 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
           }
         }
       } else {
-        // weight by 2^20*Omega(i, n) and sum over i inside each slab, exactly
+        // weight by the integer sketch entry 2^20 Omega(i, n); summed over i below
         const int i = row % (int)a.nmode;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int64_t n = n0 + j;
           const int om = (row < rows && n < a.N) ? a.Omint[i * a.ldo + n] : 0;
-          P[row * 16 + j] = V[j] * (__int128)om;
+          P[row * TN + cg * 16 + j] = V[j] * (__int128)om;
         }
-        __syncthreads();
-        const int nslab = rows / (int)a.nmode;
-        for (int task = tid; task < nslab * 16; task += NT) {
-          const int sl = task >> 4, j = task & 15;
-          const int64_t n = n0 + j;
-          if (n >= a.N) continue;
-          __int128 acc = 0;
-          for (int ii = 0; ii < (int)a.nmode; ++ii) acc += P[(sl * (int)a.nmode + ii) * 16 + j];
-          const int e_slab = rowE[sl * (int)a.nmode];
-          const int64_t aidx = (int64_t)blockIdx.x * a.g + sl;
-          a.W[aidx * a.ldw + n] = i128_to_double(acc, e_slab + a.Fmax[n] - 2044 - 7 * s - 7 - 20);
-        }
-        __syncthreads();
+      }
+    }
+    if (MODE == RLM) {
+      __syncthreads();
+      const int nslab = rows / (int)a.nmode;
+      for (int task = tid; task < nslab * TN; task += NT) {
+        const int sl = task / TN, j = task % TN;
+        const int64_t n = (int64_t)nc * TN + j;
+        if (n >= a.N) continue;
+        __int128 acc = 0;
+        for (int ii = 0; ii < (int)a.nmode; ++ii) acc += P[(sl * (int)a.nmode + ii) * TN + j];
+        const int e_slab = rowE[sl * (int)a.nmode];
+        const int64_t aidx = (int64_t)blockIdx.x * a.g + sl;
+        a.W[aidx * a.ldw + n] = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
       }
     }
   }
@@ -385,17 +398,23 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
 // image.  B(k, n) = B[k*sbk + n*sbn], K x N.
 __global__ void __launch_bounds__(256) colmax_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
                                                        int* Fmax) {
-  // grid (N-chunks, K-splits); Fmax pre-set to 1
+  // grid (N-chunks, K-chunks of 32 rows); each thread reads 8 rows of one column (all loads in
+  // flight), a warp covers 32 columns; the column maxima go to Fmax (zeroed beforehand) atomically
   const int nc = blockIdx.x, tid = threadIdx.x;
-  const int j = tid % TN, ph = tid / TN, nph = blockDim.x / TN;
+  const int j = tid % TN, grp = tid / TN;
   const int64_t n = (int64_t)nc * TN + j;
-  const int64_t kb = (int64_t)blockIdx.y * 1024, ke = min(K, kb + 1024);
   int e = 1;
   if (n < N) {
-#pragma unroll 8
-    for (int64_t k = kb + ph; k < ke; k += nph) e = max(e, exp_field(B[k * sbk + n * sbn]));
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)blockIdx.y * KC + grp * 8 + q;
+      v[q] = (k < K) ? B[k * sbk + n * sbn] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) e = max(e, exp_field(v[q]));
   }
-  atomicMax(&Fmax[nc * TN + j], e);
+  atomicMax(&Fmax[(int64_t)nc * TN + j], e);
 }
 
 // One CTA per (64-column chunk, 32-row K chunk): 256 tasks (column, group of 8 k).
@@ -404,6 +423,7 @@ __global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t s
   const int nc = blockIdx.x, kcn = blockIdx.y, u = threadIdx.x;
   const int j = u % TN, grp = u / TN;
   const int64_t n = (int64_t)nc * TN + j;
+  const int E = max(1, Fmax[n]);
   double v[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -411,27 +431,22 @@ __global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t s
     v[q] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0;
   }
   uint32_t w[MAXS][4];
-  slice8(v, Fmax[nc * TN + j], s, w);
+  slice8(v, E, s, w);
   uint4* blk = planes + ((size_t)nc * kchunks + kcn) * (size_t)s * (PLANE_B / 8);
   const int idx = ((grp * (TN / 8)) + (j >> 3)) * 8 + (j & 7);        // uint4 index in a plane
   for (int p = 0; p < s; ++p) blk[(size_t)p * (PLANE_B / 8) + idx] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
-__global__ void fill_int_kernel(int* p, int64_t n, int v) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) p[e] = v;
-}
-
-static size_t smem_bytes(int s) {
+static size_t smem_bytes(int s, int mode) {
   size_t need = 2 * (size_t)s * (PLANE_A + PLANE_B) * 2;
-  const size_t epi = (size_t)TM * 16 * sizeof(__int128);
-  need = std::max(need, epi);
+  if (mode == RLM) need = std::max(need, (size_t)TM * TN * sizeof(__int128));
   if (s <= 4) need = std::max<size_t>(need, 100 * 1024);   // at most 2 CTAs per SM: 2 x 256 TMEM columns
   return need + 1024;
 }
 
 template <int MODE, bool AKFAST>
 static int launch(Ctx& c, const Args& a, dim3 grid) {
-  const size_t sm = smem_bytes(a.s);
+  const size_t sm = smem_bytes(a.s, MODE);
   auto kern = sliced_kernel<MODE, AKFAST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
@@ -448,12 +463,11 @@ struct BPrep {
 static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int s, BPrep& p) {
   p.nchunks = (int)((N + TN - 1) / TN);
   p.kchunks = (int)((K + KC - 1) / KC);
+  const int64_t npad = (int64_t)p.nchunks * TN;
   TTR_CHECK(c.alloc(reinterpret_cast<void**>(&p.planes), (size_t)p.nchunks * p.kchunks * s * PLANE_B * 2));
-  TTR_CHECK(c.alloc_t(&p.Fmax, (size_t)p.nchunks * TN));
-  fill_int_kernel<<<1, 256, 0, c.stream>>>(p.Fmax, (int64_t)p.nchunks * TN, 1);
-  TTR_CHECK(c.check_launch("fill_int"));
-  colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)((K + 1023) / 1024)), 256, 0, c.stream>>>(B, sbk, sbn, K, N,
-                                                                                                  p.Fmax);
+  TTR_CHECK(c.alloc_t(&p.Fmax, (size_t)npad));
+  TTR_CUDA(cudaMemsetAsync(p.Fmax, 0, sizeof(int) * npad, c.stream));
+  colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, p.Fmax);
   TTR_CHECK(c.check_launch("colmax_b"));
   slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, s, p.kchunks,
                                                                                      p.Fmax, p.planes);

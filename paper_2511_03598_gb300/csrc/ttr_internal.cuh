@@ -37,6 +37,21 @@ struct Ctx {
   int64_t launches = 0;
   std::vector<void*> owned;
   int* d_flags = nullptr;          // device status flags (0 = ok); bounded waits write here
+  double* ws = nullptr;            // reduction workspace (128 x 1024 doubles) for gram_reduce
+  unsigned* ws_ticket = nullptr;   // its completion counter (kept at zero between kernels)
+  double* ac_part = nullptr;       // adaptive_core: per-CTA partial sums (two buffers)
+  double* ac_red = nullptr;        // adaptive_core: reduced projection coefficients
+  unsigned* ac_bar = nullptr;      // adaptive_core: grid barrier counter/generation
+  int* ac_io = nullptr;            // adaptive_core: status, column count, estimate count
+  int workspace();
+
+  // optional launch timeline (environment TTR_PROFILE=1): an event after every launch; the time
+  // between consecutive events is charged to the later launch (so it includes GPU idle time)
+  std::vector<std::pair<const char*, cudaEvent_t>> prof;
+  bool profiling = false;
+  cudaEvent_t prof_start = nullptr;
+  void prof_begin();
+  void prof_report();
 
   int alloc(void** p, size_t bytes);
   template <typename T>
@@ -45,7 +60,10 @@ struct Ctx {
   }
   int check_launch(const char* what);
   void release();
-  ~Ctx() { release(); }
+  ~Ctx() {
+    prof_report();
+    release();
+  }
 };
 
 // ----------------------------------------------------------------------------- kernels (FP64 SIMT)
@@ -68,9 +86,19 @@ int gemm_f64(Ctx& c, const Gemm& g);
 // C (a x b) = X^T Y over m rows (row-major operands; FP64; C zeroed here).
 int gram_tn(Ctx& c, const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t a, int64_t b,
             double* C, int64_t ldc);
-// C = alpha X P + beta C with X m x k, P k x n (small k, n), row-major.
+// C = alpha X P + beta C with X m x k, P k x n (small k, n), row-major; if sumsq_out, the sum
+// of squares of the new C is added to *sumsq_out.
 int gemm_nn_small(Ctx& c, const double* X, int64_t ldx, const double* P, int64_t ldp, int64_t m, int64_t k, int64_t n,
-                  double* C, int64_t ldc, double alpha, double beta);
+                  double* C, int64_t ldc, double alpha, double beta, double* sumsq_out = nullptr);
+// C (a x b, may be null) = X^T Y over m rows for a*b <= 1024, reduced inside the kernel; with
+// chol, also R (b x b upper, C + shift I = R^T R), invd = 1/diag(R) and *bad on breakdown;
+// zero_out (optional) is set to 0 once the reduction is complete.
+int gram_reduce(Ctx& c, const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t a, int64_t b,
+                double* C, int64_t ldc, int chol, const double* shift, double* R, double* invd, int* bad,
+                double* zero_out);
+// out = X R^{-1} (b <= 64) by row-parallel forward substitution.
+int tri_solve(Ctx& c, const double* X, int64_t ldx, int64_t m, int64_t b, const double* R, const double* invd,
+              double* out, int64_t ldo);
 
 // Omega_k(:, col0:col1) for cores k = k_lo..k_hi (1-based); block k goes to
 // dst + (k - k_lo) * ostride as row-major [i][j - col0] with leading dimension ld.
