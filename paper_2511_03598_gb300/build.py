@@ -59,7 +59,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     if force or not _newer(LIB, objs):
         tmp = LIB + ".tmp"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [cc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs, "-lcudart"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -597,7 +597,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   // Columns of W are a prefix of one counter-based stream, so how many are drawn up front (and how
   // the rest are appended) never changes a result; draw one tensor-core tile width up front and
   // grow geometrically, which keeps the number of right-to-left passes small.
-  int64_t wdev = std::min(wcap, std::max<int64_t>(w0, 64));
+  int64_t wdev = std::min(wcap, std::max<int64_t>(w0, E.natural_width()));
   if (o.width_hint > 0) wdev = std::min(wcap, std::max(w0, o.width_hint));
   TTR_CHECK(rl_pass(c, E, X, seed, 0, wdev, 2, s));
   s.width = wdev;

@@ -24,6 +24,9 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
                   int bi, int rbar, int width, int cc0, double tau, double* est_out, int* status, int* cc, int* nest);
 
+// Widest tensor-core tile (UMMA N) usable with s slices.
+int tile_width(int s);
+
 // Small helper kernels (engine.cu)
 int transpose_f64(Ctx& c, const double* A, int64_t rows, int64_t cols, double* out);
 int scale_cols_f64(Ctx& c, double* U, int64_t ld, int64_t ncols, int64_t rows, const double* s);
@@ -59,6 +62,9 @@ struct Engine {
   }
 
   int small_gemm(Ctx& c, const Gemm& g) const { return gemm_f64(c, g); }
+
+  // sketch columns worth drawing up front: one tensor-core tile in sliced mode
+  int64_t natural_width() const { return precision == TTR_PREC_SLICED ? tile_width(slices) : 64; }
 
   // S = Z W(:, cols): A row-major (sak == 1), B row-major (sbn == 1), C row-major (scn == 1)
   int sketch(Ctx& c, const Gemm& g) const {

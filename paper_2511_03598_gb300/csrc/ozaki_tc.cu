@@ -40,12 +40,13 @@ namespace ttr {
 namespace tc {
 
 constexpr int TM = 128;               // rows per tile = UMMA M
-constexpr int TN = 64;                // columns per tile = UMMA N
+constexpr int TNMAX = 256;            // largest UMMA N; the tile width tn is chosen per call
+constexpr int PB = 64;                // partial-contraction epilogue: columns per staging block
 constexpr int KC = 32;                // K per shared-memory chunk (two UMMA K-steps of 16)
 constexpr int KSEG = 256;             // K per CTA: bound for exact FP32 accumulation
 constexpr int MAXS = 8;               // slices per operand
 constexpr int PLANE_A = TM * KC;      // bf16 per A digit plane per chunk (8 KB)
-constexpr int PLANE_B = TN * KC;      // bf16 per B digit plane per chunk (4 KB)
+
 constexpr int NT = 256;               // threads per CTA (two warps per TMEM lane quarter)
 constexpr int NW = NT / 32;           // warps per CTA
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
@@ -55,8 +56,9 @@ enum Mode { PLAIN = 0, ATOMIC = 1, RLM = 2 };
 struct Args {
   const double* A;
   int64_t M, K, sam, sak;
-  const uint4* Bp;                    // digit planes [nchunk][kchunk][s][PLANE_B]
-  const int* Fmax;                    // biased exponent scale of each B column [nchunks*TN]
+  const uint4* Bp;                    // digit planes [nchunk][kchunk][s][tn*KC]
+  const int* Fmax;                    // biased exponent scale of each B column [nchunks*tn]
+  int tn;                             // tile width (UMMA N): multiple of 16, s*tn <= 512
   int64_t N;
   int kchunks;                        // ceil(K / KC)
   int s;
@@ -178,8 +180,10 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
     m0 = (int64_t)blockIdx.x * TM;
     rows = (int)(a.M - m0 < (int64_t)TM ? a.M - m0 : (int64_t)TM);
   }
-  const uint32_t tcols = (s <= 4) ? 256u : 512u;
-  const size_t buf_bytes = (size_t)s * (PLANE_A + PLANE_B) * 2;
+  const int tn = a.tn;
+  const int plane_b = tn * KC;
+  const uint32_t tcols = (s * tn <= 256) ? 256u : 512u;
+  const size_t buf_bytes = (size_t)s * (PLANE_A + plane_b) * 2;
   unsigned char* bufs[2] = {smem, smem + buf_bytes};
 
   if (warp == 0) {
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   bool ok = true;
 
   // ---- K loop over chunks of 32, double buffered
@@ -286,10 +290,10 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
     }
     // B digit planes of this chunk: a straight copy of s * 4 KB
     {
-      const uint4* src = a.Bp + ((size_t)nc * a.kchunks + (kc0 + c)) * (size_t)s * (PLANE_B / 8);
+      const uint4* src = a.Bp + ((size_t)nc * a.kchunks + (kc0 + c)) * (size_t)s * (plane_b / 8);
       uint4* dst = reinterpret_cast<uint4*>(Bpl);
 #pragma unroll 4
-      for (int e = tid; e < s * (PLANE_B / 8); e += NT) dst[e] = __ldg(src + e);
+      for (int e = tid; e < s * (plane_b / 8); e += NT) dst[e] = __ldg(src + e);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -305,10 +309,10 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
           for (int p = 0; p <= t; ++p) {
             const int q = t - p;
             const uint64_t da = umma_desc(abase + p * PLANE_A * 2 + ks * 2 * (TM / 8) * 128, (TM / 8) * 128, 128);
-            const uint64_t db = umma_desc(bbase + q * PLANE_B * 2 + ks * 2 * (TN / 8) * 128, (TN / 8) * 128, 128);
+            const uint64_t db = umma_desc(bbase + q * plane_b * 2 + ks * 2 * (tn / 8) * 128, (tn / 8) * 128, 128);
             const uint32_t accum = (c == 0 && ks == 0 && p == 0) ? 0u : 1u;
             asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(t * TN)),
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(t * tn)),
                          "l"(da), "l"(db), "r"(idesc), "r"(accum));
           }
         }
@@ -324,68 +328,74 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;");
 
-  // ---- epilogue: warp w reads TMEM lane quarter (w % 4) and column half (w / 4)
+  // ---- epilogue: warp w reads TMEM lane quarter (w % 4); the two warps of a quarter take
+  // alternate 16-column groups.  Partial contractions stage int128 products per 64-column block.
   if (ok && nchunk > 0) {
-    __int128* P = reinterpret_cast<__int128*>(smem);           // [TM][TN] for the slab sums
+    __int128* P = reinterpret_cast<__int128*>(smem);           // [TM][PB] for the slab sums
     const int quarter = warp & 3, half = warp >> 2;
     const int row = quarter * 32 + lane;
-    for (int cgi = 0; cgi < (TN / 16) / (NW / 4); ++cgi) {
-      const int cg = half * ((TN / 16) / (NW / 4)) + cgi;
-      __int128 V[16];
+    const int ngroups = tn / 16;
+    for (int blk0 = 0; blk0 < ngroups; blk0 += PB / 16) {
+      const int blk1 = min(ngroups, blk0 + PB / 16);
+      for (int cg = blk0 + half; cg < blk1; cg += 2) {
+        __int128 V[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) V[j] = 0;
+        for (int j = 0; j < 16; ++j) V[j] = 0;
 #pragma unroll 1
-      for (int t = 0; t < s; ++t) {
-        uint32_t r[16];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * TN + cg * 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int shift = 7 * (s - 1 - t);
+        for (int t = 0; t < s; ++t) {
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * tn + cg * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int shift = 7 * (s - 1 - t);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) V[j] += (__int128)__float2ll_rn(__uint_as_float(r[j])) << shift;
-      }
-      const int64_t n0 = (int64_t)nc * TN + cg * 16;
-      if (MODE != RLM) {
-        if (row < rows) {
-          const int e_row = rowE[row];
+          for (int j = 0; j < 16; ++j) V[j] += (__int128)__float2ll_rn(__uint_as_float(r[j])) << shift;
+        }
+        const int64_t n0 = (int64_t)nc * tn + cg * 16;
+        if (MODE != RLM) {
+          if (row < rows) {
+            const int e_row = rowE[row];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int64_t n = n0 + j;
+              if (n < a.N) {
+                const double out = i128_to_double(V[j], e_row + max(1, a.Fmax[n]) - 2044 - 7 * s - 7);
+                double* cp = a.C + (m0 + row) * a.scm + n * a.scn;
+                if (MODE == ATOMIC) atomicAdd(cp, out);
+                else *cp = out;
+              }
+            }
+          }
+        } else {
+          // weight by the integer sketch entry 2^20 Omega(i, n); summed over i below
+          const int i = row % (int)a.nmode;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int64_t n = n0 + j;
-            if (n < a.N) {
-              const double out = i128_to_double(V[j], e_row + max(1, a.Fmax[n]) - 2044 - 7 * s - 7);
-              double* cp = a.C + (m0 + row) * a.scm + n * a.scn;
-              if (MODE == ATOMIC) atomicAdd(cp, out);
-              else *cp = out;
-            }
+            const int om = (row < rows && n < a.N) ? a.Omint[i * a.ldo + n] : 0;
+            P[row * PB + (cg - blk0) * 16 + j] = V[j] * (__int128)om;
           }
         }
-      } else {
-        // weight by the integer sketch entry 2^20 Omega(i, n); summed over i below
-        const int i = row % (int)a.nmode;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int64_t n = n0 + j;
-          const int om = (row < rows && n < a.N) ? a.Omint[i * a.ldo + n] : 0;
-          P[row * TN + cg * 16 + j] = V[j] * (__int128)om;
-        }
       }
-    }
-    if (MODE == RLM) {
-      __syncthreads();
-      const int nslab = rows / (int)a.nmode;
-      for (int task = tid; task < nslab * TN; task += NT) {
-        const int sl = task / TN, j = task % TN;
-        const int64_t n = (int64_t)nc * TN + j;
-        if (n >= a.N) continue;
-        __int128 acc = 0;
-        for (int ii = 0; ii < (int)a.nmode; ++ii) acc += P[(sl * (int)a.nmode + ii) * TN + j];
-        const int e_slab = rowE[sl * (int)a.nmode];
-        const int64_t aidx = (int64_t)blockIdx.x * a.g + sl;
-        a.W[aidx * a.ldw + n] = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
+      if (MODE == RLM) {
+        __syncthreads();
+        const int nslab = rows / (int)a.nmode;
+        const int bcols = (blk1 - blk0) * 16;
+        for (int task = tid; task < nslab * bcols; task += NT) {
+          const int sl = task / bcols, j = task % bcols;
+          const int64_t n = (int64_t)nc * tn + blk0 * 16 + j;
+          if (n >= a.N) continue;
+          __int128 acc = 0;
+          for (int ii = 0; ii < (int)a.nmode; ++ii) acc += P[(sl * (int)a.nmode + ii) * PB + j];
+          const int e_slab = rowE[sl * (int)a.nmode];
+          const int64_t aidx = (int64_t)blockIdx.x * a.g + sl;
+          a.W[aidx * a.ldw + n] = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
+        }
+        __syncthreads();
       }
     }
   }
@@ -397,56 +407,63 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
 // ---- B operand preparation: column exponent scales, then digit planes in the shared-memory
 // image.  B(k, n) = B[k*sbk + n*sbn], K x N.
 __global__ void __launch_bounds__(256) colmax_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
-                                                       int* Fmax) {
-  // grid (N-chunks, K-chunks of 32 rows); each thread reads 8 rows of one column (all loads in
-  // flight), a warp covers 32 columns; the column maxima go to Fmax (zeroed beforehand) atomically
-  const int nc = blockIdx.x, tid = threadIdx.x;
-  const int j = tid % TN, grp = tid / TN;
-  const int64_t n = (int64_t)nc * TN + j;
-  int e = 1;
-  if (n < N) {
+                                                       int tn, int* Fmax) {
+  // grid (N-chunks, K-chunks of 32 rows); a task reads 8 rows of one column (all loads in flight);
+  // column maxima go to Fmax (zeroed beforehand) atomically
+  const int nc = blockIdx.x;
+  for (int u = threadIdx.x; u < tn * (KC / 8); u += blockDim.x) {
+    const int j = u % tn, grp = u / tn;
+    const int64_t n = (int64_t)nc * tn + j;
+    int e = 1;
+    if (n < N) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t k = (int64_t)blockIdx.y * KC + grp * 8 + q;
+        v[q] = (k < K) ? B[k * sbk + n * sbn] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) e = max(e, exp_field(v[q]));
+    }
+    atomicMax(&Fmax[(int64_t)nc * tn + j], e);
+  }
+}
+
+// One CTA per (tn-column chunk, 32-row K chunk): tasks (column, group of 8 k).
+__global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
+                                                      int s, int tn, int kchunks, const int* Fmax, uint4* planes) {
+  const int nc = blockIdx.x, kcn = blockIdx.y;
+  const int plane_b = tn * KC;
+  uint4* blk = planes + ((size_t)nc * kchunks + kcn) * (size_t)s * (plane_b / 8);
+  for (int u = threadIdx.x; u < tn * (KC / 8); u += blockDim.x) {
+    const int j = u % tn, grp = u / tn;
+    const int64_t n = (int64_t)nc * tn + j;
+    const int E = max(1, Fmax[n]);
     double v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int64_t k = (int64_t)blockIdx.y * KC + grp * 8 + q;
-      v[q] = (k < K) ? B[k * sbk + n * sbn] : 0.0;
+      const int64_t k = (int64_t)kcn * KC + grp * 8 + q;
+      v[q] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0;
     }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) e = max(e, exp_field(v[q]));
+    uint32_t w[MAXS][4];
+    slice8(v, E, s, w);
+    const int idx = ((grp * (tn / 8)) + (j >> 3)) * 8 + (j & 7);      // uint4 index in a plane
+    for (int p = 0; p < s; ++p) blk[(size_t)p * (plane_b / 8) + idx] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
   }
-  atomicMax(&Fmax[(int64_t)nc * TN + j], e);
 }
 
-// One CTA per (64-column chunk, 32-row K chunk): 256 tasks (column, group of 8 k).
-__global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
-                                                      int s, int kchunks, const int* Fmax, uint4* planes) {
-  const int nc = blockIdx.x, kcn = blockIdx.y, u = threadIdx.x;
-  const int j = u % TN, grp = u / TN;
-  const int64_t n = (int64_t)nc * TN + j;
-  const int E = max(1, Fmax[n]);
-  double v[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int64_t k = (int64_t)kcn * KC + grp * 8 + q;
-    v[q] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0;
-  }
-  uint32_t w[MAXS][4];
-  slice8(v, E, s, w);
-  uint4* blk = planes + ((size_t)nc * kchunks + kcn) * (size_t)s * (PLANE_B / 8);
-  const int idx = ((grp * (TN / 8)) + (j >> 3)) * 8 + (j & 7);        // uint4 index in a plane
-  for (int p = 0; p < s; ++p) blk[(size_t)p * (PLANE_B / 8) + idx] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-}
-
-static size_t smem_bytes(int s, int mode) {
-  size_t need = 2 * (size_t)s * (PLANE_A + PLANE_B) * 2;
-  if (mode == RLM) need = std::max(need, (size_t)TM * TN * sizeof(__int128));
-  if (s <= 4) need = std::max<size_t>(need, 100 * 1024);   // at most 2 CTAs per SM: 2 x 256 TMEM columns
+static size_t smem_bytes(int s, int tn, int mode) {
+  size_t need = 2 * (size_t)s * (PLANE_A + tn * KC) * 2;
+  if (mode == RLM) need = std::max(need, (size_t)TM * PB * sizeof(__int128));
+  // TMEM: 2 CTAs per SM only when each takes 256 columns; otherwise shared memory keeps it at 1
+  if (s * tn <= 256) need = std::max<size_t>(need, 100 * 1024);
+  else need = std::max<size_t>(need, 118 * 1024);
   return need + 1024;
 }
 
 template <int MODE, bool AKFAST>
 static int launch(Ctx& c, const Args& a, dim3 grid) {
-  const size_t sm = smem_bytes(a.s, MODE);
+  const size_t sm = smem_bytes(a.s, a.tn, MODE);
   auto kern = sliced_kernel<MODE, AKFAST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
@@ -454,23 +471,31 @@ static int launch(Ctx& c, const Args& a, dim3 grid) {
   return c.check_launch("sliced_kernel");
 }
 
+}  // namespace tc
+int tile_width(int s);
+namespace tc {
+
 struct BPrep {
   uint4* planes = nullptr;
   int* Fmax = nullptr;
-  int nchunks = 0, kchunks = 0;
+  int nchunks = 0, kchunks = 0, tn = 0;
 };
 
 static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int s, BPrep& p) {
-  p.nchunks = (int)((N + TN - 1) / TN);
+  const int tmax = tile_width(s);
+  p.nchunks = (int)((N + tmax - 1) / tmax);
+  // balance the chunks: the narrowest multiple of 16 that still needs only nchunks tiles
+  const int64_t per = (N + p.nchunks - 1) / p.nchunks;
+  p.tn = (int)std::min<int64_t>(tmax, std::max<int64_t>(16, (per + 15) / 16 * 16));
   p.kchunks = (int)((K + KC - 1) / KC);
-  const int64_t npad = (int64_t)p.nchunks * TN;
-  TTR_CHECK(c.alloc(reinterpret_cast<void**>(&p.planes), (size_t)p.nchunks * p.kchunks * s * PLANE_B * 2));
+  const int64_t npad = (int64_t)p.nchunks * p.tn;
+  TTR_CHECK(c.alloc(reinterpret_cast<void**>(&p.planes), (size_t)p.nchunks * p.kchunks * s * p.tn * KC * 2));
   TTR_CHECK(c.alloc_t(&p.Fmax, (size_t)npad));
   TTR_CUDA(cudaMemsetAsync(p.Fmax, 0, sizeof(int) * npad, c.stream));
-  colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, p.Fmax);
+  colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, p.tn, p.Fmax);
   TTR_CHECK(c.check_launch("colmax_b"));
-  slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, s, p.kchunks,
-                                                                                     p.Fmax, p.planes);
+  slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, s, p.tn,
+                                                                                     p.kchunks, p.Fmax, p.planes);
   return c.check_launch("slice_b");
 }
 
@@ -496,6 +521,12 @@ static int zero_region(Ctx& c, double* C, int64_t a, int64_t b, int64_t scm, int
 
 using namespace tc;
 
+// Widest UMMA N whose s per-diagonal accumulators fit the 512 TMEM columns.
+int tile_width(int s) {
+  const int tn = (512 / s) / 16 * 16;
+  return tn > TNMAX ? TNMAX : tn;
+}
+
 // C(i, j) = sum_r X(r, i) Y(r, j) (i < a, j < b) stored at C[i*scm + j*scn]; X, Y row-major m x a, m x b.
 // The big operand X^T is read column-major; the row dimension m is split over CTAs in segments
 // of 256 and partial results are added atomically.
@@ -508,7 +539,7 @@ int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int6
   TTR_CHECK(prep_b(c, Y, ldy, 1, m, b_cols, slices, bp));
   Args a{};
   a.A = X; a.M = a_cols; a.K = m; a.sam = 1; a.sak = ldx;
-  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = b_cols; a.kchunks = bp.kchunks; a.s = slices;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = b_cols; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
   a.C = C; a.scm = scm; a.scn = scn; a.err = c.d_flags;
   const unsigned ksplit = (unsigned)((m + KSEG - 1) / KSEG);
   dim3 grid((unsigned)((a_cols + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
@@ -527,7 +558,7 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
   TTR_CHECK(prep_b(c, Wn, ldw, 1, r1, w, slices, bp));
   Args a{};
   a.A = Xk; a.M = r0 * n; a.K = r1; a.sam = r1; a.sak = 1;
-  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = w; a.kchunks = bp.kchunks; a.s = slices;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = w; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
   a.Omint = Omi; a.ldo = ldoi; a.nmode = n; a.g = (int)(TM / n); a.slabs = r0; a.W = Wout; a.ldw = ldwo;
   a.err = c.d_flags;
   dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, 1);
@@ -542,7 +573,7 @@ int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M
   TTR_CHECK(prep_b(c, B, ldb, 1, K, N, slices, bp));
   Args a{};
   a.A = A; a.M = M; a.K = K; a.sam = lda; a.sak = 1;
-  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = N; a.kchunks = bp.kchunks; a.s = slices;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = N; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
   a.C = C; a.scm = ldc; a.scn = 1; a.err = c.d_flags;
   const unsigned ksplit = (unsigned)((K + KSEG - 1) / KSEG);
   dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
@@ -563,7 +594,7 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
   TTR_CHECK(prep_b(c, Mk, 1, ldm, K, L, slices, bp));
   Args a{};
   a.A = Xn; a.M = ncol; a.K = K; a.sam = 1; a.sak = ncol;
-  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = L; a.kchunks = bp.kchunks; a.s = slices;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = L; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
   a.C = Y; a.scm = 1; a.scn = ncol; a.err = c.d_flags;
   const unsigned ksplit = (unsigned)((K + KSEG - 1) / KSEG);
   dim3 grid((unsigned)((ncol + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
