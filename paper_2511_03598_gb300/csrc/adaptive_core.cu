@@ -11,9 +11,10 @@
 // barrier instead of kernel launches; the stopping decision is taken on the device, and the
 // host synchronizes once per core.
 //
-// Reductions over rows (Gram matrices, Q^T S) go through per-CTA partials: small ones (b x b) are
-// summed redundantly by every CTA (no second barrier); larger ones (c x b) are summed in slices,
-// one slice per CTA, then read back by all.  CholeskyQR2 needs one barrier per pass.
+// Reductions over rows (Gram matrices, Q^T S, sums of squares) are FP64 atomic additions of
+// per-CTA partials into one of three rotating accumulation buffers; after the barrier that
+// completes reduction i, every CTA reads buffer i % 3 and CTA 0 zeroes buffer (i + 2) % 3, which
+// no CTA touches again before the next barrier.  One barrier per reduction.
 //
 // The grid barrier is a counter/generation pair with a bounded spin: a wait that runs out sets
 // the error flag and the kernel returns (the host reports TTR_ERR_TIMEOUT).
