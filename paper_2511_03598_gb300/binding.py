@@ -65,8 +65,9 @@ def lib():
         L.ttr_last_error.restype = ctypes.c_char_p
         L.ttr_sketch_omega.argtypes = [u64, i32, i64, i64, i64, vp, vp]
         L.ttr_partial_contractions.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, i32, i32, PP, vp]
+        L.ttr_partial_contractions_noalloc.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, PP, vp]
         for f in ("tt_round_fixed", "tt_round_adaptive", "tt_round_deterministic", "ttr_sketch_omega",
-                  "ttr_partial_contractions"):
+                  "ttr_partial_contractions", "ttr_partial_contractions_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -240,6 +241,22 @@ def partial_contractions(cores, seed: int, col0: int, col1: int, t: int = 2, pre
     ptrs = (ctypes.c_void_p * d)(*[bufs[k + 1].data_ptr() if (k + 1) in bufs else 0 for k in range(d)])
     _check(lib().ttr_partial_contractions(d, n, r, p, ctypes.c_uint64(seed), col0, col1, t, precision, slices, ptrs,
                                           _stream_handle(stream)))
+    return bufs
+
+
+def partial_contractions_noalloc(cores, seed: int, col0: int, col1: int, t: int = 2, out: dict | None = None,
+                                 stream=None) -> dict:
+    """FP64 Algorithm 3 through ttr_partial_contractions_noalloc: the library allocates no device
+    memory (its scratch is a fixed static array); the outputs {k: W_k} are the caller's, given in
+    `out` or created here.  Enqueued on `stream` without synchronizing."""
+    import torch
+    d, n, r, p = _tt_args(cores)
+    w = col1 - col0
+    bufs = out if out is not None else {k: torch.empty((r[k - 1], w), dtype=torch.float64, device="cuda")
+                                        for k in range(t, d + 1)}
+    ptrs = (ctypes.c_void_p * d)(*[bufs[k + 1].data_ptr() if (k + 1) in bufs else 0 for k in range(d)])
+    _check(lib().ttr_partial_contractions_noalloc(d, n, r, p, ctypes.c_uint64(seed), col0, col1, t, ptrs,
+                                                  _stream_handle(stream)))
     return bufs
 
 

@@ -360,6 +360,19 @@ int omega_fill(Ctx& c, uint64_t seed, int32_t k_lo, int32_t k_hi, const int64_t*
   return c.check_launch("omega_fill");
 }
 
+// As omega_fill, with the mode sizes n_k (k = k_lo..k_lo+nc-1) already in device memory and
+// their maximum given: allocates nothing and copies nothing.
+int omega_fill_dev(Ctx& c, uint64_t seed, int32_t k_lo, int32_t nc, const int64_t* nk_dev, int64_t nmax,
+                   int64_t col0, int64_t col1, double* dst, int64_t ostride, int64_t ld) {
+  const int64_t w = col1 - col0;
+  if (nc <= 0 || w <= 0) return TTR_OK;
+  const int64_t per = nmax * w;
+  unsigned bx = (unsigned)((per + 255) / 256);
+  if (bx > 1024) bx = 1024;
+  omega_kernel<<<dim3(bx, nc), 256, 0, c.stream>>>(seed, k_lo, nk_dev, col0, w, dst, nullptr, ostride, ld);
+  return c.check_launch("omega_fill");
+}
+
 // ----------------------------------------------------------------------------- Omega reduction
 __global__ void omega_reduce_kernel(const double* T, int64_t ldt, const double* Om, int64_t ldo, int64_t r0,
                                     int64_t n, int64_t w, double* W, int64_t ldw) {
