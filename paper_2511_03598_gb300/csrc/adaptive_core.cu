@@ -51,7 +51,26 @@ struct Args {
   // outputs
   double* est_out;      // estimates in order
   int* io;              // [0] status, [1] cc, [2] number of estimates
+  unsigned long long* prof;   // optional: SM cycles per phase, seen by CTA 0 (null: off)
 };
+
+// Phase timer of CTA 0 (launch-timeline profiling only): cycles since the previous mark are
+// added to prof[phase]; prof[PH_BARRIER] collects the cycles spent waiting in grid barriers.
+enum Phase { PH_STAGE = 0, PH_FIRST_QR, PH_RESIDUAL, PH_ESTIMATE, PH_QR1, PH_REORTH, PH_QR2, PH_FINISH, PH_BARRIER,
+             PH_COUNT };
+struct Timer {
+  unsigned long long* p;
+  long long t;
+  __device__ void mark(int phase) {
+    if (p && blockIdx.x == 0 && threadIdx.x == 0) {
+      const long long n = clock64();
+      atomicAdd(p + phase, (unsigned long long)(n - t));
+      t = n;
+    }
+  }
+};
+// the CTA's copy of Args::prof, for grid_sync
+__shared__ unsigned long long* s_barrier_prof;
 
 constexpr int ACC = 8192;                         // doubles per accumulation buffer (>= rbar * BMAX)
 
@@ -78,6 +97,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
         }
         __nanosleep(20);
       }
+      if (s_barrier_prof) atomicAdd(s_barrier_prof + PH_BARRIER, (unsigned long long)(clock64() - t0));
     }
     __threadfence();
   }
@@ -119,14 +139,16 @@ __device__ __forceinline__ void red_advance(Red& r) {
 __device__ void gram_acc(const double* X, int ldx, const double* Y, int ldy, int a, int b, int nr, double* buf) {
   for (int o = threadIdx.x; o < a * b; o += NT) {
     const int i = o / b, j = o % b;
-    double s0 = 0.0, s1 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;      // four independent chains
     int r = 0;
-    for (; r + 1 < nr; r += 2) {
+    for (; r + 3 < nr; r += 4) {
       s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
       s1 = fma(X[(r + 1) * ldx + i], Y[(r + 1) * ldy + j], s1);
+      s2 = fma(X[(r + 2) * ldx + i], Y[(r + 2) * ldy + j], s2);
+      s3 = fma(X[(r + 3) * ldx + i], Y[(r + 3) * ldy + j], s3);
     }
-    if (r < nr) s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
-    if (nr > 0) atomicAdd(buf + o, s0 + s1);
+    for (; r < nr; ++r) s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
+    if (nr > 0) atomicAdd(buf + o, (s0 + s1) + (s2 + s3));
   }
 }
 
@@ -155,71 +177,110 @@ __device__ void read_totals(const double* buf, int n, double* dst) {
   __syncthreads();
 }
 
-// In shared memory: G (b x b) -> upper R (G = R^T R) and 1/diag(R), by warp 0 (lane = column).
+// ---- small dense factorization, shaped for this part's FP64 unit: a dependent FP64 operation
+// costs ~64 cycles whatever the number of active lanes, so the critical path is kept to two FP64
+// operations per column and every scaling by a power of two is done on the exponent bits.
+
+// x * 2^k, exact; integer exponent arithmetic unless x is zero, subnormal, non-finite or the
+// result leaves the normal range.
+__device__ __forceinline__ double mul_pow2(double x, int k) {
+  const long long xb = __double_as_longlong(x);
+  const int ef = (int)((xb >> 52) & 0x7FF);
+  if (ef != 0 && ef != 0x7FF && ef + k > 0 && ef + k < 0x7FF) return __longlong_as_double(xb + (long long)k * (1LL << 52));
+  if ((xb << 1) == 0) return x;
+  return ldexp(x, k);
+}
+
+// 1/sqrt(y) for positive, finite y to full double precision: y = m 2^(2h) with m in [1, 4), a
+// binary32 seed for 1/sqrt(m) (MUFU, ~22 bits; the bit patterns are moved by integer operations),
+// then one third-order correction r (1 + e/2 + 3e^2/8), e = 1 - m r^2 (error ~ e^3 / 3).
+__device__ __forceinline__ double rsqrt_full(double y) {
+  const long long yb = __double_as_longlong(y);
+  const int ef = (int)((yb >> 52) & 0x7FF);
+  if (ef == 0) return 1.0 / sqrt(y);                       // subnormal: rare, slow path
+  const int h = (ef - 1023) >> 1;                           // floor((e) / 2)
+  const double m = __longlong_as_double(yb - (long long)(2 * h) * (1LL << 52));        // in [1, 4)
+  const long long mb = __double_as_longlong(m);
+  const int mf = (int)(((((mb >> 52) & 0x7FF) - 1023 + 127) << 23) | (int)((mb >> 29) & 0x7FFFFF));
+  const float r0f = rsqrtf(__int_as_float(mf));             // in (0.5, 1]
+  const int rb = __float_as_int(r0f);
+  const double r0 = __longlong_as_double(((long long)(((rb >> 23) & 0xFF) - 127 + 1023) << 52) |
+                                         ((long long)(rb & 0x7FFFFF) << 29));
+  const double e = fma(-m * r0, r0, 1.0);
+  const double r1 = fma(r0 * e, fma(e, 0.375, 0.5), r0);
+  return __longlong_as_double(__double_as_longlong(r1) - (long long)h * (1LL << 52));
+}
+
+// G (b x b, shared, symmetric positive definite) -> Ri = R^{-1} (b x b upper, shared) with
+// G = R^T R.  Gauss-Jordan elimination of [G | I] (LDL^T with L^{-1} built alongside) without
+// divisions: step j replaces row p > j by d'_j row_p - G_pj 2^(-e_j) row_j, where the pivot
+// d_j = d'_j 2^(e_j), d'_j in [1, 2).  Row p then holds s_p = prod_{j<p} d'_j times the row of the
+// ordinary elimination, so with D the pivots and L^{-1} the right block,
+//   R^{-1}(i, j) = L^{-1}(j, i) / sqrt(D_j) = M(j, b + i) / sqrt(M(j, j) s_j).
+// Critical path per column: one FP64 product and one FMA.  Scratch M: b x 2b, sc: b + 1.
 // Every CTA computes the same factor from the same data, so all take the same branch.
-__device__ bool chol_small(double* G, int b, double* invd, double* Ri) {
+__device__ bool factor_small(const double* G, int b, double* Ri, double* M, double* sc) {
   __shared__ int fail;
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    int bad = 0;
-    for (int j = 0; j < b; ++j) {
-      double v = (lane >= j && lane < b) ? G[j * b + lane] : 0.0;
-      for (int p = 0; p < j; ++p) v -= G[p * b + j] * ((lane < b) ? G[p * b + lane] : 0.0);
-      const double dj = __shfl_sync(0xffffffffu, v, j);
-      const double dd = (dj > 0.0 && isfinite(dj)) ? dj : 1.0;
-      bad |= !(dj > 0.0 && isfinite(dj));
-      // 1/sqrt(dd): binary32 seed (~23 bits) and two Newton steps r <- r (3 - dd r^2) / 2 in FP64
-      // (quadratic convergence: ~46, then ~92 bits), instead of FP64 sqrt and divide, which are
-      // long dependent instruction sequences on this part.
-      // (dd is first split as mnt * 2^e with e even and mnt in [0.5, 2), so the binary32 seed never
-      // under- or overflows whatever the scale of the input)
-      int ex = 0;
-      double mnt = frexp(dd, &ex);
-      if (ex & 1) {
-        mnt *= 2.0;
-        ex -= 1;
-      }
-      double inv = (double)rsqrtf((float)mnt);
-      inv = inv * fma(-0.5 * mnt, inv * inv, 1.5);
-      inv = inv * fma(-0.5 * mnt, inv * inv, 1.5);
-      inv = ldexp(inv, -ex / 2);
-      const double piv = dd * inv;
-      if (lane == j) {
-        G[j * b + j] = piv;
-        invd[j] = inv;
-      } else if (lane > j && lane < b) {
-        G[j * b + lane] = v * inv;
-      }
-      __syncwarp();
-    }
-    __syncwarp();
-    // R^{-1} (upper) by back substitution, lane j computes column j:
-    //   Ri[j][j] = 1/R_jj;  Ri[i][j] = -(sum_{p=i+1..j} R[i][p] Ri[p][j]) / R_ii for i < j
-    if (lane < b) {
-      const int j = lane;
-      for (int i = 0; i < b; ++i) Ri[i * b + j] = 0.0;
-      Ri[j * b + j] = invd[j];
-      for (int i = j - 1; i >= 0; --i) {
-        double v = 0.0;
-        for (int p2 = i + 1; p2 <= j; ++p2) v = fma(G[i * b + p2], Ri[p2 * b + j], v);
-        Ri[i * b + j] = -v * invd[i];
-      }
-    }
-    if (lane == 0) fail = bad;
+  const int w2 = 2 * b;
+  for (int e = threadIdx.x; e < b * w2; e += NT) {
+    const int p = e / w2, q = e % w2;
+    M[e] = (q < b) ? G[p * b + q] : ((q - b == p) ? 1.0 : 0.0);
+  }
+  if (threadIdx.x == 0) {
+    fail = 0;
+    sc[0] = 1.0;
   }
   __syncthreads();
-  return fail == 0;
+  for (int j = 0; j < b; ++j) {
+    const double d = M[j * w2 + j];
+    const long long dbits = __double_as_longlong(d);
+    const int ef = (int)((dbits >> 52) & 0x7FF);
+    if (!(d > 0.0) || ef == 0 || ef == 0x7FF) {             // same value in every thread
+      if (threadIdx.x == 0) fail = 1;
+      break;
+    }
+    const int ej = ef - 1023;
+    const double dp = __longlong_as_double((dbits & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+    if (threadIdx.x == 0) sc[j + 1] = sc[j] * dp;
+    for (int e = threadIdx.x; e < b * w2; e += NT) {
+      const int p = e / w2, q = e % w2;
+      if (p <= j) continue;
+      // left block: columns > j; right block (L^{-1}, lower): columns <= j and the diagonal
+      if (q < b ? (q <= j) : (q - b > j && q - b != p)) continue;
+      M[e] = fma(dp, M[e], -M[p * w2 + j] * mul_pow2(M[j * w2 + q], -ej));
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (fail) return false;
+  for (int e = threadIdx.x; e < b * b; e += NT) {
+    const int i = e / b, j = e % b;
+    double v = 0.0;
+    if (i <= j) {
+      const double y = M[j * w2 + j] * sc[j];
+      v = (y > 0.0 && isfinite(y)) ? M[j * w2 + b + i] * rsqrt_full(y) : 0.0;
+    }
+    Ri[e] = v;
+  }
+  __syncthreads();
+  return true;
 }
 
 // own rows of X (b columns, shared memory) <- X R^{-1}, one thread per (row, column):
-// out(r, j) = sum_{i <= j} X(r, i) Ri(i, j), staged through T and written back after a barrier.
+// out(r, j) = sum_{i <= j} X(r, i) Ri(i, j) in two interleaved partial sums, staged through T and
+// written back after a barrier.
 __device__ void apply_rinv(double* X, int ldx, int b, const double* Ri, int nr, double* T) {
   for (int e = threadIdx.x; e < nr * b; e += NT) {
     const int r = e / b, j = e % b;
     const double* xr = X + r * ldx;
-    double v = 0.0;
-    for (int i = 0; i <= j; ++i) v = fma(xr[i], Ri[i * b + j], v);
-    T[e] = v;
+    double v0 = 0.0, v1 = 0.0;
+    int i = 0;
+    for (; i + 1 <= j; i += 2) {
+      v0 = fma(xr[i], Ri[i * b + j], v0);
+      v1 = fma(xr[i + 1], Ri[(i + 1) * b + j], v1);
+    }
+    if (i <= j) v0 = fma(xr[i], Ri[i * b + j], v0);
+    T[e] = v0 + v1;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * b; e += NT) X[(e / b) * ldx + e % b] = T[e];
@@ -233,7 +294,8 @@ __device__ bool cholqr(double* X, int ldx, int b, int nr, int npass, Red& rd, un
                        double* T, const double* pre_gram = nullptr) {
   __shared__ double G[BMAX * BMAX];
   __shared__ double Ri[BMAX * BMAX];
-  __shared__ double invd[BMAX];
+  __shared__ double M[BMAX * 2 * BMAX];
+  __shared__ double sc[BMAX + 1];
   for (int pass = 0; pass < npass; ++pass) {
     if (pass == 0 && pre_gram) {
       read_totals(pre_gram, b * b, G);
@@ -247,7 +309,7 @@ __device__ bool cholqr(double* X, int ldx, int b, int nr, int npass, Red& rd, un
       red_advance(rd);
       read_totals(buf, b * b, G);
     }
-    if (!chol_small(G, b, invd, Ri)) return false;
+    if (!factor_small(G, b, Ri, M, sc)) return false;
     apply_rinv(X, ldx, b, Ri, nr, T);
   }
   return true;
@@ -267,18 +329,20 @@ __device__ bool project_out(const double* Q, int ldq, int c, double* X, int ldx,
   for (int e = threadIdx.x; e < nr * b; e += NT) {
     const int r = e / b, j = e % b;
     const double* qr = Q + r * ldq;
-    double s0 = 0.0, s1 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;      // four independent chains
     int i = 0;
     if (in_smem) {
-      for (; i + 1 < c; i += 2) {
+      for (; i + 3 < c; i += 4) {
         s0 = fma(qr[i], Ps[i * b + j], s0);
         s1 = fma(qr[i + 1], Ps[(i + 1) * b + j], s1);
+        s2 = fma(qr[i + 2], Ps[(i + 2) * b + j], s2);
+        s3 = fma(qr[i + 3], Ps[(i + 3) * b + j], s3);
       }
-      if (i < c) s0 = fma(qr[i], Ps[i * b + j], s0);
+      for (; i < c; ++i) s0 = fma(qr[i], Ps[i * b + j], s0);
     } else {
       for (; i < c; ++i) s0 = fma(qr[i], __ldcg(buf + i * b + j), s0);
     }
-    X[r * ldx + j] -= s0 + s1;
+    X[r * ldx + j] -= (s0 + s1) + (s2 + s3);
   }
   __syncthreads();
   return true;
@@ -298,14 +362,18 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   int cc = a.cc0;
   int nest = 0;
   Red rd{a.acc, 0, a.acc_used};
+  Timer tmr{a.prof, clock64()};
+  if (threadIdx.x == 0) s_barrier_prof = (blockIdx.x == 0) ? a.prof : nullptr;
   // stage the own rows: sketch columns, and the part of Q that is already final
   for (int e = threadIdx.x; e < nr * ldw; e += NT) Ss[e] = a.Sall[(lo + e / ldw) * a.lds + e % ldw];
   for (int e = threadIdx.x; e < nr * cc; e += NT) Qs[(e / cc) * ldq + e % cc] = a.Q[(lo + e / cc) * a.ldq + e % cc];
   __syncthreads();
+  tmr.mark(PH_STAGE);
   auto finish = [&](int status) {
     // write back Q(:, 0:cc) (plus the residual block, which the host needs after a breakdown)
     for (int e = threadIdx.x; e < nr * cc; e += NT) a.Q[(lo + e / cc) * a.ldq + e % cc] = Qs[(e / cc) * ldq + e % cc];
     for (int e = threadIdx.x; e < nr * a.bi; e += NT) a.S[(lo + e / a.bi) * a.bi + e % a.bi] = Rs[e];
+    tmr.mark(PH_FINISH);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.io[0] = timeout ? ST_TIMEOUT : status;
       a.io[1] = cc;
@@ -318,6 +386,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     __syncthreads();
     if (!cholqr(Qs, ldq, a.b0, nr, 2, rd, a.bar, a.err, &timeout, Tb)) return finish(ST_BREAKDOWN);
     cc = a.b0;
+    tmr.mark(PH_FIRST_QR);
   }
   __shared__ double est_s;
   while (cc < a.rbar) {
@@ -329,6 +398,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
       timeout = true;
       return finish(ST_TIMEOUT);
     }
+    tmr.mark(PH_RESIDUAL);
     // one reduction for both the residual norm and the Gram matrix of the candidate block
     // S(:, 0:bb), which is the first CholeskyQR pass of Q_new if the loop continues
     const int bb = min(a.bi, a.rbar - cc);
@@ -345,19 +415,24 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     const double ss = est_s;                               // ||S||_F^2
     if (blockIdx.x == 0 && threadIdx.x == 0) a.est_out[nest] = ss;   // the host takes sqrt(ss / b_inc)
     ++nest;
+    tmr.mark(PH_ESTIMATE);
     // est = sqrt(ss / b_inc) > tau  <=>  ss > tau^2 b_inc  (the square root is left to the host)
     if (!(ss > a.tau * a.tau * (double)a.bi)) return finish(ST_DONE);
-    // new directions: Q_new = qr(S(:, 0:bb)) (one CholeskyQR pass), re-orthogonalized against Q,
-    // then CholeskyQR2 for an orthonormal basis
+    // new directions (Algorithm 6): Q_new = qr(S(:, 0:bb)), re-orthogonalized against Q, qr again;
+    // each qr is one CholeskyQR pass, so the pair is CholeskyQR2 with the block Gram-Schmidt step
+    // in between (the first pass leaves Q_new orthonormal to ~u cond(S)^2, the second to ~u)
     double* Qn = Qs + cc;
     for (int e = threadIdx.x; e < nr * bb; e += NT) Qn[(e / bb) * ldq + e % bb] = Rs[(e / bb) * a.bi + e % bb];
     __syncthreads();
     if (!cholqr(Qn, ldq, bb, nr, 1, rd, a.bar, a.err, &timeout, Tb, eb + 1)) return finish(ST_BREAKDOWN);
+    tmr.mark(PH_QR1);
     if (!project_out(Qs, ldq, cc, Qn, ldq, bb, nr, rd, a.bar, a.err)) {
       timeout = true;
       return finish(ST_TIMEOUT);
     }
-    if (!cholqr(Qn, ldq, bb, nr, 2, rd, a.bar, a.err, &timeout, Tb)) return finish(ST_BREAKDOWN);
+    tmr.mark(PH_REORTH);
+    if (!cholqr(Qn, ldq, bb, nr, 1, rd, a.bar, a.err, &timeout, Tb)) return finish(ST_BREAKDOWN);
+    tmr.mark(PH_QR2);
     cc += bb;
   }
   finish(ST_DONE);
@@ -383,7 +458,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const int rpc = (int)((m + nblocks - 1) / nblocks);
   const int64_t qcols = rbar;
   const size_t dyn = sizeof(double) * (size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX);
-  const size_t static_bytes = 36 * 1024;   // G, R^{-1}, invd, P staging, reductions (about 33 KB)
+  const size_t static_bytes = 52 * 1024;   // G, R^{-1}, [G | I], P staging, reductions (about 49 KB)
   if (dyn + static_bytes > (size_t)smem_optin) return TTR_ERR_UNSUPPORTED;
   TTR_CUDA(cudaFuncSetAttribute(ac::adaptive_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int per_sm = 0;
@@ -405,6 +480,13 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;
   a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.rbar = rbar; a.width = width; a.cc0 = cc0; a.tau = tau;
   a.bar = c.ac_bar; a.err = c.d_flags; a.est_out = est_out; a.io = c.ac_io;
+  if (c.profiling) {
+    if (!c.ac_prof) {
+      TTR_CHECK(c.alloc_t(&c.ac_prof, ac::PH_COUNT));
+      TTR_CUDA(cudaMemsetAsync(c.ac_prof, 0, sizeof(unsigned long long) * ac::PH_COUNT, c.stream));
+    }
+    a.prof = c.ac_prof;
+  }
   void* params[] = {&a};
   TTR_CUDA(cudaLaunchCooperativeKernel((const void*)ac::adaptive_core_kernel, dim3(nblocks), dim3(ac::NT), params, dyn,
                                        c.stream));

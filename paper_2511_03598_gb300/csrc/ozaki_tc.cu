@@ -43,11 +43,11 @@ constexpr int TM = 128;               // rows per tile = UMMA M
 constexpr int TNMAX = 256;            // largest UMMA N; the tile width tn is chosen per call
 constexpr int PB = 64;                // partial-contraction epilogue: columns per staging block
 constexpr int KC = 32;                // K per shared-memory chunk (two UMMA K-steps of 16)
-constexpr int KSEG = 256;             // K per CTA: bound for exact FP32 accumulation
+constexpr int KSEG = 256;             // largest K per CTA: bound for exact FP32 accumulation
 constexpr int MAXS = 8;               // slices per operand
 constexpr int PLANE_A = TM * KC;      // bf16 per A digit plane per chunk (8 KB)
 
-constexpr int NT = 256;               // threads per CTA (two warps per TMEM lane quarter)
+constexpr int NT = 512;               // threads per CTA (four warps per TMEM lane quarter)
 constexpr int NW = NT / 32;           // warps per CTA
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -72,6 +72,8 @@ struct Args {
   int64_t slabs;                      // r_{k-1}
   double* W;
   int64_t ldw;
+  int watomic;                        // partial contractions split over K: add into W atomically
+  int kseg;                           // K per CTA (multiple of KC, <= KSEG); blockIdx.z selects the segment
   int* err;
 };
 
@@ -150,6 +152,15 @@ __device__ __forceinline__ double i128_to_double(__int128 V, int X) {
   return __longlong_as_double((long long)(sign | ((uint64_t)field << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// Integer value of an integer-valued binary32 with |x| < 2^31, by integer operations only (the
+// hardware float-to-int64 conversion runs on the FP64 pipe of this part, ~64x slower).
+__device__ __forceinline__ int f2i_exact(uint32_t fb) {
+  const int ex = (int)((fb >> 23) & 0xFFu) - 150;          // |x| = mant * 2^ex
+  const int mant = (int)((fb & 0x7FFFFFu) | 0x800000u);
+  const int v = (ex >= 0) ? (mant << ex) : (ex > -24 ? (mant >> -ex) : 0);
+  return (fb >> 31) ? -v : v;
+}
+
 __device__ __forceinline__ int exp_field(double x) {
   return (int)(((uint64_t)__double_as_longlong(x) >> 52) & 0x7FF);
 }
@@ -164,8 +175,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s = a.s;
   const int nc = blockIdx.y;
-  const int64_t kseg0 = (int64_t)blockIdx.z * KSEG;
-  const int kseg_len = (int)(a.K - kseg0 < (int64_t)KSEG ? a.K - kseg0 : (int64_t)KSEG);
+  const int64_t kseg0 = (int64_t)blockIdx.z * a.kseg;
+  const int kseg_len = (int)(a.K - kseg0 < (int64_t)a.kseg ? a.K - kseg0 : (int64_t)a.kseg);
   const int nchunk = (kseg_len + KC - 1) / KC;
   const int kc0 = (int)(kseg0 / KC);
   // rows of this tile
@@ -332,15 +343,17 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   // alternate 16-column groups.  Partial contractions stage int128 products per 64-column block.
   if (ok && nchunk > 0) {
     __int128* P = reinterpret_cast<__int128*>(smem);           // [TM][PB] for the slab sums
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, half = warp >> 2;          // NW / 4 warps share a lane quarter
     const int row = quarter * 32 + lane;
     const int ngroups = tn / 16;
     for (int blk0 = 0; blk0 < ngroups; blk0 += PB / 16) {
       const int blk1 = min(ngroups, blk0 + PB / 16);
-      for (int cg = blk0 + half; cg < blk1; cg += 2) {
-        __int128 V[16];
+      for (int cg = blk0 + half; cg < blk1; cg += NW / 4) {
+        // V = sum_t acc_t 2^(7(s-1-t)) = Vh 2^35 + Vl, both parts in 64 bits: |acc_t| < 2^25, so
+        // Vl (shifts 0..28) < 2^56 and Vh (shifts 35..49, less 35) < 2^41
+        long long Vh[16], Vl[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) V[j] = 0;
+        for (int j = 0; j < 16; ++j) Vh[j] = Vl[j] = 0;
 #pragma unroll 1
         for (int t = 0; t < s; ++t) {
           uint32_t r[16];
@@ -352,9 +365,19 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           const int shift = 7 * (s - 1 - t);
+          if (shift >= 35) {
+            const long long mul = 1LL << (shift - 35);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) V[j] += (__int128)__float2ll_rn(__uint_as_float(r[j])) << shift;
+            for (int j = 0; j < 16; ++j) Vh[j] += (long long)f2i_exact(r[j]) * mul;
+          } else {
+            const long long mul = 1LL << shift;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) Vl[j] += (long long)f2i_exact(r[j]) * mul;
+          }
         }
+        __int128 V[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) V[j] = (__int128)Vh[j] * ((__int128)1 << 35) + (__int128)Vl[j];
         const int64_t n0 = (int64_t)nc * tn + cg * 16;
         if (MODE != RLM) {
           if (row < rows) {
@@ -393,7 +416,9 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
           for (int ii = 0; ii < (int)a.nmode; ++ii) acc += P[(sl * (int)a.nmode + ii) * PB + j];
           const int e_slab = rowE[sl * (int)a.nmode];
           const int64_t aidx = (int64_t)blockIdx.x * a.g + sl;
-          a.W[aidx * a.ldw + n] = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
+          const double out = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
+          if (a.watomic) atomicAdd(a.W + aidx * a.ldw + n, out);
+          else a.W[aidx * a.ldw + n] = out;
         }
         __syncthreads();
       }
@@ -462,13 +487,13 @@ static size_t smem_bytes(int s, int tn, int mode) {
 }
 
 template <int MODE, bool AKFAST>
-static int launch(Ctx& c, const Args& a, dim3 grid) {
+static int launch(Ctx& c, const Args& a, dim3 grid, const char* name) {
   const size_t sm = smem_bytes(a.s, a.tn, MODE);
   auto kern = sliced_kernel<MODE, AKFAST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
   kern<<<grid, NT, sm, c.stream>>>(a);
-  return c.check_launch("sliced_kernel");
+  return c.check_launch(name);
 }
 
 }  // namespace tc
@@ -497,6 +522,17 @@ static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, 
   slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, s, p.tn,
                                                                                      p.kchunks, p.Fmax, p.planes);
   return c.check_launch("slice_b");
+}
+
+// K per CTA for `tiles` output tiles: the fewest K-chunks per CTA that keep the grid within one
+// wave (one CTA per SM: the shared memory and TMEM of a CTA fill an SM), at most KSEG.
+static int kseg_for(int64_t tiles, int64_t K) {
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t kch = (K + KC - 1) / KC;
+  for (int cp = 1; cp < KSEG / KC; ++cp)
+    if (cp >= kch || tiles * ((kch + cp - 1) / cp) <= nsm) return cp * KC;
+  return KSEG;
 }
 
 static int ensure_err(Ctx& c) {
@@ -541,18 +577,20 @@ int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int6
   a.A = X; a.M = a_cols; a.K = m; a.sam = 1; a.sak = ldx;
   a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = b_cols; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
   a.C = C; a.scm = scm; a.scn = scn; a.err = c.d_flags;
-  const unsigned ksplit = (unsigned)((m + KSEG - 1) / KSEG);
+  const int64_t tiles = (a_cols + TM - 1) / TM * bp.nchunks;
+  a.kseg = kseg_for(tiles, m);
+  const unsigned ksplit = (unsigned)((m + a.kseg - 1) / a.kseg);
   dim3 grid((unsigned)((a_cols + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
   if (ksplit > 1) {
     TTR_CHECK(zero_region(c, C, a_cols, b_cols, scm, scn));
-    return launch<ATOMIC, false>(c, a, grid);
+    return launch<ATOMIC, false>(c, a, grid, "tc_gemm_tn");
   }
-  return launch<PLAIN, false>(c, a, grid);
+  return launch<PLAIN, false>(c, a, grid, "tc_gemm_tn");
 }
 
 int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
                const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo) {
-  if (n > TM || r1 > KSEG || slices < 3 || slices > MAXS || !Omi) return TTR_ERR_UNSUPPORTED;
+  if (n > TM || slices < 3 || slices > MAXS || !Omi) return TTR_ERR_UNSUPPORTED;
   TTR_CHECK(ensure_err(c));
   BPrep bp;
   TTR_CHECK(prep_b(c, Wn, ldw, 1, r1, w, slices, bp));
@@ -561,8 +599,15 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
   a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = w; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
   a.Omint = Omi; a.ldo = ldoi; a.nmode = n; a.g = (int)(TM / n); a.slabs = r0; a.W = Wout; a.ldw = ldwo;
   a.err = c.d_flags;
-  dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, 1);
-  return launch<RLM, true>(c, a, grid);
+  const int64_t tiles = (r0 + a.g - 1) / a.g * bp.nchunks;
+  a.kseg = kseg_for(tiles, r1);
+  const unsigned ksplit = (unsigned)((r1 + a.kseg - 1) / a.kseg);
+  if (ksplit > 1) {
+    a.watomic = 1;
+    TTR_CUDA(cudaMemset2DAsync(Wout, ldwo * sizeof(double), 0, w * sizeof(double), r0, c.stream));
+  }
+  dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, ksplit);
+  return launch<RLM, true>(c, a, grid, "tc_rl_step");
 }
 
 int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
@@ -575,13 +620,15 @@ int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M
   a.A = A; a.M = M; a.K = K; a.sam = lda; a.sak = 1;
   a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = N; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
   a.C = C; a.scm = ldc; a.scn = 1; a.err = c.d_flags;
-  const unsigned ksplit = (unsigned)((K + KSEG - 1) / KSEG);
+  const int64_t tiles = (M + TM - 1) / TM * bp.nchunks;
+  a.kseg = kseg_for(tiles, K);
+  const unsigned ksplit = (unsigned)((K + a.kseg - 1) / a.kseg);
   dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
   if (ksplit > 1) {
     TTR_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, N * sizeof(double), M, c.stream));
-    return launch<ATOMIC, true>(c, a, grid);
+    return launch<ATOMIC, true>(c, a, grid, "tc_sketch");
   }
-  return launch<PLAIN, true>(c, a, grid);
+  return launch<PLAIN, true>(c, a, grid, "tc_sketch");
 }
 
 // Y = Mk (L x K, row-major ldm) @ H(X_{k+1}) (K x ncol, row-major), computed as
@@ -596,13 +643,15 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
   a.A = Xn; a.M = ncol; a.K = K; a.sam = 1; a.sak = ncol;
   a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = L; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
   a.C = Y; a.scm = 1; a.scn = ncol; a.err = c.d_flags;
-  const unsigned ksplit = (unsigned)((K + KSEG - 1) / KSEG);
+  const int64_t tiles = (ncol + TM - 1) / TM * bp.nchunks;
+  a.kseg = kseg_for(tiles, K);
+  const unsigned ksplit = (unsigned)((K + a.kseg - 1) / a.kseg);
   dim3 grid((unsigned)((ncol + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
   if (ksplit > 1) {
     TTR_CUDA(cudaMemsetAsync(Y, 0, (size_t)L * ncol * sizeof(double), c.stream));
-    return launch<ATOMIC, false>(c, a, grid);
+    return launch<ATOMIC, false>(c, a, grid, "tc_project");
   }
-  return launch<PLAIN, false>(c, a, grid);
+  return launch<PLAIN, false>(c, a, grid, "tc_project");
 }
 
 }  // namespace ttr

@@ -43,6 +43,7 @@ struct Ctx {
   double* ac_red = nullptr;        // adaptive_core: reduced projection coefficients
   unsigned* ac_bar = nullptr;      // adaptive_core: grid barrier counter/generation
   int* ac_io = nullptr;            // adaptive_core: status, column count, estimate count
+  unsigned long long* ac_prof = nullptr;   // adaptive_core phase cycles (profiling only)
   int workspace();
 
   // optional launch timeline (environment TTR_PROFILE=1): an event after every launch; the time

@@ -47,7 +47,9 @@ def test_omega_bitwise(B, seed, k, n, c0, c1):
 
 # ------------------------------------------------------------------ Algorithm 3
 CASES_RL = [("c1", lambda: WL.c1().cores, 13), ("ragged", lambda: WL.random_tt(np.random.default_rng(3), 5, [3, 7, 1, 5, 4], [4, 9, 2, 6]), 21),
-            ("c3s", lambda: WL.c3(d=6, n=16, r=10).cores, 40)]
+            ("c3s", lambda: WL.c3(d=6, n=16, r=10).cores, 40),
+            # one wide bond (r_2 = 600): the tensor-core step for core 2 splits its K = 600 over CTAs
+            ("wide", lambda: WL.random_tt(np.random.default_rng(4), 4, [5, 8, 6, 3], [4, 600, 7]), 80)]
 
 
 @pytest.mark.parametrize("name,make,w", CASES_RL)
@@ -158,6 +160,36 @@ def test_adaptive_c2_full_size(B):
     flat = [e for es in info["estimates"] for e in es]
     assert np.allclose(yi["estimates"], flat, rtol=1e-8, atol=1e-14 * x.norm)
     assert rel_tensor_diff(got, ref) <= 1e-10
+
+
+def test_adaptive_c2_full_size_sliced_default(B):
+    """The bench configuration: sliced precision with the slice count chosen for tol 1e-6 (6 slices,
+    contraction error ~6 * 2^-41 of the operand scales), against the FP64 oracle.
+
+    Stated bound for this form: each sliced contraction is exact to ~6 * 2^-41 = 2.7e-12 of
+    sum_c |a_rc| |b_cj|.  The input is a formal sum of copies whose coefficients c_i partly cancel,
+    so sum |a||b| exceeds |sum a b| by up to kappa = sum |c_i| / |sum c_i| (about 20 here); a
+    residual estimate (||S||_F / sqrt(b) over a rows x b block) then moves by about
+    kappa * 2.7e-12 * sqrt(rows) ||X|| ~ 3e-9 ||X|| for rows = 3000.  The same perturbation turns
+    the sketched subspaces in the directions near the truncation level (singular values ~1e-7
+    ||X||) and moves each core's projection by ~kappa * 2.7e-12 ||X||; over d - 1 = 19 cores the
+    stated bound for the rounded tensor is 1e-8 relative (1 % of tol).  Ranks must be identical."""
+    x = WL.c2()
+    ref, info = R.tt_round_adaptive(x.cores, 1e-6, seed=2024, block=10, nrmx=x.norm)
+    with B.round_adaptive(dev(x.cores), 1e-6, 10, 2024, B.options(precision=B.TTR_PREC_SLICED, nrmx=x.norm)) as y:
+        yi = y.info
+        got = y.to_numpy()
+    assert yi["ranks"] == info["ranks"]
+    flat = [e for es in info["estimates"] for e in es]
+    coef = np.asarray(x.meta["coef"])
+    kappa = np.abs(coef).sum() / abs(coef.sum())
+    bound = kappa * 2.7e-12 * math.sqrt(3000)
+    dev_est = np.abs(np.asarray(yi["estimates"]) - np.asarray(flat)).max() / x.norm
+    diff = rel_tensor_diff(got, ref)
+    print(f"max estimate deviation {dev_est:.3e} ||X|| (bound {bound:.1e}), tensor difference {diff:.3e}")
+    assert dev_est <= bound
+    assert diff <= 1e-8
+    assert T.tt_dist(got, x.cores) <= 1e-6 * x.norm
 
 
 # ------------------------------------------------------------------ Algorithm 1
