@@ -38,7 +38,7 @@ struct Args {
   double* Q;            // m x qcap basis, leading dimension ldq
   int64_t ldq;
   double* S;            // m x bi work (leading dimension bi)
-  double* acc;          // 3 x ACC accumulation buffers (zero on entry)
+  double* acc;          // 3 accumulation buffers of acc_used doubles each (zero on entry)
   int acc_used;         // entries any reduction touches
   int64_t m;
   int64_t qcols;        // columns of Q kept per row in shared memory (>= rbar)
@@ -117,17 +117,17 @@ __device__ __forceinline__ void my_rows(int64_t m, int64_t& lo, int64_t& hi) {
 // readers (reduction i-1) finished before barrier i, and its next writers (reduction i+2) start
 // only after barrier i+1.  The totals are the same in every CTA, so all CTAs take the same branch.
 struct Red {
-  double* base;     // 3 x ACC doubles, zero on entry
+  double* base;     // 3 x used doubles, zero on entry
   int i;            // index of the next reduction
   int used;         // entries to clear per buffer
 };
 
-__device__ __forceinline__ double* red_buf(const Red& r) { return r.base + (int64_t)(r.i % 3) * ACC; }
+__device__ __forceinline__ double* red_buf(const Red& r) { return r.base + (int64_t)(r.i % 3) * r.used; }
 
 // after the barrier of the current reduction: clear the buffer two reductions ahead, advance
 __device__ __forceinline__ void red_advance(Red& r) {
   if (blockIdx.x == 0) {
-    double* z = r.base + (int64_t)((r.i + 2) % 3) * ACC;
+    double* z = r.base + (int64_t)((r.i + 2) % 3) * r.used;
     for (int o = threadIdx.x; o < r.used; o += NT) z[o] = 0.0;
   }
   r.i++;
@@ -448,11 +448,21 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   if (b0 > ac::BMAX || bi > ac::BMAX || (int64_t)rbar * bi > ac::ACC || m <= 0) return TTR_ERR_UNSUPPORTED;
   int dev = 0;
   TTR_CUDA(cudaGetDevice(&dev));
-  int nsm = 0, coop = 0, smem_optin = 0;
-  TTR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  TTR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  TTR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (!coop) return TTR_ERR_UNSUPPORTED;
+  // device properties and the kernel's shared-memory limit, looked up once per device
+  constexpr int MAXDEV = 64;
+  struct DevInfo {
+    int nsm, coop, smem_optin, raised;
+  };
+  static DevInfo info[MAXDEV] = {};
+  DevInfo local{};
+  DevInfo& di = (dev >= 0 && dev < MAXDEV) ? info[dev] : local;
+  if (di.nsm == 0) {
+    TTR_CUDA(cudaDeviceGetAttribute(&di.coop, cudaDevAttrCooperativeLaunch, dev));
+    TTR_CUDA(cudaDeviceGetAttribute(&di.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    TTR_CUDA(cudaDeviceGetAttribute(&di.nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int nsm = di.nsm, smem_optin = di.smem_optin;
+  if (!di.coop) return TTR_ERR_UNSUPPORTED;
   // no more CTAs than rows; each CTA keeps its rows of Q, of the sketch and of the residual block
   const int nblocks = (int)std::min<int64_t>(nsm, m);
   const int rpc = (int)((m + nblocks - 1) / nblocks);
@@ -460,12 +470,15 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const size_t dyn = sizeof(double) * (size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX);
   const size_t static_bytes = 52 * 1024;   // G, R^{-1}, [G | I], P staging, reductions (about 49 KB)
   if (dyn + static_bytes > (size_t)smem_optin) return TTR_ERR_UNSUPPORTED;
-  TTR_CUDA(cudaFuncSetAttribute(ac::adaptive_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-  int per_sm = 0;
-  TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ac::adaptive_core_kernel, ac::NT, dyn));
-  if (per_sm < 1) return TTR_ERR_UNSUPPORTED;
+  if (di.raised < (int)dyn) {
+    TTR_CUDA(cudaFuncSetAttribute(ac::adaptive_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int per_sm = 0;
+    TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ac::adaptive_core_kernel, ac::NT, dyn));
+    if (per_sm < 1) return TTR_ERR_UNSUPPORTED;
+    di.raised = (int)dyn;
+  }
   if (!c.ac_part) {
-    TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * ac::ACC));
+    TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * (ac::ACC + 64)));   // 3 buffers of up to ACC + 33 doubles
     TTR_CHECK(c.alloc_t(&c.ac_bar, 4));
     TTR_CHECK(c.alloc_t(&c.ac_io, 4));
     TTR_CUDA(cudaMemsetAsync(c.ac_bar, 0, 4 * sizeof(unsigned), c.stream));
@@ -474,8 +487,8 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
     TTR_CHECK(c.alloc_t(&c.d_flags, 4));
     TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
   }
-  const int used = std::max(std::max(b0 * b0, bi * bi + 1), rbar * bi) + 1;
-  TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * ac::ACC, c.stream));
+  const int used = (std::max(std::max(b0 * b0, bi * bi + 1), rbar * bi) + 1 + 31) / 32 * 32;
+  TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * used, c.stream));
   ac::Args a{};
   a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;
   a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.rbar = rbar; a.width = width; a.cc0 = cc0; a.tau = tau;

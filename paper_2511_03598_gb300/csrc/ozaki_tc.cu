@@ -431,39 +431,55 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
 
 // ---- B operand preparation: column exponent scales, then digit planes in the shared-memory
 // image.  B(k, n) = B[k*sbk + n*sbn], K x N.
+// Pass 1: grid (N-chunks, K-chunks of 32 rows); each CTA writes the largest exponent of each of its
+// tn columns over its 32 rows to Fpart[kchunk][column] (plain stores: nothing to clear first).
 __global__ void __launch_bounds__(256) colmax_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
-                                                       int tn, int* Fmax) {
-  // grid (N-chunks, K-chunks of 32 rows); a task reads 8 rows of one column (all loads in flight);
-  // column maxima go to Fmax (zeroed beforehand) atomically
+                                                       int tn, int64_t npad, int* Fpart) {
+  __shared__ int cm[TNMAX];
   const int nc = blockIdx.x;
+  for (int j = threadIdx.x; j < tn; j += blockDim.x) cm[j] = 1;
+  __syncthreads();
+  // a task reads 8 rows of one column (all loads in flight)
   for (int u = threadIdx.x; u < tn * (KC / 8); u += blockDim.x) {
     const int j = u % tn, grp = u / tn;
     const int64_t n = (int64_t)nc * tn + j;
-    int e = 1;
-    if (n < N) {
-      double v[8];
+    if (n >= N) continue;
+    double v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int64_t k = (int64_t)blockIdx.y * KC + grp * 8 + q;
-        v[q] = (k < K) ? B[k * sbk + n * sbn] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) e = max(e, exp_field(v[q]));
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)blockIdx.y * KC + grp * 8 + q;
+      v[q] = (k < K) ? B[k * sbk + n * sbn] : 0.0;
     }
-    atomicMax(&Fmax[(int64_t)nc * tn + j], e);
+    int e = 1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) e = max(e, exp_field(v[q]));
+    atomicMax(&cm[j], e);
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < tn; j += blockDim.x) Fpart[(int64_t)blockIdx.y * npad + (int64_t)nc * tn + j] = cm[j];
 }
 
-// One CTA per (tn-column chunk, 32-row K chunk): tasks (column, group of 8 k).
+// Pass 2: one CTA per (tn-column chunk, 32-row K chunk).  The column scales are the maxima of the
+// pass-1 partials (CTA (nc, 0) also stores them to Fmax); tasks (column, group of 8 k) then write
+// the s digit planes.
 __global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
-                                                      int s, int tn, int kchunks, const int* Fmax, uint4* planes) {
+                                                      int s, int tn, int kchunks, int64_t npad, const int* Fpart,
+                                                      int* Fmax, uint4* planes) {
+  __shared__ int E[TNMAX];
   const int nc = blockIdx.x, kcn = blockIdx.y;
+  for (int j = threadIdx.x; j < tn; j += blockDim.x) {
+    int e = 1;
+    const int* fp = Fpart + (int64_t)nc * tn + j;
+    for (int q = 0; q < kchunks; ++q) e = max(e, __ldg(fp + (int64_t)q * npad));
+    E[j] = e;
+    if (kcn == 0) Fmax[(int64_t)nc * tn + j] = e;
+  }
+  __syncthreads();
   const int plane_b = tn * KC;
   uint4* blk = planes + ((size_t)nc * kchunks + kcn) * (size_t)s * (plane_b / 8);
   for (int u = threadIdx.x; u < tn * (KC / 8); u += blockDim.x) {
     const int j = u % tn, grp = u / tn;
     const int64_t n = (int64_t)nc * tn + j;
-    const int E = max(1, Fmax[n]);
     double v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -471,7 +487,7 @@ __global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t s
       v[q] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0;
     }
     uint32_t w[MAXS][4];
-    slice8(v, E, s, w);
+    slice8(v, E[j], s, w);
     const int idx = ((grp * (tn / 8)) + (j >> 3)) * 8 + (j & 7);      // uint4 index in a plane
     for (int p = 0; p < s; ++p) blk[(size_t)p * (plane_b / 8) + idx] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
   }
@@ -490,8 +506,16 @@ template <int MODE, bool AKFAST>
 static int launch(Ctx& c, const Args& a, dim3 grid, const char* name) {
   const size_t sm = smem_bytes(a.s, a.tn, MODE);
   auto kern = sliced_kernel<MODE, AKFAST>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
+  // the shared-memory limit is raised once per device to the largest size requested so far
+  constexpr int MAXDEV = 64;
+  static int raised[MAXDEV] = {};
+  int dev = 0;
+  TTR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= MAXDEV || raised[dev] < (int)sm) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
+    if (dev >= 0 && dev < MAXDEV) raised[dev] = (int)sm;
+  }
   kern<<<grid, NT, sm, c.stream>>>(a);
   return c.check_launch(name);
 }
@@ -514,13 +538,26 @@ static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, 
   p.tn = (int)std::min<int64_t>(tmax, std::max<int64_t>(16, (per + 15) / 16 * 16));
   p.kchunks = (int)((K + KC - 1) / KC);
   const int64_t npad = (int64_t)p.nchunks * p.tn;
-  TTR_CHECK(c.alloc(reinterpret_cast<void**>(&p.planes), (size_t)p.nchunks * p.kchunks * s * p.tn * KC * 2));
-  TTR_CHECK(c.alloc_t(&p.Fmax, (size_t)npad));
-  TTR_CUDA(cudaMemsetAsync(p.Fmax, 0, sizeof(int) * npad, c.stream));
-  colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, p.tn, p.Fmax);
+  // one workspace per call context, reused by every preparation: planes, then Fmax, then the
+  // per-K-chunk partial maxima (calls are ordered on the context's stream)
+  const size_t plane_bytes = ((size_t)p.nchunks * p.kchunks * s * p.tn * KC * 2 + 255) / 256 * 256;
+  const size_t fmax_bytes = ((size_t)npad * sizeof(int) + 255) / 256 * 256;
+  const size_t need = plane_bytes + fmax_bytes + (size_t)p.kchunks * npad * sizeof(int);
+  if (c.bprep_bytes < need) {
+    void* ws = nullptr;
+    TTR_CHECK(c.alloc(&ws, std::max(need, (size_t)2 * c.bprep_bytes)));
+    c.bprep = ws;
+    c.bprep_bytes = std::max(need, (size_t)2 * c.bprep_bytes);
+  }
+  unsigned char* base = static_cast<unsigned char*>(c.bprep);
+  p.planes = reinterpret_cast<uint4*>(base);
+  p.Fmax = reinterpret_cast<int*>(base + plane_bytes);
+  int* Fpart = reinterpret_cast<int*>(base + plane_bytes + fmax_bytes);
+  colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, p.tn, npad,
+                                                                                      Fpart);
   TTR_CHECK(c.check_launch("colmax_b"));
-  slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, s, p.tn,
-                                                                                     p.kchunks, p.Fmax, p.planes);
+  slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(
+      B, sbk, sbn, K, N, s, p.tn, p.kchunks, npad, Fpart, p.Fmax, p.planes);
   return c.check_launch("slice_b");
 }
 

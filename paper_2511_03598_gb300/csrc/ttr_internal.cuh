@@ -44,6 +44,8 @@ struct Ctx {
   unsigned* ac_bar = nullptr;      // adaptive_core: grid barrier counter/generation
   int* ac_io = nullptr;            // adaptive_core: status, column count, estimate count
   unsigned long long* ac_prof = nullptr;   // adaptive_core phase cycles (profiling only)
+  void* bprep = nullptr;           // tensor-core B-operand workspace (digit planes, scales)
+  size_t bprep_bytes = 0;
   int workspace();
 
   // optional launch timeline (environment TTR_PROFILE=1): an event after every launch; the time
