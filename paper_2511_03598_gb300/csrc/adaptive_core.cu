@@ -56,8 +56,8 @@ struct Args {
 
 // Phase timer of CTA 0 (launch-timeline profiling only): cycles since the previous mark are
 // added to prof[phase]; prof[PH_BARRIER] collects the cycles spent waiting in grid barriers.
-enum Phase { PH_STAGE = 0, PH_FIRST_QR, PH_RESIDUAL, PH_ESTIMATE, PH_QR1, PH_REORTH, PH_QR2, PH_FINISH, PH_BARRIER,
-             PH_COUNT };
+enum Phase { PH_STAGE = 0, PH_FIRST_QR, PH_COEFF, PH_RESIDUAL, PH_REDUCE_B, PH_QR1, PH_REORTH, PH_REDUCE_A,
+             PH_FINISH, PH_BARRIER, PH_COUNT };
 struct Timer {
   unsigned long long* p;
   long long t;
@@ -183,12 +183,17 @@ __device__ void read_totals(const double* buf, int n, double* dst) {
 
 // x * 2^k, exact; integer exponent arithmetic unless x is zero, subnormal, non-finite or the
 // result leaves the normal range.
+// The rare paths below stay out of line: on this part an FP64 instruction costs its ~64 pipe
+// cycles even when its predicate is off, so if-converted slow paths would tax every call.
+__device__ __noinline__ double mul_pow2_slow(double x, int k) { return ldexp(x, k); }
+__device__ __noinline__ double rsqrt_slow(double y) { return 1.0 / sqrt(y); }
+
 __device__ __forceinline__ double mul_pow2(double x, int k) {
   const long long xb = __double_as_longlong(x);
   const int ef = (int)((xb >> 52) & 0x7FF);
   if (ef != 0 && ef != 0x7FF && ef + k > 0 && ef + k < 0x7FF) return __longlong_as_double(xb + (long long)k * (1LL << 52));
   if ((xb << 1) == 0) return x;
-  return ldexp(x, k);
+  return mul_pow2_slow(x, k);
 }
 
 // 1/sqrt(y) for positive, finite y to full double precision: y = m 2^(2h) with m in [1, 4), a
@@ -197,7 +202,7 @@ __device__ __forceinline__ double mul_pow2(double x, int k) {
 __device__ __forceinline__ double rsqrt_full(double y) {
   const long long yb = __double_as_longlong(y);
   const int ef = (int)((yb >> 52) & 0x7FF);
-  if (ef == 0) return 1.0 / sqrt(y);                       // subnormal: rare, slow path
+  if (ef == 0) return rsqrt_slow(y);                        // subnormal: rare, slow path
   const int h = (ef - 1023) >> 1;                           // floor((e) / 2)
   const double m = __longlong_as_double(yb - (long long)(2 * h) * (1LL << 52));        // in [1, 4)
   const long long mb = __double_as_longlong(m);
@@ -217,14 +222,30 @@ __device__ __forceinline__ double rsqrt_full(double y) {
 // d_j = d'_j 2^(e_j), d'_j in [1, 2).  Row p then holds s_p = prod_{j<p} d'_j times the row of the
 // ordinary elimination, so with D the pivots and L^{-1} the right block,
 //   R^{-1}(i, j) = L^{-1}(j, i) / sqrt(D_j) = M(j, b + i) / sqrt(M(j, j) s_j).
-// Critical path per column: one FP64 product and one FMA.  Scratch M: b x 2b, sc: b + 1.
-// Every CTA computes the same factor from the same data, so all take the same branch.
-__device__ bool factor_small(const double* G, int b, double* Ri, double* M, double* sc) {
+// Each thread keeps its elements of [G | I] in registers; only the pivot row and column of the
+// next step go through shared memory (double-buffered, one barrier per step).  Critical path per
+// column: one FP64 product and one FMA.  Scratch M: b x 2b, rowbuf: 2 x 2b, colbuf: 2 x b,
+// sc: b + 1.  Every CTA computes the same factor from the same data, so all take the same branch.
+constexpr int FKMAX = (BMAX * 2 * BMAX + NT - 1) / NT;    // elements of [G | I] per thread
+__device__ bool factor_small(const double* G, int b, double* Ri, double* M, double* rowbuf, double* colbuf,
+                             double* sc) {
   __shared__ int fail;
-  const int w2 = 2 * b;
-  for (int e = threadIdx.x; e < b * w2; e += NT) {
-    const int p = e / w2, q = e % w2;
-    M[e] = (q < b) ? G[p * b + q] : ((q - b == p) ? 1.0 : 0.0);
+  const int w2 = 2 * b, tot = b * w2;
+  double v[FKMAX];
+  int pp[FKMAX], qq[FKMAX];
+#pragma unroll
+  for (int k = 0; k < FKMAX; ++k) {
+    const int e = threadIdx.x + k * NT;
+    pp[k] = -1;
+    qq[k] = 0;
+    v[k] = 0.0;
+    if (e < tot) {
+      pp[k] = e / w2;
+      qq[k] = e % w2;
+      v[k] = (qq[k] < b) ? G[pp[k] * b + qq[k]] : ((qq[k] - b == pp[k]) ? 1.0 : 0.0);
+      if (pp[k] == 0) rowbuf[qq[k]] = v[k];
+      if (qq[k] == 0) colbuf[pp[k]] = v[k];
+    }
   }
   if (threadIdx.x == 0) {
     fail = 0;
@@ -232,35 +253,48 @@ __device__ bool factor_small(const double* G, int b, double* Ri, double* M, doub
   }
   __syncthreads();
   for (int j = 0; j < b; ++j) {
-    const double d = M[j * w2 + j];
-    const long long dbits = __double_as_longlong(d);
+    const double* rb = rowbuf + (j & 1) * w2;
+    const double* cb = colbuf + (j & 1) * b;
+    double* rn = rowbuf + ((j + 1) & 1) * w2;
+    double* cn = colbuf + ((j + 1) & 1) * b;
+    const long long dbits = __double_as_longlong(rb[j]);
     const int ef = (int)((dbits >> 52) & 0x7FF);
-    if (!(d > 0.0) || ef == 0 || ef == 0x7FF) {             // same value in every thread
+    if (dbits <= 0 || ef == 0 || ef == 0x7FF) {               // not positive and normal (integer tests)
       if (threadIdx.x == 0) fail = 1;
       break;
     }
     const int ej = ef - 1023;
     const double dp = __longlong_as_double((dbits & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
     if (threadIdx.x == 0) sc[j + 1] = sc[j] * dp;
-    for (int e = threadIdx.x; e < b * w2; e += NT) {
-      const int p = e / w2, q = e % w2;
-      if (p <= j) continue;
+#pragma unroll
+    for (int k = 0; k < FKMAX; ++k) {
+      if (k * NT >= tot) break;                              // same for the whole CTA
+      const int p = pp[k], q = qq[k];
       // left block: columns > j; right block (L^{-1}, lower): columns <= j and the diagonal
-      if (q < b ? (q <= j) : (q - b > j && q - b != p)) continue;
-      M[e] = fma(dp, M[e], -M[p * w2 + j] * mul_pow2(M[j * w2 + q], -ej));
+      const bool act = p > j && (q < b ? q > j : (q - b <= j || q - b == p));
+      if (__any_sync(0xffffffffu, act)) {                    // idle warps issue no FP64 work
+        const double upd = fma(dp, v[k], -cb[p < 0 ? 0 : p] * mul_pow2(rb[q], -ej));
+        if (act) v[k] = upd;
+      }
+      if (p == j + 1) rn[q] = v[k];
+      if (q == j + 1 && p > j) cn[p] = v[k];
     }
     __syncthreads();
   }
   __syncthreads();
   if (fail) return false;
+#pragma unroll
+  for (int k = 0; k < FKMAX; ++k)
+    if (pp[k] >= 0) M[pp[k] * w2 + qq[k]] = v[k];
+  __syncthreads();
   for (int e = threadIdx.x; e < b * b; e += NT) {
     const int i = e / b, j = e % b;
-    double v = 0.0;
+    double r = 0.0;
     if (i <= j) {
       const double y = M[j * w2 + j] * sc[j];
-      v = (y > 0.0 && isfinite(y)) ? M[j * w2 + b + i] * rsqrt_full(y) : 0.0;
+      r = (y > 0.0 && isfinite(y)) ? M[j * w2 + b + i] * rsqrt_full(y) : 0.0;
     }
-    Ri[e] = v;
+    Ri[e] = r;
   }
   __syncthreads();
   return true;
@@ -287,77 +321,58 @@ __device__ void apply_rinv(double* X, int ldx, int b, const double* Ri, int nr, 
   __syncthreads();
 }
 
-// CholeskyQR of the own rows of X (shared memory, b columns), npass passes, one barrier each.
-// If pre_gram is given, the first pass's Gram matrix is already summed there (its barrier and
-// buffer rotation have been done by the caller).
-__device__ bool cholqr(double* X, int ldx, int b, int nr, int npass, Red& rd, unsigned* bar, int* err, bool* timeout,
-                       double* T, const double* pre_gram = nullptr) {
-  __shared__ double G[BMAX * BMAX];
-  __shared__ double Ri[BMAX * BMAX];
-  __shared__ double M[BMAX * 2 * BMAX];
-  __shared__ double sc[BMAX + 1];
-  for (int pass = 0; pass < npass; ++pass) {
-    if (pass == 0 && pre_gram) {
-      read_totals(pre_gram, b * b, G);
-    } else {
-      double* buf = red_buf(rd);
-      gram_acc(X, ldx, X, ldx, b, b, nr, buf);
-      if (!grid_sync(bar, err)) {
-        *timeout = true;
-        return false;
-      }
-      red_advance(rd);
-      read_totals(buf, b * b, G);
-    }
-    if (!factor_small(G, b, Ri, M, sc)) return false;
-    apply_rinv(X, ldx, b, Ri, nr, T);
-  }
-  return true;
-}
-
-// own rows: X(:, 0:b) -= Q(:, 0:c) P with P = Q(:, 0:c)^T X(:, 0:b) summed over all rows.
-__device__ bool project_out(const double* Q, int ldq, int c, double* X, int ldx, int b, int nr, Red& rd,
-                            unsigned* bar, int* err) {
-  if (c <= 0) return true;
-  double* buf = red_buf(rd);
-  gram_acc(Q, ldq, X, ldx, c, b, nr, buf);
-  if (!grid_sync(bar, err)) return false;
-  red_advance(rd);
-  __shared__ double Ps[ACC / 4];
-  const bool in_smem = c * b <= ACC / 4;
-  if (in_smem) read_totals(buf, c * b, Ps);
+// own rows: X(:, 0:b) -= Q(:, 0:c) P, P (c x b, leading dimension ldp) in shared memory;
+// four independent FMA chains per element
+__device__ void sub_qp(double* X, int ldx, const double* Q, int ldq, int c, const double* P, int ldp, int b, int nr) {
+  if (c <= 0) return;
   for (int e = threadIdx.x; e < nr * b; e += NT) {
     const int r = e / b, j = e % b;
     const double* qr = Q + r * ldq;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;      // four independent chains
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int i = 0;
-    if (in_smem) {
-      for (; i + 3 < c; i += 4) {
-        s0 = fma(qr[i], Ps[i * b + j], s0);
-        s1 = fma(qr[i + 1], Ps[(i + 1) * b + j], s1);
-        s2 = fma(qr[i + 2], Ps[(i + 2) * b + j], s2);
-        s3 = fma(qr[i + 3], Ps[(i + 3) * b + j], s3);
-      }
-      for (; i < c; ++i) s0 = fma(qr[i], Ps[i * b + j], s0);
-    } else {
-      for (; i < c; ++i) s0 = fma(qr[i], __ldcg(buf + i * b + j), s0);
+    for (; i + 3 < c; i += 4) {
+      s0 = fma(qr[i], P[i * ldp + j], s0);
+      s1 = fma(qr[i + 1], P[(i + 1) * ldp + j], s1);
+      s2 = fma(qr[i + 2], P[(i + 2) * ldp + j], s2);
+      s3 = fma(qr[i + 3], P[(i + 3) * ldp + j], s3);
     }
+    for (; i < c; ++i) s0 = fma(qr[i], P[i * ldp + j], s0);
     X[r * ldx + j] -= (s0 + s1) + (s2 + s3);
   }
   __syncthreads();
-  return true;
+}
+
+// out (b x n, ld n, shared) = Ri^T (b x b lower) C (b x n, ld n, global totals): the coefficients
+// of the new basis block (X R^{-1})^T Y from X^T Y
+__device__ void mul_rinv_t_left(const double* C, int b, int n, const double* Ri, double* out) {
+  for (int e = threadIdx.x; e < b * n; e += NT) {
+    const int i = e / n, j = e % n;
+    double v = 0.0;
+    for (int k = 0; k <= i; ++k) v = fma(Ri[k * b + i], __ldcg(C + k * n + j), v);
+    out[e] = v;
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   extern __shared__ __align__(16) double sm[];
+  __shared__ double G[BMAX * BMAX];
+  __shared__ double Ri[BMAX * BMAX];
+  __shared__ double M[BMAX * 2 * BMAX];
+  __shared__ double rowbuf[2 * 2 * BMAX];
+  __shared__ double colbuf[2 * BMAX];
+  __shared__ double sc[BMAX + 1];
+  __shared__ double est_s;
   int64_t lo, hi;
   my_rows(a.m, lo, hi);
   const int nr = (int)(hi - lo);
-  const int ldq = (int)a.qcols, ldw = a.width;
-  double* Qs = sm;                                   // [rpc][ldq]
-  double* Ss = Qs + (size_t)a.rpc * ldq;             // [rpc][ldw]
-  double* Rs = Ss + (size_t)a.rpc * ldw;             // [rpc][bi]
-  double* Tb = Rs + (size_t)a.rpc * a.bi;            // [rpc][BMAX] staging for X R^{-1}
+  const int ldq = (int)a.qcols, ldw = a.width, bi = a.bi;
+  double* Qs = sm;                                   // [rpc][ldq]   own rows of Q
+  double* Ss = Qs + (size_t)a.rpc * ldq;             // [rpc][ldw]   own rows of the sketch S_all
+  double* Rs = Ss + (size_t)a.rpc * ldw;             // [rpc][bi]    residual block
+  double* Tb = Rs + (size_t)a.rpc * bi;              // [rpc][BMAX]  staging for X R^{-1}
+  double* Ps = Tb + (size_t)a.rpc * BMAX;            // [qcols][max(b0, bi)] projection coefficients
+  const int ldp = bi;
   bool timeout = false;
   int cc = a.cc0;
   int nest = 0;
@@ -372,7 +387,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   auto finish = [&](int status) {
     // write back Q(:, 0:cc) (plus the residual block, which the host needs after a breakdown)
     for (int e = threadIdx.x; e < nr * cc; e += NT) a.Q[(lo + e / cc) * a.ldq + e % cc] = Qs[(e / cc) * ldq + e % cc];
-    for (int e = threadIdx.x; e < nr * a.bi; e += NT) a.S[(lo + e / a.bi) * a.bi + e % a.bi] = Rs[e];
+    for (int e = threadIdx.x; e < nr * bi; e += NT) a.S[(lo + e / bi) * bi + e % bi] = Rs[e];
     tmr.mark(PH_FINISH);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.io[0] = timeout ? ST_TIMEOUT : status;
@@ -380,60 +395,113 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
       a.io[2] = nest;
     }
   };
-  if (cc == 0) {
-    // phase 1: Q(:, 0:b0) = qr(S_all(:, 0:b0))
-    for (int e = threadIdx.x; e < nr * a.b0; e += NT) Qs[(e / a.b0) * ldq + e % a.b0] = Ss[(e / a.b0) * ldw + e % a.b0];
-    __syncthreads();
-    if (!cholqr(Qs, ldq, a.b0, nr, 2, rd, a.bar, a.err, &timeout, Tb)) return finish(ST_BREAKDOWN);
-    cc = a.b0;
-    tmr.mark(PH_FIRST_QR);
-  }
-  __shared__ double est_s;
-  while (cc < a.rbar) {
-    if (cc + a.bi > a.width) return finish(ST_EXTEND);
-    // residual sketch of the next block (Eqs. (3.4)-(3.5)) and its norm
-    for (int e = threadIdx.x; e < nr * a.bi; e += NT) Rs[e] = Ss[(e / a.bi) * ldw + cc + e % a.bi];
-    __syncthreads();
-    if (!project_out(Qs, ldq, cc, Rs, a.bi, a.bi, nr, rd, a.bar, a.err)) {
-      timeout = true;
-      return finish(ST_TIMEOUT);
-    }
-    tmr.mark(PH_RESIDUAL);
-    // one reduction for both the residual norm and the Gram matrix of the candidate block
-    // S(:, 0:bb), which is the first CholeskyQR pass of Q_new if the loop continues
-    const int bb = min(a.bi, a.rbar - cc);
-    double* eb = red_buf(rd);
-    sumsq_acc(Rs, a.bi, a.bi, nr, eb);
-    gram_acc(Rs, a.bi, Rs, a.bi, bb, bb, nr, eb + 1);
+  // one cross-CTA reduction: everything accumulated into red_buf(rd) before the call is summed
+  auto reduce = [&]() -> double* {
+    double* buf = red_buf(rd);
     if (!grid_sync(a.bar, a.err)) {
       timeout = true;
-      return finish(ST_TIMEOUT);
+      return nullptr;
     }
     red_advance(rd);
-    if (threadIdx.x == 0) est_s = __ldcg(eb);
+    return buf;
+  };
+  // In the loop, P = Q^T S_all(:, cc:cc+bi) for the next block is carried over from the previous
+  // iteration's second reduction whenever that block lies within the sketch (have_p).
+  bool have_p = false;
+  if (cc == 0) {
+    // first block: Q(:, 0:b0) = qr(S_all(:, 0:b0)) by CholeskyQR2; the second pass's reduction also
+    // sums Q1^T S_all(:, b0:b0+bi), the projection coefficients of the first residual block
+    const int b0 = a.b0;
+    for (int e = threadIdx.x; e < nr * b0; e += NT) Qs[(e / b0) * ldq + e % b0] = Ss[(e / b0) * ldw + e % b0];
+    __syncthreads();
+    gram_acc(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
+    double* buf = reduce();
+    if (!buf) return finish(ST_TIMEOUT);
+    read_totals(buf, b0 * b0, G);
+    if (!factor_small(G, b0, Ri, M, rowbuf, colbuf, sc)) return finish(ST_BREAKDOWN);
+    apply_rinv(Qs, ldq, b0, Ri, nr, Tb);
+    const bool want = b0 < a.rbar && b0 + bi <= a.width;
+    gram_acc(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
+    if (want) gram_acc(Qs, ldq, Ss + b0, ldw, b0, bi, nr, red_buf(rd) + b0 * b0);
+    buf = reduce();
+    if (!buf) return finish(ST_TIMEOUT);
+    read_totals(buf, b0 * b0, G);
+    if (!factor_small(G, b0, Ri, M, rowbuf, colbuf, sc)) return finish(ST_BREAKDOWN);
+    apply_rinv(Qs, ldq, b0, Ri, nr, Tb);
+    if (want) mul_rinv_t_left(buf + b0 * b0, b0, bi, Ri, Ps);      // (Q1 R2^{-1})^T S = R2^{-T} Q1^T S
+    have_p = want;
+    cc = b0;
+    tmr.mark(PH_FIRST_QR);
+  }
+  while (cc < a.rbar) {
+    if (cc + bi > a.width) return finish(ST_EXTEND);
+    if (!have_p) {
+      gram_acc(Qs, ldq, Ss + cc, ldw, cc, bi, nr, red_buf(rd));
+      double* buf = reduce();
+      if (!buf) return finish(ST_TIMEOUT);
+      read_totals(buf, cc * bi, Ps);
+    }
+    tmr.mark(PH_COEFF);
+    // residual sketch of the next block (Eqs. (3.4)-(3.5)): S = S_all(:, cc:cc+bi) - Q P
+    for (int e = threadIdx.x; e < nr * bi; e += NT) Rs[e] = Ss[(e / bi) * ldw + cc + e % bi];
+    __syncthreads();
+    sub_qp(Rs, bi, Qs, ldq, cc, Ps, ldp, bi, nr);
+    tmr.mark(PH_RESIDUAL);
+    // reduction B: ||S||_F^2 and the Gram matrix of the candidate block S(:, 0:bb)
+    const int bb = min(bi, a.rbar - cc);
+    {
+      double* eb = red_buf(rd);
+      sumsq_acc(Rs, bi, bi, nr, eb);
+      gram_acc(Rs, bi, Rs, bi, bb, bb, nr, eb + 1);
+    }
+    double* bufB = reduce();
+    if (!bufB) return finish(ST_TIMEOUT);
+    if (threadIdx.x == 0) est_s = __ldcg(bufB);
     __syncthreads();
     const double ss = est_s;                               // ||S||_F^2
     if (blockIdx.x == 0 && threadIdx.x == 0) a.est_out[nest] = ss;   // the host takes sqrt(ss / b_inc)
     ++nest;
-    tmr.mark(PH_ESTIMATE);
+    tmr.mark(PH_REDUCE_B);
     // est = sqrt(ss / b_inc) > tau  <=>  ss > tau^2 b_inc  (the square root is left to the host)
-    if (!(ss > a.tau * a.tau * (double)a.bi)) return finish(ST_DONE);
-    // new directions (Algorithm 6): Q_new = qr(S(:, 0:bb)), re-orthogonalized against Q, qr again;
-    // each qr is one CholeskyQR pass, so the pair is CholeskyQR2 with the block Gram-Schmidt step
-    // in between (the first pass leaves Q_new orthonormal to ~u cond(S)^2, the second to ~u)
+    if (!(ss > a.tau * a.tau * (double)bi)) return finish(ST_DONE);
+    // new directions (Algorithm 6): Q_new = qr(S(:, 0:bb)); Q_new -= Q (Q^T Q_new); Q_new = qr(Q_new).
+    // Each qr is one CholeskyQR pass (CholeskyQR2 with the block Gram-Schmidt step in between:
+    // the first pass leaves Q_new orthonormal to ~u cond(S)^2, the second to ~u).
+    read_totals(bufB + 1, bb * bb, G);
+    if (!factor_small(G, bb, Ri, M, rowbuf, colbuf, sc)) return finish(ST_BREAKDOWN);
     double* Qn = Qs + cc;
-    for (int e = threadIdx.x; e < nr * bb; e += NT) Qn[(e / bb) * ldq + e % bb] = Rs[(e / bb) * a.bi + e % bb];
+    for (int e = threadIdx.x; e < nr * bb; e += NT) Qn[(e / bb) * ldq + e % bb] = Rs[(e / bb) * bi + e % bb];
     __syncthreads();
-    if (!cholqr(Qn, ldq, bb, nr, 1, rd, a.bar, a.err, &timeout, Tb, eb + 1)) return finish(ST_BREAKDOWN);
+    apply_rinv(Qn, ldq, bb, Ri, nr, Tb);
     tmr.mark(PH_QR1);
-    if (!project_out(Qs, ldq, cc, Qn, ldq, bb, nr, rd, a.bar, a.err)) {
-      timeout = true;
-      return finish(ST_TIMEOUT);
+    // block Gram-Schmidt against Q on the Q_new just formed (its rounding errors included)
+    if (cc > 0) {
+      gram_acc(Qs, ldq, Qn, ldq, cc, bb, nr, red_buf(rd));
+      double* bufR = reduce();
+      if (!bufR) return finish(ST_TIMEOUT);
+      read_totals(bufR, cc * bb, Ps);
+      sub_qp(Qn, ldq, Qs, ldq, cc, Ps, bb, bb, nr);
     }
     tmr.mark(PH_REORTH);
-    if (!cholqr(Qn, ldq, bb, nr, 1, rd, a.bar, a.err, &timeout, Tb)) return finish(ST_BREAKDOWN);
-    tmr.mark(PH_QR2);
-    cc += bb;
+    // reduction A: the Gram matrix of Q_new (second CholeskyQR pass) and, when the next block lies
+    // within the sketch, [Q, Q_new]^T S_all(:, next:next+bi) for its residual
+    const int nxt = cc + bb;
+    const bool want = nxt < a.rbar && nxt + bi <= a.width;
+    gram_acc(Qn, ldq, Qn, ldq, bb, bb, nr, red_buf(rd));
+    if (want) gram_acc(Qs, ldq, Ss + nxt, ldw, nxt, bi, nr, red_buf(rd) + bb * bb);
+    double* bufA = reduce();
+    if (!bufA) return finish(ST_TIMEOUT);
+    read_totals(bufA, bb * bb, G);
+    if (!factor_small(G, bb, Ri, M, rowbuf, colbuf, sc)) return finish(ST_BREAKDOWN);
+    apply_rinv(Qn, ldq, bb, Ri, nr, Tb);
+    if (want) {
+      // P = [Q^T S_next; R2^{-T} Q_new^T S_next]
+      read_totals(bufA + bb * bb, cc * bi, Ps);
+      mul_rinv_t_left(bufA + bb * bb + cc * bi, bb, bi, Ri, Ps + cc * bi);
+    }
+    have_p = want;
+    cc = nxt;
+    tmr.mark(PH_REDUCE_A);
   }
   finish(ST_DONE);
 }
@@ -467,8 +535,9 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const int nblocks = (int)std::min<int64_t>(nsm, m);
   const int rpc = (int)((m + nblocks - 1) / nblocks);
   const int64_t qcols = rbar;
-  const size_t dyn = sizeof(double) * (size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX);
-  const size_t static_bytes = 52 * 1024;   // G, R^{-1}, [G | I], P staging, reductions (about 49 KB)
+  const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
+                                        (size_t)qcols * (size_t)std::max(b0, bi));
+  const size_t static_bytes = 36 * 1024;   // G, R^{-1}, [G | I], pivot buffers, reductions (about 34 KB)
   if (dyn + static_bytes > (size_t)smem_optin) return TTR_ERR_UNSUPPORTED;
   if (di.raised < (int)dyn) {
     TTR_CUDA(cudaFuncSetAttribute(ac::adaptive_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
@@ -487,7 +556,10 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
     TTR_CHECK(c.alloc_t(&c.d_flags, 4));
     TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
   }
-  const int used = (std::max(std::max(b0 * b0, bi * bi + 1), rbar * bi) + 1 + 31) / 32 * 32;
+  // largest reduction: first block (b0^2 + b0 bi), reduction A (bi^2 + rbar bi); reduction B
+  // (1 + bi^2), re-orthogonalization and fresh coefficients (rbar bi) are smaller
+  const int used = (std::max(b0 * b0 + b0 * bi, 1 + bi * bi + rbar * bi) + 1 + 31) / 32 * 32;
+  if (used > ac::ACC + 64) return TTR_ERR_UNSUPPORTED;
   TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * used, c.stream));
   ac::Args a{};
   a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;

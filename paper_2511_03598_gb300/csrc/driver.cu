@@ -72,16 +72,17 @@ void Ctx::prof_report() {
     fprintf(stderr, "[ttr profile] %-22s n=%5d  %9.3f ms  %5.1f%%  %8.2f us/launch\n", a.first.c_str(), a.second.n,
             a.second.ms, 100.0 * a.second.ms / std::max(total, 1e-9), 1e3 * a.second.ms / a.second.n);
   if (ac_prof) {
-    static const char* names[] = {"stage rows", "first block QR", "residual sketch", "estimate + Gram",
-                                  "QR pass 1", "re-orthogonalize", "QR pass 2", "write back", "(barrier waits)"};
-    unsigned long long cyc[9] = {};
+    static const char* names[] = {"stage rows", "first block QR", "fresh Q^T S", "residual (local)",
+                                  "reduce B + estimate", "QR pass 1", "re-orthogonalize", "reduce A + QR 2",
+                                  "write back", "(barrier waits)"};
+    unsigned long long cyc[10] = {};
     cudaMemcpy(cyc, ac_prof, sizeof(cyc), cudaMemcpyDeviceToHost);
     int dev = 0, khz = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
     const double mhz = khz > 0 ? khz / 1e3 : 2070.0;
-    for (int i = 0; i < 9; ++i)
-      fprintf(stderr, "[ttr profile]   adaptive_core %-18s %9.3f ms (CTA 0, %.0f MHz)\n", names[i], cyc[i] / mhz / 1e3,
+    for (int i = 0; i < 10; ++i)
+      fprintf(stderr, "[ttr profile]   adaptive_core %-22s %9.3f ms (CTA 0, %.0f MHz)\n", names[i], cyc[i] / mhz / 1e3,
               mhz);
   }
   for (auto& pe : prof) cudaEventDestroy(pe.second);
