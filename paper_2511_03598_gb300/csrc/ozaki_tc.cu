@@ -47,8 +47,10 @@ constexpr int KSEG = 256;             // largest K per CTA: bound for exact FP32
 constexpr int MAXS = 8;               // slices per operand
 constexpr int PLANE_A = TM * KC;      // bf16 per A digit plane per chunk (8 KB)
 
-constexpr int NT = 512;               // threads per CTA (four warps per TMEM lane quarter)
-constexpr int NW = NT / 32;           // warps per CTA
+constexpr int NP = 512;               // producer threads: slicing, then the epilogue (4 warps per TMEM lane quarter)
+constexpr int NWP = NP / 32;          // producer warps
+constexpr int MMA_WARP = NWP;         // one more warp issues the tensor-core instructions
+constexpr int NT = NP + 32;           // threads per CTA
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 enum Mode { PLAIN = 0, ATOMIC = 1, RLM = 2 };
@@ -100,31 +102,81 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
   }
 }
 
-// s base-128 digits (BF16 bit patterns) of 8 values sharing the biased exponent scale E.
-__device__ __forceinline__ void slice8(const double* v, int E, int s, uint32_t (&w)[MAXS][4]) {
+// s base-128 digits (BF16 bit patterns, sign attached) of 8 values sharing the biased exponent
+// scale E: each value becomes the 7s-bit integer floor(|v| 2^(7s - E + 1022)), cut into s digits,
+// most significant first.
+// The slice count is fixed at compile time (constant digit offsets), and each pair of
+// BF16 digits is packed by one byte permute of the two binary32 images (a digit d < 128 is the
+// binary32 0x4B000000 | d minus 2^23, exactly; BF16 is its upper half).
+template <int S>
+__device__ __forceinline__ void slice8_t(const double* v, int E, uint32_t (&w)[S][4]) {
 #pragma unroll
-  for (int p = 0; p < MAXS; ++p)
+  for (int h = 0; h < 4; ++h) {
+    uint64_t fx[2];
+    uint32_t sg[2];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) w[p][h] = 0u;
+    for (int u = 0; u < 2; ++u) {
+      const uint64_t bits = (uint64_t)__double_as_longlong(v[2 * h + u]);
+      sg[u] = (uint32_t)(bits >> 32) & 0x80000000u;
+      const int ef = (int)((bits >> 52) & 0x7FF);
+      const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
+      const int sh = 53 - 7 * S + (E - (ef ? ef : 1));
+      fx[u] = (sh >= 64) ? 0ull : (sh >= 0 ? (mant >> sh) : (mant << (-sh)));
+    }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const uint64_t bits = (uint64_t)__double_as_longlong(v[q]);
-    const uint32_t neg = (uint32_t)(bits >> 63);
-    const int ef = (int)((bits >> 52) & 0x7FF);
-    const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
-    const int e = ef ? ef : 1;
-    const int sh = 53 - 7 * s + (E - e);
-    const uint64_t fx = (sh >= 64) ? 0ull : (sh >= 0 ? (mant >> sh) : (mant << (-sh)));
-#pragma unroll
-    for (int p = 0; p < MAXS; ++p) {
-      if (p < s) {
-        const uint32_t dg = (uint32_t)(fx >> (7 * (s - 1 - p))) & 127u;
-        const float f = __uint_as_float(0x4B000000u | dg) - 8388608.0f;   // exact: dg < 2^23
-        const uint32_t b16 = (__float_as_uint(f) >> 16) | (neg << 15);
-        w[p][q >> 1] |= b16 << (16 * (q & 1));
-      }
+    for (int p = 0; p < S; ++p) {
+      const int off = 7 * (S - 1 - p);
+      const uint32_t d0 = (uint32_t)(fx[0] >> off) & 127u, d1 = (uint32_t)(fx[1] >> off) & 127u;
+      const uint32_t f0 = __float_as_uint(__uint_as_float(0x4B000000u | d0) - 8388608.0f) | sg[0];
+      const uint32_t f1 = __float_as_uint(__uint_as_float(0x4B000000u | d1) - 8388608.0f) | sg[1];
+      w[p][h] = __byte_perm(f0, f1, 0x7632);
     }
   }
+}
+
+// The s digit planes of 8 values (one 16-byte store per plane at bf16 index idx of each plane).
+template <int S>
+__device__ __forceinline__ void store_digits(const double* v, int E, uint16_t* planes, size_t plane_stride, int idx) {
+  uint32_t w[S][4];
+  slice8_t<S>(v, E, w);
+#pragma unroll
+  for (int p = 0; p < S; ++p)
+    *reinterpret_cast<uint4*>(planes + (size_t)p * plane_stride + idx) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+
+__device__ __forceinline__ void store_digits_s(int s, const double* v, int E, uint16_t* planes, size_t plane_stride,
+                                               int idx) {
+  switch (s) {
+    case 3: store_digits<3>(v, E, planes, plane_stride, idx); break;
+    case 4: store_digits<4>(v, E, planes, plane_stride, idx); break;
+    case 5: store_digits<5>(v, E, planes, plane_stride, idx); break;
+    case 6: store_digits<6>(v, E, planes, plane_stride, idx); break;
+    case 7: store_digits<7>(v, E, planes, plane_stride, idx); break;
+    default: store_digits<8>(v, E, planes, plane_stride, idx); break;
+  }
+}
+
+// V * 2^X as a double for |V| < 2^63 (round to nearest even; underflow to zero); integer only.
+__device__ __forceinline__ double i64_to_double(long long V, int X) {
+  if (V == 0) return 0.0;
+  const uint64_t sign = V < 0 ? (1ull << 63) : 0ull;
+  uint64_t u = V < 0 ? (uint64_t)(-V) : (uint64_t)V;
+  const int lz = __clzll((long long)u);
+  u <<= lz;                                                  // top bit at position 63
+  uint64_t mant = u >> 11;                                   // 53 bits
+  const uint64_t rest = u & 0x7FFull;
+  int e = 63 - lz + X;
+  if (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) {
+    ++mant;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  const int field = e + 1023;
+  if (field <= 0) return __longlong_as_double((long long)sign);
+  if (field >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((uint64_t)field << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 // V * 2^X as a double (round to nearest even; underflow to zero).
@@ -169,7 +221,8 @@ template <int MODE, bool AKFAST>
 __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_slot;
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[2];    // digit buffer b filled (NP producer arrivals)
+  __shared__ __align__(8) uint64_t empty[2];   // MMAs reading digit buffer b done (tcgen05.commit)
   __shared__ int rowE[TM];
   __shared__ int slabE[TM];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -203,8 +256,10 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])), "r"(NP));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (tid < TM) {
@@ -214,8 +269,10 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   __syncthreads();
 
   // ---- pass 1: exponent scale of every row over this K segment (many loads in flight)
-  if (AKFAST) {
-    constexpr int RPW = TM / NW;              // rows per warp
+  if (warp >= NWP) {
+    // the MMA warp takes no part in the scan
+  } else if (AKFAST) {
+    constexpr int RPW = TM / NWP;             // rows per warp
     int em[RPW];
 #pragma unroll
     for (int r = 0; r < RPW; ++r) em[r] = 1;
@@ -232,9 +289,9 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
       if (lane == 0) rowE[warp * RPW + r] = e;
     }
   } else {
-    // NT/TM threads per row, interleaved over k
+    // NP/TM threads per row, interleaved over k
     const int row = tid % TM, part = tid / TM;
-    constexpr int PARTS = NT / TM;
+    constexpr int PARTS = NP / TM;
     int e0 = 1, e1 = 1;
     if (row < rows) {
       const double* colp = a.A + (m0 + row) * a.sam + kseg0 * a.sak;
@@ -261,80 +318,85 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   bool ok = true;
 
-  // ---- K loop over chunks of 32, double buffered
-  for (int c = 0; c < nchunk && ok; ++c) {
-    const int b = c & 1;
-    if (c >= 2) ok = mbar_wait(smem_u32(&mbar[b]), (uint32_t)(((c - 2) >> 1) & 1), a.err);
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-    uint16_t* Ap = (uint16_t*)bufs[b];
-    uint16_t* Bpl = Ap + (size_t)s * PLANE_A;
-    // A digits: 128 rows x 4 groups of 8 consecutive k = 512 tasks, TASKS per thread, all loads first
-    {
-      constexpr int TASKS = (TM * (KC / 8)) / NT;
-      double v[TASKS][8];
-#pragma unroll
-      for (int i = 0; i < TASKS; ++i) {
-        const int u = tid + NT * i;
-        const int row = AKFAST ? (u >> 2) : (u % TM);
-        const int grp = AKFAST ? (u & 3) : (u / TM);
-        const int kl = c * KC + grp * 8;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int kk = kl + q;
-          v[i][q] = (row < rows && kk < kseg_len) ? __ldg(a.A + (m0 + row) * a.sam + (kseg0 + kk) * a.sak) : 0.0;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < TASKS; ++i) {
-        const int u = tid + NT * i;
-        const int row = AKFAST ? (u >> 2) : (u % TM);
-        const int grp = AKFAST ? (u & 3) : (u / TM);
-        uint32_t w[MAXS][4];
-        slice8(v[i], rowE[row], s, w);
-        const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
-#pragma unroll
-        for (int p = 0; p < MAXS; ++p)
-          if (p < s)
-            *reinterpret_cast<uint4*>(Ap + (size_t)p * PLANE_A + idx) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-      }
-    }
-    // B digit planes of this chunk: a straight copy of s * 4 KB
-    {
-      const uint4* src = a.Bp + ((size_t)nc * a.kchunks + (kc0 + c)) * (size_t)s * (plane_b / 8);
-      uint4* dst = reinterpret_cast<uint4*>(Bpl);
-#pragma unroll 4
-      for (int e = tid; e < s * (plane_b / 8); e += NT) dst[e] = __ldg(src + e);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      const uint32_t abase = smem_u32(Ap), bbase = smem_u32(Bpl);
+  // ---- K loop over chunks of 32: the producer warps slice chunk c into digit buffer c % 2 and
+  // arrive on full[c % 2]; the MMA warp waits for it, issues the chunk's products and commits them
+  // to empty[c % 2], which the producers wait for before refilling that buffer (chunk c + 2).
+  // Every wait is bounded; a wait that runs out sets the error flag and the CTA winds down.
+  if (warp == MMA_WARP) {
+    if (lane == 0) {
+      for (int c = 0; c < nchunk && ok; ++c) {
+        const int b = c & 1;
+        ok = mbar_wait(smem_u32(&full[b]), (uint32_t)((c >> 1) & 1), a.err);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t abase = smem_u32(bufs[b]), bbase = abase + (uint32_t)(s * PLANE_A * 2);
 #pragma unroll 1
-      for (int ks = 0; ks < KC / 16; ++ks) {
+        for (int ks = 0; ks < KC / 16; ++ks) {
 #pragma unroll 1
-        for (int t = 0; t < s; ++t) {
+          for (int t = 0; t < s; ++t) {
 #pragma unroll 1
-          for (int p = 0; p <= t; ++p) {
-            const int q = t - p;
-            const uint64_t da = umma_desc(abase + p * PLANE_A * 2 + ks * 2 * (TM / 8) * 128, (TM / 8) * 128, 128);
-            const uint64_t db = umma_desc(bbase + q * plane_b * 2 + ks * 2 * (tn / 8) * 128, (tn / 8) * 128, 128);
-            const uint32_t accum = (c == 0 && ks == 0 && p == 0) ? 0u : 1u;
-            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(t * tn)),
-                         "l"(da), "l"(db), "r"(idesc), "r"(accum));
+            for (int p = 0; p <= t; ++p) {
+              const int q = t - p;
+              const uint64_t da = umma_desc(abase + p * PLANE_A * 2 + ks * 2 * (TM / 8) * 128, (TM / 8) * 128, 128);
+              const uint64_t db = umma_desc(bbase + q * plane_b * 2 + ks * 2 * (tn / 8) * 128, (tn / 8) * 128, 128);
+              const uint32_t accum = (c == 0 && ks == 0 && p == 0) ? 0u : 1u;
+              asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(t * tn)),
+                           "l"(da), "l"(db), "r"(idesc), "r"(accum));
+            }
           }
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&empty[b])));
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&mbar[b])));
+    }
+    __syncwarp();
+  } else {
+    for (int c = 0; c < nchunk && ok; ++c) {
+      const int b = c & 1;
+      if (c >= 2) ok = mbar_wait(smem_u32(&empty[b]), (uint32_t)(((c - 2) >> 1) & 1), a.err);
+      if (!ok) break;
+      uint16_t* Ap = (uint16_t*)bufs[b];
+      uint16_t* Bpl = Ap + (size_t)s * PLANE_A;
+      // A digits: 128 rows x 4 groups of 8 consecutive k = 512 tasks, TASKS per thread, all loads first
+      {
+        constexpr int TASKS = (TM * (KC / 8)) / NP;
+        double v[TASKS][8];
+#pragma unroll
+        for (int i = 0; i < TASKS; ++i) {
+          const int u = tid + NP * i;
+          const int row = AKFAST ? (u >> 2) : (u % TM);
+          const int grp = AKFAST ? (u & 3) : (u / TM);
+          const int kl = c * KC + grp * 8;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int kk = kl + q;
+            v[i][q] = (row < rows && kk < kseg_len) ? __ldg(a.A + (m0 + row) * a.sam + (kseg0 + kk) * a.sak) : 0.0;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < TASKS; ++i) {
+          const int u = tid + NP * i;
+          const int row = AKFAST ? (u >> 2) : (u % TM);
+          const int grp = AKFAST ? (u & 3) : (u / TM);
+          const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
+          store_digits_s(s, v[i], rowE[row], Ap, PLANE_A, idx);
+        }
+      }
+      // B digit planes of this chunk: a straight copy of s * tn * 64 bytes
+      {
+        const uint4* src = a.Bp + ((size_t)nc * a.kchunks + (kc0 + c)) * (size_t)s * (plane_b / 8);
+        uint4* dst = reinterpret_cast<uint4*>(Bpl);
+#pragma unroll 4
+        for (int e = tid; e < s * (plane_b / 8); e += NP) dst[e] = __ldg(src + e);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[b])) : "memory");
     }
   }
   if (ok && nchunk > 0) {
     const int c = nchunk - 1;
-    ok = mbar_wait(smem_u32(&mbar[c & 1]), (uint32_t)((c >> 1) & 1), a.err);
+    ok = mbar_wait(smem_u32(&empty[c & 1]), (uint32_t)((c >> 1) & 1), a.err);
   }
   ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -342,13 +404,15 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   // ---- epilogue: warp w reads TMEM lane quarter (w % 4); the two warps of a quarter take
   // alternate 16-column groups.  Partial contractions stage int128 products per 64-column block.
   if (ok && nchunk > 0) {
-    __int128* P = reinterpret_cast<__int128*>(smem);           // [TM][PB] for the slab sums
-    const int quarter = warp & 3, half = warp >> 2;          // NW / 4 warps share a lane quarter
+    // [TM][PB] int128 staging for the slab sums; column index XOR (row % 8) spreads the 16-byte
+    // stores of 32 consecutive rows over all banks
+    __int128* P = reinterpret_cast<__int128*>(smem);
+    const int quarter = warp & 3, half = warp >> 2;          // NWP / 4 warps share a lane quarter
     const int row = quarter * 32 + lane;
     const int ngroups = tn / 16;
     for (int blk0 = 0; blk0 < ngroups; blk0 += PB / 16) {
       const int blk1 = min(ngroups, blk0 + PB / 16);
-      for (int cg = blk0 + half; cg < blk1; cg += NW / 4) {
+      for (int cg = blk0 + half; warp < NWP && cg < blk1; cg += NWP / 4) {
         // V = sum_t acc_t 2^(7(s-1-t)) = Vh 2^35 + Vl, both parts in 64 bits: |acc_t| < 2^25, so
         // Vl (shifts 0..28) < 2^56 and Vh (shifts 35..49, less 35) < 2^41
         long long Vh[16], Vl[16];
@@ -375,6 +439,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
             for (int j = 0; j < 16; ++j) Vl[j] += (long long)f2i_exact(r[j]) * mul;
           }
         }
+        // with s <= 6, Vh is the top diagonal alone (|Vh| < 2^25), so V < 2^61 fits in 64 bits
+        const bool v64 = s <= 6;
         __int128 V[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) V[j] = (__int128)Vh[j] * ((__int128)1 << 35) + (__int128)Vl[j];
@@ -386,7 +452,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
             for (int j = 0; j < 16; ++j) {
               const int64_t n = n0 + j;
               if (n < a.N) {
-                const double out = i128_to_double(V[j], e_row + max(1, a.Fmax[n]) - 2044 - 7 * s - 7);
+                const int X = e_row + max(1, a.Fmax[n]) - 2044 - 7 * s - 7;
+                const double out = v64 ? i64_to_double(Vh[j] * (1LL << 35) + Vl[j], X) : i128_to_double(V[j], X);
                 double* cp = a.C + (m0 + row) * a.scm + n * a.scn;
                 if (MODE == ATOMIC) atomicAdd(cp, out);
                 else *cp = out;
@@ -400,7 +467,7 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
           for (int j = 0; j < 16; ++j) {
             const int64_t n = n0 + j;
             const int om = (row < rows && n < a.N) ? a.Omint[i * a.ldo + n] : 0;
-            P[row * PB + (cg - blk0) * 16 + j] = V[j] * (__int128)om;
+            P[row * PB + (((cg - blk0) * 16 + j) ^ (row & 7))] = V[j] * (__int128)om;
           }
         }
       }
@@ -413,7 +480,10 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
           const int64_t n = (int64_t)nc * tn + blk0 * 16 + j;
           if (n >= a.N) continue;
           __int128 acc = 0;
-          for (int ii = 0; ii < (int)a.nmode; ++ii) acc += P[(sl * (int)a.nmode + ii) * PB + j];
+          for (int ii = 0; ii < (int)a.nmode; ++ii) {
+            const int r = sl * (int)a.nmode + ii;
+            acc += P[r * PB + (j ^ (r & 7))];
+          }
           const int e_slab = rowE[sl * (int)a.nmode];
           const int64_t aidx = (int64_t)blockIdx.x * a.g + sl;
           const double out = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
@@ -486,10 +556,8 @@ __global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t s
       const int64_t k = (int64_t)kcn * KC + grp * 8 + q;
       v[q] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0;
     }
-    uint32_t w[MAXS][4];
-    slice8(v, E[j], s, w);
     const int idx = ((grp * (tn / 8)) + (j >> 3)) * 8 + (j & 7);      // uint4 index in a plane
-    for (int p = 0; p < s; ++p) blk[(size_t)p * (plane_b / 8) + idx] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    store_digits_s(s, v, E[j], reinterpret_cast<uint16_t*>(blk), plane_b, idx * 8);
   }
 }
 
