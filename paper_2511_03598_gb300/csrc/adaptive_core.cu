@@ -300,6 +300,158 @@ __device__ bool factor_small(const double* G, int b, double* Ri, double* M, doub
   return true;
 }
 
+// ---- double-float (pairs of binary32, ~48 significant bits) for the first CholeskyQR pass, whose
+// factor only has to bring the condition number of the block near 1 (the second pass restores full
+// FP64 orthogonality).  Its dependent operations run on the FP32 pipe (~4 cycles each instead of
+// ~64 for FP64 on this part).  Error-free transformations: Dekker / Knuth two-product and two-sum.
+struct dfl {
+  float h, l;
+};
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = p + e;
+  return {s, e - (s - p)};
+}
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) {
+  const float s = a.h - b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (-b.h - bb);
+  e += a.l - b.l;
+  const float t = s + e;
+  return {t, e - (t - s)};
+}
+__device__ __forceinline__ dfl df_scale(dfl a, float p2) { return {a.h * p2, a.l * p2}; }   // p2 a power of two
+__device__ __forceinline__ dfl df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
+
+// factor_small with the elimination in double-float: G is scaled by 2^(-2 sigma) (exact) so that
+// its largest diagonal entry is near 1 and every intermediate stays in the binary32 range.  Same
+// outputs and contract as factor_small; fails (false) on a non-positive pivot.
+__device__ bool factor_small_df(const double* G, int b, double* Ri, double* M, dfl* rowbuf, dfl* colbuf, double* sc) {
+  __shared__ int fail;
+  __shared__ int sigma_s;
+  const int w2 = 2 * b, tot = b * w2;
+  if (threadIdx.x < 32) {
+    int e = -1022;
+    for (int j = threadIdx.x; j < b; j += 32) {
+      const long long gb = __double_as_longlong(G[j * b + j]);
+      e = max(e, (int)((gb >> 52) & 0x7FF) - 1023);
+    }
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (threadIdx.x == 0) {
+      sigma_s = e >> 1;
+      fail = 0;
+      sc[0] = 1.0;
+    }
+  }
+  __syncthreads();
+  const int sigma = sigma_s;
+  dfl v[FKMAX];
+  int pp[FKMAX], qq[FKMAX];
+#pragma unroll
+  for (int k = 0; k < FKMAX; ++k) {
+    const int e = threadIdx.x + k * NT;
+    pp[k] = -1;
+    qq[k] = 0;
+    v[k] = {0.f, 0.f};
+    if (e < tot) {
+      pp[k] = e / w2;
+      qq[k] = e % w2;
+      v[k] = (qq[k] < b) ? df_from(mul_pow2(G[pp[k] * b + qq[k]], -2 * sigma))
+                         : dfl{(qq[k] - b == pp[k]) ? 1.f : 0.f, 0.f};
+      if (pp[k] == 0) rowbuf[qq[k]] = v[k];
+      if (qq[k] == 0) colbuf[pp[k]] = v[k];
+    }
+  }
+  __syncthreads();
+  dfl scp = {1.f, 0.f};                                       // running product of the d'_j (thread 0)
+  for (int j = 0; j < b; ++j) {
+    const dfl* rb = rowbuf + (j & 1) * w2;
+    const dfl* cb = colbuf + (j & 1) * b;
+    dfl* rn = rowbuf + ((j + 1) & 1) * w2;
+    dfl* cn = colbuf + ((j + 1) & 1) * b;
+    const dfl d = rb[j];
+    const int db = __float_as_int(d.h);
+    const int ef = (db >> 23) & 0xFF;
+    if (db <= 0 || ef == 0 || ef == 0xFF) {                  // not positive and normal
+      if (threadIdx.x == 0) fail = 1;
+      break;
+    }
+    const float inv2 = __int_as_float((254 - ef) << 23);      // 2^-(ef - 127)
+    const dfl dp = df_scale(d, inv2);
+    if (threadIdx.x == 0) {
+      scp = df_mul(scp, dp);
+      sc[j + 1] = df_to(scp);
+    }
+#pragma unroll
+    for (int k = 0; k < FKMAX; ++k) {
+      if (k * NT >= tot) break;
+      const int p = pp[k], q = qq[k];
+      const bool act = p > j && (q < b ? q > j : (q - b <= j || q - b == p));
+      if (act) v[k] = df_sub(df_mul(dp, v[k]), df_mul(cb[p], df_scale(rb[q], inv2)));
+      if (p == j + 1) rn[q] = v[k];
+      if (q == j + 1 && p > j) cn[p] = v[k];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (fail) return false;
+#pragma unroll
+  for (int k = 0; k < FKMAX; ++k)
+    if (pp[k] >= 0 && (qq[k] == pp[k] || (qq[k] >= b && qq[k] - b <= pp[k]))) M[pp[k] * w2 + qq[k]] = df_to(v[k]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * b; e += NT) {
+    const int i = e / b, j = e % b;
+    double r = 0.0;
+    if (i <= j) {
+      const double y = M[j * w2 + j] * sc[j];
+      r = (y > 0.0 && isfinite(y)) ? mul_pow2(M[j * w2 + b + i] * rsqrt_full(y), -sigma) : 0.0;
+    }
+    Ri[e] = r;
+  }
+  __syncthreads();
+  return true;
+}
+
+// R^{-1} for G = R^T R close to the identity (the second CholeskyQR pass): with E = G - I,
+// N = triu(E) - diag(E)/2 and Z = triu(N^T N) - diag(N^T N)/2, R = I + N - Z + O(|E|^3), so
+// R^{-1} = I - N + Z + N^2 + O(|E|^3).  Parallel products only (no dependent elimination).
+// Returns false without touching Ri when b * max|E_ij| > 1e-6 (then the O(|E|^3) term could exceed
+// 1e-18); the caller uses the elimination.  Scratch Nb: b x b.
+__device__ bool rinv_near_identity(const double* G, int b, double* Ri, double* Nb) {
+  __shared__ int too_far;
+  if (threadIdx.x == 0) too_far = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * b; e += NT) {
+    const int i = e / b, j = e % b;
+    const double ev = G[e] - (i == j ? 1.0 : 0.0);
+    if (!(fabs(ev) * b <= 1e-6)) too_far = 1;
+    Nb[e] = (i < j) ? ev : (i == j ? 0.5 * ev : 0.0);
+  }
+  __syncthreads();
+  if (too_far) return false;
+  for (int e = threadIdx.x; e < b * b; e += NT) {
+    const int i = e / b, j = e % b;
+    double r = 0.0;
+    if (i <= j) {
+      double n2 = 0.0, z = 0.0;
+      for (int k = i; k <= j; ++k) n2 = fma(Nb[i * b + k], Nb[k * b + j], n2);      // (N N)_ij, N upper
+      for (int k = 0; k <= i; ++k) z = fma(Nb[k * b + i], Nb[k * b + j], z);        // (N^T N)_ij
+      if (i == j) z *= 0.5;
+      r = (i == j ? 1.0 : 0.0) - Nb[e] + z + n2;
+    }
+    Ri[e] = r;
+  }
+  __syncthreads();
+  return true;
+}
+
 // own rows of X (b columns, shared memory) <- X R^{-1}, one thread per (row, column):
 // out(r, j) = sum_{i <= j} X(r, i) Ri(i, j) in two interleaved partial sums, staged through T and
 // written back after a barrier.
@@ -361,8 +513,16 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   __shared__ double M[BMAX * 2 * BMAX];
   __shared__ double rowbuf[2 * 2 * BMAX];
   __shared__ double colbuf[2 * BMAX];
+  __shared__ dfl rowbuf_df[2 * 2 * BMAX];
+  __shared__ dfl colbuf_df[2 * BMAX];
   __shared__ double sc[BMAX + 1];
   __shared__ double est_s;
+  // first CholeskyQR pass: double-float elimination; second pass: near-identity series, else the
+  // FP64 elimination
+  auto factor1 = [&](int bb) { return factor_small_df(G, bb, Ri, M, rowbuf_df, colbuf_df, sc); };
+  auto factor2 = [&](int bb) {
+    return rinv_near_identity(G, bb, Ri, M) || factor_small(G, bb, Ri, M, rowbuf, colbuf, sc);
+  };
   int64_t lo, hi;
   my_rows(a.m, lo, hi);
   const int nr = (int)(hi - lo);
@@ -418,7 +578,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     double* buf = reduce();
     if (!buf) return finish(ST_TIMEOUT);
     read_totals(buf, b0 * b0, G);
-    if (!factor_small(G, b0, Ri, M, rowbuf, colbuf, sc)) return finish(ST_BREAKDOWN);
+    if (!factor1(b0)) return finish(ST_BREAKDOWN);
     apply_rinv(Qs, ldq, b0, Ri, nr, Tb);
     const bool want = b0 < a.rbar && b0 + bi <= a.width;
     gram_acc(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
@@ -426,7 +586,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     buf = reduce();
     if (!buf) return finish(ST_TIMEOUT);
     read_totals(buf, b0 * b0, G);
-    if (!factor_small(G, b0, Ri, M, rowbuf, colbuf, sc)) return finish(ST_BREAKDOWN);
+    if (!factor2(b0)) return finish(ST_BREAKDOWN);
     apply_rinv(Qs, ldq, b0, Ri, nr, Tb);
     if (want) mul_rinv_t_left(buf + b0 * b0, b0, bi, Ri, Ps);      // (Q1 R2^{-1})^T S = R2^{-T} Q1^T S
     have_p = want;
@@ -468,7 +628,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     // Each qr is one CholeskyQR pass (CholeskyQR2 with the block Gram-Schmidt step in between:
     // the first pass leaves Q_new orthonormal to ~u cond(S)^2, the second to ~u).
     read_totals(bufB + 1, bb * bb, G);
-    if (!factor_small(G, bb, Ri, M, rowbuf, colbuf, sc)) return finish(ST_BREAKDOWN);
+    if (!factor1(bb)) return finish(ST_BREAKDOWN);
     double* Qn = Qs + cc;
     for (int e = threadIdx.x; e < nr * bb; e += NT) Qn[(e / bb) * ldq + e % bb] = Rs[(e / bb) * bi + e % bb];
     __syncthreads();
@@ -492,7 +652,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     double* bufA = reduce();
     if (!bufA) return finish(ST_TIMEOUT);
     read_totals(bufA, bb * bb, G);
-    if (!factor_small(G, bb, Ri, M, rowbuf, colbuf, sc)) return finish(ST_BREAKDOWN);
+    if (!factor2(bb)) return finish(ST_BREAKDOWN);
     apply_rinv(Qn, ldq, bb, Ri, nr, Tb);
     if (want) {
       // P = [Q^T S_next; R2^{-T} Q_new^T S_next]
@@ -537,7 +697,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const int64_t qcols = rbar;
   const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
                                         (size_t)qcols * (size_t)std::max(b0, bi));
-  const size_t static_bytes = 36 * 1024;   // G, R^{-1}, [G | I], pivot buffers, reductions (about 34 KB)
+  const size_t static_bytes = 40 * 1024;   // G, R^{-1}, [G | I], pivot buffers, reductions (about 36 KB)
   if (dyn + static_bytes > (size_t)smem_optin) return TTR_ERR_UNSUPPORTED;
   if (di.raised < (int)dyn) {
     TTR_CUDA(cudaFuncSetAttribute(ac::adaptive_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));

@@ -85,6 +85,17 @@ void Ctx::prof_report() {
       fprintf(stderr, "[ttr profile]   adaptive_core %-22s %9.3f ms (CTA 0, %.0f MHz)\n", names[i], cyc[i] / mhz / 1e3,
               mhz);
   }
+  if (tc_prof) {
+    static const char* modes[] = {"plain", "atomic", "partial contraction"};
+    static const char* names[] = {"setup", "row scan", "producer chunks", "MMA drain", "epilogue", "(MMA issue loop)"};
+    unsigned long long cyc[18] = {};
+    cudaMemcpy(cyc, tc_prof, sizeof(cyc), cudaMemcpyDeviceToHost);
+    for (int m = 0; m < 3; ++m)
+      for (int i = 0; i < 6; ++i)
+        if (cyc[m * 6 + i])
+          fprintf(stderr, "[ttr profile]   sliced %-20s %-18s %9.3f ms (CTA 0, cycles / 2070 MHz)\n", modes[m], names[i],
+                  cyc[m * 6 + i] / 2070.0 / 1e3);
+  }
   for (auto& pe : prof) cudaEventDestroy(pe.second);
   cudaEventDestroy(prof_start);
   prof.clear();

@@ -168,14 +168,16 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* X, int64
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the partials of the other CTAs are read through L2 (__ldcg): L1 is not coherent across SMs
+  // and the workspace is reused by every reduction of the call
   for (int o = threadIdx.x; o < ab; o += blockDim.x) {
     double t0 = 0.0, t1 = 0.0;
     unsigned blk = 0;
     for (; blk + 1 < gridDim.x; blk += 2) {
-      t0 += ws[(int64_t)blk * ab + o];
-      t1 += ws[(int64_t)(blk + 1) * ab + o];
+      t0 += __ldcg(ws + (int64_t)blk * ab + o);
+      t1 += __ldcg(ws + (int64_t)(blk + 1) * ab + o);
     }
-    if (blk < gridDim.x) t0 += ws[(int64_t)blk * ab + o];
+    if (blk < gridDim.x) t0 += __ldcg(ws + (int64_t)blk * ab + o);
     const double v = t0 + t1;
     G[o] = v;
     if (C) C[(o / b) * ldc + (o % b)] = v;

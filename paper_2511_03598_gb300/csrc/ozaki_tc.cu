@@ -77,7 +77,12 @@ struct Args {
   int watomic;                        // partial contractions split over K: add into W atomically
   int kseg;                           // K per CTA (multiple of KC, <= KSEG); blockIdx.z selects the segment
   int* err;
+  unsigned long long* prof;           // optional phase cycles of CTA (0, 0, 0) (launch-timeline profiling)
 };
+
+// phases of one CTA, timed by thread 0 (setup, row scan, producers' chunk loop, waiting for the
+// last MMAs, epilogue) and by the MMA thread (its chunk loop)
+enum TcPhase { TP_SETUP = 0, TP_SCAN, TP_CHUNKS, TP_DRAIN, TP_EPILOGUE, TP_MMA_LOOP, TP_COUNT };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -266,43 +271,70 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
     slabE[tid] = 1;
     rowE[tid] = 1;
   }
+  const bool timed = a.prof && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+  const int pslot = TP_COUNT * MODE;
+  long long t_prev = clock64();
+  auto mark = [&](int ph) {
+    if (timed && tid == 0) {
+      const long long t = clock64();
+      atomicAdd(a.prof + pslot + ph, (unsigned long long)(t - t_prev));
+      t_prev = t;
+    }
+  };
   __syncthreads();
+  mark(TP_SETUP);
 
   // ---- pass 1: exponent scale of every row over this K segment (many loads in flight)
   if (warp >= NWP) {
     // the MMA warp takes no part in the scan
   } else if (AKFAST) {
-    constexpr int RPW = TM / NWP;             // rows per warp
-    int em[RPW];
+    // row-major A: a warp scans 8 rows, two at a time, each lane 8 k values per row (16 loads in
+    // flight per lane)
+    constexpr int RPW = TM / NWP;
+    constexpr int KPL = KSEG / 32;
+#pragma unroll 1
+    for (int r0 = 0; r0 < RPW; r0 += 2) {
+      double x[2][KPL];
 #pragma unroll
-    for (int r = 0; r < RPW; ++r) em[r] = 1;
-    for (int k = lane; k < kseg_len; k += 32) {
+      for (int rr = 0; rr < 2; ++rr) {
+        const int row = warp * RPW + r0 + rr;
+        const double* rp = a.A + (m0 + row) * a.sam + kseg0;
 #pragma unroll
-      for (int r = 0; r < RPW; ++r) {
-        const int row = warp * RPW + r;
-        if (row < rows) em[r] = max(em[r], exp_field(__ldg(a.A + (m0 + row) * a.sam + kseg0 + k)));
+        for (int j = 0; j < KPL; ++j) {
+          const int k = lane + 32 * j;
+          x[rr][j] = (row < rows && k < kseg_len) ? __ldcg(rp + k) : 0.0;
+        }
       }
-    }
 #pragma unroll
-    for (int r = 0; r < RPW; ++r) {
-      const int e = __reduce_max_sync(0xffffffffu, em[r]);
-      if (lane == 0) rowE[warp * RPW + r] = e;
+      for (int rr = 0; rr < 2; ++rr) {
+        int e = 1;
+#pragma unroll
+        for (int j = 0; j < KPL; ++j) e = max(e, exp_field(x[rr][j]));
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0) rowE[warp * RPW + r0 + rr] = e;
+      }
     }
   } else {
-    // NP/TM threads per row, interleaved over k
-    const int row = tid % TM, part = tid / TM;
-    constexpr int PARTS = NP / TM;
-    int e0 = 1, e1 = 1;
+    // column-major A: lanes take 32 consecutive rows (coalesced), the four warps of a row group
+    // interleave over k, 16 loads in flight per lane
+    const int row = (warp & 3) * 32 + lane, kp = warp >> 2;
+    constexpr int KP = NWP / 4;
+    int e = 1;
     if (row < rows) {
       const double* colp = a.A + (m0 + row) * a.sam + kseg0 * a.sak;
-      int k = part;
-      for (; k + PARTS < kseg_len; k += 2 * PARTS) {
-        e0 = max(e0, exp_field(__ldg(colp + (int64_t)k * a.sak)));
-        e1 = max(e1, exp_field(__ldg(colp + (int64_t)(k + PARTS) * a.sak)));
+#pragma unroll 1
+      for (int k0 = kp; k0 < kseg_len; k0 += 16 * KP) {
+        double x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k = k0 + KP * j;
+          x[j] = (k < kseg_len) ? __ldcg(colp + (int64_t)k * a.sak) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) e = max(e, exp_field(x[j]));
       }
-      if (k < kseg_len) e0 = max(e0, exp_field(__ldg(colp + (int64_t)k * a.sak)));
     }
-    atomicMax(&rowE[row], max(e0, e1));
+    atomicMax(&rowE[row], e);
   }
   __syncthreads();
   if (MODE == RLM) {
@@ -317,6 +349,7 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   bool ok = true;
+  mark(TP_SCAN);
 
   // ---- K loop over chunks of 32: the producer warps slice chunk c into digit buffer c % 2 and
   // arrive on full[c % 2]; the MMA warp waits for it, issues the chunk's products and commits them
@@ -324,6 +357,7 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   // Every wait is bounded; a wait that runs out sets the error flag and the CTA winds down.
   if (warp == MMA_WARP) {
     if (lane == 0) {
+      const long long tm0 = clock64();
       for (int c = 0; c < nchunk && ok; ++c) {
         const int b = c & 1;
         ok = mbar_wait(smem_u32(&full[b]), (uint32_t)((c >> 1) & 1), a.err);
@@ -349,57 +383,74 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&empty[b])));
       }
+      if (timed) atomicAdd(a.prof + pslot + TP_MMA_LOOP, (unsigned long long)(clock64() - tm0));
     }
     __syncwarp();
   } else {
+    // A digits: 128 rows x 4 groups of 8 consecutive k = 512 tasks, TASKS per thread; the values of
+    // chunk c + 1 are loaded into registers while chunk c is being sliced
+    constexpr int TASKS = (TM * (KC / 8)) / NP;
+    int trow[TASKS], tgrp[TASKS];
+#pragma unroll
+    for (int i = 0; i < TASKS; ++i) {
+      const int u = tid + NP * i;
+      trow[i] = AKFAST ? (u >> 2) : (u % TM);
+      tgrp[i] = AKFAST ? (u & 3) : (u / TM);
+    }
+    auto load_chunk = [&](int c, double (&v)[TASKS][8]) {
+#pragma unroll
+      for (int i = 0; i < TASKS; ++i) {
+        const double* src = a.A + (m0 + trow[i]) * a.sam + (kseg0 + c * KC + tgrp[i] * 8) * a.sak;
+        const int klim = kseg_len - (c * KC + tgrp[i] * 8);
+        const bool rok = trow[i] < rows;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[i][q] = (rok && q < klim) ? __ldcg(src + q * a.sak) : 0.0;
+      }
+    };
+    double vc[TASKS][8];
+    if (nchunk > 0) load_chunk(0, vc);
     for (int c = 0; c < nchunk && ok; ++c) {
       const int b = c & 1;
       if (c >= 2) ok = mbar_wait(smem_u32(&empty[b]), (uint32_t)(((c - 2) >> 1) & 1), a.err);
       if (!ok) break;
       uint16_t* Ap = (uint16_t*)bufs[b];
       uint16_t* Bpl = Ap + (size_t)s * PLANE_A;
-      // A digits: 128 rows x 4 groups of 8 consecutive k = 512 tasks, TASKS per thread, all loads first
-      {
-        constexpr int TASKS = (TM * (KC / 8)) / NP;
-        double v[TASKS][8];
-#pragma unroll
-        for (int i = 0; i < TASKS; ++i) {
-          const int u = tid + NP * i;
-          const int row = AKFAST ? (u >> 2) : (u % TM);
-          const int grp = AKFAST ? (u & 3) : (u / TM);
-          const int kl = c * KC + grp * 8;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int kk = kl + q;
-            v[i][q] = (row < rows && kk < kseg_len) ? __ldg(a.A + (m0 + row) * a.sam + (kseg0 + kk) * a.sak) : 0.0;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < TASKS; ++i) {
-          const int u = tid + NP * i;
-          const int row = AKFAST ? (u >> 2) : (u % TM);
-          const int grp = AKFAST ? (u & 3) : (u / TM);
-          const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
-          store_digits_s(s, v[i], rowE[row], Ap, PLANE_A, idx);
-        }
-      }
-      // B digit planes of this chunk: a straight copy of s * tn * 64 bytes
-      {
+      if (tid == 0) {
+        // B digit planes of this chunk (s * tn * 64 contiguous bytes, 16-byte aligned at both ends):
+        // one bulk async copy that completes on full[b]
         const uint4* src = a.Bp + ((size_t)nc * a.kchunks + (kc0 + c)) * (size_t)s * (plane_b / 8);
-        uint4* dst = reinterpret_cast<uint4*>(Bpl);
-#pragma unroll 4
-        for (int e = tid; e < s * (plane_b / 8); e += NP) dst[e] = __ldg(src + e);
+        const uint32_t bytes = (uint32_t)(s * plane_b * 2);
+        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])), "r"(bytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(Bpl)),
+                     "l"(src), "r"(bytes), "r"(smem_u32(&full[b]))
+                     : "memory");
       }
+      double vn[TASKS][8];
+      if (c + 1 < nchunk) load_chunk(c + 1, vn);
+#pragma unroll
+      for (int i = 0; i < TASKS; ++i) {
+        const int row = trow[i], grp = tgrp[i];
+        const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
+        store_digits_s(s, vc[i], rowE[row], Ap, PLANE_A, idx);
+      }
+#pragma unroll
+      for (int i = 0; i < TASKS; ++i)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) vc[i][q] = vn[i][q];
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[b])) : "memory");
     }
   }
+  mark(TP_CHUNKS);
   if (ok && nchunk > 0) {
     const int c = nchunk - 1;
     ok = mbar_wait(smem_u32(&empty[c & 1]), (uint32_t)((c >> 1) & 1), a.err);
   }
   ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;");
+  mark(TP_DRAIN);
 
   // ---- epilogue: warp w reads TMEM lane quarter (w % 4); the two warps of a quarter take
   // alternate 16-column groups.  Partial contractions stage int128 products per 64-column block.
@@ -496,6 +547,7 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
+  mark(TP_EPILOGUE);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
@@ -571,7 +623,15 @@ static size_t smem_bytes(int s, int tn, int mode) {
 }
 
 template <int MODE, bool AKFAST>
-static int launch(Ctx& c, const Args& a, dim3 grid, const char* name) {
+static int launch(Ctx& c, const Args& a_in, dim3 grid, const char* name) {
+  Args a = a_in;
+  if (c.profiling) {
+    if (!c.tc_prof) {
+      TTR_CHECK(c.alloc_t(&c.tc_prof, 3 * TP_COUNT));
+      TTR_CUDA(cudaMemsetAsync(c.tc_prof, 0, sizeof(unsigned long long) * 3 * TP_COUNT, c.stream));
+    }
+    a.prof = c.tc_prof;
+  }
   const size_t sm = smem_bytes(a.s, a.tn, MODE);
   auto kern = sliced_kernel<MODE, AKFAST>;
   // the shared-memory limit is raised once per device to the largest size requested so far

@@ -44,6 +44,7 @@ struct Ctx {
   unsigned* ac_bar = nullptr;      // adaptive_core: grid barrier counter/generation
   int* ac_io = nullptr;            // adaptive_core: status, column count, estimate count
   unsigned long long* ac_prof = nullptr;   // adaptive_core phase cycles (profiling only)
+  unsigned long long* tc_prof = nullptr;   // tensor-core kernel phase cycles per mode (profiling only)
   void* bprep = nullptr;           // tensor-core B-operand workspace (digit planes, scales)
   size_t bprep_bytes = 0;
   int workspace();
