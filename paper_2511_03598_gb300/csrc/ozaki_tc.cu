@@ -209,15 +209,6 @@ __device__ __forceinline__ double i128_to_double(__int128 V, int X) {
   return __longlong_as_double((long long)(sign | ((uint64_t)field << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
-// Integer value of an integer-valued binary32 with |x| < 2^31, by integer operations only (the
-// hardware float-to-int64 conversion runs on the FP64 pipe of this part, ~64x slower).
-__device__ __forceinline__ int f2i_exact(uint32_t fb) {
-  const int ex = (int)((fb >> 23) & 0xFFu) - 150;          // |x| = mant * 2^ex
-  const int mant = (int)((fb & 0x7FFFFFu) | 0x800000u);
-  const int v = (ex >= 0) ? (mant << ex) : (ex > -24 ? (mant >> -ex) : 0);
-  return (fb >> 31) ? -v : v;
-}
-
 __device__ __forceinline__ int exp_field(double x) {
   return (int)(((uint64_t)__double_as_longlong(x) >> 52) & 0x7FF);
 }
@@ -288,31 +279,22 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   if (warp >= NWP) {
     // the MMA warp takes no part in the scan
   } else if (AKFAST) {
-    // row-major A: a warp scans 8 rows, two at a time, each lane 8 k values per row (16 loads in
-    // flight per lane)
+    // row-major A: a warp scans 8 rows; each step loads one value of each row per lane
     constexpr int RPW = TM / NWP;
-    constexpr int KPL = KSEG / 32;
-#pragma unroll 1
-    for (int r0 = 0; r0 < RPW; r0 += 2) {
-      double x[2][KPL];
+    int em[RPW];
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int row = warp * RPW + r0 + rr;
-        const double* rp = a.A + (m0 + row) * a.sam + kseg0;
+    for (int r = 0; r < RPW; ++r) em[r] = 1;
+    for (int k = lane; k < kseg_len; k += 32) {
 #pragma unroll
-        for (int j = 0; j < KPL; ++j) {
-          const int k = lane + 32 * j;
-          x[rr][j] = (row < rows && k < kseg_len) ? __ldcg(rp + k) : 0.0;
-        }
+      for (int r = 0; r < RPW; ++r) {
+        const int row = warp * RPW + r;
+        if (row < rows) em[r] = max(em[r], exp_field(__ldcg(a.A + (m0 + row) * a.sam + kseg0 + k)));
       }
+    }
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        int e = 1;
-#pragma unroll
-        for (int j = 0; j < KPL; ++j) e = max(e, exp_field(x[rr][j]));
-        e = __reduce_max_sync(0xffffffffu, e);
-        if (lane == 0) rowE[warp * RPW + r0 + rr] = e;
-      }
+    for (int r = 0; r < RPW; ++r) {
+      const int e = __reduce_max_sync(0xffffffffu, em[r]);
+      if (lane == 0) rowE[warp * RPW + r] = e;
     }
   } else {
     // column-major A: lanes take 32 consecutive rows (coalesced), the four warps of a row group
@@ -465,7 +447,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
       const int blk1 = min(ngroups, blk0 + PB / 16);
       for (int cg = blk0 + half; warp < NWP && cg < blk1; cg += NWP / 4) {
         // V = sum_t acc_t 2^(7(s-1-t)) = Vh 2^35 + Vl, both parts in 64 bits: |acc_t| < 2^25, so
-        // Vl (shifts 0..28) < 2^56 and Vh (shifts 35..49, less 35) < 2^41
+        // Vl (shifts 0..28) < 2^56 and Vh (shifts 35..49, less 35) < 2^41.  The accumulators are
+        // integer-valued binary32 values, so the float-to-int32 conversion is exact.
         long long Vh[16], Vl[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) Vh[j] = Vl[j] = 0;
@@ -483,11 +466,11 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
           if (shift >= 35) {
             const long long mul = 1LL << (shift - 35);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) Vh[j] += (long long)f2i_exact(r[j]) * mul;
+            for (int j = 0; j < 16; ++j) Vh[j] += (long long)__float2int_rz(__uint_as_float(r[j])) * mul;
           } else {
             const long long mul = 1LL << shift;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) Vl[j] += (long long)f2i_exact(r[j]) * mul;
+            for (int j = 0; j < 16; ++j) Vl[j] += (long long)__float2int_rz(__uint_as_float(r[j])) * mul;
           }
         }
         // with s <= 6, Vh is the top diagonal alone (|Vh| < 2^25), so V < 2^61 fits in 64 bits
