@@ -73,6 +73,8 @@ typedef struct {
   int64_t width_hint;     /* initial sketch width drawn on the device (0 = automatic); never
                              changes results, only how often the partial contractions are
                              extended (Algorithm 5) */
+  int32_t kernel_timing;  /* 1: time the block-loop and partial-contraction kernels with CUDA
+                             events on `stream` (fields ms_block_loop ... of ttr_result) */
 } ttr_options;
 
 typedef struct {
@@ -92,10 +94,18 @@ typedef struct {
   float ms_sweep_lr;      /* device time of the left-to-right sweep */
   float ms_total;         /* device time of the whole call */
   int64_t kernel_launches;/* kernels this call launched */
+  /* with opts->kernel_timing (else 0): device time, from CUDA events recorded around each launch
+   * on `stream`, and algorithmic work of the two dominant kernels */
+  double ms_block_loop;   /* persistent adaptive block-loop kernel (Algorithm 6), all launches */
+  double flops_block_loop;/* its FP64 arithmetic (2 flops per multiply-add) for the blocks run */
+  double ms_rl_kernel;    /* tensor-core partial-contraction kernel (Algorithm 3), all launches */
+  double bytes_rl_kernel; /* its algorithmic bytes: each core read once, W_{k+1} read, W_k written */
+  int32_t n_block_loop;   /* launches timed */
+  int32_t n_rl_kernel;
 } ttr_result;
 
 /* Fill `opts` with defaults: FP64, adap_r off, scale 1, nrmx 0 (estimate), f_init 0.1,
- * f_inc 0.05 (the values of Sec. 4.2), width_hint 0. */
+ * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0. */
 void ttr_default_options(ttr_options* opts);
 
 /* Algorithm 4 (Sec. 3.2): fixed-rank randomize-then-orthogonalize with a KRP sketch.

@@ -24,7 +24,7 @@ STATUS = {0: "TTR_OK", 1: "TTR_ERR_ARG", 2: "TTR_ERR_OOM", 3: "TTR_ERR_NONFINITE
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("slices", ctypes.c_int32), ("adap_r", ctypes.c_int32),
                 ("adap_r_tau_scale", ctypes.c_double), ("nrmx", ctypes.c_double), ("f_init", ctypes.c_double),
-                ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64)]
+                ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64), ("kernel_timing", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -33,7 +33,10 @@ class Result(ctypes.Structure):
                 ("nrmx", ctypes.c_double), ("width", ctypes.c_int64), ("extensions", ctypes.c_int32),
                 ("n_estimates", ctypes.c_int32), ("estimates", ctypes.POINTER(ctypes.c_double)),
                 ("est_core", ctypes.POINTER(ctypes.c_int32)), ("ms_sketch_rl", ctypes.c_float),
-                ("ms_sweep_lr", ctypes.c_float), ("ms_total", ctypes.c_float), ("kernel_launches", ctypes.c_int64)]
+                ("ms_sweep_lr", ctypes.c_float), ("ms_total", ctypes.c_float), ("kernel_launches", ctypes.c_int64),
+                ("ms_block_loop", ctypes.c_double), ("flops_block_loop", ctypes.c_double),
+                ("ms_rl_kernel", ctypes.c_double), ("bytes_rl_kernel", ctypes.c_double),
+                ("n_block_loop", ctypes.c_int32), ("n_rl_kernel", ctypes.c_int32)]
 
 
 class TTRoundError(RuntimeError):
@@ -98,11 +101,13 @@ def _tt_args(cores):
 
 
 def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = False, adap_r_tau_scale: float = 1.0,
-            nrmx: float = 0.0, f_init: float = 0.1, f_inc: float = 0.05, width_hint: int = 0) -> Options:
+            nrmx: float = 0.0, f_init: float = 0.1, f_inc: float = 0.05, width_hint: int = 0,
+            kernel_timing: bool = False) -> Options:
     o = Options()
     lib().ttr_default_options(ctypes.byref(o))
     o.precision, o.slices, o.adap_r = precision, slices, int(adap_r)
     o.adap_r_tau_scale, o.nrmx, o.f_init, o.f_inc, o.width_hint = adap_r_tau_scale, nrmx, f_init, f_inc, width_hint
+    o.kernel_timing = int(kernel_timing)
     return o
 
 
@@ -129,7 +134,9 @@ class Rounded:
                 "estimates": [r.estimates[i] for i in range(ne)] if ne else [],
                 "est_core": [int(r.est_core[i]) for i in range(ne)] if ne else [],
                 "ms_sketch_rl": r.ms_sketch_rl, "ms_sweep_lr": r.ms_sweep_lr, "ms_total": r.ms_total,
-                "kernel_launches": int(r.kernel_launches)}
+                "kernel_launches": int(r.kernel_launches),
+                "ms_block_loop": r.ms_block_loop, "flops_block_loop": r.flops_block_loop, "n_block_loop": r.n_block_loop,
+                "ms_rl_kernel": r.ms_rl_kernel, "bytes_rl_kernel": r.bytes_rl_kernel, "n_rl_kernel": r.n_rl_kernel}
 
     def core_ptr(self, k: int) -> int:
         return int(self._res.cores[k])

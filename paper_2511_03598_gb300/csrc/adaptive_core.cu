@@ -733,6 +733,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
     a.prof = c.ac_prof;
   }
   void* params[] = {&a};
+  c.time_begin(Ctx::KT_BLOCK_LOOP);
   TTR_CUDA(cudaLaunchCooperativeKernel((const void*)ac::adaptive_core_kernel, dim3(nblocks), dim3(ac::NT), params, dyn,
                                        c.stream));
   TTR_CHECK(c.check_launch("adaptive_core"));
@@ -743,6 +744,30 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   *status = io[0];
   *cc = io[1];
   *nest = io[2];
+  if (c.timing) {
+    // FP64 arithmetic of the blocks the kernel ran (2 flops per multiply-add), in its order:
+    // first block (two CholeskyQR passes and the first coefficients), then per estimate the
+    // residual, its norm and Gram matrix and, when the loop went on, the two passes with the block
+    // Gram-Schmidt step between them and the next block's coefficients
+    const double M = (double)m;
+    double f = 0.0;
+    int cur = cc0;
+    if (cc0 == 0) {
+      f += 2.0 * (2.0 * M * b0 * b0 + M * b0 * b0) + 2.0 * M * b0 * bi;
+      cur = b0;
+    } else {
+      f += 2.0 * M * cur * bi;
+    }
+    for (int i = 0; i < *nest && cur < rbar; ++i) {
+      const int bb = std::min(bi, rbar - cur);
+      f += 2.0 * M * cur * bi + 2.0 * M * bi + 2.0 * M * bb * bb;
+      if (i + 1 < *nest || *status != ac::ST_DONE) {
+        f += M * bb * bb + 4.0 * M * cur * bb + 2.0 * M * bb * bb + 2.0 * M * (cur + bb) * bi + M * bb * bb;
+        cur += bb;
+      }
+    }
+    c.time_end(f);
+  }
   return TTR_OK;
 }
 

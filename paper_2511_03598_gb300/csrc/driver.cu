@@ -118,6 +118,41 @@ int Ctx::check_launch(const char* what) {
   return TTR_OK;
 }
 
+void Ctx::time_begin(int kind) {
+  if (!timing) return;
+  KernelTime t{nullptr, nullptr, kind, 0.0};
+  cudaEventCreate(&t.a);
+  cudaEventCreate(&t.b);
+  cudaEventRecord(t.a, stream);
+  ktimes.push_back(t);
+}
+
+void Ctx::time_end(double work) {
+  if (!timing || ktimes.empty()) return;
+  cudaEventRecord(ktimes.back().b, stream);
+  ktimes.back().work = work;
+}
+
+void Ctx::time_collect(ttr_result* out) {
+  for (auto& t : ktimes) {
+    float ms = 0.f;
+    if (out && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      if (t.kind == KT_BLOCK_LOOP) {
+        out->ms_block_loop += ms;
+        out->flops_block_loop += t.work;
+        out->n_block_loop++;
+      } else {
+        out->ms_rl_kernel += ms;
+        out->bytes_rl_kernel += t.work;
+        out->n_rl_kernel++;
+      }
+    }
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  ktimes.clear();
+}
+
 int Ctx::workspace() {
   if (ws) return TTR_OK;
   TTR_CHECK(alloc_t(&ws, 128 * 1024));
@@ -127,6 +162,7 @@ int Ctx::workspace() {
 }
 
 void Ctx::release() {
+  time_collect(nullptr);
   for (void* p : owned) cudaFreeAsync(p, stream);
   owned.clear();
 }
@@ -536,6 +572,7 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   Ctx c;
   c.stream = stream;
   c.prof_begin();
+  c.timing = o.kernel_timing != 0;
   Timer tm;
   tm.rec(0, stream);
   Engine E;
@@ -593,6 +630,7 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   out->ms_sweep_lr = tm.ms(1, 2);
   out->ms_total = tm.ms(0, 2);
   out->kernel_launches = c.launches;
+  c.time_collect(out);
   disown(c, out->arena);
   return TTR_OK;
 }
@@ -606,6 +644,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   Ctx c;
   c.stream = stream;
   c.prof_begin();
+  c.timing = o.kernel_timing != 0;
   Timer tm;
   tm.rec(0, stream);
   const int d = X.d;
@@ -846,6 +885,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   out->ms_sweep_lr = tm.ms(1, 2);
   out->ms_total = tm.ms(0, 2);
   out->kernel_launches = c.launches;
+  c.time_collect(out);
   disown(c, out->arena);
   return TTR_OK;
 }
@@ -1049,6 +1089,7 @@ void ttr_default_options(ttr_options* o) {
   o->f_init = 0.1;
   o->f_inc = 0.05;
   o->width_hint = 0;
+  o->kernel_timing = 0;
 }
 
 static int finish(int st, ttr_result* out, cudaStream_t s) {

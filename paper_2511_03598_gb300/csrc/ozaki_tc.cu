@@ -755,7 +755,10 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
     TTR_CUDA(cudaMemset2DAsync(Wout, ldwo * sizeof(double), 0, w * sizeof(double), r0, c.stream));
   }
   dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, ksplit);
-  return launch<RLM, true>(c, a, grid, "tc_rl_step");
+  c.time_begin(Ctx::KT_RL);
+  TTR_CHECK((launch<RLM, true>(c, a, grid, "tc_rl_step")));
+  c.time_end(8.0 * ((double)r0 * n * r1 + (double)r1 * w + (double)r0 * w));
+  return TTR_OK;
 }
 
 int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,

@@ -57,6 +57,19 @@ struct Ctx {
   void prof_begin();
   void prof_report();
 
+  // optional kernel timing (ttr_options::kernel_timing): event pairs around selected launches
+  enum { KT_BLOCK_LOOP = 0, KT_RL = 1 };
+  struct KernelTime {
+    cudaEvent_t a, b;
+    int kind;
+    double work;
+  };
+  bool timing = false;
+  std::vector<KernelTime> ktimes;
+  void time_begin(int kind);
+  void time_end(double work);
+  void time_collect(ttr_result* out);   // after the stream has been synchronized
+
   int alloc(void** p, size_t bytes);
   template <typename T>
   int alloc_t(T** p, size_t count) {
