@@ -52,6 +52,7 @@ struct Args {
   double* est_out;      // estimates in order
   int* io;              // [0] status, [1] cc, [2] number of estimates
   unsigned long long* prof;   // optional: SM cycles per phase, seen by CTA 0 (null: off)
+  int sshift;           // the sketch is held scaled by 2^sshift (double-float range; 0 in FP64)
 };
 
 // Phase timer of CTA 0 (launch-timeline profiling only): cycles since the previous mark are
@@ -133,35 +134,97 @@ __device__ __forceinline__ void red_advance(Red& r) {
   r.i++;
 }
 
+// ---- arithmetic of the block loop.  F64: native FP64.  DF: double-float (pairs of binary32,
+// ~48 significant bits) on the FP32 pipe, which runs ~64x the FP64 rate of this part; used with the
+// sliced precision form, whose contractions already carry errors of ~1e-12.  Both keep the
+// cross-CTA sums in FP64 (atomic additions in L2) and the small factorizations as they are.
+struct dfl {
+  float h, l;
+};
+__device__ __forceinline__ dfl df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
+// c + a b
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = c.h + p;
+  const float bb = s - c.h;
+  const float err = (c.h - (s - bb)) + (p - bb);
+  const float lo = err + (e + c.l);
+  const float t = s + lo;
+  return {t, lo - (t - s)};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float err = (a.h - (s - bb)) + (b.h - bb);
+  const float lo = err + (a.l + b.l);
+  const float t = s + lo;
+  return {t, lo - (t - s)};
+}
+
+struct F64 {
+  using T = double;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T from(double x) { return x; }
+  static __device__ __forceinline__ double to(T x) { return x; }
+  static __device__ __forceinline__ T fma(T a, T b, T c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T neg(T a) { return -a; }
+  static __device__ __forceinline__ T shfl_xor(T a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+};
+struct DF {
+  using T = dfl;
+  static __device__ __forceinline__ T zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ T from(double x) { return df_from(x); }
+  static __device__ __forceinline__ double to(T x) { return df_to(x); }
+  static __device__ __forceinline__ T fma(T a, T b, T c) { return df_fma(a, b, c); }
+  static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+  static __device__ __forceinline__ T neg(T a) { return {-a.h, -a.l}; }
+  static __device__ __forceinline__ T shfl_xor(T a, int o) {
+    return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+  }
+};
+
 // Each CTA keeps its own rows resident in shared memory:
 //   Qs  [nr][ldq]  rows of Q,    Ss [nr][ldw] rows of the sketch S_all,   Rs [nr][bi] residual block.
 // buf[i*b + j] += sum_{own rows} X(r, i) Y(r, j), i < a, j < b   (X, Y in shared memory)
-__device__ void gram_acc(const double* X, int ldx, const double* Y, int ldy, int a, int b, int nr, double* buf) {
+template <class A>
+__device__ void gram_acc(const typename A::T* X, int ldx, const typename A::T* Y, int ldy, int a, int b, int nr,
+                         double* buf) {
+  using T = typename A::T;
   for (int o = threadIdx.x; o < a * b; o += NT) {
     const int i = o / b, j = o % b;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;      // four independent chains
+    T s0 = A::zero(), s1 = A::zero(), s2 = A::zero(), s3 = A::zero();      // four independent chains
     int r = 0;
     for (; r + 3 < nr; r += 4) {
-      s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
-      s1 = fma(X[(r + 1) * ldx + i], Y[(r + 1) * ldy + j], s1);
-      s2 = fma(X[(r + 2) * ldx + i], Y[(r + 2) * ldy + j], s2);
-      s3 = fma(X[(r + 3) * ldx + i], Y[(r + 3) * ldy + j], s3);
+      s0 = A::fma(X[r * ldx + i], Y[r * ldy + j], s0);
+      s1 = A::fma(X[(r + 1) * ldx + i], Y[(r + 1) * ldy + j], s1);
+      s2 = A::fma(X[(r + 2) * ldx + i], Y[(r + 2) * ldy + j], s2);
+      s3 = A::fma(X[(r + 3) * ldx + i], Y[(r + 3) * ldy + j], s3);
     }
-    for (; r < nr; ++r) s0 = fma(X[r * ldx + i], Y[r * ldy + j], s0);
-    if (nr > 0) atomicAdd(buf + o, (s0 + s1) + (s2 + s3));
+    for (; r < nr; ++r) s0 = A::fma(X[r * ldx + i], Y[r * ldy + j], s0);
+    if (nr > 0) atomicAdd(buf + o, A::to(A::add(A::add(s0, s1), A::add(s2, s3))));
   }
 }
 
 // buf[0] += sum of squares of the own rows of X (b columns, shared memory)
-__device__ void sumsq_acc(const double* X, int ldx, int b, int nr, double* buf) {
+template <class A>
+__device__ void sumsq_acc(const typename A::T* X, int ldx, int b, int nr, double* buf) {
+  using T = typename A::T;
   __shared__ double red[NT / 32];
-  double s = 0.0;
+  T s = A::zero();
   for (int e = threadIdx.x; e < nr * b; e += NT) {
-    const double v = X[(e / b) * ldx + e % b];
-    s = fma(v, v, s);
+    const T v = X[(e / b) * ldx + e % b];
+    s = A::fma(v, v, s);
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl_xor(s, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = A::to(s);
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -174,6 +237,11 @@ __device__ void sumsq_acc(const double* X, int ldx, int b, int nr, double* buf) 
 // shared-memory copy of the first n totals of buf (written by other CTAs: read through L2)
 __device__ void read_totals(const double* buf, int n, double* dst) {
   for (int o = threadIdx.x; o < n; o += NT) dst[o] = __ldcg(buf + o);
+  __syncthreads();
+}
+template <class A>
+__device__ void read_totals_t(const double* buf, int n, typename A::T* dst) {
+  for (int o = threadIdx.x; o < n; o += NT) dst[o] = A::from(__ldcg(buf + o));
   __syncthreads();
 }
 
@@ -304,9 +372,6 @@ __device__ bool factor_small(const double* G, int b, double* Ri, double* M, doub
 // factor only has to bring the condition number of the block near 1 (the second pass restores full
 // FP64 orthogonality).  Its dependent operations run on the FP32 pipe (~4 cycles each instead of
 // ~64 for FP64 on this part).  Error-free transformations: Dekker / Knuth two-product and two-sum.
-struct dfl {
-  float h, l;
-};
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   const float p = a.h * b.h;
   float e = fmaf(a.h, b.h, -p);
@@ -324,12 +389,6 @@ __device__ __forceinline__ dfl df_sub(dfl a, dfl b) {
   return {t, e - (t - s)};
 }
 __device__ __forceinline__ dfl df_scale(dfl a, float p2) { return {a.h * p2, a.l * p2}; }   // p2 a power of two
-__device__ __forceinline__ dfl df_from(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
-
 // factor_small with the elimination in double-float: G is scaled by 2^(-2 sigma) (exact) so that
 // its largest diagonal entry is near 1 and every intermediate stays in the binary32 range.  Same
 // outputs and contract as factor_small; fails (false) on a non-positive pivot.
@@ -455,59 +514,75 @@ __device__ bool rinv_near_identity(const double* G, int b, double* Ri, double* N
 // own rows of X (b columns, shared memory) <- X R^{-1}, one thread per (row, column):
 // out(r, j) = sum_{i <= j} X(r, i) Ri(i, j) in two interleaved partial sums, staged through T and
 // written back after a barrier.
-__device__ void apply_rinv(double* X, int ldx, int b, const double* Ri, int nr, double* T) {
+template <class A>
+__device__ void apply_rinv(typename A::T* X, int ldx, int b, const typename A::T* Ri, int nr, typename A::T* T) {
+  using V = typename A::T;
   for (int e = threadIdx.x; e < nr * b; e += NT) {
     const int r = e / b, j = e % b;
-    const double* xr = X + r * ldx;
-    double v0 = 0.0, v1 = 0.0;
+    const V* xr = X + r * ldx;
+    V v0 = A::zero(), v1 = A::zero();
     int i = 0;
     for (; i + 1 <= j; i += 2) {
-      v0 = fma(xr[i], Ri[i * b + j], v0);
-      v1 = fma(xr[i + 1], Ri[(i + 1) * b + j], v1);
+      v0 = A::fma(xr[i], Ri[i * b + j], v0);
+      v1 = A::fma(xr[i + 1], Ri[(i + 1) * b + j], v1);
     }
-    if (i <= j) v0 = fma(xr[i], Ri[i * b + j], v0);
-    T[e] = v0 + v1;
+    if (i <= j) v0 = A::fma(xr[i], Ri[i * b + j], v0);
+    T[e] = A::add(v0, v1);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * b; e += NT) X[(e / b) * ldx + e % b] = T[e];
   __syncthreads();
 }
 
+// dst[0:n] = the FP64 values src[0:n] in the block loop's arithmetic (shared memory)
+template <class A>
+__device__ void to_arith(const double* src, int n, typename A::T* dst) {
+  for (int o = threadIdx.x; o < n; o += NT) dst[o] = A::from(src[o]);
+  __syncthreads();
+}
+
 // own rows: X(:, 0:b) -= Q(:, 0:c) P, P (c x b, leading dimension ldp) in shared memory;
 // four independent FMA chains per element
-__device__ void sub_qp(double* X, int ldx, const double* Q, int ldq, int c, const double* P, int ldp, int b, int nr) {
+template <class A>
+__device__ void sub_qp(typename A::T* X, int ldx, const typename A::T* Q, int ldq, int c, const typename A::T* P,
+                       int ldp, int b, int nr) {
+  using V = typename A::T;
   if (c <= 0) return;
   for (int e = threadIdx.x; e < nr * b; e += NT) {
     const int r = e / b, j = e % b;
-    const double* qr = Q + r * ldq;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const V* qr = Q + r * ldq;
+    V s0 = A::zero(), s1 = A::zero(), s2 = A::zero(), s3 = A::zero();
     int i = 0;
     for (; i + 3 < c; i += 4) {
-      s0 = fma(qr[i], P[i * ldp + j], s0);
-      s1 = fma(qr[i + 1], P[(i + 1) * ldp + j], s1);
-      s2 = fma(qr[i + 2], P[(i + 2) * ldp + j], s2);
-      s3 = fma(qr[i + 3], P[(i + 3) * ldp + j], s3);
+      s0 = A::fma(qr[i], P[i * ldp + j], s0);
+      s1 = A::fma(qr[i + 1], P[(i + 1) * ldp + j], s1);
+      s2 = A::fma(qr[i + 2], P[(i + 2) * ldp + j], s2);
+      s3 = A::fma(qr[i + 3], P[(i + 3) * ldp + j], s3);
     }
-    for (; i < c; ++i) s0 = fma(qr[i], P[i * ldp + j], s0);
-    X[r * ldx + j] -= (s0 + s1) + (s2 + s3);
+    for (; i < c; ++i) s0 = A::fma(qr[i], P[i * ldp + j], s0);
+    X[r * ldx + j] = A::add(X[r * ldx + j], A::neg(A::add(A::add(s0, s1), A::add(s2, s3))));
   }
   __syncthreads();
 }
 
 // out (b x n, ld n, shared) = Ri^T (b x b lower) C (b x n, ld n, global totals): the coefficients
 // of the new basis block (X R^{-1})^T Y from X^T Y
-__device__ void mul_rinv_t_left(const double* C, int b, int n, const double* Ri, double* out) {
+template <class A>
+__device__ void mul_rinv_t_left(const double* C, int b, int n, const double* Ri, typename A::T* out) {
   for (int e = threadIdx.x; e < b * n; e += NT) {
     const int i = e / n, j = e % n;
     double v = 0.0;
     for (int k = 0; k <= i; ++k) v = fma(Ri[k * b + i], __ldcg(C + k * n + j), v);
-    out[e] = v;
+    out[e] = A::from(v);
   }
   __syncthreads();
 }
 
+template <class A>
 __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
+  using T = typename A::T;
   extern __shared__ __align__(16) double sm[];
+  __shared__ T RiT[BMAX * BMAX];
   __shared__ double G[BMAX * BMAX];
   __shared__ double Ri[BMAX * BMAX];
   __shared__ double M[BMAX * 2 * BMAX];
@@ -527,11 +602,12 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   my_rows(a.m, lo, hi);
   const int nr = (int)(hi - lo);
   const int ldq = (int)a.qcols, ldw = a.width, bi = a.bi;
-  double* Qs = sm;                                   // [rpc][ldq]   own rows of Q
-  double* Ss = Qs + (size_t)a.rpc * ldq;             // [rpc][ldw]   own rows of the sketch S_all
-  double* Rs = Ss + (size_t)a.rpc * ldw;             // [rpc][bi]    residual block
-  double* Tb = Rs + (size_t)a.rpc * bi;              // [rpc][BMAX]  staging for X R^{-1}
-  double* Ps = Tb + (size_t)a.rpc * BMAX;            // [qcols][max(b0, bi)] projection coefficients
+  static_assert(sizeof(T) == sizeof(double), "the shared-memory layout assumes 8-byte elements");
+  T* Qs = reinterpret_cast<T*>(sm);                  // [rpc][ldq]   own rows of Q
+  T* Ss = Qs + (size_t)a.rpc * ldq;                  // [rpc][ldw]   own rows of the sketch S_all (x 2^sshift)
+  T* Rs = Ss + (size_t)a.rpc * ldw;                  // [rpc][bi]    residual block (x 2^sshift)
+  T* Tb = Rs + (size_t)a.rpc * bi;                   // [rpc][BMAX]  staging for X R^{-1}
+  T* Ps = Tb + (size_t)a.rpc * BMAX;                 // [qcols][max(b0, bi)] projection coefficients
   const int ldp = bi;
   bool timeout = false;
   int cc = a.cc0;
@@ -540,14 +616,17 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   Timer tmr{a.prof, clock64()};
   if (threadIdx.x == 0) s_barrier_prof = (blockIdx.x == 0) ? a.prof : nullptr;
   // stage the own rows: sketch columns, and the part of Q that is already final
-  for (int e = threadIdx.x; e < nr * ldw; e += NT) Ss[e] = a.Sall[(lo + e / ldw) * a.lds + e % ldw];
-  for (int e = threadIdx.x; e < nr * cc; e += NT) Qs[(e / cc) * ldq + e % cc] = a.Q[(lo + e / cc) * a.ldq + e % cc];
+  for (int e = threadIdx.x; e < nr * ldw; e += NT)
+    Ss[e] = A::from(mul_pow2(a.Sall[(lo + e / ldw) * a.lds + e % ldw], a.sshift));
+  for (int e = threadIdx.x; e < nr * cc; e += NT)
+    Qs[(e / cc) * ldq + e % cc] = A::from(a.Q[(lo + e / cc) * a.ldq + e % cc]);
   __syncthreads();
   tmr.mark(PH_STAGE);
   auto finish = [&](int status) {
     // write back Q(:, 0:cc) (plus the residual block, which the host needs after a breakdown)
-    for (int e = threadIdx.x; e < nr * cc; e += NT) a.Q[(lo + e / cc) * a.ldq + e % cc] = Qs[(e / cc) * ldq + e % cc];
-    for (int e = threadIdx.x; e < nr * bi; e += NT) a.S[(lo + e / bi) * bi + e % bi] = Rs[e];
+    for (int e = threadIdx.x; e < nr * cc; e += NT)
+      a.Q[(lo + e / cc) * a.ldq + e % cc] = A::to(Qs[(e / cc) * ldq + e % cc]);
+    for (int e = threadIdx.x; e < nr * bi; e += NT) a.S[(lo + e / bi) * bi + e % bi] = mul_pow2(A::to(Rs[e]), -a.sshift);
     tmr.mark(PH_FINISH);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.io[0] = timeout ? ST_TIMEOUT : status;
@@ -574,21 +653,23 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     const int b0 = a.b0;
     for (int e = threadIdx.x; e < nr * b0; e += NT) Qs[(e / b0) * ldq + e % b0] = Ss[(e / b0) * ldw + e % b0];
     __syncthreads();
-    gram_acc(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
+    gram_acc<A>(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
     double* buf = reduce();
     if (!buf) return finish(ST_TIMEOUT);
     read_totals(buf, b0 * b0, G);
     if (!factor1(b0)) return finish(ST_BREAKDOWN);
-    apply_rinv(Qs, ldq, b0, Ri, nr, Tb);
+    to_arith<A>(Ri, b0 * b0, RiT);
+    apply_rinv<A>(Qs, ldq, b0, RiT, nr, Tb);
     const bool want = b0 < a.rbar && b0 + bi <= a.width;
-    gram_acc(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
-    if (want) gram_acc(Qs, ldq, Ss + b0, ldw, b0, bi, nr, red_buf(rd) + b0 * b0);
+    gram_acc<A>(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
+    if (want) gram_acc<A>(Qs, ldq, Ss + b0, ldw, b0, bi, nr, red_buf(rd) + b0 * b0);
     buf = reduce();
     if (!buf) return finish(ST_TIMEOUT);
     read_totals(buf, b0 * b0, G);
     if (!factor2(b0)) return finish(ST_BREAKDOWN);
-    apply_rinv(Qs, ldq, b0, Ri, nr, Tb);
-    if (want) mul_rinv_t_left(buf + b0 * b0, b0, bi, Ri, Ps);      // (Q1 R2^{-1})^T S = R2^{-T} Q1^T S
+    to_arith<A>(Ri, b0 * b0, RiT);
+    apply_rinv<A>(Qs, ldq, b0, RiT, nr, Tb);
+    if (want) mul_rinv_t_left<A>(buf + b0 * b0, b0, bi, Ri, Ps);      // (Q1 R2^{-1})^T S = R2^{-T} Q1^T S
     have_p = want;
     cc = b0;
     tmr.mark(PH_FIRST_QR);
@@ -596,68 +677,71 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   while (cc < a.rbar) {
     if (cc + bi > a.width) return finish(ST_EXTEND);
     if (!have_p) {
-      gram_acc(Qs, ldq, Ss + cc, ldw, cc, bi, nr, red_buf(rd));
+      gram_acc<A>(Qs, ldq, Ss + cc, ldw, cc, bi, nr, red_buf(rd));
       double* buf = reduce();
       if (!buf) return finish(ST_TIMEOUT);
-      read_totals(buf, cc * bi, Ps);
+      read_totals_t<A>(buf, cc * bi, Ps);
     }
     tmr.mark(PH_COEFF);
     // residual sketch of the next block (Eqs. (3.4)-(3.5)): S = S_all(:, cc:cc+bi) - Q P
     for (int e = threadIdx.x; e < nr * bi; e += NT) Rs[e] = Ss[(e / bi) * ldw + cc + e % bi];
     __syncthreads();
-    sub_qp(Rs, bi, Qs, ldq, cc, Ps, ldp, bi, nr);
+    sub_qp<A>(Rs, bi, Qs, ldq, cc, Ps, ldp, bi, nr);
     tmr.mark(PH_RESIDUAL);
     // reduction B: ||S||_F^2 and the Gram matrix of the candidate block S(:, 0:bb)
     const int bb = min(bi, a.rbar - cc);
     {
       double* eb = red_buf(rd);
-      sumsq_acc(Rs, bi, bi, nr, eb);
-      gram_acc(Rs, bi, Rs, bi, bb, bb, nr, eb + 1);
+      sumsq_acc<A>(Rs, bi, bi, nr, eb);
+      gram_acc<A>(Rs, bi, Rs, bi, bb, bb, nr, eb + 1);
     }
     double* bufB = reduce();
     if (!bufB) return finish(ST_TIMEOUT);
     if (threadIdx.x == 0) est_s = __ldcg(bufB);
     __syncthreads();
     const double ss = est_s;                               // ||S||_F^2
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.est_out[nest] = ss;   // the host takes sqrt(ss / b_inc)
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.est_out[nest] = mul_pow2(ss, -2 * a.sshift);   // host: sqrt(ss / b_inc)
     ++nest;
     tmr.mark(PH_REDUCE_B);
     // est = sqrt(ss / b_inc) > tau  <=>  ss > tau^2 b_inc  (the square root is left to the host)
-    if (!(ss > a.tau * a.tau * (double)bi)) return finish(ST_DONE);
+    const double tau_s = mul_pow2(a.tau, a.sshift);
+    if (!(ss > tau_s * tau_s * (double)bi)) return finish(ST_DONE);
     // new directions (Algorithm 6): Q_new = qr(S(:, 0:bb)); Q_new -= Q (Q^T Q_new); Q_new = qr(Q_new).
     // Each qr is one CholeskyQR pass (CholeskyQR2 with the block Gram-Schmidt step in between:
     // the first pass leaves Q_new orthonormal to ~u cond(S)^2, the second to ~u).
     read_totals(bufB + 1, bb * bb, G);
     if (!factor1(bb)) return finish(ST_BREAKDOWN);
-    double* Qn = Qs + cc;
+    T* Qn = Qs + cc;
     for (int e = threadIdx.x; e < nr * bb; e += NT) Qn[(e / bb) * ldq + e % bb] = Rs[(e / bb) * bi + e % bb];
     __syncthreads();
-    apply_rinv(Qn, ldq, bb, Ri, nr, Tb);
+    to_arith<A>(Ri, bb * bb, RiT);
+    apply_rinv<A>(Qn, ldq, bb, RiT, nr, Tb);
     tmr.mark(PH_QR1);
     // block Gram-Schmidt against Q on the Q_new just formed (its rounding errors included)
     if (cc > 0) {
-      gram_acc(Qs, ldq, Qn, ldq, cc, bb, nr, red_buf(rd));
+      gram_acc<A>(Qs, ldq, Qn, ldq, cc, bb, nr, red_buf(rd));
       double* bufR = reduce();
       if (!bufR) return finish(ST_TIMEOUT);
-      read_totals(bufR, cc * bb, Ps);
-      sub_qp(Qn, ldq, Qs, ldq, cc, Ps, bb, bb, nr);
+      read_totals_t<A>(bufR, cc * bb, Ps);
+      sub_qp<A>(Qn, ldq, Qs, ldq, cc, Ps, bb, bb, nr);
     }
     tmr.mark(PH_REORTH);
     // reduction A: the Gram matrix of Q_new (second CholeskyQR pass) and, when the next block lies
     // within the sketch, [Q, Q_new]^T S_all(:, next:next+bi) for its residual
     const int nxt = cc + bb;
     const bool want = nxt < a.rbar && nxt + bi <= a.width;
-    gram_acc(Qn, ldq, Qn, ldq, bb, bb, nr, red_buf(rd));
-    if (want) gram_acc(Qs, ldq, Ss + nxt, ldw, nxt, bi, nr, red_buf(rd) + bb * bb);
+    gram_acc<A>(Qn, ldq, Qn, ldq, bb, bb, nr, red_buf(rd));
+    if (want) gram_acc<A>(Qs, ldq, Ss + nxt, ldw, nxt, bi, nr, red_buf(rd) + bb * bb);
     double* bufA = reduce();
     if (!bufA) return finish(ST_TIMEOUT);
     read_totals(bufA, bb * bb, G);
     if (!factor2(bb)) return finish(ST_BREAKDOWN);
-    apply_rinv(Qn, ldq, bb, Ri, nr, Tb);
+    to_arith<A>(Ri, bb * bb, RiT);
+    apply_rinv<A>(Qn, ldq, bb, RiT, nr, Tb);
     if (want) {
       // P = [Q^T S_next; R2^{-T} Q_new^T S_next]
-      read_totals(bufA + bb * bb, cc * bi, Ps);
-      mul_rinv_t_left(bufA + bb * bb + cc * bi, bb, bi, Ri, Ps + cc * bi);
+      read_totals_t<A>(bufA + bb * bb, cc * bi, Ps);
+      mul_rinv_t_left<A>(bufA + bb * bb + cc * bi, bb, bi, Ri, Ps + cc * bi);
     }
     have_p = want;
     cc = nxt;
@@ -672,14 +756,15 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
 // (ST_DONE, ST_EXTEND: more sketch columns are needed, ST_BREAKDOWN: a CholeskyQR pivot failed
 // at column *cc), or TTR_ERR_UNSUPPORTED when this path does not apply.
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
-                  int bi, int rbar, int width, int cc0, double tau, double* est_out, int* status, int* cc, int* nest) {
+                  int bi, int rbar, int width, int cc0, double tau, double* est_out, int* status, int* cc, int* nest,
+                  bool double_float, double scale) {
   if (b0 > ac::BMAX || bi > ac::BMAX || (int64_t)rbar * bi > ac::ACC || m <= 0) return TTR_ERR_UNSUPPORTED;
   int dev = 0;
   TTR_CUDA(cudaGetDevice(&dev));
   // device properties and the kernel's shared-memory limit, looked up once per device
   constexpr int MAXDEV = 64;
   struct DevInfo {
-    int nsm, coop, smem_optin, raised;
+    int nsm, coop, smem_optin, raised[2];
   };
   static DevInfo info[MAXDEV] = {};
   DevInfo local{};
@@ -697,14 +782,17 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const int64_t qcols = rbar;
   const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
                                         (size_t)qcols * (size_t)std::max(b0, bi));
-  const size_t static_bytes = 40 * 1024;   // G, R^{-1}, [G | I], pivot buffers, reductions (about 36 KB)
+  const size_t static_bytes = 48 * 1024;   // G, R^{-1} (FP64 and working type), [G | I], pivot buffers (about 44 KB)
   if (dyn + static_bytes > (size_t)smem_optin) return TTR_ERR_UNSUPPORTED;
-  if (di.raised < (int)dyn) {
-    TTR_CUDA(cudaFuncSetAttribute(ac::adaptive_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  const void* kern = double_float ? (const void*)ac::adaptive_core_kernel<ac::DF>
+                                  : (const void*)ac::adaptive_core_kernel<ac::F64>;
+  const int ki = double_float ? 1 : 0;
+  if (di.raised[ki] < (int)dyn) {
+    TTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
-    TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ac::adaptive_core_kernel, ac::NT, dyn));
+    TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ac::NT, dyn));
     if (per_sm < 1) return TTR_ERR_UNSUPPORTED;
-    di.raised = (int)dyn;
+    di.raised[ki] = (int)dyn;
   }
   if (!c.ac_part) {
     TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * (ac::ACC + 64)));   // 3 buffers of up to ACC + 33 doubles
@@ -725,6 +813,13 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;
   a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.rbar = rbar; a.width = width; a.cc0 = cc0; a.tau = tau;
   a.bar = c.ac_bar; a.err = c.d_flags; a.est_out = est_out; a.io = c.ac_io;
+  // double-float keeps binary32 exponents: hold the sketch scaled so that ||X|| maps near 1
+  a.sshift = 0;
+  if (double_float && scale > 0.0 && isfinite(scale)) {
+    int ex = 0;
+    frexp(scale, &ex);
+    a.sshift = -ex;
+  }
   if (c.profiling) {
     if (!c.ac_prof) {
       TTR_CHECK(c.alloc_t(&c.ac_prof, ac::PH_COUNT));
@@ -734,8 +829,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   }
   void* params[] = {&a};
   c.time_begin(Ctx::KT_BLOCK_LOOP);
-  TTR_CUDA(cudaLaunchCooperativeKernel((const void*)ac::adaptive_core_kernel, dim3(nblocks), dim3(ac::NT), params, dyn,
-                                       c.stream));
+  TTR_CUDA(cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(ac::NT), params, dyn, c.stream));
   TTR_CHECK(c.check_launch("adaptive_core"));
   int io[4] = {0, 0, 0, 0};
   TTR_CUDA(cudaMemcpyAsync(io, c.ac_io, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));

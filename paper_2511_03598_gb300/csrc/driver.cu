@@ -760,7 +760,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
         if (++guard > 4 * (int)rbar + 16) return set_error("adaptive loop did not terminate"), TTR_ERR_TIMEOUT;
         int status = 0, ccn = 0, nest = 0;
         st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)b0, (int)bi, (int)rbar, (int)sk_cols, (int)cc, tau,
-                           dest, &status, &ccn, &nest);
+                           dest, &status, &ccn, &nest, E.precision == TTR_PREC_SLICED && E.slices <= 6, nrmx);
         if (st == TTR_ERR_UNSUPPORTED) break;
         if (st != TTR_OK) return st;
         if (nest > 0) {
