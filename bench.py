@@ -89,6 +89,21 @@ class ClockSampler:
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The job's time: the largest of the ranks' timed regions (all_reduce MAX when world > 1)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps: int, world: int, job_ms: float) -> float:
+    """Whole-job throughput: every rank rounds `steps` tensors (replicas, weak scaling)."""
+    return world * steps / (job_ms / 1e3)
+
+
 def cpu_oracle_rate(x, budget_s=15.0):
     """The oracle as it stands, on a bounded sample: whole adaptive roundings of the same input."""
     from oracle import rounding as R
@@ -206,11 +221,8 @@ def main():
     clk.stop()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    tmax = torch.tensor([total_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, "cuda")
+    value = job_rate(args.steps, world, total_ms)
 
     if args.only_main:
         if rank == 0:

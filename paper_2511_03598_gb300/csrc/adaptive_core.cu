@@ -19,6 +19,7 @@
 // The grid barrier is a counter/generation pair with a bounded spin: a wait that runs out sets
 // the error flag and the kernel returns (the host reports TTR_ERR_TIMEOUT).
 #include <math.h>
+#include <stdlib.h>
 #include <stdint.h>
 
 #include "engine.cuh"
@@ -777,9 +778,10 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const int nsm = di.nsm, smem_optin = di.smem_optin;
   if (!di.coop) return TTR_ERR_UNSUPPORTED;
   // no more CTAs than rows; each CTA keeps its rows of Q, of the sketch and of the residual block
+  // one CTA per SM (a sweep of 38..152 CTAs on the 20-core workload: 152 is fastest)
   const int nblocks = (int)std::min<int64_t>(nsm, m);
   const int rpc = (int)((m + nblocks - 1) / nblocks);
-  const int64_t qcols = rbar;
+  const int64_t qcols = std::min(rbar, width);     // columns of Q never exceed the sketch width
   const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
                                         (size_t)qcols * (size_t)std::max(b0, bi));
   const size_t static_bytes = 48 * 1024;   // G, R^{-1} (FP64 and working type), [G | I], pivot buffers (about 44 KB)
