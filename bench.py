@@ -211,10 +211,10 @@ def main():
     ev[0].record(stream)
     for i in range(args.steps):
         y = B.round_adaptive(cores, TOL, BLOCK, SEED, topts)
-        yi = y.info
-        launches += yi["kernel_launches"]
+        res = y.result                           # the C struct: no per-step Python lists
+        launches += res.kernel_launches
         for key in kt:
-            kt[key] += yi[key]
+            kt[key] += getattr(res, key)
         y.free()
         ev[i + 1].record(stream)
     barrier()

@@ -21,10 +21,14 @@
  *            work is ordered on it.  The call returns after the result is complete on the
  *            device and its ranks are known on the host (it synchronizes the stream).
  *   opts     optional (NULL = defaults, see ttr_default_options).
- *   out      result; on success the library owns out->cores (one device allocation made
- *            with cudaMallocAsync on `stream`) and out->ranks / out->estimates (host); the
- *            caller releases them with ttr_free.  On error nothing is allocated and *out is
- *            zeroed except out->status.
+ *   out      result; on success the library owns out->cores (one stream-ordered device
+ *            allocation on `stream`) and out->ranks / out->estimates (host); the caller
+ *            releases them with ttr_free.  On error nothing is allocated and *out is zeroed
+ *            except out->status.
+ *
+ * Device memory: stream-ordered allocations come from a memory pool private to the library (one
+ * per device) that keeps up to 8 GiB of freed memory for reuse by later calls; it is returned to
+ * the driver when the process exits.
  *
  * Errors: every call returns a ttr_status; the library never aborts, traps or exits.  Device
  * waits inside kernels are bounded; a wait that runs out reports TTR_ERR_TIMEOUT.

@@ -122,6 +122,11 @@ class Rounded:
         return self._res.d
 
     @property
+    def result(self) -> Result:
+        """The underlying ttr_result (valid until free())."""
+        return self._res
+
+    @property
     def ranks(self) -> list:
         return [int(self._res.ranks[i]) for i in range(self._res.d + 1)]
 

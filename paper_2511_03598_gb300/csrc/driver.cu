@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -18,10 +19,41 @@ namespace ttr {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+// Stream-ordered allocations come from a memory pool of the library's own, one per device, which
+// keeps up to kPoolKeepBytes of freed memory for the next call instead of handing it back to the
+// driver at every synchronization (the default pool's release threshold is 0).  The pool is
+// private to this process and this library; it changes no device setting.
+static constexpr uint64_t kPoolKeepBytes = 8ull << 30;
+
+static cudaMemPool_t library_pool(cudaStream_t stream) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  (void)stream;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = kPoolKeepBytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
 int Ctx::alloc(void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(p, bytes, stream);
+  cudaMemPool_t pool = library_pool(stream);
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMallocAsync(p, bytes, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
