@@ -354,6 +354,7 @@ struct Sketch {
   int64_t om_stride = 0, ldom = 0;
   double* T = nullptr;      // (max r_{k-1} n_k) x ldw scratch
   int extensions = 0;
+  std::vector<BPlanes> wplanes;   // digit planes of W_{k+1}(:, 0:width) made by the first pass (index k)
 };
 
 static int rl_pass(Ctx& c, const Engine& E, const TT& X, uint64_t seed, int64_t col0, int64_t col1, int t,
@@ -372,10 +373,11 @@ static int rl_pass(Ctx& c, const Engine& E, const TT& X, uint64_t seed, int64_t 
     g.C = s.W[d - 1] + col0; g.scm = s.ldw; g.scn = 1;
     TTR_CHECK(E.small_gemm(c, g));
   }
+  if (col0 == 0) s.wplanes.assign(d + 1, BPlanes{});
   for (int k = d - 1; k >= t; --k) {
     TTR_CHECK(E.rl_step(c, X.cores[k - 1], X.r[k - 1], X.n[k - 1], X.r[k], s.W[k] + col0, s.ldw,
                         s.Om + (int64_t)(k - 1) * s.om_stride, s.Omi + (int64_t)(k - 1) * s.om_stride, s.ldom, w,
-                        s.W[k - 1] + col0, s.ldw, s.T));
+                        s.W[k - 1] + col0, s.ldw, s.T, col0 == 0 ? &s.wplanes[k] : nullptr));
   }
   return TTR_OK;
 }
@@ -748,7 +750,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
     g.A = Z; g.sam = cols; g.sak = 1;
     g.B = s.W[k] + c0; g.sbk = s.ldw; g.sbn = 1;
     g.C = Sall + c0; g.scm = wcap; g.scn = 1;
-    return E.sketch(c, g);
+    return E.sketch(c, g, (size_t)k < s.wplanes.size() ? &s.wplanes[k] : nullptr);
   };
   auto ensure = [&](int k, int64_t need, int64_t rows, int64_t cols) -> int {
     if (s.width < need) {

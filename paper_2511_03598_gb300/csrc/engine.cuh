@@ -8,14 +8,25 @@
 
 namespace ttr {
 
+// Digit planes and column scales of a B operand (K x N, row-major, leading dimension ld), kept
+// by the call context so that a later contraction with the same operand need not slice it again.
+struct BPlanes {
+  uint4* planes = nullptr;
+  int* Fmax = nullptr;
+  int nchunks = 0, kchunks = 0, tn = 0, s = 0;
+  const double* src = nullptr;
+  int64_t ld = 0, K = 0, N = 0;
+};
+
 // Tensor-core path (ozaki_tc.cu).  Each returns TTR_ERR_UNSUPPORTED when a shape is outside
 // what the kernel handles; the engine then uses the FP64 kernel for that call.
 int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn,
-               int64_t ldw, const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo);
+               int64_t ldw, const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo,
+               BPlanes* keep = nullptr);
 int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int64_t a_cols, const double* Y,
                int64_t ldy, int64_t b_cols, double* C, int64_t scm, int64_t scn);
 int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
-                     int64_t ldb, int64_t N, double* C, int64_t ldc);
+                     int64_t ldb, int64_t N, double* C, int64_t ldc, const BPlanes* reuse = nullptr);
 int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn,
                int64_t ncol, double* Y);
 
@@ -70,11 +81,12 @@ struct Engine {
   // sketch columns worth drawing up front: one tensor-core tile in sliced mode
   int64_t natural_width() const { return precision == TTR_PREC_SLICED ? tile_width(slices) : 64; }
 
-  // S = Z W(:, cols): A row-major (sak == 1), B row-major (sbn == 1), C row-major (scn == 1)
-  int sketch(Ctx& c, const Gemm& g) const {
+  // S = Z W(:, cols): A row-major (sak == 1), B row-major (sbn == 1), C row-major (scn == 1);
+  // `reuse`: planes of W kept by the right-to-left pass
+  int sketch(Ctx& c, const Gemm& g, const BPlanes* reuse = nullptr) const {
     if (precision == TTR_PREC_SLICED && g.sak == 1 && g.sbn == 1 && g.scn == 1 && g.split_k <= 1 &&
         g.alpha == 1.0 && g.beta == 0.0) {
-      int st = tc_gemm_rowmajor(c, slices, g.A, g.sam, g.M, g.K, g.B, g.sbk, g.N, g.C, g.scm);
+      int st = tc_gemm_rowmajor(c, slices, g.A, g.sam, g.M, g.K, g.B, g.sbk, g.N, g.C, g.scm, reuse);
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
     return gemm_f64(c, g);
@@ -82,9 +94,10 @@ struct Engine {
 
   // W_k = sum_i [V(X_k) W_{k+1}](a, i, :) * Omega_k(i, :)   (Algorithm 3, one step)
   int rl_step(Ctx& c, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
-              const double* Om, const int* Omi, int64_t ldom, int64_t w, double* Wout, int64_t ldwo, double* T) const {
+              const double* Om, const int* Omi, int64_t ldom, int64_t w, double* Wout, int64_t ldwo, double* T,
+              BPlanes* keep = nullptr) const {
     if (precision == TTR_PREC_SLICED) {
-      int st = tc_rl_step(c, slices, Xk, r0, n, r1, Wn, ldw, Omi, ldom, w, Wout, ldwo);
+      int st = tc_rl_step(c, slices, Xk, r0, n, r1, Wn, ldw, Omi, ldom, w, Wout, ldwo, keep);
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
     Gemm g;

@@ -641,7 +641,8 @@ struct BPrep {
   int nchunks = 0, kchunks = 0, tn = 0;
 };
 
-static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int s, BPrep& p) {
+static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int s, BPrep& p,
+                  BPlanes* keep = nullptr) {
   const int tmax = tile_width(s);
   p.nchunks = (int)((N + tmax - 1) / tmax);
   // balance the chunks: the narrowest multiple of 16 that still needs only nchunks tiles
@@ -654,13 +655,21 @@ static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, 
   const size_t plane_bytes = ((size_t)p.nchunks * p.kchunks * s * p.tn * KC * 2 + 255) / 256 * 256;
   const size_t fmax_bytes = ((size_t)npad * sizeof(int) + 255) / 256 * 256;
   const size_t need = plane_bytes + fmax_bytes + (size_t)p.kchunks * npad * sizeof(int);
-  if (c.bprep_bytes < need) {
-    void* ws = nullptr;
-    TTR_CHECK(c.alloc(&ws, std::max(need, (size_t)2 * c.bprep_bytes)));
-    c.bprep = ws;
-    c.bprep_bytes = std::max(need, (size_t)2 * c.bprep_bytes);
+  unsigned char* base = nullptr;
+  if (keep) {
+    // planes kept for a later call on the same operand (an allocation of the call context)
+    void* mem = nullptr;
+    TTR_CHECK(c.alloc(&mem, need));
+    base = static_cast<unsigned char*>(mem);
+  } else {
+    if (c.bprep_bytes < need) {
+      void* ws = nullptr;
+      TTR_CHECK(c.alloc(&ws, std::max(need, (size_t)2 * c.bprep_bytes)));
+      c.bprep = ws;
+      c.bprep_bytes = std::max(need, (size_t)2 * c.bprep_bytes);
+    }
+    base = static_cast<unsigned char*>(c.bprep);
   }
-  unsigned char* base = static_cast<unsigned char*>(c.bprep);
   p.planes = reinterpret_cast<uint4*>(base);
   p.Fmax = reinterpret_cast<int*>(base + plane_bytes);
   int* Fpart = reinterpret_cast<int*>(base + plane_bytes + fmax_bytes);
@@ -669,7 +678,20 @@ static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, 
   TTR_CHECK(c.check_launch("colmax_b"));
   slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(
       B, sbk, sbn, K, N, s, p.tn, p.kchunks, npad, Fpart, p.Fmax, p.planes);
-  return c.check_launch("slice_b");
+  TTR_CHECK(c.check_launch("slice_b"));
+  if (keep) {
+    keep->planes = p.planes;
+    keep->Fmax = p.Fmax;
+    keep->nchunks = p.nchunks;
+    keep->kchunks = p.kchunks;
+    keep->tn = p.tn;
+    keep->s = s;
+    keep->src = B;
+    keep->ld = sbk;
+    keep->K = K;
+    keep->N = N;
+  }
+  return TTR_OK;
 }
 
 // K per CTA for `tiles` output tiles: the fewest K-chunks per CTA that keep the grid within one
@@ -737,11 +759,11 @@ int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int6
 }
 
 int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
-               const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo) {
+               const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo, BPlanes* keep) {
   if (n > TM || slices < 3 || slices > MAXS || !Omi) return TTR_ERR_UNSUPPORTED;
   TTR_CHECK(ensure_err(c));
   BPrep bp;
-  TTR_CHECK(prep_b(c, Wn, ldw, 1, r1, w, slices, bp));
+  TTR_CHECK(prep_b(c, Wn, ldw, 1, r1, w, slices, bp, keep));
   Args a{};
   a.A = Xk; a.M = r0 * n; a.K = r1; a.sam = r1; a.sak = 1;
   a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = w; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
@@ -762,11 +784,20 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
 }
 
 int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
-                     int64_t ldb, int64_t N, double* C, int64_t ldc) {
+                     int64_t ldb, int64_t N, double* C, int64_t ldc, const BPlanes* reuse) {
   if (slices < 3 || slices > MAXS || M <= 0 || N <= 0 || K <= 0) return TTR_ERR_UNSUPPORTED;
   TTR_CHECK(ensure_err(c));
   BPrep bp;
-  TTR_CHECK(prep_b(c, B, ldb, 1, K, N, slices, bp));
+  if (reuse && reuse->planes && reuse->src == B && reuse->ld == ldb && reuse->K == K && reuse->N == N &&
+      reuse->s == slices) {
+    bp.planes = reuse->planes;                 // the digit planes of this operand are already made
+    bp.Fmax = reuse->Fmax;
+    bp.nchunks = reuse->nchunks;
+    bp.kchunks = reuse->kchunks;
+    bp.tn = reuse->tn;
+  } else {
+    TTR_CHECK(prep_b(c, B, ldb, 1, K, N, slices, bp));
+  }
   Args a{};
   a.A = A; a.M = M; a.K = K; a.sam = lda; a.sak = 1;
   a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = N; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
