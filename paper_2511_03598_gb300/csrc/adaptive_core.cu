@@ -21,6 +21,10 @@
 #include <math.h>
 #include <stdlib.h>
 #include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "engine.cuh"
 
@@ -757,7 +761,8 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
 // (ST_DONE, ST_EXTEND: more sketch columns are needed, ST_BREAKDOWN: a CholeskyQR pivot failed
 // at column *cc), or TTR_ERR_UNSUPPORTED when this path does not apply.
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
-                  int bi, int rbar, int width, int cc0, double tau, double* est_out, int* status, int* cc, int* nest,
+                  int bi, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status, int* cc,
+                  int* nest,
                   bool double_float, double scale) {
   if (b0 > ac::BMAX || bi > ac::BMAX || (int64_t)rbar * bi > ac::ACC || m <= 0) return TTR_ERR_UNSUPPORTED;
   int dev = 0;
@@ -799,8 +804,16 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   if (!c.ac_part) {
     TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * (ac::ACC + 64)));   // 3 buffers of up to ACC + 33 doubles
     TTR_CHECK(c.alloc_t(&c.ac_bar, 4));
-    TTR_CHECK(c.alloc_t(&c.ac_io, 4));
     TTR_CUDA(cudaMemsetAsync(c.ac_bar, 0, 4 * sizeof(unsigned), c.stream));
+  }
+  // status words and the estimates share one device buffer, read back by a single copy:
+  // [status, cc, count, -] ints, then up to est_cap doubles
+  const int cap = std::max(est_cap, 8);
+  if (c.ac_io_cap < cap) {
+    void* mem = nullptr;
+    TTR_CHECK(c.alloc(&mem, 16 + sizeof(double) * (size_t)cap));
+    c.ac_io = static_cast<int*>(mem);
+    c.ac_io_cap = cap;
   }
   if (!c.d_flags) {
     TTR_CHECK(c.alloc_t(&c.d_flags, 4));
@@ -814,7 +827,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   ac::Args a{};
   a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;
   a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.rbar = rbar; a.width = width; a.cc0 = cc0; a.tau = tau;
-  a.bar = c.ac_bar; a.err = c.d_flags; a.est_out = est_out; a.io = c.ac_io;
+  a.bar = c.ac_bar; a.err = c.d_flags; a.est_out = reinterpret_cast<double*>(c.ac_io + 4); a.io = c.ac_io;
   // double-float keeps binary32 exponents: hold the sketch scaled so that ||X|| maps near 1
   a.sshift = 0;
   if (double_float && scale > 0.0 && isfinite(scale)) {
@@ -833,13 +846,19 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   c.time_begin(Ctx::KT_BLOCK_LOOP);
   TTR_CUDA(cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(ac::NT), params, dyn, c.stream));
   TTR_CHECK(c.check_launch("adaptive_core"));
-  int io[4] = {0, 0, 0, 0};
-  TTR_CUDA(cudaMemcpyAsync(io, c.ac_io, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  // one launch makes at most one estimate per block it runs
+  const int est_max = std::min(cap, (rbar - cc0) / std::max(1, bi) + 3);
+  std::vector<unsigned char> back(16 + sizeof(double) * (size_t)est_max);
+  TTR_CUDA(cudaMemcpyAsync(back.data(), c.ac_io, back.size(), cudaMemcpyDeviceToHost, c.stream));
   TTR_CUDA(cudaStreamSynchronize(c.stream));
+  int io[4];
+  memcpy(io, back.data(), sizeof(io));
   if (io[0] == ac::ST_TIMEOUT) return set_error("adaptive loop: grid barrier wait ran out"), TTR_ERR_TIMEOUT;
+  if (io[2] < 0 || io[2] > est_max || io[2] > est_cap) return set_error("adaptive loop: estimate count"), TTR_ERR_CUDA;
   *status = io[0];
   *cc = io[1];
   *nest = io[2];
+  memcpy(est_host, back.data() + 16, sizeof(double) * (size_t)io[2]);
   if (c.timing) {
     // FP64 arithmetic of the blocks the kernel ran (2 flops per multiply-add), in its order:
     // first block (two CholeskyQR passes and the first coefficients), then per estimate the

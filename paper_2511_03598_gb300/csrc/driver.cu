@@ -774,8 +774,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
     return chol_pass(c, E, w.qr.tmp, b, m, b, Xq, ldx, q2, nullptr);
   };
   // estimates of one core land here (the device loop writes them, the host copies them out)
-  double* dest = nullptr;
-  TTR_CHECK(c.alloc_t(&dest, rmax + 8));
+  std::vector<double> hest((size_t)rmax + 8);
   const bool device_loop = getenv("TTR_HOST_LOOP") == nullptr;
   for (int k = 1; k < d; ++k) {
     const int64_t rows = lprev * X.n[k - 1], cols = X.r[k];
@@ -794,18 +793,15 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
         if (++guard > 4 * (int)rbar + 16) return set_error("adaptive loop did not terminate"), TTR_ERR_TIMEOUT;
         int status = 0, ccn = 0, nest = 0;
         st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)b0, (int)bi, (int)rbar, (int)sk_cols, (int)cc, tau,
-                           dest, &status, &ccn, &nest, E.precision == TTR_PREC_SLICED && E.slices <= 6, nrmx);
+                           hest.data(), (int)hest.size(), &status, &ccn, &nest,
+                           E.precision == TTR_PREC_SLICED && E.slices <= 6, nrmx);
         if (st == TTR_ERR_UNSUPPORTED) break;
         if (st != TTR_OK) return st;
-        if (nest > 0) {
-          std::vector<double> h(nest);
-          TTR_CUDA(cudaMemcpy(h.data(), dest, sizeof(double) * nest, cudaMemcpyDeviceToHost));
-          for (double ss : h) {
-            const double e = sqrt(ss) / sqrt((double)bi);      // the device returns ||S||_F^2
-            if (!isfinite(e)) return set_error("non-finite residual estimate"), TTR_ERR_NONFINITE;
-            ests.push_back(e);
-            est_core.push_back(k);
-          }
+        for (int q = 0; q < nest; ++q) {
+          const double e = sqrt(hest[q]) / sqrt((double)bi);      // the device returns ||S||_F^2
+          if (!isfinite(e)) return set_error("non-finite residual estimate"), TTR_ERR_NONFINITE;
+          ests.push_back(e);
+          est_core.push_back(k);
         }
         cc = ccn;
         if (status == 0) {

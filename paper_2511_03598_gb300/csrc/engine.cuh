@@ -35,9 +35,11 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
 // double_float: block-loop arithmetic in double-float on the FP32 pipe (~2^-48 relative; used by
 // the sliced form with at most 6 slices, whose contractions already err by ~3e-12, never where
 // FP64 accuracy is promised); scale: a value of the order of the sketch entries (the input norm).
+// The estimates (||S||_F^2 of each residual block, in order) come back in est_host (host, room for
+// est_cap values; *nest of them are written).
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
-                  int bi, int rbar, int width, int cc0, double tau, double* est_out, int* status, int* cc, int* nest,
-                  bool double_float, double scale);
+                  int bi, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status, int* cc,
+                  int* nest, bool double_float, double scale);
 
 // Widest tensor-core tile (UMMA N) usable with s slices.
 int tile_width(int s);

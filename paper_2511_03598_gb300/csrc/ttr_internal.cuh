@@ -42,7 +42,8 @@ struct Ctx {
   double* ac_part = nullptr;       // adaptive_core: per-CTA partial sums (two buffers)
   double* ac_red = nullptr;        // adaptive_core: reduced projection coefficients
   unsigned* ac_bar = nullptr;      // adaptive_core: grid barrier counter/generation
-  int* ac_io = nullptr;            // adaptive_core: status, column count, estimate count
+  int* ac_io = nullptr;            // adaptive_core: status, column count, estimate count, estimates
+  int ac_io_cap = 0;               // estimates it can hold
   unsigned long long* ac_prof = nullptr;   // adaptive_core phase cycles (profiling only)
   unsigned long long* tc_prof = nullptr;   // tensor-core kernel phase cycles per mode (profiling only)
   void* bprep = nullptr;           // tensor-core B-operand workspace (digit planes, scales)
