@@ -596,6 +596,88 @@ __global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t s
   }
 }
 
+// Both passes in one cooperative launch: each CTA keeps its B values in registers across a bounded
+// grid barrier (counter and generation in bar[0], bar[1], left at counter 0 for the next use), so B
+// is read once and one launch replaces two.
+constexpr int PREP_TASKS = (TNMAX * (KC / 8) + 255) / 256;
+__global__ void __launch_bounds__(256) prep_b_fused_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K,
+                                                           int64_t N, int s, int tn, int kchunks, int64_t npad,
+                                                           int* Fpart, int* Fmax, uint4* planes, unsigned* bar,
+                                                           int* err) {
+  __shared__ int cm[TNMAX];
+  __shared__ int ok_s;
+  const int nc = blockIdx.x, kcn = blockIdx.y;
+  for (int j = threadIdx.x; j < tn; j += blockDim.x) cm[j] = 1;
+  __syncthreads();
+  double v[PREP_TASKS][8];
+#pragma unroll
+  for (int t = 0; t < PREP_TASKS; ++t) {
+    const int u = threadIdx.x + 256 * t;
+    const int j = u % tn, grp = u / tn;
+    const int64_t n = (int64_t)nc * tn + j;
+    const bool live = u < tn * (KC / 8) && n < N;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)kcn * KC + grp * 8 + q;
+      v[t][q] = (live && k < K) ? B[k * sbk + n * sbn] : 0.0;
+    }
+    if (live) {
+      int e = 1;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) e = max(e, exp_field(v[t][q]));
+      atomicMax(&cm[j], e);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < tn; j += blockDim.x) Fpart[(int64_t)kcn * npad + (int64_t)nc * tn + j] = cm[j];
+  // grid barrier
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok_s = 1;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned total = gridDim.x * gridDim.y;
+    if (atomicAdd(bar, 1u) == total - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > WAIT_CYCLES) {
+          atomicExch(err, 1);
+          ok_s = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (!ok_s) return;
+  for (int j = threadIdx.x; j < tn; j += blockDim.x) {
+    int e = 1;
+    const int* fp = Fpart + (int64_t)nc * tn + j;
+    for (int q = 0; q < kchunks; ++q) e = max(e, __ldcg(fp + (int64_t)q * npad));
+    cm[j] = e;
+    if (kcn == 0) Fmax[(int64_t)nc * tn + j] = e;
+  }
+  __syncthreads();
+  const int plane_b = tn * KC;
+  uint4* blk = planes + ((size_t)nc * kchunks + kcn) * (size_t)s * (plane_b / 8);
+#pragma unroll
+  for (int t = 0; t < PREP_TASKS; ++t) {
+    const int u = threadIdx.x + 256 * t;
+    if (u >= tn * (KC / 8)) continue;
+    const int j = u % tn, grp = u / tn;
+    const int idx = ((grp * (tn / 8)) + (j >> 3)) * 8 + (j & 7);      // uint4 index in a plane
+    store_digits_s(s, v[t], cm[j], reinterpret_cast<uint16_t*>(blk), plane_b, idx * 8);
+  }
+}
+
 static size_t smem_bytes(int s, int tn, int mode) {
   size_t need = 2 * (size_t)s * (PLANE_A + tn * KC) * 2;
   if (mode == RLM) need = std::max(need, (size_t)TM * PB * sizeof(__int128));
@@ -641,6 +723,14 @@ struct BPrep {
   int nchunks = 0, kchunks = 0, tn = 0;
 };
 
+static int ensure_err(Ctx& c) {
+  if (!c.d_flags) {
+    TTR_CHECK(c.alloc_t(&c.d_flags, 4));
+    TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
+  }
+  return TTR_OK;
+}
+
 static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int s, BPrep& p,
                   BPlanes* keep = nullptr) {
   const int tmax = tile_width(s);
@@ -673,12 +763,41 @@ static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, 
   p.planes = reinterpret_cast<uint4*>(base);
   p.Fmax = reinterpret_cast<int*>(base + plane_bytes);
   int* Fpart = reinterpret_cast<int*>(base + plane_bytes + fmax_bytes);
-  colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, p.tn, npad,
-                                                                                      Fpart);
-  TTR_CHECK(c.check_launch("colmax_b"));
-  slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(
-      B, sbk, sbn, K, N, s, p.tn, p.kchunks, npad, Fpart, p.Fmax, p.planes);
-  TTR_CHECK(c.check_launch("slice_b"));
+  const int64_t ctas = (int64_t)p.nchunks * p.kchunks;
+  int nsm = 0;
+  {
+    int dev = 0;
+    TTR_CUDA(cudaGetDevice(&dev));
+    TTR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  if (ctas <= (int64_t)nsm) {
+    // one cooperative launch (all CTAs co-resident: one per SM at most)
+    TTR_CHECK(ensure_err(c));
+    if (!c.prep_bar) {
+      TTR_CHECK(c.alloc_t(&c.prep_bar, 4));
+      TTR_CUDA(cudaMemsetAsync(c.prep_bar, 0, 4 * sizeof(unsigned), c.stream));
+    }
+    int kchunks = p.kchunks;
+    int tn = p.tn;
+    int sl = s;
+    int* fmax = p.Fmax;
+    uint4* planes = p.planes;
+    unsigned* bar = c.prep_bar;
+    int* err = c.d_flags;
+    void* params[] = {(void*)&B, (void*)&sbk, (void*)&sbn, (void*)&K, (void*)&N, (void*)&sl, (void*)&tn,
+                      (void*)&kchunks, (void*)&npad, (void*)&Fpart, (void*)&fmax, (void*)&planes, (void*)&bar,
+                      (void*)&err};
+    TTR_CUDA(cudaLaunchCooperativeKernel((const void*)prep_b_fused_kernel, dim3((unsigned)p.nchunks, (unsigned)p.kchunks),
+                                         dim3(256), params, 0, c.stream));
+    TTR_CHECK(c.check_launch("prep_b"));
+  } else {
+    colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, p.tn,
+                                                                                        npad, Fpart);
+    TTR_CHECK(c.check_launch("colmax_b"));
+    slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(
+        B, sbk, sbn, K, N, s, p.tn, p.kchunks, npad, Fpart, p.Fmax, p.planes);
+    TTR_CHECK(c.check_launch("slice_b"));
+  }
   if (keep) {
     keep->planes = p.planes;
     keep->Fmax = p.Fmax;
@@ -705,13 +824,6 @@ static int kseg_for(int64_t tiles, int64_t K) {
   return KSEG;
 }
 
-static int ensure_err(Ctx& c) {
-  if (!c.d_flags) {
-    TTR_CHECK(c.alloc_t(&c.d_flags, 4));
-    TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
-  }
-  return TTR_OK;
-}
 
 // Zero the a x b region C(i, j) = C[i*scm + j*scn] where one of the strides is 1.
 static int zero_region(Ctx& c, double* C, int64_t a, int64_t b, int64_t scm, int64_t scn) {

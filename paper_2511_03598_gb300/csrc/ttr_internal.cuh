@@ -47,6 +47,7 @@ struct Ctx {
   unsigned long long* ac_prof = nullptr;   // adaptive_core phase cycles (profiling only)
   unsigned long long* tc_prof = nullptr;   // tensor-core kernel phase cycles per mode (profiling only)
   void* bprep = nullptr;           // tensor-core B-operand workspace (digit planes, scales)
+  unsigned* prep_bar = nullptr;    // grid barrier of the fused B preparation (counter, generation)
   size_t bprep_bytes = 0;
   int workspace();
 
