@@ -613,6 +613,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   T* Rs = Ss + (size_t)a.rpc * ldw;                  // [rpc][bi]    residual block (x 2^sshift)
   T* Tb = Rs + (size_t)a.rpc * bi;                   // [rpc][BMAX]  staging for X R^{-1}
   T* Ps = Tb + (size_t)a.rpc * BMAX;                 // [qcols][max(b0, bi)] projection coefficients
+  T* Cs = Ps + (size_t)a.qcols * max(a.b0, bi);      // [qcols][max(b0, bi)] Q^T Q_new of the current block
   const int ldp = bi;
   bool timeout = false;
   int cc = a.cc0;
@@ -722,32 +723,53 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     to_arith<A>(Ri, bb * bb, RiT);
     apply_rinv<A>(Qn, ldq, bb, RiT, nr, Tb);
     tmr.mark(PH_QR1);
-    // block Gram-Schmidt against Q on the Q_new just formed (its rounding errors included)
-    if (cc > 0) {
-      gram_acc<A>(Qs, ldq, Qn, ldq, cc, bb, nr, red_buf(rd));
-      double* bufR = reduce();
-      if (!bufR) return finish(ST_TIMEOUT);
-      read_totals_t<A>(bufR, cc * bb, Ps);
-      sub_qp<A>(Qn, ldq, Qs, ldq, cc, Ps, bb, bb, nr);
-    }
-    tmr.mark(PH_REORTH);
-    // reduction A: the Gram matrix of Q_new (second CholeskyQR pass) and, when the next block lies
-    // within the sketch, [Q, Q_new]^T S_all(:, next:next+bi) for its residual
+    // One reduction for both the block Gram-Schmidt step and the second CholeskyQR pass, on the
+    // Q_new just formed (so its rounding errors are seen): [Q, Q_new]^T Q_new gives C = Q^T Q_new and
+    // G = Q_new^T Q_new, and when the next block lies within the sketch, [Q, Q_new]^T S_next.  After
+    // Q_new <- Q_new - Q C, its Gram matrix is G - C^T C and its coefficients against S_next are
+    // Q_new^T S_next - C^T Q^T S_next (Q^T Q = I to rounding; G is near I and C^T C tiny, so the
+    // subtraction loses nothing).
     const int nxt = cc + bb;
     const bool want = nxt < a.rbar && nxt + bi <= a.width;
-    gram_acc<A>(Qn, ldq, Qn, ldq, bb, bb, nr, red_buf(rd));
-    if (want) gram_acc<A>(Qs, ldq, Ss + nxt, ldw, nxt, bi, nr, red_buf(rd) + bb * bb);
+    {
+      double* eb = red_buf(rd);
+      gram_acc<A>(Qs, ldq, Qn, ldq, nxt, bb, nr, eb);                                  // (cc + bb) x bb
+      if (want) gram_acc<A>(Qs, ldq, Ss + nxt, ldw, nxt, bi, nr, eb + nxt * bb);      // (cc + bb) x bi
+    }
     double* bufA = reduce();
     if (!bufA) return finish(ST_TIMEOUT);
-    read_totals(bufA, bb * bb, G);
+    if (cc > 0) read_totals_t<A>(bufA, cc * bb, Cs);
+    for (int o = threadIdx.x; o < bb * bb; o += NT) {
+      const int i = o / bb, j = o % bb;
+      T t = A::zero();
+      for (int k = 0; k < cc; ++k) t = A::fma(Cs[k * bb + i], Cs[k * bb + j], t);
+      G[o] = __ldcg(bufA + (cc + i) * bb + j) - A::to(t);
+    }
+    __syncthreads();
+    if (cc > 0) sub_qp<A>(Qn, ldq, Qs, ldq, cc, Cs, bb, bb, nr);
+    tmr.mark(PH_REORTH);
     if (!factor2(bb)) return finish(ST_BREAKDOWN);
+    if (want) {
+      // P = [Q^T S_next; R2^{-T} (Q_new^T S_next - C^T Q^T S_next)]; the middle term goes through M
+      const double* pb = bufA + nxt * bb;
+      read_totals_t<A>(pb, cc * bi, Ps);
+      for (int o = threadIdx.x; o < bb * bi; o += NT) {
+        const int i = o / bi, j = o % bi;
+        T t = A::zero();
+        for (int k = 0; k < cc; ++k) t = A::fma(Cs[k * bb + i], Ps[k * bi + j], t);
+        M[o] = __ldcg(pb + (cc + i) * bi + j) - A::to(t);
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < bb * bi; o += NT) {
+        const int i = o / bi, j = o % bi;
+        double v = 0.0;
+        for (int k = 0; k <= i; ++k) v = fma(Ri[k * bb + i], M[k * bi + j], v);
+        Ps[cc * bi + o] = A::from(v);
+      }
+      __syncthreads();
+    }
     to_arith<A>(Ri, bb * bb, RiT);
     apply_rinv<A>(Qn, ldq, bb, RiT, nr, Tb);
-    if (want) {
-      // P = [Q^T S_next; R2^{-T} Q_new^T S_next]
-      read_totals_t<A>(bufA + bb * bb, cc * bi, Ps);
-      mul_rinv_t_left<A>(bufA + bb * bb + cc * bi, bb, bi, Ri, Ps + cc * bi);
-    }
     have_p = want;
     cc = nxt;
     tmr.mark(PH_REDUCE_A);
@@ -788,7 +810,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const int rpc = (int)((m + nblocks - 1) / nblocks);
   const int64_t qcols = std::min(rbar, width);     // columns of Q never exceed the sketch width
   const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
-                                        (size_t)qcols * (size_t)std::max(b0, bi));
+                                        2 * (size_t)qcols * (size_t)std::max(b0, bi));
   const size_t static_bytes = 48 * 1024;   // G, R^{-1} (FP64 and working type), [G | I], pivot buffers (about 44 KB)
   if (dyn + static_bytes > (size_t)smem_optin) return TTR_ERR_UNSUPPORTED;
   const void* kern = double_float ? (const void*)ac::adaptive_core_kernel<ac::DF>
@@ -819,9 +841,9 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
     TTR_CHECK(c.alloc_t(&c.d_flags, 4));
     TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
   }
-  // largest reduction: first block (b0^2 + b0 bi), reduction A (bi^2 + rbar bi); reduction B
-  // (1 + bi^2), re-orthogonalization and fresh coefficients (rbar bi) are smaller
-  const int used = (std::max(b0 * b0 + b0 * bi, 1 + bi * bi + rbar * bi) + 1 + 31) / 32 * 32;
+  // largest reduction: first block (b0^2 + b0 bi) or the second one of a block ((cc + bb)(bb + bi)
+  // <= 2 rbar bi); the estimate's (1 + bi^2) and fresh coefficients (rbar bi) are smaller
+  const int used = (std::max(b0 * b0 + b0 * bi, 1 + 2 * rbar * bi) + 1 + 31) / 32 * 32;
   if (used > ac::ACC + 64) return TTR_ERR_UNSUPPORTED;
   TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * used, c.stream));
   ac::Args a{};

@@ -105,7 +105,7 @@ void Ctx::prof_report() {
             a.second.ms, 100.0 * a.second.ms / std::max(total, 1e-9), 1e3 * a.second.ms / a.second.n);
   if (ac_prof) {
     static const char* names[] = {"stage rows", "first block QR", "fresh Q^T S", "residual (local)",
-                                  "reduce B + estimate", "QR pass 1", "re-orthogonalize", "reduce A + QR 2",
+                                  "reduce B + estimate", "QR pass 1", "reduce A + reorth", "QR 2 + next P",
                                   "write back", "(barrier waits)"};
     unsigned long long cyc[10] = {};
     cudaMemcpy(cyc, ac_prof, sizeof(cyc), cudaMemcpyDeviceToHost);
