@@ -104,6 +104,52 @@ def job_rate(steps: int, world: int, job_ms: float) -> float:
     return world * steps / (job_ms / 1e3)
 
 
+def concurrent_rate(B, cores, opts_kw, streams: int, rounds: int) -> dict:
+    """`streams` host threads, each on its own CUDA stream with 1/streams of the SMs for the block
+    loop, round the same resident input `rounds` times each: throughput and per-rounding latency."""
+    import threading
+
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    share = max(1, nsm // streams)
+    lat = [[] for _ in range(streams)]
+    errs = []
+    start = threading.Barrier(streams + 1)
+
+    def run(i):
+        try:
+            s = torch.cuda.Stream()
+            opts = B.options(max_sms=share, **opts_kw)
+            with torch.cuda.stream(s):
+                B.round_adaptive(cores, TOL, BLOCK, SEED, opts, stream=s).free()      # warm-up
+                start.wait()
+                for _ in range(rounds):
+                    t0 = time.perf_counter()
+                    B.round_adaptive(cores, TOL, BLOCK, SEED, opts, stream=s).free()
+                    lat[i].append(1e3 * (time.perf_counter() - t0))
+        except Exception as e:
+            errs.append(repr(e))
+            start.abort()
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(streams)]
+    for t in threads:
+        t.start()
+    try:
+        start.wait()
+    except threading.BrokenBarrierError:
+        pass
+    t0 = time.perf_counter()
+    for t in threads:
+        t.join()
+    wall = time.perf_counter() - t0
+    if errs:
+        return {"streams": streams, "error": errs[0]}
+    all_lat = [v for l in lat for v in l]
+    return {"streams": streams, "max_sms_per_stream": share, "roundings_per_s": len(all_lat) / wall,
+            "p50_ms": float(np.percentile(all_lat, 50)), "p99_ms": float(np.percentile(all_lat, 99)),
+            "roundings": len(all_lat)}
+
+
 def cpu_oracle_rate(x, budget_s=15.0):
     """The oracle as it stands, on a bounded sample: whole adaptive roundings of the same input."""
     from oracle import rounding as R
@@ -257,6 +303,10 @@ def main():
     roof = max(cand, key=lambda r: r["share_of_step"]) if cand else None
     roof_other = [r for r in cand if r is not roof]
 
+    # ---- several roundings at once: one stream per host thread, the SMs shared between them
+    conc = [concurrent_rate(B, cores, {"precision": prec, "nrmx": x.norm}, k, max(5, args.steps // (2 * k)))
+            for k in (2, 3)] if world == 1 else []
+
     # ---- deterministic FP64 TT-rounding on the same GPU (the comparison the metric names)
     det_ms = []
     for i in range(args.det_steps + 1):
@@ -292,6 +342,7 @@ def main():
             "det_fp64": {"roundings_per_s": 1e3 / float(np.mean(det_ms)), "ms": float(np.mean(det_ms)),
                          "ranks_out": det_ranks, "speedup_of_adaptive": value / world / (1e3 / float(np.mean(det_ms)))},
             "roofline": roof, "roofline_other": roof_other[0] if roof_other else None, "gpu_launches": int(launches),
+            "concurrent_streams": conc,
             "e2e": {"value": e2e, "unit": "roundings/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

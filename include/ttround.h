@@ -33,7 +33,9 @@
  * Errors: every call returns a ttr_status; the library never aborts, traps or exits.  Device
  * waits inside kernels are bounded; a wait that runs out reports TTR_ERR_TIMEOUT.
  *
- * Threading: calls on different streams may run concurrently from different host threads.
+ * Threading: calls on different streams may run concurrently from different host threads; give
+ * each a share of the SMs (ttr_options::max_sms) so that their block loops can be resident
+ * together.
  */
 #ifndef TTROUND_H
 #define TTROUND_H
@@ -79,6 +81,9 @@ typedef struct {
                              extended (Algorithm 5) */
   int32_t kernel_timing;  /* 1: time the block-loop and partial-contraction kernels with CUDA
                              events on `stream` (fields ms_block_loop ... of ttr_result) */
+  int32_t max_sms;        /* largest number of SMs the persistent block-loop kernel (one CTA per
+                             SM, all resident at once) may take; 0 = all.  Lets calls on different
+                             streams run side by side: e.g. two calls with half the SMs each */
 } ttr_options;
 
 typedef struct {
@@ -109,7 +114,7 @@ typedef struct {
 } ttr_result;
 
 /* Fill `opts` with defaults: FP64, adap_r off, scale 1, nrmx 0 (estimate), f_init 0.1,
- * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0. */
+ * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0, max_sms 0. */
 void ttr_default_options(ttr_options* opts);
 
 /* Algorithm 4 (Sec. 3.2): fixed-rank randomize-then-orthogonalize with a KRP sketch.

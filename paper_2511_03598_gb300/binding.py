@@ -24,7 +24,8 @@ STATUS = {0: "TTR_OK", 1: "TTR_ERR_ARG", 2: "TTR_ERR_OOM", 3: "TTR_ERR_NONFINITE
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("slices", ctypes.c_int32), ("adap_r", ctypes.c_int32),
                 ("adap_r_tau_scale", ctypes.c_double), ("nrmx", ctypes.c_double), ("f_init", ctypes.c_double),
-                ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64), ("kernel_timing", ctypes.c_int32)]
+                ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64), ("kernel_timing", ctypes.c_int32),
+                ("max_sms", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -102,12 +103,13 @@ def _tt_args(cores):
 
 def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = False, adap_r_tau_scale: float = 1.0,
             nrmx: float = 0.0, f_init: float = 0.1, f_inc: float = 0.05, width_hint: int = 0,
-            kernel_timing: bool = False) -> Options:
+            kernel_timing: bool = False, max_sms: int = 0) -> Options:
     o = Options()
     lib().ttr_default_options(ctypes.byref(o))
     o.precision, o.slices, o.adap_r = precision, slices, int(adap_r)
     o.adap_r_tau_scale, o.nrmx, o.f_init, o.f_inc, o.width_hint = adap_r_tau_scale, nrmx, f_init, f_inc, width_hint
     o.kernel_timing = int(kernel_timing)
+    o.max_sms = int(max_sms)
     return o
 
 
@@ -147,16 +149,19 @@ class Rounded:
         return int(self._res.cores[k])
 
     def to_torch(self):
-        """Copies of the cores as torch CUDA tensors."""
+        """Copies of the cores as torch CUDA tensors (ordered before later work on the current stream)."""
         import torch
         out = []
         rk = self.ranks
-        for k in range(self.d):
-            shape = (rk[k], self._res_n[k], rk[k + 1])
-            t = torch.empty(shape, dtype=torch.float64, device="cuda")
-            nbytes = t.numel() * 8
-            _cuda_memcpy_d2d(t.data_ptr(), self.core_ptr(k), nbytes, self._stream)
-            out.append(t)
+        s = torch.cuda.ExternalStream(self._stream.value) if self._stream.value else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            for k in range(self.d):
+                shape = (rk[k], self._res_n[k], rk[k + 1])
+                t = torch.empty(shape, dtype=torch.float64, device="cuda")
+                nbytes = t.numel() * 8
+                _cuda_memcpy_d2d(t.data_ptr(), self.core_ptr(k), nbytes, self._stream)
+                out.append(t)
+        torch.cuda.current_stream().wait_stream(s)
         return out
 
     def to_numpy(self):

@@ -24,6 +24,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "engine.cuh"
@@ -784,8 +785,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
 // at column *cc), or TTR_ERR_UNSUPPORTED when this path does not apply.
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
                   int bi, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status, int* cc,
-                  int* nest,
-                  bool double_float, double scale) {
+                  int* nest, bool double_float, double scale, int max_sms) {
   if (b0 > ac::BMAX || bi > ac::BMAX || (int64_t)rbar * bi > ac::ACC || m <= 0) return TTR_ERR_UNSUPPORTED;
   int dev = 0;
   TTR_CUDA(cudaGetDevice(&dev));
@@ -804,9 +804,11 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   }
   const int nsm = di.nsm, smem_optin = di.smem_optin;
   if (!di.coop) return TTR_ERR_UNSUPPORTED;
-  // no more CTAs than rows; each CTA keeps its rows of Q, of the sketch and of the residual block
-  // one CTA per SM (a sweep of 38..152 CTAs on the 20-core workload: 152 is fastest)
-  const int nblocks = (int)std::min<int64_t>(nsm, m);
+  // no more CTAs than rows; each CTA keeps its rows of Q, of the sketch and of the residual block.
+  // One CTA per SM (a sweep of 38..152 CTAs on the 20-core workload: 152 is fastest), or the
+  // caller's share of the SMs.
+  const int sms = (max_sms > 0 && max_sms < nsm) ? max_sms : nsm;
+  const int nblocks = (int)std::min<int64_t>(sms, m);
   const int rpc = (int)((m + nblocks - 1) / nblocks);
   const int64_t qcols = std::min(rbar, width);     // columns of Q never exceed the sketch width
   const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
@@ -816,12 +818,17 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const void* kern = double_float ? (const void*)ac::adaptive_core_kernel<ac::DF>
                                   : (const void*)ac::adaptive_core_kernel<ac::F64>;
   const int ki = double_float ? 1 : 0;
-  if (di.raised[ki] < (int)dyn) {
-    TTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    int per_sm = 0;
-    TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ac::NT, dyn));
-    if (per_sm < 1) return TTR_ERR_UNSUPPORTED;
-    di.raised[ki] = (int)dyn;
+  {
+    // the limit belongs to the kernel, shared by every thread that calls it: only ever raise it
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (di.raised[ki] < (int)dyn) {
+      TTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      int per_sm = 0;
+      TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ac::NT, dyn));
+      if (per_sm < 1) return TTR_ERR_UNSUPPORTED;
+      di.raised[ki] = (int)dyn;
+    }
   }
   if (!c.ac_part) {
     TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * (ac::ACC + 64)));   // 3 buffers of up to ACC + 33 doubles

@@ -794,7 +794,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
         int status = 0, ccn = 0, nest = 0;
         st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)b0, (int)bi, (int)rbar, (int)sk_cols, (int)cc, tau,
                            hest.data(), (int)hest.size(), &status, &ccn, &nest,
-                           E.precision == TTR_PREC_SLICED && E.slices <= 6, nrmx);
+                           E.precision == TTR_PREC_SLICED && E.slices <= 6, nrmx, o.max_sms);
         if (st == TTR_ERR_UNSUPPORTED) break;
         if (st != TTR_OK) return st;
         for (int q = 0; q < nest; ++q) {
@@ -1120,6 +1120,7 @@ void ttr_default_options(ttr_options* o) {
   o->f_inc = 0.05;
   o->width_hint = 0;
   o->kernel_timing = 0;
+  o->max_sms = 0;
 }
 
 static int finish(int st, ttr_result* out, cudaStream_t s) {

@@ -39,7 +39,7 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
 // est_cap values; *nest of them are written).
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
                   int bi, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status, int* cc,
-                  int* nest, bool double_float, double scale);
+                  int* nest, bool double_float, double scale, int max_sms);
 
 // Widest tensor-core tile (UMMA N) usable with s slices.
 int tile_width(int s);

@@ -33,6 +33,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "engine.cuh"
 
@@ -699,15 +700,21 @@ static int launch(Ctx& c, const Args& a_in, dim3 grid, const char* name) {
   }
   const size_t sm = smem_bytes(a.s, a.tn, MODE);
   auto kern = sliced_kernel<MODE, AKFAST>;
-  // the shared-memory limit is raised once per device to the largest size requested so far
+  // the shared-memory limit belongs to the kernel and every calling thread shares it: raise it per
+  // device to the largest size requested so far, never lower it
   constexpr int MAXDEV = 64;
   static int raised[MAXDEV] = {};
+  static std::mutex mu;
   int dev = 0;
   TTR_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= MAXDEV || raised[dev] < (int)sm) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
-    if (dev >= 0 && dev < MAXDEV) raised[dev] = (int)sm;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const int have = (dev >= 0 && dev < MAXDEV) ? raised[dev] : 0;
+    if (have < (int)sm) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
+      if (dev >= 0 && dev < MAXDEV) raised[dev] = (int)sm;
+    }
   }
   kern<<<grid, NT, sm, c.stream>>>(a);
   return c.check_launch(name);
