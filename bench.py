@@ -166,6 +166,37 @@ def concurrent_timed(B, cores, opts_kw, streams: int, rounds: int) -> dict:
     return {"span_ms": span, "latencies_ms": all_lat, "launches": sum(launches), "max_sms_per_stream": share}
 
 
+def torch_deterministic(cores, tol):
+    """Comparison only (not this library's path): Algorithm 1 with torch's FP64 GPU QR and SVD
+    (cuSOLVER), for the speed of a tuned library deterministic TT-rounding on the same GPU."""
+    import math
+
+    import torch
+    d = len(cores)
+    Y = [c.clone() for c in cores]
+    for k in range(d - 1, 0, -1):                                 # right-to-left orthogonalization
+        r0, n, r1 = Y[k].shape
+        Q, R = torch.linalg.qr(Y[k].reshape(r0, n * r1).T)
+        rk = Q.shape[1]
+        Y[k] = Q.T.reshape(rk, n, r1)
+        Y[k - 1] = (Y[k - 1].reshape(-1, r0) @ R.T).reshape(Y[k - 1].shape[0], Y[k - 1].shape[1], rk)
+    tau = float(torch.linalg.norm(Y[0])) * tol / math.sqrt(d - 1)
+    ranks = [1]
+    for k in range(d - 1):
+        r0, n, r1 = Y[k].shape
+        Q, R = torch.linalg.qr(Y[k].reshape(r0 * n, r1))
+        U, sv, Vt = torch.linalg.svd(R, full_matrices=False)
+        tail = torch.sqrt(torch.flip(torch.cumsum(torch.flip(sv * sv, [0]), 0), [0]))
+        keep = int((tail > tau).sum().item())
+        rp = max(1, keep)
+        Y[k] = (Q @ U[:, :rp]).reshape(r0, n, rp)
+        q0, qn, q1 = Y[k + 1].shape
+        Y[k + 1] = ((sv[:rp, None] * Vt[:rp]) @ Y[k + 1].reshape(q0, qn * q1)).reshape(rp, qn, q1)
+        ranks.append(rp)
+    ranks.append(1)
+    return ranks
+
+
 def cpu_oracle_rate(x, budget_s=15.0):
     """The oracle as it stands, on a bounded sample: whole adaptive roundings of the same input."""
     from oracle import rounding as R
@@ -344,6 +375,16 @@ def main():
         if i > 0:
             det_ms.append(1e3 * (time.perf_counter() - t0))
 
+    # ---- the same algorithm on torch's FP64 cuSOLVER QR/SVD, as context for that comparison
+    tdet_ms = []
+    for i in range(max(1, args.det_steps) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tdet_ranks = torch_deterministic(cores, TOL)
+        torch.cuda.synchronize()
+        if i > 0:
+            tdet_ms.append(1e3 * (time.perf_counter() - t0))
+
     # ---- end to end through host buffers: H2D of the cores, rounding, D2H of the result
     host = [torch.from_numpy(c).pin_memory() for c in x.cores]
     h2d = sum(c.nbytes for c in x.cores)
@@ -369,6 +410,9 @@ def main():
             "config": config(x, args.streams), "ranks_out": out_ranks, "sketch_width": w, "extensions": info["extensions"],
             "det_fp64": {"roundings_per_s": 1e3 / float(np.mean(det_ms)), "ms": float(np.mean(det_ms)),
                          "ranks_out": det_ranks, "speedup_of_adaptive": value / world / (1e3 / float(np.mean(det_ms)))},
+            "det_torch_cusolver_fp64": {"ms": float(np.mean(tdet_ms)), "roundings_per_s": 1e3 / float(np.mean(tdet_ms)),
+                                        "ranks_out": tdet_ranks,
+                                        "note": "Algorithm 1 on torch.linalg.qr/svd (cuSOLVER), FP64, comparison only"},
             "roofline": roof, "roofline_other": roof_other[0] if roof_other else None, "gpu_launches": int(launches),
             "max_sms_per_stream": conc["max_sms_per_stream"],
             "e2e": {"value": e2e, "unit": "roundings/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
