@@ -214,6 +214,34 @@ __device__ __forceinline__ int exp_field(double x) {
   return (int)(((uint64_t)__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
+// The products of one K-chunk: for each of the two 16-deep K-steps and each diagonal t < S, the
+// digit products p + q = t accumulate into TMEM columns [t tn, (t+1) tn).  Descriptors are built
+// once and advanced by constant offsets in their 14-bit start-address field (every operand lies
+// inside this CTA's shared memory, so the field cannot overflow).
+template <int S>
+__device__ __forceinline__ void issue_chunk(uint64_t da0, uint64_t db0, uint32_t tmem, int tn, int plane_b,
+                                            uint32_t idesc, bool first) {
+  constexpr uint32_t PA = (PLANE_A * 2) >> 4;            // one A digit plane
+  constexpr uint32_t KSA = (2 * (TM / 8) * 128) >> 4;     // one 16-deep K-step of A
+  const uint32_t pb = (uint32_t)(plane_b * 2) >> 4;      // one B digit plane
+  const uint32_t ksb = (uint32_t)(2 * (tn / 8) * 128) >> 4;
+#pragma unroll
+  for (int ks = 0; ks < KC / 16; ++ks) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+#pragma unroll
+      for (int p = 0; p <= t; ++p) {
+        const uint64_t da = da0 + (uint64_t)(p * PA + ks * KSA);
+        const uint64_t db = db0 + (uint64_t)((uint32_t)(t - p) * pb + (uint32_t)ks * ksb);
+        const uint32_t accum = (first && ks == 0 && p == 0) ? 0u : 1u;
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(t * tn)),
+                     "l"(da), "l"(db), "r"(idesc), "r"(accum));
+      }
+    }
+  }
+}
+
 template <int MODE, bool AKFAST>
 __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -347,21 +375,15 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t abase = smem_u32(bufs[b]), bbase = abase + (uint32_t)(s * PLANE_A * 2);
-#pragma unroll 1
-        for (int ks = 0; ks < KC / 16; ++ks) {
-#pragma unroll 1
-          for (int t = 0; t < s; ++t) {
-#pragma unroll 1
-            for (int p = 0; p <= t; ++p) {
-              const int q = t - p;
-              const uint64_t da = umma_desc(abase + p * PLANE_A * 2 + ks * 2 * (TM / 8) * 128, (TM / 8) * 128, 128);
-              const uint64_t db = umma_desc(bbase + q * plane_b * 2 + ks * 2 * (tn / 8) * 128, (tn / 8) * 128, 128);
-              const uint32_t accum = (c == 0 && ks == 0 && p == 0) ? 0u : 1u;
-              asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(t * tn)),
-                           "l"(da), "l"(db), "r"(idesc), "r"(accum));
-            }
-          }
+        const uint64_t da0 = umma_desc(abase, (TM / 8) * 128, 128);
+        const uint64_t db0 = umma_desc(bbase, (tn / 8) * 128, 128);
+        switch (s) {
+          case 3: issue_chunk<3>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
+          case 4: issue_chunk<4>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
+          case 5: issue_chunk<5>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
+          case 6: issue_chunk<6>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
+          case 7: issue_chunk<7>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
+          default: issue_chunk<8>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&empty[b])));
@@ -415,6 +437,11 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
 #pragma unroll
       for (int i = 0; i < TASKS; ++i) {
         const int row = trow[i], grp = tgrp[i];
+        // From the third chunk on, tasks with no data (padding rows, k beyond the segment) keep
+        // the digits this buffer held two chunks ago: those meet zero B digits (k >= K) or land in
+        // accumulator rows the epilogue drops.  Chunks 0 and 1 write every position, so no
+        // uninitialised shared memory ever reaches the tensor cores.
+        if (c >= 2 && (row >= rows || c * KC + grp * 8 >= kseg_len)) continue;
         const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
         store_digits_s(s, vc[i], rowE[row], Ap, PLANE_A, idx);
       }
