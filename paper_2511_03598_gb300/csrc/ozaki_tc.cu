@@ -214,28 +214,32 @@ __device__ __forceinline__ int exp_field(double x) {
   return (int)(((uint64_t)__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// The products of one K-chunk: for each of the two 16-deep K-steps and each diagonal t < S, the
-// digit products p + q = t accumulate into TMEM columns [t tn, (t+1) tn).  Descriptors are built
-// once and advanced by constant offsets in their 14-bit start-address field (every operand lies
-// inside this CTA's shared memory, so the field cannot overflow).
+// The products of one K-chunk.  For each of the two 16-deep K-steps and each A digit plane p, the
+// B planes q = 0 .. S-1-p go to the accumulators of diagonals p + q, TMEM columns [(p + q) tn, ..);
+// with the B layout of b_digit_index those planes are adjacent along N, so one MMA covers up to
+// floor(256 / tn) of them (N <= 256).  Descriptors are built once and advanced by constant offsets
+// in their 14-bit start-address field (every operand lies inside this CTA's shared memory, so the
+// field cannot overflow).  The first write of every accumulator comes from p = 0.
 template <int S>
-__device__ __forceinline__ void issue_chunk(uint64_t da0, uint64_t db0, uint32_t tmem, int tn, int plane_b,
-                                            uint32_t idesc, bool first) {
+__device__ __forceinline__ void issue_chunk(uint64_t da0, uint64_t db0, uint32_t tmem, int tn, uint32_t idesc0,
+                                            bool first) {
   constexpr uint32_t PA = (PLANE_A * 2) >> 4;            // one A digit plane
   constexpr uint32_t KSA = (2 * (TM / 8) * 128) >> 4;     // one 16-deep K-step of A
-  const uint32_t pb = (uint32_t)(plane_b * 2) >> 4;      // one B digit plane
-  const uint32_t ksb = (uint32_t)(2 * (tn / 8) * 128) >> 4;
+  const uint32_t pb = (uint32_t)((tn / 8) * 128) >> 4;   // one B digit plane (its row groups)
+  const uint32_t ksb = (uint32_t)(2 * S * (tn / 8) * 128) >> 4;
+  const int G = 256 / tn;                                 // B planes per MMA
 #pragma unroll
   for (int ks = 0; ks < KC / 16; ++ks) {
 #pragma unroll
-    for (int t = 0; t < S; ++t) {
-#pragma unroll
-      for (int p = 0; p <= t; ++p) {
-        const uint64_t da = da0 + (uint64_t)(p * PA + ks * KSA);
-        const uint64_t db = db0 + (uint64_t)((uint32_t)(t - p) * pb + (uint32_t)ks * ksb);
+    for (int p = 0; p < S; ++p) {
+      const uint64_t da = da0 + (uint64_t)(p * PA + ks * KSA);
+      for (int q0 = 0; q0 < S - p; q0 += G) {
+        const int nq = min(G, S - p - q0);
+        const uint64_t db = db0 + (uint64_t)((uint32_t)q0 * pb + (uint32_t)ks * ksb);
+        const uint32_t idesc = idesc0 | ((uint32_t)((nq * tn) >> 3) << 17);
         const uint32_t accum = (first && ks == 0 && p == 0) ? 0u : 1u;
         asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(t * tn)),
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)((p + q0) * tn)),
                      "l"(da), "l"(db), "r"(idesc), "r"(accum));
       }
     }
@@ -358,7 +362,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  // instruction descriptor without N (set per MMA): FP32 accumulation, BF16 A and B, K-major, M = 128
+  const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TM >> 4) << 24);
   bool ok = true;
   mark(TP_SCAN);
 
@@ -376,14 +381,14 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t abase = smem_u32(bufs[b]), bbase = abase + (uint32_t)(s * PLANE_A * 2);
         const uint64_t da0 = umma_desc(abase, (TM / 8) * 128, 128);
-        const uint64_t db0 = umma_desc(bbase, (tn / 8) * 128, 128);
+        const uint64_t db0 = umma_desc(bbase, s * (tn / 8) * 128, 128);
         switch (s) {
-          case 3: issue_chunk<3>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
-          case 4: issue_chunk<4>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
-          case 5: issue_chunk<5>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
-          case 6: issue_chunk<6>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
-          case 7: issue_chunk<7>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
-          default: issue_chunk<8>(da0, db0, tmem, tn, plane_b, idesc, c == 0); break;
+          case 3: issue_chunk<3>(da0, db0, tmem, tn, idesc0, c == 0); break;
+          case 4: issue_chunk<4>(da0, db0, tmem, tn, idesc0, c == 0); break;
+          case 5: issue_chunk<5>(da0, db0, tmem, tn, idesc0, c == 0); break;
+          case 6: issue_chunk<6>(da0, db0, tmem, tn, idesc0, c == 0); break;
+          case 7: issue_chunk<7>(da0, db0, tmem, tn, idesc0, c == 0); break;
+          default: issue_chunk<8>(da0, db0, tmem, tn, idesc0, c == 0); break;
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&empty[b])));
@@ -562,6 +567,16 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
+// B digit layout of one (column chunk, K-chunk) block, in BF16 elements: the 8x16-byte core
+// matrices are ordered (k block, digit plane, row group), so that for each 8-deep k block the row
+// groups of all s planes follow each other at a 128-byte stride.  One UMMA descriptor (row-group
+// stride 128 B, k-block stride s (tn / 8) 128 B) then spans several planes along N, and one MMA
+// accumulates several digit diagonals into adjacent TMEM columns.  Digit plane p of (k group grp,
+// column j) is at b_digit_index(grp, j, s, tn) + p * tn * 8.
+__host__ __device__ __forceinline__ int b_digit_index(int grp, int j, int s, int tn) {
+  return ((grp * s * (tn / 8)) + (j >> 3)) * 64 + (j & 7) * 8;
+}
+
 // ---- B operand preparation: column exponent scales, then digit planes in the shared-memory
 // image.  B(k, n) = B[k*sbk + n*sbn], K x N.
 // Pass 1: grid (N-chunks, K-chunks of 32 rows); each CTA writes the largest exponent of each of its
@@ -619,8 +634,7 @@ __global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t s
       const int64_t k = (int64_t)kcn * KC + grp * 8 + q;
       v[q] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0;
     }
-    const int idx = ((grp * (tn / 8)) + (j >> 3)) * 8 + (j & 7);      // uint4 index in a plane
-    store_digits_s(s, v, E[j], reinterpret_cast<uint16_t*>(blk), plane_b, idx * 8);
+    store_digits_s(s, v, E[j], reinterpret_cast<uint16_t*>(blk), tn * 8, b_digit_index(grp, j, s, tn));
   }
 }
 
@@ -701,8 +715,7 @@ __global__ void __launch_bounds__(256) prep_b_fused_kernel(const double* B, int6
     const int u = threadIdx.x + 256 * t;
     if (u >= tn * (KC / 8)) continue;
     const int j = u % tn, grp = u / tn;
-    const int idx = ((grp * (tn / 8)) + (j >> 3)) * 8 + (j & 7);      // uint4 index in a plane
-    store_digits_s(s, v[t], cm[j], reinterpret_cast<uint16_t*>(blk), plane_b, idx * 8);
+    store_digits_s(s, v[t], cm[j], reinterpret_cast<uint16_t*>(blk), tn * 8, b_digit_index(grp, j, s, tn));
   }
 }
 
