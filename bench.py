@@ -91,6 +91,12 @@ class ClockSampler:
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# this workload in sliced precision, for the kernels as they stand (the capture command is in
+# profiles/): the block loop's figure is the median over full-rank cores, the partial
+# contraction's the mean over all 18 launches of one pass.  Other precisions run other kernels.
+TRAFFIC_SLICED = {"block_loop": 2.44e6, "rl_kernel": 18.02e6}
+
 
 def max_over_ranks(ms: float, world: int, device) -> float:
     """The job's time: the largest of the ranks' timed regions (all_reduce MAX when world > 1)."""
@@ -337,11 +343,12 @@ def main():
     # ---- rooflines from the library's CUDA events around each launch in the timed region
     w = int(info["width"])
     pk, pk_kind = peaks()
+    traffic = TRAFFIC_SLICED if args.precision == "sliced" else {}
     roof_bl = None
     if kt["n_block_loop"]:
         ach = kt["flops_block_loop"] / (kt["ms_block_loop"] / 1e3) / 1e12
         roof_bl = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                   "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                   "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic.get("block_loop"),
                    "kernel": "adaptive block loop (Algorithm 6): persistent cooperative FP64 kernel, one launch per core",
                    "peak_source": "derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                    "per_unit": f"{kt['flops_block_loop'] / kt['n_block_loop']:.3e} FP64 flop per launch (one core's "
@@ -353,7 +360,7 @@ def main():
     if kt["n_rl_kernel"]:
         ach = kt["bytes_rl_kernel"] / (kt["ms_rl_kernel"] / 1e3) / 1e9
         roof_rl = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
-                   "traffic": None, "kernel": "partial contractions (Algorithm 3): sliced FP64 on BF16 tcgen05, one launch per core",
+                   "traffic": traffic.get("rl_kernel"), "kernel": "partial contractions (Algorithm 3): sliced FP64 on BF16 tcgen05, one launch per core",
                    "peak_source": f"hbm_gbs {pk_kind}",
                    "per_unit": f"{kt['bytes_rl_kernel'] / kt['n_rl_kernel']:.3e} B per launch (core read once, "
                                "W_k+1 read, W_k written)",
