@@ -11,6 +11,10 @@ Contents (paper sections / algorithms):
 * ``tt_round_adaptive``        - Algorithm 6 (adaptive-rank Rand-Orth with KRP), Sec. 3.3
 * ``norm_estimate``            - Remark 3.1, Eq. (3.6)
 * ``svd_pass_rl``              - Remark 3.2 (the "Adap-R" compression pass, right to left)
+* ``partial_contractions_rl_sum`` / ``tt_round_adaptive_sum``
+                               - Remark 3.3 and Appendix C (the algorithms for a sum of TT
+                                 tensors): every summand sketched with the shared Omega, the
+                                 sum never formed
 * ``tt_round_deterministic``   - Algorithm 1 (TT-Rounding, Oseledets)
 
 Library primitives used as single steps: matrix product, Householder QR (numpy.linalg.qr)
@@ -33,6 +37,14 @@ and the SVD (numpy.linalg.svd).  Readings of points where the paper is silent or
   R7  The tau-truncated SVD keeps the smallest rank whose discarded tail is <= tau (see
       ``oracle.tt.truncation_rank``); the Adap-R pass reuses tau (Remark 3.2) unless
       ``adap_r_tau`` is given.
+  R12 Sum of TTs, block sizes: block > 0 gives b_init = b_inc = block as in R3; otherwise the
+      appendix's b_init = max_i r_k^(i) (clamped to rbar_k) and b_inc = ceil(f_inc * rbar_k).
+      The norm estimate uses the first w0 columns of the stacked W_2, w0 = block in block mode,
+      else the appendix's sketch width max_{i,k} r_k^(i).
+  R13 Sum of TTs, the last core: the appendix writes H(Y_{k+1}) = [Y^(1) ... Y^(s)] for every k.
+      For k + 1 = d the summands' last cores share the right bond 1 (the formal sum stacks them
+      vertically), so H(Y_d) = sum_i M^(i) H(X_d^(i)); for k + 1 < d the blocks sit side by side
+      in the concatenated right bond, ordered by summand.
 """
 from __future__ import annotations
 
@@ -101,11 +113,16 @@ def tt_round_fixed(cores, ell, seed: int):
 
 
 class _Sketches:
-    """The growing partial contractions W_{k+1..d} of Algorithm 6 (all share one width)."""
+    """The growing partial contractions W_{k+1..d} of Algorithm 6 (all share one width).
 
-    def __init__(self, cores, seed: int, w0: int):
+    ``rl`` computes them for columns [c0, c1): Algorithm 3 for one TT, or its per-summand form
+    for a sum of TTs (``cores`` is then the list of summands).
+    """
+
+    def __init__(self, cores, seed: int, w0: int, rl=None):
         self.cores, self.seed = cores, seed
-        self.W = partial_contractions_rl(cores, seed, 0, w0)
+        self.rl = partial_contractions_rl if rl is None else rl
+        self.W = self.rl(cores, seed, 0, w0)
         self.width = w0
         self.extensions = 0
 
@@ -113,7 +130,7 @@ class _Sketches:
         """Algorithm 5, first branch: if col(W_{k+1}) < need, append columns for j = k+1..d (R2)."""
         if self.width >= need:
             return
-        new = partial_contractions_rl(self.cores, self.seed, self.width, need, t=k + 1)
+        new = self.rl(self.cores, self.seed, self.width, need, t=k + 1)
         for j, wj in new.items():
             self.W[j] = np.concatenate([self.W[j], wj], axis=1)
         self.width = need
@@ -177,6 +194,101 @@ def tt_round_adaptive(cores, tol: float, seed: int, block: int = 0, f_init: floa
     out_ranks.append(1)
     info = {"ranks": out_ranks, "tau": tau, "nrmx": nrmx, "estimates": ests,
             "width": sk.width, "extensions": sk.extensions, "w0": w0}
+    if adap_r:
+        Y = svd_pass_rl(Y, tau if adap_r_tau is None else adap_r_tau)
+        info["ranks_before_adap_r"] = out_ranks
+        info["ranks"] = ranks(Y)
+    return Y, info
+
+
+def _check_summands(summands):
+    if len(summands) < 1:
+        raise ValueError("at least one summand")
+    d = len(summands[0])
+    n = modes(summands[0])
+    for x in summands:
+        if len(x) != d or modes(x) != n:
+            raise ValueError("summands must share d and the mode sizes")
+        r = ranks(x)
+        if r[0] != 1 or r[d] != 1:
+            raise ValueError("summand boundary ranks must be 1")
+    return d, n
+
+
+def partial_contractions_rl_sum(summands, seed: int, col0: int, col1: int, t: int = 2):
+    """Algorithm 3 on every summand with the same Omega, stacked by rows (Remark 3.3).
+
+    W_k = [W_k^(1); ...; W_k^(s)]: the sketch of the sum is the sum of the summands' sketches, and
+    stacked, these are the partial contractions of the block-diagonal formal sum.
+    """
+    parts = [partial_contractions_rl(x, seed, col0, col1, t) for x in summands]
+    return {k: np.concatenate([p[k] for p in parts], axis=0) for k in parts[0]}
+
+
+def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_init: float = 0.1,
+                          f_inc: float = 0.05, nrmx: float | None = None, adap_r: bool = False,
+                          adap_r_tau: float | None = None):
+    """Adaptive-rank rounding of X = X^(1) + ... + X^(s) without forming the formal sum
+    (Appendix C: the sum forms of Algorithms 5 and 6; readings R12, R13).
+
+    Y_1 = [X_1^(1) ... X_1^(s)] (first cores side by side); at core k the sketch is
+    V(Y_k) [W_{k+1}^(1); ...; W_{k+1}^(s)], and the next core is projected summand by summand,
+    M^(i) H(X_{k+1}^(i)) with [M^(1) ... M^(s)] = Q_k^T V(Y_k).  ``f_init`` is unused (R12).
+    Returns (Y cores, info).
+    """
+    d, n = _check_summands(summands)
+    rs = [ranks(x) for x in summands]
+    off = [np.cumsum([0] + [r[k] for r in rs]).tolist() for k in range(d + 1)]   # bond-k block offsets
+    rmax_part = max(max(r[1:d]) for r in rs)
+    w0 = block if block > 0 else rmax_part                         # R12
+    w0 = max(1, w0)
+    sk = _Sketches(summands, seed, w0, rl=partial_contractions_rl_sum)
+    Yk = np.concatenate([x[0] for x in summands], axis=2)          # Y_1 = [X_1^(1) ... X_1^(s)]
+    if nrmx is None:
+        nrmx = norm_estimate(Yk, sk.W[2][:, :w0])
+    tau = tol * nrmx / math.sqrt(d - 1)
+    Y = [None] * d
+    out_ranks, ests, b_inits = [1], [], []
+
+    def project(Mq, k):
+        # rows of H(Y_{k+1}) for the directions Mq = Q^T V(Y_k), one block per summand
+        return [Mq[:, off[k][i]:off[k][i + 1]] @ H(x[k]) for i, x in enumerate(summands)]
+
+    for k in range(1, d):
+        Z = V(Yk)                                                  # (l_{k-1} n_k) x (sum_i r_k^(i))
+        rbar = min(Z.shape)
+        b_init = block_size(rbar, block, f_init) if block > 0 else min(rbar, max(r[k] for r in rs))
+        b_inits.append(b_init)
+        sk.ensure(k, b_init)
+        S = Z @ sk.W[k + 1][:, :b_init]
+        Q, _ = np.linalg.qr(S)
+        parts = project(Q.T @ Z, k)
+        b_inc = block_size(rbar, block, f_inc)
+        est_k = []
+        while Q.shape[1] < rbar:                                   # R4
+            S = residual_sketch(sk, Z, Q, k, b_inc)                # stacked W: the sum form of Alg. 5
+            est = float(np.linalg.norm(S) / math.sqrt(b_inc))
+            est_k.append(est)
+            if not est > tau:
+                break
+            bb = min(b_inc, rbar - Q.shape[1])
+            Qn, _ = np.linalg.qr(S[:, :bb])
+            Qn, _ = np.linalg.qr(Qn - Q @ (Q.T @ Qn))              # re-orthogonalization
+            Q = np.concatenate([Q, Qn], axis=1)
+            parts = [np.concatenate([p, q], axis=0) for p, q in zip(parts, project(Qn.T @ Z, k))]
+        lk = Q.shape[1]
+        Y[k - 1] = Q.reshape(out_ranks[-1], n[k - 1], lk)
+        if k + 1 < d:
+            Yk = np.concatenate([p.reshape(lk, n[k], rs[i][k + 1]) for i, p in enumerate(parts)], axis=2)
+        else:
+            Yk = sum(parts).reshape(lk, n[k], 1)                   # R13
+        out_ranks.append(lk)
+        ests.append(est_k)
+    Y[d - 1] = Yk
+    out_ranks.append(1)
+    info = {"ranks": out_ranks, "tau": tau, "nrmx": nrmx, "estimates": ests, "width": sk.width,
+            "extensions": sk.extensions, "w0": w0, "b_init": b_inits,
+            "formal_ranks": [1] + [off[k][-1] for k in range(1, d)] + [1]}
     if adap_r:
         Y = svd_pass_rl(Y, tau if adap_r_tau is None else adap_r_tau)
         info["ranks_before_adap_r"] = out_ranks

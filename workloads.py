@@ -14,6 +14,10 @@ of Sec. 4.3):
 * ``c4`` - a stream of random formal sums (sizes, ranks and tolerances drawn from a seed).
 * ``c5`` - 4 scaled copies of a random TT (d=50, n=100, rank 200) + rank-10 noise at 1e-8: formal rank 810.
 
+The sums (c1, c2, c5) also come as their list of summands (``TTInput.summands``: the scaled
+copies, whose cores after the first are the same arrays, and the noise TT), the input of the
+sum-of-TTs rounding that never forms the block-diagonal formal sum.
+
 Core entries of random TTs are iid N(0, 1) / sqrt(n * r).  Copy coefficients are N(0, 1),
 redrawn while |sum c| < 0.1 so the sum is not nearly cancelled.  The noise TT is scaled so
 that ||noise|| = eta * ||T||.  Every generator also returns the exact input norm ||X||
@@ -34,6 +38,7 @@ class TTInput:
     cores: list
     norm: float                    # exact ||X||
     meta: dict = field(default_factory=dict)
+    summands: list | None = None   # the same X as a list of TTs (cores of each), when it is a sum
 
     @property
     def d(self) -> int:
@@ -107,7 +112,8 @@ def copies_plus_noise(seed: int, d: int, n: int, r: int, copies: int, noise_rank
     norm2 = s * s * nT2 + 2.0 * s * _gram_inner(T, N) + _gram_inner(N, N)
     meta = {"seed": seed, "d": d, "n": n, "r": r, "copies": copies, "noise_rank": noise_rank,
             "eta": eta, "coef": c.tolist(), "true_rank": r + noise_rank}
-    return TTInput(name, block_sum(terms), math.sqrt(norm2), meta)
+    summands = [[ci * T[0]] + T[1:] for ci, T in ((float(c_), T) for c_ in c)] + [N]
+    return TTInput(name, block_sum(terms), math.sqrt(norm2), meta, summands)
 
 
 def c1(seed: int = 1) -> TTInput:
