@@ -48,6 +48,7 @@ extern "C" {
 #endif
 
 #define TTR_MAX_D 4096
+#define TTR_MAX_SUMMANDS 4096
 
 typedef enum {
   TTR_OK = 0,
@@ -140,6 +141,29 @@ int tt_round_fixed(int32_t d, const int64_t* n, const int64_t* r, const double* 
 int tt_round_adaptive(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
                       double tol, int64_t block, uint64_t seed, const ttr_options* opts,
                       void* stream, ttr_result* out);
+
+/* Adaptive-rank rounding of a sum X = X^(1) + ... + X^(s) of TT tensors without forming the
+ * block-diagonal formal sum (Remark 3.3; the sum forms of Algorithms 5 and 6 in Appendix C).
+ *   s      number of summands, 1 <= s <= TTR_MAX_SUMMANDS.
+ *   d, n   shared by every summand (n: host array of d mode sizes).
+ *   r      host array of s pointers; r[i] points to the d+1 ranks of summand i (r[i][0] =
+ *          r[i][d] = 1).
+ *   cores  host array of s pointers; cores[i] points to the d device pointers of summand i, each
+ *          core row-major [a][i][c] as in tt_round_fixed.  Summands may share core buffers (scaled
+ *          copies that differ only in one core), which are read, never written or retained.
+ *   tol, seed, opts, stream, out   as in tt_round_adaptive.
+ *   block  > 0: b_init = b_inc = block; <= 0: b_init = max_i r_k^(i) clamped to rbar_k (the
+ *          appendix's rule) and b_inc = ceil(opts->f_inc * rbar_k); opts->f_init is unused.
+ * Every summand is contracted right to left with the same Omega into its own rows of W_k, so the
+ * stacked W_k are the partial contractions of the formal sum, and V(Y_1) holds the summands'
+ * first cores side by side.  Each next core is projected summand by summand, M^(i) H(X_{k+1}^(i)),
+ * which costs sum_i r^(i)^2 instead of (sum_i r^(i))^2 per core.  In block mode the result is that
+ * of tt_round_adaptive on the formal sum with the same seed, up to rounding.  Device memory is
+ * sized by the formal ranks R_k = sum_i r_k^(i).  Errors: TTR_ERR_ARG for a bad summand (same
+ * checks as tt_round_adaptive) or s out of range; otherwise as tt_round_adaptive. */
+int tt_round_adaptive_sum(int32_t s, int32_t d, const int64_t* n, const int64_t* const* r,
+                          const double* const* const* cores, double tol, int64_t block,
+                          uint64_t seed, const ttr_options* opts, void* stream, ttr_result* out);
 
 /* Algorithm 1 (Sec. 2.3, Oseledets' TT-Rounding), FP64: right-to-left orthogonalization,
  * tau = ||Y_1|| tol / sqrt(d-1), left-to-right tau-truncated SVDs (smallest rank whose

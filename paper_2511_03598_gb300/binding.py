@@ -70,7 +70,9 @@ def lib():
         L.ttr_sketch_omega.argtypes = [u64, i32, i64, i64, i64, vp, vp]
         L.ttr_partial_contractions.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, i32, i32, PP, vp]
         L.ttr_partial_contractions_noalloc.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, PP, vp]
-        for f in ("tt_round_fixed", "tt_round_adaptive", "tt_round_deterministic", "ttr_sketch_omega",
+        L.tt_round_adaptive_sum.argtypes = [i32, i32, P64, ctypes.POINTER(P64), ctypes.POINTER(PP), dbl, i64, u64,
+                                            ctypes.POINTER(Options), vp, ctypes.POINTER(Result)]
+        for f in ("tt_round_fixed", "tt_round_adaptive", "tt_round_adaptive_sum", "tt_round_deterministic", "ttr_sketch_omega",
                   "ttr_partial_contractions", "ttr_partial_contractions_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -228,6 +230,28 @@ def round_adaptive(cores, tol: float, block: int, seed: int, opts: Options | Non
     s = _stream_handle(stream)
     st = lib().tt_round_adaptive(d, n, r, p, float(tol), int(block), ctypes.c_uint64(seed),
                                  ctypes.byref(opts) if opts else None, s, ctypes.byref(res))
+    return _finish(res, st, s, list(n))
+
+
+def round_adaptive_sum(summands, tol: float, block: int, seed: int, opts: Options | None = None,
+                       stream=None) -> Rounded:
+    """Adaptive rounding of the sum of the TTs in ``summands`` (a list of core lists sharing d and
+    the mode sizes) without forming the formal sum; see tt_round_adaptive_sum."""
+    if len(summands) < 1:
+        raise ValueError("at least one summand")
+    args = [_tt_args(x) for x in summands]
+    d, n = args[0][0], args[0][1]
+    for a in args[1:]:
+        if a[0] != d or list(a[1]) != list(n):
+            raise ValueError("summands must share d and the mode sizes")
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    rs = (P64 * len(args))(*[ctypes.cast(a[2], P64) for a in args])
+    ps = (PP * len(args))(*[ctypes.cast(a[3], PP) for a in args])
+    res = Result()
+    s = _stream_handle(stream)
+    st = lib().tt_round_adaptive_sum(len(args), d, n, rs, ps, float(tol), int(block), ctypes.c_uint64(seed),
+                                     ctypes.byref(opts) if opts else None, s, ctypes.byref(res))
     return _finish(res, st, s, list(n))
 
 

@@ -228,6 +228,63 @@ static int validate(const TT& X) {
   return TTR_OK;
 }
 
+// Input of the right-to-left pass and of the adaptive rounding: one TT, or the sum of TTs that
+// share d and the mode sizes, never formed (Remark 3.3).  R are the ranks of the formal sum, and
+// off[i][k] is the first index of summand i in bond k of the formal sum (its rows of W_{k+1}, its
+// columns of V(Y_k)); the outer bonds (k = 0, d) are shared.
+struct SumTT {
+  int d = 0;
+  const int64_t* n = nullptr;
+  std::vector<TT> parts;
+  std::vector<int64_t> R;
+  std::vector<std::vector<int64_t>> off;
+  bool single() const { return parts.size() == 1; }
+  TT shape() const { return TT{d, n, R.data(), nullptr}; }   // sizes of the formal sum only
+  int64_t part_rank_max(int k) const {
+    int64_t m = 1;
+    for (const TT& P : parts) m = std::max(m, P.r[k]);
+    return m;
+  }
+};
+
+static SumTT single_sum(const TT& X) {
+  SumTT S;
+  S.d = X.d;
+  S.n = X.n;
+  S.parts.assign(1, X);
+  S.R.assign(X.r, X.r + X.d + 1);
+  S.off.assign(1, std::vector<int64_t>(X.d + 1, 0));
+  return S;
+}
+
+static int make_sum(int32_t s, int32_t d, const int64_t* n, const int64_t* const* r, const double* const* const* cores,
+                    SumTT& S) {
+  if (s < 1 || s > TTR_MAX_SUMMANDS) return set_error("number of summands must be in [1, TTR_MAX_SUMMANDS]"), TTR_ERR_ARG;
+  if (!r || !cores) return set_error("r and cores must be non-null"), TTR_ERR_ARG;
+  S = SumTT{};
+  S.d = d;
+  S.n = n;
+  for (int i = 0; i < s; ++i) {
+    if (!r[i] || !cores[i]) return set_error("null rank or core array of a summand"), TTR_ERR_ARG;
+    TT P{d, n, r[i], cores[i]};
+    TTR_CHECK(validate(P));
+    S.parts.push_back(P);
+  }
+  S.R.assign(d + 1, 1);
+  S.off.assign(s, std::vector<int64_t>(d + 1, 0));
+  for (int k = 1; k < d; ++k) {
+    int64_t acc = 0;
+    for (int i = 0; i < s; ++i) {
+      S.off[i][k] = acc;
+      acc += r[i][k];
+    }
+    S.R[k] = acc;
+  }
+  for (int k = 0; k < d; ++k)
+    if ((double)S.R[k] * (double)n[k] * (double)S.R[k + 1] > 9.0e15) return set_error("formal sum too large"), TTR_ERR_ARG;
+  return TTR_OK;
+}
+
 static int64_t block_size(int64_t rbar, int64_t block, double frac) {
   int64_t b = block > 0 ? block : (int64_t)ceil((double)rbar * frac - 1e-9);
   return std::max<int64_t>(1, std::min<int64_t>(rbar, b));
@@ -357,27 +414,33 @@ struct Sketch {
   std::vector<BPlanes> wplanes;   // digit planes of W_{k+1}(:, 0:width) made by the first pass (index k)
 };
 
-static int rl_pass(Ctx& c, const Engine& E, const TT& X, uint64_t seed, int64_t col0, int64_t col1, int t,
+static int rl_pass(Ctx& c, const Engine& E, const SumTT& X, uint64_t seed, int64_t col0, int64_t col1, int t,
                    Sketch& s) {
   const int d = X.d;
   const int64_t w = col1 - col0;
   if (w <= 0) return TTR_OK;
   TTR_CHECK(omega_fill(c, seed, t, d, X.n, col0, col1, s.Om + (int64_t)(t - 1) * s.om_stride,
                        s.Omi + (int64_t)(t - 1) * s.om_stride, s.om_stride, s.ldom));
-  // W_d = H(X_d) Omega_d  (r_{d-1} x n_d) (n_d x w)
-  {
-    Gemm g;
-    g.M = X.r[d - 1]; g.N = w; g.K = X.n[d - 1];
-    g.A = X.cores[d - 1]; g.sam = X.n[d - 1]; g.sak = 1;
-    g.B = s.Om + (int64_t)(d - 1) * s.om_stride; g.sbk = s.ldom; g.sbn = 1;
-    g.C = s.W[d - 1] + col0; g.scm = s.ldw; g.scn = 1;
-    TTR_CHECK(E.small_gemm(c, g));
-  }
-  if (col0 == 0) s.wplanes.assign(d + 1, BPlanes{});
-  for (int k = d - 1; k >= t; --k) {
-    TTR_CHECK(E.rl_step(c, X.cores[k - 1], X.r[k - 1], X.n[k - 1], X.r[k], s.W[k] + col0, s.ldw,
-                        s.Om + (int64_t)(k - 1) * s.om_stride, s.Omi + (int64_t)(k - 1) * s.om_stride, s.ldom, w,
-                        s.W[k - 1] + col0, s.ldw, s.T, col0 == 0 ? &s.wplanes[k] : nullptr));
+  // digit planes of W_{k+1} are kept for the sketch only when W is one summand's
+  const bool keep = col0 == 0 && X.single();
+  if (keep) s.wplanes.assign(d + 1, BPlanes{});
+  // each summand with the same Omega, into its own rows of the stacked W_k (Remark 3.3)
+  for (size_t p = 0; p < X.parts.size(); ++p) {
+    const TT& P = X.parts[p];
+    const std::vector<int64_t>& off = X.off[p];
+    {  // W_d = H(X_d) Omega_d  (r_{d-1} x n_d) (n_d x w)
+      Gemm g;
+      g.M = P.r[d - 1]; g.N = w; g.K = X.n[d - 1];
+      g.A = P.cores[d - 1]; g.sam = X.n[d - 1]; g.sak = 1;
+      g.B = s.Om + (int64_t)(d - 1) * s.om_stride; g.sbk = s.ldom; g.sbn = 1;
+      g.C = s.W[d - 1] + off[d - 1] * s.ldw + col0; g.scm = s.ldw; g.scn = 1;
+      TTR_CHECK(E.small_gemm(c, g));
+    }
+    for (int k = d - 1; k >= t; --k) {
+      TTR_CHECK(E.rl_step(c, P.cores[k - 1], P.r[k - 1], X.n[k - 1], P.r[k], s.W[k] + off[k] * s.ldw + col0, s.ldw,
+                          s.Om + (int64_t)(k - 1) * s.om_stride, s.Omi + (int64_t)(k - 1) * s.om_stride, s.ldom, w,
+                          s.W[k - 1] + off[k - 1] * s.ldw + col0, s.ldw, s.T, keep ? &s.wplanes[k] : nullptr));
+    }
   }
   return TTR_OK;
 }
@@ -462,6 +525,7 @@ struct Sweep {
   double* S = nullptr;                 // rows x bcap
   double* P = nullptr;                 // rmax x bcap
   double* M = nullptr;                 // rmax x rmax
+  double* ytmp = nullptr;              // one summand's block of the next core (sums only)
   int64_t bcap = 0;
   QrWork qr;
 };
@@ -491,12 +555,36 @@ static int sweep_alloc(Ctx& c, const TT& X, int64_t bcap, Sweep& s) {
   return TTR_OK;
 }
 
-// M = Q^T Z  (c x cols), then Ynext = M H(X_{k+1})  (c x n r)
+// M = Q^T Z  (c x cols), then Ynext = M H(X_{k+1})  (c x n r).  For a sum of TTs, M splits into
+// the column blocks M^(i) of the summands and the next core is projected summand by summand:
+// M^(i) H(X_{k+1}^(i)) fills the columns of summand i in the right bond of Ynext, and at the last
+// core (shared right bond 1) the summands' products add up (Appendix C).
 static int project_next(Ctx& c, const Engine& E, const Sweep& s, const double* Z, int64_t rows, int64_t cols,
-                        int64_t ccols, const TT& X, int k, double* Ynext) {
+                        int64_t ccols, const SumTT& X, int k, double* Ynext) {
   TTR_CHECK(E.left_project(c, s.Q, s.qcap, Z, rows, cols, ccols, s.M));
-  // H(X_{k+1}) is cols x (n_{k+1} r_{k+2}), row-major
-  return E.project(c, s.M, ccols, cols, X.cores[k], X.n[k] * X.r[k + 1], Ynext);
+  const int64_t nk = X.n[k];
+  if (X.single()) {
+    // H(X_{k+1}) is cols x (n_{k+1} r_{k+2}), row-major
+    return E.project(c, s.M, cols, ccols, cols, X.parts[0].cores[k], nk * X.parts[0].r[k + 1], Ynext);
+  }
+  for (size_t p = 0; p < X.parts.size(); ++p) {
+    const TT& P = X.parts[p];
+    const double* Mp = s.M + X.off[p][k];
+    if (k == X.d - 1) {
+      Gemm g;
+      g.M = ccols; g.N = nk; g.K = P.r[k];
+      g.A = Mp; g.sam = cols; g.sak = 1;
+      g.B = P.cores[k]; g.sbk = nk; g.sbn = 1;
+      g.C = Ynext; g.scm = nk; g.scn = 1;
+      g.beta = p == 0 ? 0.0 : 1.0;
+      TTR_CHECK(E.small_gemm(c, g));
+    } else {
+      const int64_t rn = P.r[k + 1];
+      TTR_CHECK(E.project(c, Mp, cols, ccols, P.r[k], P.cores[k], nk * rn, s.ytmp));
+      TTR_CHECK(copy2d(c, Ynext + X.off[p][k + 1], X.R[k + 1], s.ytmp, rn, ccols * nk, rn));
+    }
+  }
+  return TTR_OK;
 }
 
 // ----------------------------------------------------------------------------- SVD pass (Remark 3.2)
@@ -612,9 +700,10 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   Engine E;
   TTR_CHECK(E.init(c, o.precision, o.slices, 0.0));
   const int d = X.d;
+  const SumTT XS = single_sum(X);
   Sketch s;
   TTR_CHECK(sketch_alloc(c, X, ell, s));
-  TTR_CHECK(rl_pass(c, E, X, seed, 0, ell, 2, s));
+  TTR_CHECK(rl_pass(c, E, XS, seed, 0, ell, 2, s));
   s.width = ell;
   tm.rec(1, stream);
   Sweep w;
@@ -642,7 +731,7 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
     TTR_CHECK(E.sketch(c, g));
     TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, lk, w.qr));
     double* Ynext = w.Y[cur];
-    TTR_CHECK(project_next(c, E, w, Z, rows, cols, lk, X, k, Ynext));
+    TTR_CHECK(project_next(c, E, w, Z, rows, cols, lk, XS, k, Ynext));
     TTR_CHECK(copy2d(c, arena + off, lk, w.Q, w.qcap, rows, lk));
     out->cores[k - 1] = arena + off;
     out->ranks[k] = lk;
@@ -670,10 +759,12 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
 }
 
 // ----------------------------------------------------------------------------- adaptive
-static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed, const ttr_options& o,
-                          cudaStream_t stream, ttr_result* out) {
+// appendix_blocks: the block rule of the sum algorithm in Appendix C when block <= 0 (b_init =
+// max_i r_k^(i), initial sketch width max_{i,k} r_k^(i)) instead of the fractions f_init of Sec. 3.3.
+static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t seed, const ttr_options& o,
+                          cudaStream_t stream, ttr_result* out, bool appendix_blocks = false) {
   if (!(tol > 0.0) || !isfinite(tol)) return set_error("tol must be positive and finite"), TTR_ERR_ARG;
-  if (block <= 0 && !(o.f_init > 0.0 && o.f_init < 1.0 && o.f_inc > 0.0 && o.f_inc < 1.0))
+  if (block <= 0 && !((appendix_blocks || (o.f_init > 0.0 && o.f_init < 1.0)) && o.f_inc > 0.0 && o.f_inc < 1.0))
     return set_error("f_init and f_inc must lie in (0, 1)"), TTR_ERR_ARG;
   Ctx c;
   c.stream = stream;
@@ -682,16 +773,21 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   Timer tm;
   tm.rec(0, stream);
   const int d = X.d;
-  int64_t rmax = 1;
-  for (int k = 1; k < d; ++k) rmax = std::max(rmax, X.r[k]);
-  const int64_t w0 = std::max<int64_t>(1, block > 0 ? block : (int64_t)ceil((double)rmax * o.f_init - 1e-9));
+  int64_t rmax = 1, rpart = 1;
+  for (int k = 1; k < d; ++k) {
+    rmax = std::max(rmax, X.R[k]);
+    rpart = std::max(rpart, X.part_rank_max(k));
+  }
+  const bool appendix = appendix_blocks && block <= 0;
+  const int64_t w0 = std::max<int64_t>(1, block > 0 ? block
+                                                    : appendix ? rpart : (int64_t)ceil((double)rmax * o.f_init - 1e-9));
   const int64_t binc_max = block > 0 ? std::min(block, rmax) : block_size(rmax, 0, o.f_inc);
-  const int64_t binit_max = block > 0 ? std::min(block, rmax) : block_size(rmax, 0, o.f_init);
+  const int64_t binit_max = block > 0 ? std::min(block, rmax) : appendix ? rpart : block_size(rmax, 0, o.f_init);
   const int64_t wcap = std::max(w0, rmax + binc_max);
   Engine E;
   TTR_CHECK(E.init(c, o.precision, o.slices, tol));
   Sketch s;
-  TTR_CHECK(sketch_alloc(c, X, wcap, s));
+  TTR_CHECK(sketch_alloc(c, X.shape(), wcap, s));
   // Columns of W are a prefix of one counter-based stream, so how many are drawn up front (and how
   // the rest are appended) never changes a result; draw one tensor-core tile width up front and
   // grow geometrically, which keeps the number of right-to-left passes small.
@@ -699,6 +795,15 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   if (o.width_hint > 0) wdev = std::min(wcap, std::max(w0, o.width_hint));
   TTR_CHECK(rl_pass(c, E, X, seed, 0, wdev, 2, s));
   s.width = wdev;
+  // V(Y_1): the first core, or for a sum the summands' first cores side by side (Appendix C)
+  const double* Z1 = X.parts[0].cores[0];
+  if (!X.single()) {
+    double* z = nullptr;
+    TTR_CHECK(c.alloc_t(&z, X.n[0] * X.R[1]));
+    for (size_t p = 0; p < X.parts.size(); ++p)
+      TTR_CHECK(copy2d(c, z + X.off[p][1], X.R[1], X.parts[p].cores[0], X.parts[p].r[1], X.n[0], X.parts[p].r[1]));
+    Z1 = z;
+  }
   // norm: given, or Eq. (3.6) with the first w0 columns of W_2
   double* dscal = nullptr;
   TTR_CHECK(c.alloc_t(&dscal, 8));
@@ -708,8 +813,8 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
     double* E1 = nullptr;
     TTR_CHECK(c.alloc_t(&E1, X.n[0] * w0));
     Gemm g;
-    g.M = X.n[0]; g.N = w0; g.K = X.r[1];
-    g.A = X.cores[0]; g.sam = X.r[1]; g.sak = 1;
+    g.M = X.n[0]; g.N = w0; g.K = X.R[1];
+    g.A = Z1; g.sam = X.R[1]; g.sak = 1;
     g.B = s.W[1]; g.sbk = s.ldw; g.sbn = 1;
     g.C = E1; g.scm = w0; g.scn = 1;
     TTR_CHECK(E.small_gemm(c, g));
@@ -723,10 +828,15 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   const double tau = tol * nrmx / sqrt((double)(d - 1));
   tm.rec(1, stream);
   Sweep w;
-  TTR_CHECK(sweep_alloc(c, X, std::max(binc_max, binit_max), w));
-  TTR_CHECK(result_alloc(c, X, out));
+  TTR_CHECK(sweep_alloc(c, X.shape(), std::max(binc_max, binit_max), w));
+  if (!X.single()) {
+    int64_t ymax = 1;
+    for (int k = 1; k < d; ++k) ymax = std::max(ymax, X.n[k] * X.part_rank_max(k + 1));
+    TTR_CHECK(c.alloc_t(&w.ytmp, w.qcap * ymax));
+  }
+  TTR_CHECK(result_alloc(c, X.shape(), out));
   int64_t rowsmax = 1;
-  for (int k = 0; k < d; ++k) rowsmax = std::max(rowsmax, X.r[k] * X.n[k]);
+  for (int k = 0; k < d; ++k) rowsmax = std::max(rowsmax, X.R[k] * X.n[k]);
   double* Sall = nullptr;                       // Z W_{k+1}(:, 0:width): every sketch column of core k
   TTR_CHECK(c.alloc_t(&Sall, rowsmax * wcap));
   struct Probe {
@@ -739,7 +849,7 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   std::vector<int32_t> est_core;
   double* arena = (double*)out->arena;
   int64_t off = 0, lprev = 1;
-  const double* Z = X.cores[0];
+  const double* Z = Z1;
   int cur = 0;
   out->ranks[0] = 1;
   int64_t sk_cols = 0;                          // columns of Sall computed for the current core
@@ -777,9 +887,9 @@ static int round_adaptive(const TT& X, double tol, int64_t block, uint64_t seed,
   std::vector<double> hest((size_t)rmax + 8);
   const bool device_loop = getenv("TTR_HOST_LOOP") == nullptr;
   for (int k = 1; k < d; ++k) {
-    const int64_t rows = lprev * X.n[k - 1], cols = X.r[k];
+    const int64_t rows = lprev * X.n[k - 1], cols = X.R[k];
     const int64_t rbar = std::min(rows, cols);
-    const int64_t b0 = block_size(rbar, block, o.f_init);
+    const int64_t b0 = appendix ? std::min(rbar, X.part_rank_max(k)) : block_size(rbar, block, o.f_init);
     const int64_t bi = block_size(rbar, block, o.f_inc);
     sk_cols = 0;
     TTR_CHECK(ensure(k, std::min(rbar, b0) + bi, rows, cols));
@@ -1155,7 +1265,20 @@ int tt_round_adaptive(int32_t d, const int64_t* n, const int64_t* r, const doubl
   if (opts) o = *opts; else ttr_default_options(&o);
   TT X{d, n, r, cores};
   int st = validate(X);
-  if (st == TTR_OK) st = round_adaptive(X, tol, block, seed, o, (cudaStream_t)stream, out);
+  if (st == TTR_OK) st = round_adaptive(single_sum(X), tol, block, seed, o, (cudaStream_t)stream, out);
+  return finish(st, out, (cudaStream_t)stream);
+}
+
+int tt_round_adaptive_sum(int32_t s, int32_t d, const int64_t* n, const int64_t* const* r,
+                          const double* const* const* cores, double tol, int64_t block, uint64_t seed,
+                          const ttr_options* opts, void* stream, ttr_result* out) {
+  if (!out) return set_error("out must be non-null"), TTR_ERR_ARG;
+  result_zero(out);
+  ttr_options o;
+  if (opts) o = *opts; else ttr_default_options(&o);
+  SumTT X;
+  int st = make_sum(s, d, n, r, cores, X);
+  if (st == TTR_OK) st = round_adaptive(X, tol, block, seed, o, (cudaStream_t)stream, out, true);
   return finish(st, out, (cudaStream_t)stream);
 }
 
@@ -1223,7 +1346,7 @@ int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r, cons
   TTR_CHECK(sketch_alloc(c, X, w, s));
   for (int k = t; k <= d; ++k) s.W[k - 1] = W[k - 1] - col0;   // caller buffers: [a][j - col0], ld w
   s.ldw = w;
-  TTR_CHECK(rl_pass(c, E, X, seed, col0, col1, t, s));
+  TTR_CHECK(rl_pass(c, E, single_sum(X), seed, col0, col1, t, s));
   cudaError_t e = cudaStreamSynchronize(c.stream);
   if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
   return check_device_flags(c);

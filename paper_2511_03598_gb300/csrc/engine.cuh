@@ -111,15 +111,16 @@ struct Engine {
     return omega_reduce(c, T, w, Om, ldom, r0, n, w, Wout, ldwo);
   }
 
-  // Y = M H(X_{k+1}):  (L x K)(K x ncol), all row-major
-  int project(Ctx& c, const double* Mk, int64_t L, int64_t K, const double* Xn, int64_t ncol, double* Y) const {
+  // Y = M H(X_{k+1}):  (L x K)(K x ncol), all row-major; M has leading dimension ldm >= K
+  int project(Ctx& c, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn, int64_t ncol,
+              double* Y) const {
     if (precision == TTR_PREC_SLICED) {
-      int st = tc_project(c, slices, Mk, K, L, K, Xn, ncol, Y);
+      int st = tc_project(c, slices, Mk, ldm, L, K, Xn, ncol, Y);
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
     Gemm g;
     g.M = L; g.N = ncol; g.K = K;
-    g.A = Mk; g.sam = K; g.sak = 1;
+    g.A = Mk; g.sam = ldm; g.sak = 1;
     g.B = Xn; g.sbk = ncol; g.sbn = 1;
     g.C = Y; g.scm = ncol; g.scn = 1;
     return gemm_f64(c, g);

@@ -69,3 +69,24 @@ def test_argument_errors_are_reported_not_raised_on_host(libpath):
     p_bad = (ctypes.c_void_p * 2)(8, 12)       # misaligned core pointer
     st = L.tt_round_deterministic(2, n, r2, p_bad, 1e-6, None, ctypes.byref(res))
     assert st == 1
+
+
+def test_sum_argument_errors_on_host(libpath):
+    """tt_round_adaptive_sum checks the summand count and every summand before any device work."""
+    from paper_2511_03598_gb300 import binding as B
+    L = B.lib()
+    res = B.Result()
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    n = (ctypes.c_int64 * 2)(3, 3)
+    good = (ctypes.c_int64 * 3)(1, 2, 1)
+    bad = (ctypes.c_int64 * 3)(1, 2, 2)            # r[d] != 1
+    p = (ctypes.c_void_p * 2)(8, 16)
+    rs = (P64 * 2)(ctypes.cast(good, P64), ctypes.cast(bad, P64))
+    ps = (PP * 2)(ctypes.cast(p, PP), ctypes.cast(p, PP))
+    st = L.tt_round_adaptive_sum(0, 2, n, rs, ps, 1e-6, 1, ctypes.c_uint64(1), None, None, ctypes.byref(res))
+    assert st == 1 and b"summands" in L.ttr_last_error()
+    st = L.tt_round_adaptive_sum(2, 2, n, rs, ps, 1e-6, 1, ctypes.c_uint64(1), None, None, ctypes.byref(res))
+    assert st == 1 and b"r[d]" in L.ttr_last_error()
+    st = L.tt_round_adaptive_sum(1, 2, n, rs, ps, 0.0, 1, ctypes.c_uint64(1), None, None, ctypes.byref(res))
+    assert st == 1 and res.status == 1

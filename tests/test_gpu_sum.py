@@ -1,0 +1,124 @@
+"""GPU parity of the rounding of a sum of TTs (tt_round_adaptive_sum, Remark 3.3 / Appendix C)
+against the oracle's sum algorithm on the same seeded inputs.
+
+Bars as for the single-TT adaptive rounding: FP64 form identical ranks, represented tensors within
+1e-10 relative, estimates within 1e-8 relative; sliced form identical ranks and the stated
+contraction-error bounds of the full-size test in test_gpu_parity.py.  Summands that share core
+arrays on the host share device buffers too, as a caller holding scaled copies would pass them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as WL
+from oracle import rounding as R
+from oracle import tt as T
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2511_03598_gb300 import build
+    build.build()
+    from paper_2511_03598_gb300 import binding
+    assert torch.cuda.is_available()
+    return binding
+
+
+def dev_summands(summands):
+    cache = {}
+    out = []
+    for x in summands:
+        cs = []
+        for c in x:
+            if id(c) not in cache:
+                cache[id(c)] = torch.from_numpy(np.ascontiguousarray(c)).to("cuda")
+            cs.append(cache[id(c)])
+        out.append(cs)
+    return out
+
+
+def rel(a, b):
+    return T.tt_dist(a, b) / max(T.tt_norm(b), 1e-300)
+
+
+def mixed_summands(seed):
+    rng = np.random.default_rng(seed)
+    n = [3, 4, 5, 4, 3]
+    xs = [WL.random_tt(rng, 5, n, r) for r in ([2, 3, 4, 2], [1, 2, 2, 3], [3, 3, 1, 2])]
+    for x, c in zip(xs, (1.0, -0.6, 0.3)):
+        x[0] = x[0] * c
+    return xs
+
+
+@pytest.mark.parametrize("block", [2, 0])
+def test_sum_c1_fp64(B, block):
+    x = WL.c1()
+    ref, info = R.tt_round_adaptive_sum(x.summands, 1e-6, 2024, block=block, nrmx=x.norm)
+    with B.round_adaptive_sum(dev_summands(x.summands), 1e-6, block, 2024, B.options(nrmx=x.norm)) as y:
+        yi = y.info
+        got = y.to_numpy()
+    assert yi["ranks"] == info["ranks"]
+    flat = [e for es in info["estimates"] for e in es]
+    np.testing.assert_allclose(yi["estimates"], flat, rtol=1e-8, atol=1e-14 * x.norm)
+    assert rel(got, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("given_norm", [True, False])
+def test_sum_mixed_ranks(B, prec, given_norm):
+    xs = mixed_summands(8)
+    nrmx = T.tt_norm(WL.block_sum([(1.0, x) for x in xs])) if given_norm else None
+    ref, info = R.tt_round_adaptive_sum(xs, 1e-3, 17, block=0, f_inc=0.2, nrmx=nrmx)
+    opts = B.options(precision=prec, slices=8, f_inc=0.2, nrmx=nrmx or 0.0)
+    with B.round_adaptive_sum(dev_summands(xs), 1e-3, 0, 17, opts) as y:
+        yi = y.info
+        got = y.to_numpy()
+    assert yi["ranks"] == info["ranks"]
+    assert math.isclose(yi["tau"], info["tau"], rel_tol=1e-10 if prec == 0 else 1e-9)
+    assert rel(got, ref) <= (1e-10 if prec == 0 else 1e-9)
+
+
+def test_sum_single_summand_equals_adaptive(B):
+    x = WL.random_tt(np.random.default_rng(5), 6, 7, 9)
+    opts = B.options(nrmx=T.tt_norm(x))
+    with B.round_adaptive_sum(dev_summands([x]), 1e-2, 3, 9, opts) as y:
+        ys = y.to_numpy()
+        rs = y.info["ranks"]
+    with B.round_adaptive([torch.from_numpy(c).to("cuda") for c in x], 1e-2, 3, 9, opts) as y:
+        yf = y.to_numpy()
+        rf = y.info["ranks"]
+    assert rs == rf
+    assert rel(ys, yf) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sum_c2_full_size(B, prec):
+    """The d=20, n=50 workload as its 5 summands (4 scaled copies of a rank-50 TT sharing their
+    cores after the first, and the rank-10 noise TT), tol 1e-6, block 10: the same ranks as the
+    oracle's sum algorithm and as the formal-sum rounding on the GPU; tensors within the bars of
+    the formal-sum tests (FP64 1e-10, sliced 1e-8)."""
+    x = WL.c2()
+    ref, info = R.tt_round_adaptive_sum(x.summands, 1e-6, 2024, block=10, nrmx=x.norm)
+    opts = B.options(precision=prec, nrmx=x.norm)
+    with B.round_adaptive_sum(dev_summands(x.summands), 1e-6, 10, 2024, opts) as y:
+        yi = y.info
+        got = y.to_numpy()
+    assert yi["ranks"] == info["ranks"]
+    assert rel(got, ref) <= (1e-10 if prec == 0 else 1e-8)
+    assert T.tt_dist(got, x.cores) <= 1e-6 * x.norm
+    with B.round_adaptive([torch.from_numpy(c).to("cuda") for c in x.cores], 1e-6, 10, 2024, opts) as y:
+        assert y.info["ranks"] == yi["ranks"]
+
+
+def test_sum_argument_errors(B):
+    xs = mixed_summands(1)
+    with pytest.raises(ValueError):
+        B.round_adaptive_sum([], 1e-3, 1, 1)
+    bad = [xs[0], xs[1][:4]]
+    with pytest.raises(ValueError):
+        B.round_adaptive_sum(dev_summands(bad), 1e-3, 1, 1)
