@@ -421,25 +421,48 @@ static int rl_pass(Ctx& c, const Engine& E, const SumTT& X, uint64_t seed, int64
   if (w <= 0) return TTR_OK;
   TTR_CHECK(omega_fill(c, seed, t, d, X.n, col0, col1, s.Om + (int64_t)(t - 1) * s.om_stride,
                        s.Omi + (int64_t)(t - 1) * s.om_stride, s.om_stride, s.ldom));
-  // digit planes of W_{k+1} are kept for the sketch only when W is one summand's
-  const bool keep = col0 == 0 && X.single();
+  // digit planes of W_{k+1} (all summands' rows) are kept for the sketch
+  const bool keep = col0 == 0;
   if (keep) s.wplanes.assign(d + 1, BPlanes{});
   // each summand with the same Omega, into its own rows of the stacked W_k (Remark 3.3)
-  for (size_t p = 0; p < X.parts.size(); ++p) {
-    const TT& P = X.parts[p];
-    const std::vector<int64_t>& off = X.off[p];
-    {  // W_d = H(X_d) Omega_d  (r_{d-1} x n_d) (n_d x w)
-      Gemm g;
-      g.M = P.r[d - 1]; g.N = w; g.K = X.n[d - 1];
-      g.A = P.cores[d - 1]; g.sam = X.n[d - 1]; g.sak = 1;
-      g.B = s.Om + (int64_t)(d - 1) * s.om_stride; g.sbk = s.ldom; g.sbn = 1;
-      g.C = s.W[d - 1] + off[d - 1] * s.ldw + col0; g.scm = s.ldw; g.scn = 1;
-      TTR_CHECK(E.small_gemm(c, g));
+  const int ns = (int)X.parts.size();
+  for (int p0 = 0; p0 < ns; p0 += kMaxGroup) {   // W_d = H(X_d) Omega_d  (r_{d-1} x n_d) (n_d x w)
+    const int ng = std::min(kMaxGroup, ns - p0);
+    const double* A[kMaxGroup];
+    int64_t M[kMaxGroup];
+    double* C[kMaxGroup];
+    for (int g = 0; g < ng; ++g) {
+      A[g] = X.parts[p0 + g].cores[d - 1];
+      M[g] = X.parts[p0 + g].r[d - 1];
+      C[g] = s.W[d - 1] + X.off[p0 + g][d - 1] * s.ldw + col0;
     }
-    for (int k = d - 1; k >= t; --k) {
-      TTR_CHECK(E.rl_step(c, P.cores[k - 1], P.r[k - 1], X.n[k - 1], P.r[k], s.W[k] + off[k] * s.ldw + col0, s.ldw,
-                          s.Om + (int64_t)(k - 1) * s.om_stride, s.Omi + (int64_t)(k - 1) * s.om_stride, s.ldom, w,
-                          s.W[k - 1] + off[k - 1] * s.ldw + col0, s.ldw, s.T, keep ? &s.wplanes[k] : nullptr));
+    TTR_CHECK(E.last_core_group(c, ng, A, M, X.n[d - 1], s.Om + (int64_t)(d - 1) * s.om_stride, s.ldom, w, C, s.ldw));
+  }
+  for (int k = d - 1; k >= t; --k) {
+    const double* Om = s.Om + (int64_t)(k - 1) * s.om_stride;
+    const int* Omi = s.Omi + (int64_t)(k - 1) * s.om_stride;
+    if (X.single()) {
+      const TT& P = X.parts[0];
+      TTR_CHECK(E.rl_step(c, P.cores[k - 1], P.r[k - 1], X.n[k - 1], P.r[k], s.W[k] + col0, s.ldw, Om, Omi, s.ldom, w,
+                          s.W[k - 1] + col0, s.ldw, s.T, keep ? &s.wplanes[k] : nullptr));
+      continue;
+    }
+    // the summands of one core, kMaxGroup per launch
+    for (int p0 = 0; p0 < ns; p0 += kMaxGroup) {
+      const int ng = std::min(kMaxGroup, ns - p0);
+      const double* Xk[kMaxGroup];
+      int64_t r0[kMaxGroup], r1[kMaxGroup], offn[kMaxGroup], offo[kMaxGroup];
+      for (int g = 0; g < ng; ++g) {
+        const TT& P = X.parts[p0 + g];
+        Xk[g] = P.cores[k - 1];
+        r0[g] = P.r[k - 1];
+        r1[g] = P.r[k];
+        offn[g] = X.off[p0 + g][k];
+        offo[g] = X.off[p0 + g][k - 1];
+      }
+      // planes are kept when one launch takes every summand (they then cover all rows of W_{k+1})
+      TTR_CHECK(E.rl_step_group(c, ng, Xk, r0, X.n[k - 1], r1, s.W[k] + col0, s.ldw, X.R[k], offn, Om, Omi, s.ldom,
+                                w, s.W[k - 1] + col0, s.ldw, offo, s.T, keep && ns <= kMaxGroup ? &s.wplanes[k] : nullptr));
     }
   }
   return TTR_OK;
@@ -559,15 +582,20 @@ static int sweep_alloc(Ctx& c, const TT& X, int64_t bcap, Sweep& s) {
 // the column blocks M^(i) of the summands and the next core is projected summand by summand:
 // M^(i) H(X_{k+1}^(i)) fills the columns of summand i in the right bond of Ynext, and at the last
 // core (shared right bond 1) the summands' products add up (Appendix C).
+// Zd: for a sum, the summands' last cores stacked (R_{d-1} x n_d, the formal sum's last core)
 static int project_next(Ctx& c, const Engine& E, const Sweep& s, const double* Z, int64_t rows, int64_t cols,
-                        int64_t ccols, const SumTT& X, int k, double* Ynext) {
+                        int64_t ccols, const SumTT& X, int k, double* Ynext, const double* Zd = nullptr) {
   TTR_CHECK(E.left_project(c, s.Q, s.qcap, Z, rows, cols, ccols, s.M));
   const int64_t nk = X.n[k];
   if (X.single()) {
     // H(X_{k+1}) is cols x (n_{k+1} r_{k+2}), row-major
     return E.project(c, s.M, cols, ccols, cols, X.parts[0].cores[k], nk * X.parts[0].r[k + 1], Ynext);
   }
-  for (size_t p = 0; p < X.parts.size(); ++p) {
+  if (k == X.d - 1 && Zd) return E.project(c, s.M, cols, ccols, cols, Zd, nk, Ynext);   // H(Y_d) = M H(X_d)
+  const int ns = (int)X.parts.size();
+  // one summand: M^(p) H(X_{k+1}^(p)) through a scratch block into its columns of Ynext, or at the
+  // last core added into Ynext
+  auto one = [&](int p) -> int {
     const TT& P = X.parts[p];
     const double* Mp = s.M + X.off[p][k];
     if (k == X.d - 1) {
@@ -577,12 +605,33 @@ static int project_next(Ctx& c, const Engine& E, const Sweep& s, const double* Z
       g.B = P.cores[k]; g.sbk = nk; g.sbn = 1;
       g.C = Ynext; g.scm = nk; g.scn = 1;
       g.beta = p == 0 ? 0.0 : 1.0;
-      TTR_CHECK(E.small_gemm(c, g));
-    } else {
-      const int64_t rn = P.r[k + 1];
-      TTR_CHECK(E.project(c, Mp, cols, ccols, P.r[k], P.cores[k], nk * rn, s.ytmp));
-      TTR_CHECK(copy2d(c, Ynext + X.off[p][k + 1], X.R[k + 1], s.ytmp, rn, ccols * nk, rn));
+      return E.small_gemm(c, g);
     }
+    const int64_t rn = P.r[k + 1];
+    TTR_CHECK(E.project(c, Mp, cols, ccols, P.r[k], P.cores[k], nk * rn, s.ytmp));
+    return copy2d(c, Ynext + X.off[p][k + 1], X.R[k + 1], s.ytmp, rn, ccols * nk, rn);
+  };
+  for (int p0 = 0; p0 < ns; p0 += kMaxGroup) {
+    const int ng = std::min(kMaxGroup, ns - p0);
+    if (k < X.d - 1) {
+      // the chunk's blocks of the next core in one launch, straight into Ynext
+      const double* Xn[kMaxGroup];
+      int64_t koff[kMaxGroup], K[kMaxGroup], rn[kMaxGroup], yoff[kMaxGroup];
+      for (int g = 0; g < ng; ++g) {
+        const TT& P = X.parts[p0 + g];
+        Xn[g] = P.cores[k];
+        koff[g] = X.off[p0 + g][k];
+        K[g] = P.r[k];
+        rn[g] = P.r[k + 1];
+        yoff[g] = X.off[p0 + g][k + 1];
+      }
+      const int st = E.project_group(c, ng, s.M, cols, ccols, cols, koff, K, Xn, nk, rn, Ynext, X.R[k + 1], yoff);
+      if (st != TTR_ERR_UNSUPPORTED) {
+        TTR_CHECK(st);
+        continue;
+      }
+    }
+    for (int g = 0; g < ng; ++g) TTR_CHECK(one(p0 + g));
   }
   return TTR_OK;
 }
@@ -804,6 +853,14 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
       TTR_CHECK(copy2d(c, z + X.off[p][1], X.R[1], X.parts[p].cores[0], X.parts[p].r[1], X.n[0], X.parts[p].r[1]));
     Z1 = z;
   }
+  // for a sum, the last cores stacked: the formal sum's last core, projected in one product
+  double* Zd = nullptr;
+  if (!X.single()) {
+    TTR_CHECK(c.alloc_t(&Zd, X.R[d - 1] * X.n[d - 1]));
+    for (size_t p = 0; p < X.parts.size(); ++p)
+      TTR_CUDA(cudaMemcpyAsync(Zd + X.off[p][d - 1] * X.n[d - 1], X.parts[p].cores[d - 1],
+                               sizeof(double) * X.parts[p].r[d - 1] * X.n[d - 1], cudaMemcpyDeviceToDevice, stream));
+  }
   // norm: given, or Eq. (3.6) with the first w0 columns of W_2
   double* dscal = nullptr;
   TTR_CHECK(c.alloc_t(&dscal, 8));
@@ -994,7 +1051,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
     }
     }
     double* Ynext = w.Y[cur];
-    TTR_CHECK(project_next(c, E, w, Z, rows, cols, cc, X, k, Ynext));
+    TTR_CHECK(project_next(c, E, w, Z, rows, cols, cc, X, k, Ynext, Zd));
     TTR_CHECK(copy2d(c, arena + off, cc, w.Q, w.qcap, rows, cc));
     out->cores[k - 1] = arena + off;
     out->ranks[k] = cc;

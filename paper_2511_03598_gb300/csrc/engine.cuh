@@ -23,6 +23,21 @@ struct BPlanes {
 int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn,
                int64_t ldw, const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo,
                BPlanes* keep = nullptr);
+// The partial-contraction step of one core for up to kMaxGroup summands in one launch: summand g
+// reads rows off_n[g].. of the stacked W_{k+1} (Kall rows) and writes rows off_out[g].. of the
+// stacked W_k.  `keep`: the digit planes of the stacked W_{k+1}, for the sketch.
+constexpr int kMaxGroup = 8;
+int tc_rl_step_grouped(Ctx& c, int slices, int ng, const double* const* Xk, const int64_t* r0, int64_t n,
+                       const int64_t* r1, const double* Wn, int64_t ldw, int64_t Kall, const int64_t* off_n,
+                       const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo, const int64_t* off_out,
+                       BPlanes* keep);
+// C_g = A_g B for up to kMaxGroup row-major A_g sharing one row-major B, in one launch.
+int tc_gemm_shared_b(Ctx& c, int slices, int ng, const double* const* A, const int64_t* M, const int64_t* lda,
+                     int64_t K, const double* B, int64_t ldb, int64_t N, double* const* C, int64_t ldc);
+// The next-core projections of up to kMaxGroup summands in one launch (see Engine::project_group).
+int tc_project_grouped(Ctx& c, int slices, int ng, const double* M, int64_t ldm, int64_t L, int64_t Kall,
+                       const int64_t* koff, const int64_t* K, const double* const* Xn, const int64_t* ncol,
+                       const int64_t* rn, double* Y, int64_t ldy, int64_t rstride, const int64_t* yoff);
 int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int64_t a_cols, const double* Y,
                int64_t ldy, int64_t b_cols, double* C, int64_t scm, int64_t scn);
 int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
@@ -111,6 +126,44 @@ struct Engine {
     return omega_reduce(c, T, w, Om, ldom, r0, n, w, Wout, ldwo);
   }
 
+  // W_d = H(X_d) Omega_d for ng <= kMaxGroup summands (A[g]: r_{d-1} x n_d row-major, rows M[g]) sharing
+  // Omega_d (n_d x w, leading dimension ldo), into C[g] (leading dimension ldc)
+  int last_core_group(Ctx& c, int ng, const double* const* A, const int64_t* M, int64_t n, const double* Om,
+                      int64_t ldo, int64_t w, double* const* C, int64_t ldc) const {
+    if (precision == TTR_PREC_SLICED) {
+      int64_t lda[kMaxGroup];
+      for (int g = 0; g < ng; ++g) lda[g] = n;
+      int st = tc_gemm_shared_b(c, slices, ng, A, M, lda, n, Om, ldo, w, C, ldc);
+      if (st != TTR_ERR_UNSUPPORTED) return st;
+    }
+    for (int g = 0; g < ng; ++g) {
+      Gemm q;
+      q.M = M[g]; q.N = w; q.K = n;
+      q.A = A[g]; q.sam = n; q.sak = 1;
+      q.B = Om; q.sbk = ldo; q.sbn = 1;
+      q.C = C[g]; q.scm = ldc; q.scn = 1;
+      TTR_CHECK(gemm_f64(c, q));
+    }
+    return TTR_OK;
+  }
+
+  // rl_step for ng <= kMaxGroup summands of a sum of TTs at once (rows off_n[g] of the stacked W_{k+1},
+  // rows off_out[g] of the stacked W_k); one summand at a time where the grouped kernel does not apply
+  int rl_step_group(Ctx& c, int ng, const double* const* Xk, const int64_t* r0, int64_t n, const int64_t* r1,
+                    const double* Wn, int64_t ldw, int64_t Kall, const int64_t* off_n, const double* Om,
+                    const int* Omi, int64_t ldom, int64_t w, double* Wout, int64_t ldwo, const int64_t* off_out,
+                    double* T, BPlanes* keep = nullptr) const {
+    if (precision == TTR_PREC_SLICED) {
+      int st = tc_rl_step_grouped(c, slices, ng, Xk, r0, n, r1, Wn, ldw, Kall, off_n, Omi, ldom, w, Wout, ldwo,
+                                  off_out, keep);
+      if (st != TTR_ERR_UNSUPPORTED) return st;
+    }
+    for (int g = 0; g < ng; ++g)
+      TTR_CHECK(rl_step(c, Xk[g], r0[g], n, r1[g], Wn + off_n[g] * ldw, ldw, Om, Omi, ldom, w,
+                        Wout + off_out[g] * ldwo, ldwo, T));
+    return TTR_OK;
+  }
+
   // Y = M H(X_{k+1}):  (L x K)(K x ncol), all row-major; M has leading dimension ldm >= K
   int project(Ctx& c, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn, int64_t ncol,
               double* Y) const {
@@ -159,6 +212,18 @@ struct Engine {
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
     return gram_tn(c, Q, ldq, Z, cols, rows, ccols, cols, M, cols);
+  }
+
+  // Next core of a sum of TTs, ng <= kMaxGroup summands at once: for summand g, the L x (n r_g) product
+  // M(:, koff[g]:koff[g]+K[g]) H(X^(g)) goes to Ynext(a, i, yoff[g] + c), Ynext being L x n x R row-major.
+  // Returns TTR_ERR_UNSUPPORTED when the grouped kernel does not apply (the caller goes summand by summand).
+  int project_group(Ctx& c, int ng, const double* M, int64_t ldm, int64_t L, int64_t Kall, const int64_t* koff,
+                    const int64_t* K, const double* const* Xn, int64_t n, const int64_t* rn, double* Ynext, int64_t R,
+                    const int64_t* yoff) const {
+    if (precision != TTR_PREC_SLICED) return TTR_ERR_UNSUPPORTED;
+    int64_t ncol[kMaxGroup];
+    for (int g = 0; g < ng; ++g) ncol[g] = n * rn[g];
+    return tc_project_grouped(c, slices, ng, M, ldm, L, Kall, koff, K, Xn, ncol, rn, Ynext, n * R, R, yoff);
   }
 
   int transpose(Ctx& c, const double* A, int64_t rows, int64_t cols, double* out) const {

@@ -79,6 +79,31 @@ struct Args {
   int kseg;                           // K per CTA (multiple of KC, <= KSEG); blockIdx.z selects the segment
   int* err;
   unsigned long long* prof;           // optional phase cycles of CTA (0, 0, 0) (launch-timeline profiling)
+  // plain mode: output row m lands at row (m / rp) * rstride + m % rp of C (rp = 0: at row m), which
+  // places the columns (i, c) of one summand's block of H(Y_{k+1}) inside the stacked right bond
+  int64_t rp, rstride;
+};
+
+// Up to MAXG independent products of one grouped launch (the summands of a sum of TTs): each
+// group has its own A, K, rows and output, and its own rows koff .. koff + K - 1 of one stacked B
+// operand.  A group reads the B chunks that hold its rows and places its A columns at the same
+// positions (shifted by koff % KC); the rows of other groups in a shared boundary chunk meet zero
+// A digits.
+constexpr int MAXG = 8;
+static_assert(MAXG == kMaxGroup, "group table size");
+struct Groups {
+  int n;                      // 0: one product, described by Args alone
+  int tile0[MAXG + 1];        // first blockIdx.x of each group (tile0[n] = gridDim.x)
+  const double* A[MAXG];
+  int64_t M[MAXG];            // rows (plain mode; slabs * nmode in partial-contraction mode)
+  int64_t K[MAXG];
+  int64_t sam[MAXG], sak[MAXG];
+  int64_t slabs[MAXG];        // partial-contraction mode: r_{k-1} of the group
+  int64_t koff[MAXG];         // first row of the group in the stacked B
+  double* C[MAXG];            // plain mode output (strides scm, scn of the group)
+  int64_t scm[MAXG], scn[MAXG];
+  double* W[MAXG];            // partial-contraction mode output rows (leading dimension Args::ldw)
+  int64_t rp[MAXG];           // plain mode output row blocks (Args::rp), stride Args::rstride
 };
 
 // phases of one CTA, timed by thread 0 (setup, row scan, producers' chunk loop, waiting for the
@@ -246,9 +271,31 @@ __device__ __forceinline__ void issue_chunk(uint64_t da0, uint64_t db0, uint32_t
   }
 }
 
-template <int MODE, bool AKFAST>
-__global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
+// 17 warps: one SM sub-partition holds 5 of them, so its 16K registers cap a thread at 96.
+template <int MODE, bool AKFAST, bool GROUPED>
+__global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Groups gr) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  // this CTA's product: the launch's, or that of its group (tiles numbered within the group)
+  Args a = a0;
+  int64_t bx = blockIdx.x;
+  int kcb = 0;          // first B chunk of this CTA's product
+  int ksh = 0;          // position of its first K column within that chunk
+  if (GROUPED) {
+    int g = 0;
+#pragma unroll
+    for (int q = 1; q < MAXG; ++q)
+      if (q < gr.n && (int)blockIdx.x >= gr.tile0[q]) g = q;
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q) {
+      if (q == g) {
+        a.A = gr.A[q]; a.M = gr.M[q]; a.K = gr.K[q]; a.sam = gr.sam[q]; a.sak = gr.sak[q];
+        a.slabs = gr.slabs[q]; a.C = gr.C[q]; a.scm = gr.scm[q]; a.scn = gr.scn[q]; a.W = gr.W[q]; a.rp = gr.rp[q];
+        kcb = (int)(gr.koff[q] / KC);
+        ksh = (int)(gr.koff[q] % KC);
+        bx -= gr.tile0[q];
+      }
+    }
+  }
   __shared__ uint32_t tmem_slot;
   __shared__ __align__(8) uint64_t full[2];    // digit buffer b filled (NP producer arrivals)
   __shared__ __align__(8) uint64_t empty[2];   // MMAs reading digit buffer b done (tcgen05.commit)
@@ -259,18 +306,18 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
   const int nc = blockIdx.y;
   const int64_t kseg0 = (int64_t)blockIdx.z * a.kseg;
   const int kseg_len = (int)(a.K - kseg0 < (int64_t)a.kseg ? a.K - kseg0 : (int64_t)a.kseg);
-  const int nchunk = (kseg_len + KC - 1) / KC;
+  const int nchunk = (ksh + kseg_len + KC - 1) / KC;
   const int kc0 = (int)(kseg0 / KC);
   // rows of this tile
   int64_t m0;
   int rows;
   if (MODE == RLM) {
-    const int64_t a0 = (int64_t)blockIdx.x * a.g;
-    const int64_t na = (a.slabs - a0 < (int64_t)a.g) ? a.slabs - a0 : (int64_t)a.g;
-    m0 = a0 * a.nmode;
+    const int64_t s0 = bx * a.g;
+    const int64_t na = (a.slabs - s0 < (int64_t)a.g) ? a.slabs - s0 : (int64_t)a.g;
+    m0 = s0 * a.nmode;
     rows = (int)(na * a.nmode);
   } else {
-    m0 = (int64_t)blockIdx.x * TM;
+    m0 = bx * TM;
     rows = (int)(a.M - m0 < (int64_t)TM ? a.M - m0 : (int64_t)TM);
   }
   const int tn = a.tn;
@@ -410,11 +457,14 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
     auto load_chunk = [&](int c, double (&v)[TASKS][8]) {
 #pragma unroll
       for (int i = 0; i < TASKS; ++i) {
-        const double* src = a.A + (m0 + trow[i]) * a.sam + (kseg0 + c * KC + tgrp[i] * 8) * a.sak;
-        const int klim = kseg_len - (c * KC + tgrp[i] * 8);
+        const int kb = c * KC + tgrp[i] * 8 - ksh;        // K column of the task's first value (< 0 only
+                                                          // in a grouped launch's first chunk)
+        const double* src = a.A + (m0 + trow[i]) * a.sam + (kseg0 + kb) * a.sak;
+        const int klim = kseg_len - kb;
         const bool rok = trow[i] < rows;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[i][q] = (rok && q < klim) ? __ldcg(src + q * a.sak) : 0.0;
+        for (int q = 0; q < 8; ++q)
+          v[i][q] = (rok && q < klim && (!GROUPED || q >= -kb)) ? __ldcg(src + q * a.sak) : 0.0;
       }
     };
     double vc[TASKS][8];
@@ -428,7 +478,7 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
       if (tid == 0) {
         // B digit planes of this chunk (s * tn * 64 contiguous bytes, 16-byte aligned at both ends):
         // one bulk async copy that completes on full[b]
-        const uint4* src = a.Bp + ((size_t)nc * a.kchunks + (kc0 + c)) * (size_t)s * (plane_b / 8);
+        const uint4* src = a.Bp + ((size_t)nc * a.kchunks + (kcb + kc0 + c)) * (size_t)s * (plane_b / 8);
         const uint32_t bytes = (uint32_t)(s * plane_b * 2);
         asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])), "r"(bytes)
                      : "memory");
@@ -446,7 +496,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
         // the digits this buffer held two chunks ago: those meet zero B digits (k >= K) or land in
         // accumulator rows the epilogue drops.  Chunks 0 and 1 write every position, so no
         // uninitialised shared memory ever reaches the tensor cores.
-        if (c >= 2 && (row >= rows || c * KC + grp * 8 >= kseg_len)) continue;
+        // (A grouped launch writes every position: its B chunks may hold other groups' rows.)
+        if (!GROUPED && c >= 2 && (row >= rows || c * KC + grp * 8 >= kseg_len)) continue;
         const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
         store_digits_s(s, vc[i], rowE[row], Ap, PLANE_A, idx);
       }
@@ -515,13 +566,19 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
         if (MODE != RLM) {
           if (row < rows) {
             const int e_row = rowE[row];
+            const int64_t mrow = m0 + row;
+            int64_t maddr = mrow;
+            if (GROUPED && a.rp > 0) {   // rows < 2^31 (checked by the host)
+              const uint32_t q = (uint32_t)mrow / (uint32_t)a.rp;
+              maddr = (int64_t)q * a.rstride + ((uint32_t)mrow - q * (uint32_t)a.rp);
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int64_t n = n0 + j;
               if (n < a.N) {
                 const int X = e_row + max(1, a.Fmax[n]) - 2044 - 7 * s - 7;
                 const double out = v64 ? i64_to_double(Vh[j] * (1LL << 35) + Vl[j], X) : i128_to_double(V[j], X);
-                double* cp = a.C + (m0 + row) * a.scm + n * a.scn;
+                double* cp = a.C + maddr * a.scm + n * a.scn;
                 if (MODE == ATOMIC) atomicAdd(cp, out);
                 else *cp = out;
               }
@@ -552,7 +609,7 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(Args a) {
             acc += P[r * PB + (j ^ (r & 7))];
           }
           const int e_slab = rowE[sl * (int)a.nmode];
-          const int64_t aidx = (int64_t)blockIdx.x * a.g + sl;
+          const int64_t aidx = bx * a.g + sl;
           const double out = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
           if (a.watomic) atomicAdd(a.W + aidx * a.ldw + n, out);
           else a.W[aidx * a.ldw + n] = out;
@@ -729,8 +786,10 @@ static size_t smem_bytes(int s, int tn, int mode) {
 }
 
 template <int MODE, bool AKFAST>
-static int launch(Ctx& c, const Args& a_in, dim3 grid, const char* name) {
+static int launch(Ctx& c, const Args& a_in, dim3 grid, const char* name, const Groups* groups = nullptr) {
   Args a = a_in;
+  Groups gr{};
+  if (groups) gr = *groups;
   if (c.profiling) {
     if (!c.tc_prof) {
       TTR_CHECK(c.alloc_t(&c.tc_prof, 3 * TP_COUNT));
@@ -739,24 +798,25 @@ static int launch(Ctx& c, const Args& a_in, dim3 grid, const char* name) {
     a.prof = c.tc_prof;
   }
   const size_t sm = smem_bytes(a.s, a.tn, MODE);
-  auto kern = sliced_kernel<MODE, AKFAST>;
+  auto kern = groups ? sliced_kernel<MODE, AKFAST, true> : sliced_kernel<MODE, AKFAST, false>;
   // the shared-memory limit belongs to the kernel and every calling thread shares it: raise it per
   // device to the largest size requested so far, never lower it
   constexpr int MAXDEV = 64;
-  static int raised[MAXDEV] = {};
+  static int raised[2][MAXDEV] = {};           // [grouped kernel][device]
   static std::mutex mu;
   int dev = 0;
   TTR_CUDA(cudaGetDevice(&dev));
   {
     std::lock_guard<std::mutex> lock(mu);
-    const int have = (dev >= 0 && dev < MAXDEV) ? raised[dev] : 0;
+    int* slot = (dev >= 0 && dev < MAXDEV) ? &raised[groups ? 1 : 0][dev] : nullptr;
+    const int have = slot ? *slot : 0;
     if (have < (int)sm) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return set_error(std::string("sliced kernel attribute: ") + cudaGetErrorString(e)), TTR_ERR_CUDA;
-      if (dev >= 0 && dev < MAXDEV) raised[dev] = (int)sm;
+      if (slot) *slot = (int)sm;
     }
   }
-  kern<<<grid, NT, sm, c.stream>>>(a);
+  kern<<<grid, NT, sm, c.stream>>>(a, gr);
   return c.check_launch(name);
 }
 
@@ -942,6 +1002,41 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
   return TTR_OK;
 }
 
+int tc_rl_step_grouped(Ctx& c, int slices, int ng, const double* const* Xk, const int64_t* r0, int64_t n,
+                       const int64_t* r1, const double* Wn, int64_t ldw, int64_t Kall, const int64_t* off_n,
+                       const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo, const int64_t* off_out,
+                       BPlanes* keep) {
+  if (ng < 1 || ng > MAXG || n > TM || slices < 3 || slices > MAXS || !Omi) return TTR_ERR_UNSUPPORTED;
+  for (int g = 0; g < ng; ++g)   // one K segment per group, inside the stacked rows
+    if (r1[g] < 1 || r0[g] < 1 || off_n[g] % KC + r1[g] > KSEG || off_n[g] + r1[g] > Kall) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b(c, Wn, ldw, 1, Kall, w, slices, bp, keep));   // the whole stacked W_{k+1}
+  Args a{};
+  a.sak = 1;
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = w; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
+  a.Omint = Omi; a.ldo = ldoi; a.nmode = n; a.g = (int)(TM / n); a.ldw = ldwo;
+  a.err = c.d_flags;
+  a.kseg = KSEG;
+  Groups gr{};
+  gr.n = ng;
+  int tiles = 0;
+  double bytes = 0.0;
+  for (int g = 0; g < ng; ++g) {
+    gr.tile0[g] = tiles;
+    gr.A[g] = Xk[g]; gr.M[g] = r0[g] * n; gr.K[g] = r1[g]; gr.sam[g] = r1[g]; gr.sak[g] = 1;
+    gr.slabs[g] = r0[g]; gr.koff[g] = off_n[g]; gr.W[g] = Wout + off_out[g] * ldwo;
+    tiles += (int)((r0[g] + a.g - 1) / a.g);
+    bytes += 8.0 * ((double)r0[g] * n * r1[g] + (double)r1[g] * w + (double)r0[g] * w);
+  }
+  gr.tile0[ng] = tiles;
+  dim3 grid((unsigned)tiles, (unsigned)bp.nchunks, 1);
+  c.time_begin(Ctx::KT_RL);
+  TTR_CHECK((launch<RLM, true>(c, a, grid, "tc_rl_step", &gr)));
+  c.time_end(bytes);
+  return TTR_OK;
+}
+
 int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
                      int64_t ldb, int64_t N, double* C, int64_t ldc, const BPlanes* reuse) {
   if (slices < 3 || slices > MAXS || M <= 0 || N <= 0 || K <= 0) return TTR_ERR_UNSUPPORTED;
@@ -993,6 +1088,65 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
     return launch<ATOMIC, false>(c, a, grid, "tc_project");
   }
   return launch<PLAIN, false>(c, a, grid, "tc_project");
+}
+
+// C_g = A_g B for up to MAXG row-major A_g (M[g] x K, leading dimension lda[g]) sharing one row-major
+// B (K x N, leading dimension ldb), in one launch: C_g row-major with leading dimension ldc.
+int tc_gemm_shared_b(Ctx& c, int slices, int ng, const double* const* A, const int64_t* M, const int64_t* lda,
+                     int64_t K, const double* B, int64_t ldb, int64_t N, double* const* C, int64_t ldc) {
+  if (ng < 1 || ng > MAXG || slices < 3 || slices > MAXS || K < 1 || K > KSEG || N <= 0) return TTR_ERR_UNSUPPORTED;
+  for (int g = 0; g < ng; ++g)
+    if (M[g] < 1) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b(c, B, ldb, 1, K, N, slices, bp));
+  Args a{};
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = N; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
+  a.err = c.d_flags; a.kseg = KSEG;
+  Groups gr{};
+  gr.n = ng;
+  int tiles = 0;
+  for (int g = 0; g < ng; ++g) {
+    gr.tile0[g] = tiles;
+    gr.A[g] = A[g]; gr.M[g] = M[g]; gr.K[g] = K; gr.sam[g] = lda[g]; gr.sak[g] = 1;
+    gr.koff[g] = 0; gr.C[g] = C[g]; gr.scm[g] = ldc; gr.scn[g] = 1;
+    tiles += (int)((M[g] + TM - 1) / TM);
+  }
+  gr.tile0[ng] = tiles;
+  dim3 grid((unsigned)tiles, (unsigned)bp.nchunks, 1);
+  return launch<PLAIN, true>(c, a, grid, "tc_gemm_shared_b", &gr);
+}
+
+// Y^(g) = M(:, koff[g] : koff[g] + K[g]) H(X^(g)) for up to MAXG summands in one launch (the per-summand
+// projection of a sum of TTs): summand g's result, L x (n_{k+1} rn[g]) with columns (i, c), is written
+// to rows a, columns i * rstride + yoff[g] + c of Y (row length ldy).  M is L x Kall row-major
+// (leading dimension ldm); H(X^(g)) is K[g] x ncol[g] row-major.
+int tc_project_grouped(Ctx& c, int slices, int ng, const double* M, int64_t ldm, int64_t L, int64_t Kall,
+                       const int64_t* koff, const int64_t* K, const double* const* Xn, const int64_t* ncol,
+                       const int64_t* rn, double* Y, int64_t ldy, int64_t rstride, const int64_t* yoff) {
+  if (ng < 1 || ng > MAXG || slices < 3 || slices > MAXS || L <= 0) return TTR_ERR_UNSUPPORTED;
+  for (int g = 0; g < ng; ++g)
+    if (K[g] < 1 || koff[g] % KC + K[g] > KSEG || koff[g] + K[g] > Kall || ncol[g] < 1 || rn[g] < 1 ||
+        ncol[g] >= (int64_t)1 << 31)
+      return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b(c, M, 1, ldm, Kall, L, slices, bp));   // B(k, j) = M(j, k), all Kall columns of M
+  Args a{};
+  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = L; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
+  a.err = c.d_flags; a.kseg = KSEG; a.rstride = rstride;
+  Groups gr{};
+  gr.n = ng;
+  int tiles = 0;
+  for (int g = 0; g < ng; ++g) {
+    gr.tile0[g] = tiles;
+    gr.A[g] = Xn[g]; gr.M[g] = ncol[g]; gr.K[g] = K[g]; gr.sam[g] = 1; gr.sak[g] = ncol[g];
+    gr.koff[g] = koff[g]; gr.C[g] = Y + yoff[g]; gr.scm[g] = 1; gr.scn[g] = ldy; gr.rp[g] = rn[g];
+    tiles += (int)((ncol[g] + TM - 1) / TM);
+  }
+  gr.tile0[ng] = tiles;
+  dim3 grid((unsigned)tiles, (unsigned)bp.nchunks, 1);
+  return launch<PLAIN, false>(c, a, grid, "tc_project", &gr);
 }
 
 }  // namespace ttr

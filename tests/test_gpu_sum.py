@@ -122,3 +122,19 @@ def test_sum_argument_errors(B):
     bad = [xs[0], xs[1][:4]]
     with pytest.raises(ValueError):
         B.round_adaptive_sum(dev_summands(bad), 1e-3, 1, 1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sum_more_summands_than_one_launch(B, prec):
+    """10 summands: the grouped launches take 8 and then 2."""
+    rng = np.random.default_rng(21)
+    n = [6, 5, 7, 4, 6, 5]
+    xs = [WL.random_tt(rng, 6, n, int(r)) for r in rng.integers(1, 6, size=10)]
+    for x, c in zip(xs, rng.standard_normal(10)):
+        x[0] = x[0] * c
+    ref, info = R.tt_round_adaptive_sum(xs, 1e-4, 5, block=3)
+    with B.round_adaptive_sum(dev_summands(xs), 1e-4, 3, 5, B.options(precision=prec, slices=8)) as y:
+        yi = y.info
+        got = y.to_numpy()
+    assert yi["ranks"] == info["ranks"]
+    assert rel(got, ref) <= (1e-10 if prec == 0 else 1e-9)
