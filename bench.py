@@ -371,6 +371,34 @@ def main():
     roof = max(cand, key=lambda r: r["share_of_step"]) if cand else None
     roof_other = [r for r in cand if r is not roof]
 
+    # ---- the same input as its summands, rounded without forming the formal sum (Remark 3.3,
+    # Appendix C): one at a time on one stream, CUDA events around each call as in `single_stream`
+    dev_of = {}
+    summands = [[dev_of.setdefault(id(c), torch.from_numpy(np.ascontiguousarray(c)).to("cuda")) for c in part]
+                for part in x.summands]
+    for _ in range(args.warmup):
+        with B.round_adaptive_sum(summands, TOL, BLOCK, SEED, opts) as y:
+            sum_ranks = y.ranks
+    sum_steps = max(3, min(args.steps, 100))
+    barrier()
+    sev = [torch.cuda.Event(enable_timing=True) for _ in range(sum_steps + 1)]
+    sev[0].record(stream)
+    for i in range(sum_steps):
+        y = B.round_adaptive_sum(summands, TOL, BLOCK, SEED, opts)
+        sum_ranks = y.ranks
+        y.free()
+        sev[i + 1].record(stream)
+    barrier()
+    sum_step_ms = [sev[i].elapsed_time(sev[i + 1]) for i in range(sum_steps)]
+    sum_ms = max_over_ranks(sev[0].elapsed_time(sev[-1]), world, "cuda")
+    sum_round = {"roundings_per_s": job_rate(sum_steps, world, sum_ms), "ms_per_rounding": sum_ms / sum_steps,
+                 "p50_ms": float(np.percentile(sum_step_ms, 50)), "p99_ms": float(np.percentile(sum_step_ms, 99)),
+                 "steps": sum_steps, "summands": len(summands), "ranks_out": sum_ranks,
+                 "ranks_equal_formal": sum_ranks == out_ranks,
+                 "speedup_over_formal_single_stream": single["ms_per_rounding"] / (sum_ms / sum_steps),
+                 "note": "tt_round_adaptive_sum on the 4 scaled copies + noise TT (copies share their cores after the "
+                         "first), one stream; compare with single_stream, the formal sum of the same input"}
+
     # ---- deterministic FP64 TT-rounding on the same GPU (the comparison the metric names)
     det_ms = []
     for i in range(args.det_steps + 1):
@@ -411,7 +439,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "latency": f"per rounding, host call to return, with {args.streams} roundings in flight",
-            "single_stream": single,
+            "single_stream": single, "sum_round": sum_round,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else
             f"f64 via bf16 slices (tcgen05)", "data": "synthetic",
             "config": config(x, args.streams), "ranks_out": out_ranks, "sketch_width": w, "extensions": info["extensions"],

@@ -225,6 +225,20 @@ def partial_contractions_rl_sum(summands, seed: int, col0: int, col1: int, t: in
     return {k: np.concatenate([p[k] for p in parts], axis=0) for k in parts[0]}
 
 
+def project_summands(Mq: np.ndarray, summands, off, k: int) -> list:
+    """Rows of H(Y_{k+1}) for the directions Mq = Q^T V(Y_k), one block per summand (Appendix C):
+    [M^(1) ... M^(s)] = Mq split at the bond-k offsets, block i = M^(i) H(X_{k+1}^(i))."""
+    return [Mq[:, off[k][i]:off[k][i + 1]] @ H(x[k]) for i, x in enumerate(summands)]
+
+
+def next_core_of_sum(parts, lk: int, n_next: int, right_ranks, last: bool) -> np.ndarray:
+    """H(Y_{k+1}) from the summands' blocks: side by side in the concatenated right bond, or at the
+    last core (shared right bond 1) their sum (reading R13)."""
+    if last:
+        return sum(parts).reshape(lk, n_next, 1)
+    return np.concatenate([p.reshape(lk, n_next, rr) for p, rr in zip(parts, right_ranks)], axis=2)
+
+
 def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_init: float = 0.1,
                           f_inc: float = 0.05, nrmx: float | None = None, adap_r: bool = False,
                           adap_r_tau: float | None = None):
@@ -250,10 +264,6 @@ def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_ini
     Y = [None] * d
     out_ranks, ests, b_inits = [1], [], []
 
-    def project(Mq, k):
-        # rows of H(Y_{k+1}) for the directions Mq = Q^T V(Y_k), one block per summand
-        return [Mq[:, off[k][i]:off[k][i + 1]] @ H(x[k]) for i, x in enumerate(summands)]
-
     for k in range(1, d):
         Z = V(Yk)                                                  # (l_{k-1} n_k) x (sum_i r_k^(i))
         rbar = min(Z.shape)
@@ -262,7 +272,7 @@ def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_ini
         sk.ensure(k, b_init)
         S = Z @ sk.W[k + 1][:, :b_init]
         Q, _ = np.linalg.qr(S)
-        parts = project(Q.T @ Z, k)
+        parts = project_summands(Q.T @ Z, summands, off, k)
         b_inc = block_size(rbar, block, f_inc)
         est_k = []
         while Q.shape[1] < rbar:                                   # R4
@@ -275,13 +285,10 @@ def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_ini
             Qn, _ = np.linalg.qr(S[:, :bb])
             Qn, _ = np.linalg.qr(Qn - Q @ (Q.T @ Qn))              # re-orthogonalization
             Q = np.concatenate([Q, Qn], axis=1)
-            parts = [np.concatenate([p, q], axis=0) for p, q in zip(parts, project(Qn.T @ Z, k))]
+            parts = [np.concatenate([p, q], axis=0) for p, q in zip(parts, project_summands(Qn.T @ Z, summands, off, k))]
         lk = Q.shape[1]
         Y[k - 1] = Q.reshape(out_ranks[-1], n[k - 1], lk)
-        if k + 1 < d:
-            Yk = np.concatenate([p.reshape(lk, n[k], rs[i][k + 1]) for i, p in enumerate(parts)], axis=2)
-        else:
-            Yk = sum(parts).reshape(lk, n[k], 1)                   # R13
+        Yk = next_core_of_sum(parts, lk, n[k], [r[k + 1] for r in rs], last=(k + 1 == d))
         out_ranks.append(lk)
         ests.append(est_k)
     Y[d - 1] = Yk

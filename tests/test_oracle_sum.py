@@ -9,7 +9,9 @@ something other than the sum code itself.
   core breaks this.
 * The relative error against the dense sum of the summands' full tensors is <= tol.
 * Block sizes in fraction mode follow the appendix (b_init = max summand rank).
-* A planted mistake (summand blocks stacked in the wrong order) must fail the identity pin.
+* Planted mistakes (summand blocks stacked in the wrong order, a summand's projected block
+  attached to the wrong directions of Q, the last core taken from one summand instead of summed)
+  must fail the identity pin.
 """
 import math
 
@@ -156,3 +158,26 @@ def test_c1_sum_equals_formal_sum_rounding():
     Yf, inff = R.tt_round_adaptive(x.cores, 1e-6, 2024, block=2, nrmx=x.norm)
     assert infs["ranks"] == inff["ranks"]
     assert T.tt_dist(Ys, Yf) <= 1e-11 * x.norm
+
+
+def _identity_gap(xs, nrmx, Yf):
+    Yb, _ = R.tt_round_adaptive_sum(xs, 1e-2, 5, block=2, nrmx=nrmx)
+    return T.tt_dist(Yb, Yf) / T.tt_norm(Yf)
+
+
+def test_planted_projection_and_last_core_mistakes_are_caught(monkeypatch):
+    xs = summands_of(7, 5, 4, [3, 2, 4], coef=[1.0, -0.7, 0.4])
+    xf = formal_sum(xs)
+    nrmx = T.tt_norm(xf)
+    Yf, _ = R.tt_round_adaptive(xf, 1e-2, 5, block=2, nrmx=nrmx)
+    assert _identity_gap(xs, nrmx, Yf) <= 1e-11
+    good_project, good_next = R.project_summands, R.next_core_of_sum
+    with monkeypatch.context() as m:
+        # each summand's projected rows in reverse order: attached to the wrong directions of Q
+        m.setattr(R, "project_summands",
+                  lambda Mq, summands, off, k: [b[::-1] if b.shape[0] > 1 else b for b in good_project(Mq, summands, off, k)])
+        assert _identity_gap(xs, nrmx, Yf) > 1e-6
+    with monkeypatch.context() as m:
+        m.setattr(R, "next_core_of_sum",
+                  lambda parts, lk, n_next, rr, last: good_next(parts[:1] if last else parts, lk, n_next, rr, last))
+        assert _identity_gap(xs, nrmx, Yf) > 1e-6
