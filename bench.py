@@ -98,6 +98,53 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 TRAFFIC_SLICED = {"block_loop": 2.44e6, "rl_kernel": 18.02e6}
 
 
+def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
+    """The serving stream (Poisson arrivals, mean gap 2 ms; each request a sum of 2-6 random TTs
+    with d 8-32, n 16-128, ranks 20-100, tol 1e-4/1e-6/1e-8): its first `nreq` requests, given to
+    the library's request server as summands in host memory.  Closed loop: all queued at once
+    (throughput).  Open loop: each submitted at its arrival time (latency under that load)."""
+    import workloads as WL
+    reqs = list(WL.c4_stream(count=nreq, formal=False))
+    srv = B.Server(workers=workers, device_budget=budget)
+
+    def opts_for(q):
+        return B.options(precision=B.TTR_PREC_SLICED)
+
+    try:
+        # warm-up: the smallest request once (kernel attributes, memory pool)
+        small = min(reqs, key=lambda q: q.tt.meta["formal_bytes"])
+        srv.wait(srv.submit(small.tt.summands, small.tol, 0, 7, opts_for(small)))
+        out = {}
+        for mode in ("closed_loop", "open_loop"):
+            t0 = time.perf_counter()
+            ids = []
+            for q in reqs:
+                if mode == "open_loop":
+                    delay = q.arrival_ms / 1e3 - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                ids.append(srv.submit(q.tt.summands, q.tol, 0, 1000 + q.rid, opts_for(q)))
+            lat, ranks_max = [], 0
+            for rid in ids:
+                cores, info = srv.wait(rid)
+                lat.append(info["ms_queue"] + info["ms_run"])
+                ranks_max = max(ranks_max, max(info["ranks"]))
+            span = time.perf_counter() - t0
+            st = srv.stats()
+            out[mode] = {"roundings_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "span_s": span,
+                         "peak_device_bytes_admitted": int(st["peak_in_use"]), "max_output_rank": ranks_max}
+        out.update({"requests": len(reqs), "workers": workers, "device_budget": budget,
+                    "formal_bytes_total": int(sum(q.tt.meta["formal_bytes"] for q in reqs)),
+                    "input_bytes_total": int(sum(c.nbytes for q in reqs for x in q.tt.summands for c in x)),
+                    "precision": "sliced, slices from each request's tol", "block": "appendix rule (block 0)",
+                    "note": "first requests of the seeded serving stream (seed 4), summands in pageable host "
+                            "memory; latency = submit to result in host memory"})
+        return out
+    finally:
+        srv.close()
+
+
 def max_over_ranks(ms: float, world: int, device) -> float:
     """The job's time: the largest of the ranks' timed regions (all_reduce MAX when world > 1)."""
     import torch
@@ -268,6 +315,8 @@ def main():
     ap.add_argument("--det-steps", type=int, default=2)
     ap.add_argument("--streams", type=int, default=3, help="roundings in flight at once (one stream each)")
     ap.add_argument("--only-main", action="store_true", help="timed rounding loop only (for profiler runs)")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the serving stream run through the request server (0: skip)")
     args = ap.parse_args()
 
     import workloads as WL
@@ -399,6 +448,9 @@ def main():
                  "note": "tt_round_adaptive_sum on the 4 scaled copies + noise TT (copies share their cores after the "
                          "first), one stream; compare with single_stream, the formal sum of the same input"}
 
+    # ---- the serving stream through the library's request server
+    serving = serving_run(B, args.serve_requests, args.streams, 120 << 30) if args.serve_requests > 0 else None
+
     # ---- deterministic FP64 TT-rounding on the same GPU (the comparison the metric names)
     det_ms = []
     for i in range(args.det_steps + 1):
@@ -439,7 +491,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "latency": f"per rounding, host call to return, with {args.streams} roundings in flight",
-            "single_stream": single, "sum_round": sum_round,
+            "single_stream": single, "sum_round": sum_round, "serving": serving,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else
             f"f64 via bf16 slices (tcgen05)", "data": "synthetic",
             "config": config(x, args.streams), "ranks_out": out_ranks, "sketch_width": w, "extensions": info["extensions"],

@@ -173,6 +173,71 @@ int tt_round_deterministic(int32_t d, const int64_t* n, const int64_t* r,
                            const double* const* cores, double tol, void* stream,
                            ttr_result* out);
 
+/* ---------------------------------------------------------------------------------------
+ * Request server (serving loop; no counterpart in the paper).  Rounding requests of different
+ * d, n, ranks, tolerances and precisions are admitted in arrival order while their estimated
+ * device footprint fits a memory budget, and run by `workers` host threads, each with its own
+ * CUDA stream and an SM share of the persistent block-loop kernel, so that several roundings are
+ * in flight at once.  A request is a sum of TTs (one summand for a plain TT) given in HOST
+ * memory: the worker copies its cores to the device, rounds it with tt_round_adaptive_sum, and
+ * copies the result back to host memory.  Times are host-clock: queueing (submit to admission)
+ * and running (admission to result in host memory).
+ * -------------------------------------------------------------------------------------- */
+typedef struct ttr_server ttr_server;
+
+typedef struct {
+  int32_t workers;          /* roundings in flight at once (host thread + stream each), >= 1 */
+  int32_t max_sms;          /* SMs the block loop of one request may take; 0 = SMs / workers */
+  uint64_t device_budget;   /* bytes of device memory all admitted requests may hold at once */
+  int32_t device;           /* CUDA device ordinal */
+} ttr_server_config;
+
+typedef struct {
+  int32_t status;           /* ttr_status of the rounding */
+  int32_t d;
+  int64_t* ranks;           /* host, d+1 output ranks */
+  double* data;             /* host, the output cores back to back */
+  double** cores;           /* d host pointers into data */
+  double ms_queue;          /* submit -> admission */
+  double ms_run;            /* admission -> result in host memory (H2D, rounding, D2H) */
+  uint64_t footprint;       /* device bytes the request was admitted with (estimate) */
+  uint64_t bytes_in;        /* bytes of input cores copied to the device */
+  int64_t admit_order;      /* 0-based position of the request in the order of admission */
+  char message[256];        /* error text of a failed request (the worker's ttr_last_error) */
+} ttr_server_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, waiting, running;
+  uint64_t in_use, peak_in_use;   /* admitted footprint now and at most so far */
+} ttr_server_stats;
+
+/* Start the worker threads (they make no CUDA call until a request arrives).  TTR_ERR_ARG for
+ * workers < 1, a zero budget or a negative device; TTR_ERR_OOM if the server cannot be made. */
+int ttr_server_create(const ttr_server_config* cfg, ttr_server** out);
+
+/* Queue one rounding of X^(1) + ... + X^(s) to relative tolerance tol (arguments as in
+ * tt_round_adaptive_sum, but `host_cores` are HOST pointers; pinned memory copies fastest).  The
+ * caller keeps the n, r and core arrays valid until ttr_server_wait for this id returns.  opts may
+ * be NULL (defaults); its max_sms is replaced by the server's.  The request id goes to *id.
+ * Errors: TTR_ERR_ARG for bad shapes (checked here, before queueing), TTR_ERR_UNSUPPORTED when
+ * the request's estimated footprint exceeds the whole budget. */
+int ttr_server_submit(ttr_server* srv, int32_t s, int32_t d, const int64_t* n, const int64_t* const* r,
+                      const double* const* const* host_cores, double tol, int64_t block, uint64_t seed,
+                      const ttr_options* opts, int64_t* id);
+
+/* Block until request `id` is done and hand over its result (release with
+ * ttr_server_result_free).  Each id can be waited for once; TTR_ERR_ARG for an unknown id. */
+int ttr_server_wait(ttr_server* srv, int64_t id, ttr_server_result* out);
+
+void ttr_server_result_free(ttr_server_result* res);
+
+/* Counters of the server (any thread). */
+int ttr_server_get_stats(ttr_server* srv, ttr_server_stats* out);
+
+/* Let the running and queued requests finish, join the workers and release the server.
+ * Results not waited for are freed. */
+void ttr_server_destroy(ttr_server* srv);
+
 /* Release what a successful call allocated (device arena on `stream`, host arrays) and zero
  * *out.  Safe on a zeroed or already freed result. */
 void ttr_free(ttr_result* out, void* stream);

@@ -41,6 +41,11 @@ and the SVD (numpy.linalg.svd).  Readings of points where the paper is silent or
       appendix's b_init = max_i r_k^(i) (clamped to rbar_k) and b_inc = ceil(f_inc * rbar_k).
       The norm estimate uses the first w0 columns of the stacked W_2, w0 = block in block mode,
       else the appendix's sketch width max_{i,k} r_k^(i).
+  R14 The largest rank of core k, rbar_k, is also bounded by the right part: V(Y_k) H(X_{k+1:d})
+      has rank at most prod_{j>k} n_j, so rbar_k = min(rows, cols of V(Y_k), prod_{j>k} n_j) (the
+      adaptive counterpart of R6).  Without it an initial block wider than that rank (possible
+      with the appendix's b_init = max_i r_k^(i) at the last cores) would sketch an exactly
+      rank-deficient matrix.
   R13 Sum of TTs, the last core: the appendix writes H(Y_{k+1}) = [Y^(1) ... Y^(s)] for every k.
       For k + 1 = d the summands' last cores share the right bond 1 (the formal sum stacks them
       vertically), so H(Y_d) = sum_i M^(i) H(X_d^(i)); for k + 1 < d the blocks sit side by side
@@ -145,6 +150,14 @@ def residual_sketch(sk: _Sketches, Z: np.ndarray, Q: np.ndarray, k: int, b: int)
     return S - Q @ (Q.T @ S)                                       # Eq. (3.5)
 
 
+def right_bound(n, k: int) -> int:
+    """prod_{j>k} n_j (1-based k), capped well above any rank (reading R14)."""
+    p = 1
+    for v in n[k:]:
+        p = min(p * int(v), 1 << 62)
+    return p
+
+
 def tt_round_adaptive(cores, tol: float, seed: int, block: int = 0, f_init: float = 0.1,
                       f_inc: float = 0.05, nrmx: float | None = None, adap_r: bool = False,
                       adap_r_tau: float | None = None):
@@ -166,7 +179,7 @@ def tt_round_adaptive(cores, tol: float, seed: int, block: int = 0, f_init: floa
     out_ranks, ests = [1], []
     for k in range(1, d):
         Z = V(Yk)
-        rbar = min(Z.shape)
+        rbar = min(min(Z.shape), right_bound(n, k))                # R4, R14
         b_init = block_size(rbar, block, f_init)
         sk.ensure(k, b_init)
         S = Z @ sk.W[k + 1][:, :b_init]                            # phase 1 sketch
@@ -266,7 +279,7 @@ def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_ini
 
     for k in range(1, d):
         Z = V(Yk)                                                  # (l_{k-1} n_k) x (sum_i r_k^(i))
-        rbar = min(Z.shape)
+        rbar = min(min(Z.shape), right_bound(n, k))                # R4, R14
         b_init = block_size(rbar, block, f_init) if block > 0 else min(rbar, max(r[k] for r in rs))
         b_inits.append(b_init)
         sk.ensure(k, b_init)

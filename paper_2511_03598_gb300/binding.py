@@ -40,6 +40,24 @@ class Result(ctypes.Structure):
                 ("n_block_loop", ctypes.c_int32), ("n_rl_kernel", ctypes.c_int32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_sms", ctypes.c_int32), ("device_budget", ctypes.c_uint64),
+                ("device", ctypes.c_int32)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("d", ctypes.c_int32), ("ranks", ctypes.POINTER(ctypes.c_int64)),
+                ("data", ctypes.POINTER(ctypes.c_double)), ("cores", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("ms_queue", ctypes.c_double), ("ms_run", ctypes.c_double), ("footprint", ctypes.c_uint64),
+                ("bytes_in", ctypes.c_uint64), ("admit_order", ctypes.c_int64), ("message", ctypes.c_char * 256)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("waiting", ctypes.c_int64), ("running", ctypes.c_int64), ("in_use", ctypes.c_uint64),
+                ("peak_in_use", ctypes.c_uint64)]
+
+
 class TTRoundError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -72,6 +90,17 @@ def lib():
         L.ttr_partial_contractions_noalloc.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, PP, vp]
         L.tt_round_adaptive_sum.argtypes = [i32, i32, P64, ctypes.POINTER(P64), ctypes.POINTER(PP), dbl, i64, u64,
                                             ctypes.POINTER(Options), vp, ctypes.POINTER(Result)]
+        L.ttr_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
+        L.ttr_server_submit.argtypes = [vp, i32, i32, P64, ctypes.POINTER(P64), ctypes.POINTER(PP), dbl, i64, u64,
+                                        ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_int64)]
+        L.ttr_server_wait.argtypes = [vp, i64, ctypes.POINTER(ServerResult)]
+        L.ttr_server_result_free.argtypes = [ctypes.POINTER(ServerResult)]
+        L.ttr_server_result_free.restype = None
+        L.ttr_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.ttr_server_destroy.argtypes = [vp]
+        L.ttr_server_destroy.restype = None
+        for f in ("ttr_server_create", "ttr_server_submit", "ttr_server_wait", "ttr_server_get_stats"):
+            getattr(L, f).restype = ctypes.c_int
         for f in ("tt_round_fixed", "tt_round_adaptive", "tt_round_adaptive_sum", "tt_round_deterministic", "ttr_sketch_omega",
                   "ttr_partial_contractions", "ttr_partial_contractions_noalloc"):
             getattr(L, f).restype = ctypes.c_int
@@ -315,3 +344,87 @@ def round_adaptive_host(cores_np, tol: float, block: int, seed: int, opts: Optio
     with round_adaptive(dev, tol, block, seed, opts) as y:
         out = [t.cpu().numpy() for t in y.to_torch()]
         return HostRounding(out, y.ranks, y.info)
+
+
+class Server:
+    """The library's request server (ttr_server_*): requests are sums of TTs in host memory, admitted
+    in arrival order within a device-memory budget and rounded by `workers` threads at once."""
+
+    def __init__(self, workers: int = 3, device_budget: int = 64 << 30, max_sms: int = 0, device: int = 0):
+        cfg = ServerConfig(int(workers), int(max_sms), int(device_budget), int(device))
+        h = ctypes.c_void_p()
+        _check(lib().ttr_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, summands, tol: float, block: int, seed: int, opts: Options | None = None) -> int:
+        """Queue the rounding of sum(summands); each summand is a list of C-contiguous float64 numpy
+        arrays of shape (r0, n, r1) (pinned memory copies fastest).  Returns the request id."""
+        import numpy as np
+        if len(summands) < 1:
+            raise ValueError("at least one summand")
+        d = len(summands[0])
+        modes = [int(c.shape[1]) for c in summands[0]]
+        keep = [summands]
+        P64 = ctypes.POINTER(ctypes.c_int64)
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        rs, ps = [], []
+        for x in summands:
+            if len(x) != d or [int(c.shape[1]) for c in x] != modes:
+                raise ValueError("summands must share d and the mode sizes")
+            for c in x:
+                if not (isinstance(c, np.ndarray) and c.dtype == np.float64 and c.ndim == 3 and c.flags.c_contiguous):
+                    raise ValueError("cores must be C-contiguous float64 arrays of shape (r0, n, r1)")
+            r = (ctypes.c_int64 * (d + 1))(*([int(x[0].shape[0])] + [int(c.shape[2]) for c in x]))
+            p = (ctypes.c_void_p * d)(*[c.ctypes.data for c in x])
+            keep += [r, p]
+            rs.append(ctypes.cast(r, P64))
+            ps.append(ctypes.cast(p, PP))
+        n = (ctypes.c_int64 * d)(*modes)
+        ra = (P64 * len(rs))(*rs)
+        pa = (PP * len(ps))(*ps)
+        keep += [n, ra, pa]
+        rid = ctypes.c_int64()
+        _check(lib().ttr_server_submit(self._h, len(summands), d, n, ra, pa, float(tol), int(block),
+                                       ctypes.c_uint64(seed), ctypes.byref(opts) if opts else None,
+                                       ctypes.byref(rid)))
+        self._keep[rid.value] = (keep, modes)
+        return rid.value
+
+    def wait(self, rid: int):
+        """(cores as numpy arrays, info) of request rid; raises TTRoundError if it failed."""
+        import numpy as np
+        res = ServerResult()
+        st = lib().ttr_server_wait(self._h, int(rid), ctypes.byref(res))
+        _, modes = self._keep.pop(rid, (None, None))
+        try:
+            if st != 0:
+                raise TTRoundError(st, f"request {rid}: " + res.message.decode(errors="replace"))
+            rk = [int(res.ranks[k]) for k in range(res.d + 1)]
+            cores = []
+            for k in range(res.d):
+                cnt = rk[k] * modes[k] * rk[k + 1]
+                a = np.ctypeslib.as_array(res.cores[k], shape=(cnt,)).copy()
+                cores.append(a.reshape(rk[k], modes[k], rk[k + 1]))
+            info = {"ranks": rk, "ms_queue": res.ms_queue, "ms_run": res.ms_run, "footprint": int(res.footprint),
+                    "bytes_in": int(res.bytes_in), "admit_order": int(res.admit_order)}
+            return cores, info
+        finally:
+            lib().ttr_server_result_free(ctypes.byref(res))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().ttr_server_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().ttr_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -945,7 +945,10 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   const bool device_loop = getenv("TTR_HOST_LOOP") == nullptr;
   for (int k = 1; k < d; ++k) {
     const int64_t rows = lprev * X.n[k - 1], cols = X.R[k];
-    const int64_t rbar = std::min(rows, cols);
+    // the rank of V(Y_k) H(X_{k+1:d}) is also at most prod_{j>k} n_j (reading R14)
+    int64_t right = 1;
+    for (int j = k; j < d && right < rows; ++j) right = std::min<int64_t>(right * X.n[j], (int64_t)1 << 62);
+    const int64_t rbar = std::min(std::min(rows, cols), right);
     const int64_t b0 = appendix ? std::min(rbar, X.part_rank_max(k)) : block_size(rbar, block, o.f_init);
     const int64_t bi = block_size(rbar, block, o.f_inc);
     sk_cols = 0;

@@ -90,3 +90,30 @@ def test_sum_argument_errors_on_host(libpath):
     assert st == 1 and b"r[d]" in L.ttr_last_error()
     st = L.tt_round_adaptive_sum(1, 2, n, rs, ps, 0.0, 1, ctypes.c_uint64(1), None, None, ctypes.byref(res))
     assert st == 1 and res.status == 1
+
+
+def test_server_host_paths_without_gpu(libpath):
+    """The request server starts and stops without a GPU; bad requests and requests larger than the
+    whole budget are refused at submit, before any device work."""
+    import numpy as np
+    from paper_2511_03598_gb300 import binding as B
+    import workloads as WL
+    x = WL.c1()
+    with B.Server(workers=2, device_budget=1 << 20, max_sms=10) as srv:
+        with pytest.raises(B.TTRoundError) as e:
+            srv.submit(x.summands, 1e-6, 2, 1)
+        assert e.value.status == 7                       # TTR_ERR_UNSUPPORTED: over the budget
+        with pytest.raises(B.TTRoundError) as e:
+            srv.submit(x.summands, 0.0, 2, 1)
+        assert e.value.status == 1
+        bad = [[c.copy() for c in x.summands[0]]]
+        bad[0][0] = np.ascontiguousarray(np.concatenate([bad[0][0], bad[0][0]], axis=0))   # r_0 = 2
+        with pytest.raises(B.TTRoundError):
+            srv.submit(bad, 1e-6, 2, 1)
+        st = srv.stats()
+        assert st["submitted"] == 0 and st["in_use"] == 0
+        res = B.ServerResult()
+        assert B.lib().ttr_server_wait(srv._h, 12345, ctypes.byref(res)) == 1   # unknown id
+    cfg = B.ServerConfig(0, 0, 1 << 20, 0)
+    h = ctypes.c_void_p()
+    assert B.lib().ttr_server_create(ctypes.byref(cfg), ctypes.byref(h)) == 1   # no workers

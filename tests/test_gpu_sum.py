@@ -138,3 +138,16 @@ def test_sum_more_summands_than_one_launch(B, prec):
         got = y.to_numpy()
     assert yi["ranks"] == info["ranks"]
     assert rel(got, ref) <= (1e-10 if prec == 0 else 1e-9)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sum_first_block_wider_than_the_last_unfolding(B, prec):
+    """b_init = max summand rank (6) exceeds the rank of the last unfolding (n_d = 4): reading R14
+    clamps it, and the CholeskyQR of the first block sees a full-rank sketch."""
+    rng = np.random.default_rng(13)
+    xs = [WL.random_tt(rng, 5, 4, r) for r in (6, 5)]
+    xs[1][0] = xs[1][0] * 0.8
+    ref, info = R.tt_round_adaptive_sum(xs, 1e-8, 3, block=0)
+    with B.round_adaptive_sum(dev_summands(xs), 1e-8, 0, 3, B.options(precision=prec, slices=8)) as y:
+        assert y.info["ranks"] == info["ranks"]
+        assert rel(y.to_numpy(), ref) <= (1e-10 if prec == 0 else 1e-9)

@@ -133,7 +133,7 @@ def dense_adaptive(cores, tol, seed, block, nrmx, f_init=0.1, f_inc=0.05):
         Xk = X.reshape(int(np.prod(n[:k])), -1)
         B = np.kron(U, np.eye(n[k - 1]))
         A = B.T @ Xk                                      # = V(Y_k) H(X_{k+1:d}) up to column order
-        rbar = min(B.shape[1], T.ranks(cores)[k])
+        rbar = min(B.shape[1], T.ranks(cores)[k], int(np.prod(n[k:])))    # readings R4, R14
         om = lambda c0, c1: krp_columns(seed, list(range(k + 1, d + 1)), list(n), c0, c1)
         b0 = R.block_size(rbar, block, f_init)
         Q, _ = np.linalg.qr(A @ om(0, b0))

@@ -181,3 +181,14 @@ def test_planted_projection_and_last_core_mistakes_are_caught(monkeypatch):
         m.setattr(R, "next_core_of_sum",
                   lambda parts, lk, n_next, rr, last: good_next(parts[:1] if last else parts, lk, n_next, rr, last))
         assert _identity_gap(xs, nrmx, Yf) > 1e-6
+
+
+def test_first_block_wider_than_the_last_unfolding():
+    """Reading R14: with the appendix's b_init = max_i r_k^(i) = 6 and n_d = 4, the last core's
+    unfolding has rank at most 4; rbar_k is clamped to it, so no sketch block is wider than the
+    rank it can have, and the result is still within tol of the dense sum."""
+    xs = summands_of(13, 5, 4, [6, 5], coef=[1.0, 0.8])
+    X = dense(xs)
+    Y, info = R.tt_round_adaptive_sum(xs, 1e-10, 3, block=0, nrmx=float(np.linalg.norm(X)))
+    assert info["ranks"][4] <= 4 and info["b_init"][3] <= 4
+    assert np.linalg.norm(T.full(Y) - X) <= 1e-10 * np.linalg.norm(X)

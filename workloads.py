@@ -174,10 +174,14 @@ class Request:
     tt: TTInput
 
 
-def c4_stream(seed: int = 4, count: int = 512, mean_gap_ms: float = 2.0, max_bytes: float | None = None):
-    """Serving stream: Poisson arrivals; each request is a formal sum of s in [2, 6] random TTs with
-    d in [8, 32], n in [16, 128], component ranks in [20, 100] and tol in {1e-4, 1e-6, 1e-8}.
-    Yields requests lazily (the whole stream is larger than host or device memory)."""
+def c4_stream(seed: int = 4, count: int = 512, mean_gap_ms: float = 2.0, max_bytes: float | None = None,
+              formal: bool = True):
+    """Serving stream: Poisson arrivals; each request is a sum of s in [2, 6] random TTs with d in
+    [8, 32], n in [16, 128], component ranks in [20, 100] (all bonds of a summand equal), coefficients
+    N(0, 1) on the first cores, and tol in {1e-4, 1e-6, 1e-8}.  Yields requests lazily (the whole
+    stream is larger than host or device memory).  Each request carries its summands; with
+    ``formal`` it also carries the block-diagonal formal sum as ``cores`` (costly for large
+    requests), else ``cores`` is empty.  ``max_bytes`` skips requests whose formal sum is larger."""
     rng = np.random.default_rng(seed)
     t = 0.0
     for rid in range(count):
@@ -187,11 +191,15 @@ def c4_stream(seed: int = 4, count: int = 512, mean_gap_ms: float = 2.0, max_byt
         n = int(rng.integers(16, 129))
         comp = [int(rng.integers(20, 101)) for _ in range(s)]
         tol = float([1e-4, 1e-6, 1e-8][int(rng.integers(0, 3))])
-        sub = np.random.default_rng([seed, rid])
-        terms = [(float(sub.standard_normal()), random_tt(sub, d, n, rc)) for rc in comp]
-        cores = block_sum(terms)
-        nb = sum(c.nbytes for c in cores)
+        R = sum(comp)
+        nb = 8 * (2 * n * R + (d - 2) * n * R * R)
         if max_bytes is not None and nb > max_bytes:
             continue
+        sub = np.random.default_rng([seed, rid])
+        terms = [(float(sub.standard_normal()), random_tt(sub, d, n, rc)) for rc in comp]
+        summands = []
+        for c, x in terms:
+            summands.append([c * x[0]] + x[1:])
+        cores = block_sum(terms) if formal else []
         yield Request(rid, t, tol, TTInput(f"c4_req{rid}", cores, float("nan"),
-                                           {"s": s, "d": d, "n": n, "ranks": comp}))
+                                           {"s": s, "d": d, "n": n, "ranks": comp, "formal_bytes": nb}, summands))
