@@ -64,6 +64,9 @@ int transpose_f64(Ctx& c, const double* A, int64_t rows, int64_t cols, double* o
 int scale_cols_f64(Ctx& c, double* U, int64_t ld, int64_t ncols, int64_t rows, const double* s);
 int scale_rows_rsqrt_f64(Ctx& c, double* Vt, int64_t ld, int64_t nrows, int64_t ncols, const double* lam);
 
+// rows x cc x bcols of a block projection from which the sliced form uses the tensor cores
+constexpr double kSlicedProjectWork = 1 << 24;
+
 struct Engine {
   int precision = TTR_PREC_FP64;
   int slices = 0;
@@ -187,6 +190,24 @@ struct Engine {
       if (!sumsq_out) return TTR_OK;
       TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
       return sumsq(c, S, rows, bcols, lds, 1, sumsq_out);
+    }
+    if (precision == TTR_PREC_SLICED && (double)rows * cc * bcols >= kSlicedProjectWork) {
+      // wide blocks (the host-driven loop): both products on the tensor cores, each exact to the
+      // sliced form's stated error, instead of FP64 at 2 FMA per clock per SM
+      int st = tc_gemm_tn(c, slices, Q, ldq, rows, cc, S, lds, bcols, P, bcols, 1);   // P = Q^T S
+      if (st == TTR_OK) {
+        const size_t need = sizeof(double) * (size_t)rows * bcols;
+        if (c.ptmp_bytes < need) {
+          void* t = nullptr;
+          TTR_CHECK(c.alloc(&t, std::max(need, 2 * c.ptmp_bytes)));
+          c.ptmp = static_cast<double*>(t);
+          c.ptmp_bytes = std::max(need, 2 * c.ptmp_bytes);
+        }
+        TTR_CHECK(tc_gemm_rowmajor(c, slices, Q, ldq, rows, cc, P, bcols, bcols, c.ptmp, bcols));  // Q P
+        if (sumsq_out) TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
+        return sub2d(c, S, lds, c.ptmp, bcols, rows, bcols, sumsq_out);
+      }
+      if (st != TTR_ERR_UNSUPPORTED) return st;
     }
     int st = gram_reduce(c, Q, ldq, S, lds, rows, cc, bcols, P, bcols, 0, nullptr, nullptr, nullptr, nullptr, sumsq_out);
     if (st == TTR_ERR_UNSUPPORTED) {

@@ -423,6 +423,35 @@ int sumsq(Ctx& c, const double* S, int64_t m, int64_t b, int64_t sm, int64_t sb,
   return c.check_launch("sumsq");
 }
 
+// S <- S - T (rows x cols, row-major), adding the sum of squares of the new S to *out if given.
+__global__ void sub2d_kernel(double* S, int64_t lds, const double* T, int64_t ldt, int64_t m, int64_t b, double* out) {
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * b; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / b, j = e % b;
+    const double v = S[i * lds + j] - T[i * ldt + j];
+    S[i * lds + j] = v;
+    s = fma(v, v, s);
+  }
+  if (!out) return;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+int sub2d(Ctx& c, double* S, int64_t lds, const double* T, int64_t ldt, int64_t m, int64_t b, double* sumsq_out) {
+  const int64_t tot = m * b;
+  if (tot <= 0) return TTR_OK;
+  unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 1216);
+  sub2d_kernel<<<blocks, 256, 0, c.stream>>>(S, lds, T, ldt, m, b, sumsq_out);
+  return c.check_launch("sub2d");
+}
+
 // ----------------------------------------------------------------------------- perturbation
 // X(i, j) += scale * g(i, j), g standard Gaussian from the sketch generator with core index 0
 // (a counter range the sketches never use).  Used to lift an exactly rank-deficient sketch.

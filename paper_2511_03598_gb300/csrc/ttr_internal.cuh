@@ -47,6 +47,8 @@ struct Ctx {
   unsigned long long* ac_prof = nullptr;   // adaptive_core phase cycles (profiling only)
   unsigned long long* tc_prof = nullptr;   // tensor-core kernel phase cycles per mode (profiling only)
   void* bprep = nullptr;           // tensor-core B-operand workspace (digit planes, scales)
+  double* ptmp = nullptr;          // sliced block projection: the product Q P before S -= Q P
+  size_t ptmp_bytes = 0;
   unsigned* prep_bar = nullptr;    // grid barrier of the fused B preparation (counter, generation)
   size_t bprep_bytes = 0;
   int workspace();
@@ -136,6 +138,8 @@ int omega_reduce(Ctx& c, const double* T, int64_t ldt, const double* Om, int64_t
 
 // Sum of squares of an m x b strided matrix, accumulated into *out (device, zeroed by caller).
 int sumsq(Ctx& c, const double* S, int64_t m, int64_t b, int64_t sm, int64_t sb, double* out);
+// S <- S - T (m x b, row-major); with sumsq_out, the sum of squares of the new S is added there.
+int sub2d(Ctx& c, double* S, int64_t lds, const double* T, int64_t ldt, int64_t m, int64_t b, double* sumsq_out);
 
 // Upper Cholesky of a b x b symmetric matrix (row-major, ld) in place, plus the inverse of
 // the factor into Rinv (row-major, ld).  shift is added to the diagonal first.  *bad is set

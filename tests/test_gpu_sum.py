@@ -151,3 +151,23 @@ def test_sum_first_block_wider_than_the_last_unfolding(B, prec):
     with B.round_adaptive_sum(dev_summands(xs), 1e-8, 0, 3, B.options(precision=prec, slices=8)) as y:
         assert y.info["ranks"] == info["ranks"]
         assert rel(y.to_numpy(), ref) <= (1e-10 if prec == 0 else 1e-9)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_host_driven_block_loop(B, prec, monkeypatch):
+    """The host-driven block loop (used where a block or the sketch is too wide for the persistent
+    kernel), forced here: C1's summands, and a full-rank sum (formal rank 120, rows up to 6000,
+    blocks of 30) whose block projections take the tensor-core branch in sliced form.  The slice
+    count follows the tolerance (5 slices at 1e-4, each product exact to ~5 * 2^-31 = 2e-9 of the
+    operand scales), so the sliced bar is 1e-3 * tol, at least 1e-8."""
+    monkeypatch.setenv("TTR_HOST_LOOP", "1")
+    rng = np.random.default_rng(77)
+    wide = [WL.random_tt(rng, 6, 50, r) for r in (40, 40, 40)]
+    for x, c in zip(wide, (1.0, -0.5, 0.7)):
+        x[0] = x[0] * c
+    x1 = WL.c1()
+    for xs, tol, block, nrmx in ((x1.summands, 1e-6, 2, x1.norm), (wide, 1e-4, 30, None)):
+        ref, info = R.tt_round_adaptive_sum(xs, tol, 5, block=block, nrmx=nrmx)
+        with B.round_adaptive_sum(dev_summands(xs), tol, block, 5, B.options(precision=prec, nrmx=nrmx or 0.0)) as y:
+            assert y.info["ranks"] == info["ranks"]
+            assert rel(y.to_numpy(), ref) <= (1e-10 if prec == 0 else max(1e-8, 1e-3 * tol))
