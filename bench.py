@@ -95,7 +95,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # this workload in sliced precision, for the kernels as they stand (the capture command is in
 # profiles/): the block loop's figure is the median over full-rank cores, the partial
 # contraction's the mean over all 18 launches of one pass.  Other precisions run other kernels.
-TRAFFIC_SLICED = {"block_loop": 2.44e6, "rl_kernel": 18.02e6}
+TRAFFIC_SLICED = {"block_loop": 2.44e6, "rl_kernel": 17.98e6}
 
 
 def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
