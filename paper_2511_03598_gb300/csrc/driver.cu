@@ -324,9 +324,13 @@ static int check_device_flags(Ctx& c) {
 
 // ----------------------------------------------------------------------------- QR
 // Thin QR of the m x b row-major matrix X (leading dimension ldx), in place: X <- Q.
-// CholeskyQR2; if a Cholesky pivot breaks down, shifted CholeskyQR3 (Fukaya, Kannan,
-// Nakatsukasa, Yamamoto, Yanagisawa 2020) from the saved input.  Scratch: tmp and save
-// (m x b, ld b), G and Rinv (b x b, ld b), dscal (>= 2 doubles), dflag (1 int).
+// CholeskyQR3: three CholeskyQR passes.  Two passes orthonormalise a block of condition up to
+// ~1e8; a numerically rank-deficient block (a sketch wider than the rank it has, as in a fixed
+// rank above the true rank) leaves the completing directions of the second pass orthonormal only
+// to O(1), and the third pass, on a block that is now near-orthonormal, restores them.  If a
+// Cholesky pivot breaks down, shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto,
+// Yanagisawa 2020) from the saved input.  Scratch: tmp and save (m x b, ld b), G and Rinv
+// (b x b, ld b), dscal (>= 2 doubles), dflag (1 int).
 struct QrWork {
   double* tmp = nullptr;
   double* save = nullptr;
@@ -357,6 +361,8 @@ static int qr_inplace(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m
   TTR_CHECK(copy2d(c, w.save, b, X, ldx, m, b));
   TTR_CHECK(chol_pass(c, E, w.save, b, m, b, w.tmp, b, w, nullptr));
   TTR_CHECK(chol_pass(c, E, w.tmp, b, m, b, X, ldx, w, nullptr));
+  TTR_CHECK(chol_pass(c, E, X, ldx, m, b, w.tmp, b, w, nullptr));
+  TTR_CHECK(copy2d(c, X, ldx, w.tmp, b, m, b));
   int st = TTR_OK;
   const int bad = isync_read(c, w.dflag, &st);
   if (st != TTR_OK) return st;

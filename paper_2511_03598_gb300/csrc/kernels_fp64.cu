@@ -141,27 +141,42 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* X, int64
   const int64_t r0 = (int64_t)blockIdx.x * rpb;
   const int64_t r1 = min(m, r0 + rpb);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // warps split the outputs (16 at a time), lanes split the rows of this block
-  for (int o0 = warp * 16; o0 < ab; o0 += nw * 16) {
-    double acc[16];
+  // Rows of this block in tiles staged in shared memory (coalesced row loads); every thread owns up
+  // to GRAM_MAX / 256 outputs (i, j) and accumulates X(r, i) Y(r, j) over the tile's rows.
+  __shared__ double tile[4096];
+  const int tr = max(1, min(64, 4096 / (a + b)));
+  double* Xs = tile;
+  double* Ys = tile + tr * a;
+  constexpr int OPT = GRAM_MAX / 256;
+  int oi[OPT], oj[OPT];
+  double acc[OPT];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-    for (int64_t r = r0 + lane; r < r1; r += 32) {
-      const double* xr = X + r * ldx;
-      const double* yr = Y + r * ldy;
+  for (int q = 0; q < OPT; ++q) {
+    const int o = threadIdx.x + q * 256;
+    oi[q] = o < ab ? o / b : 0;
+    oj[q] = o < ab ? o % b : 0;
+    acc[q] = 0.0;
+  }
+  for (int64_t t0 = r0; t0 < r1; t0 += tr) {
+    const int nr = (int)min((int64_t)tr, r1 - t0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * a; e += blockDim.x) Xs[e] = X[(t0 + e / a) * ldx + e % a];
+    for (int e = threadIdx.x; e < nr * b; e += blockDim.x) Ys[e] = Y[(t0 + e / b) * ldy + e % b];
+    __syncthreads();
+    for (int r = 0; r < nr; ++r) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int o = o0 + q;
-        if (o < ab) acc[q] = fma(xr[o / b], yr[o % b], acc[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      double v = acc[q];
-      for (int sft = 16; sft > 0; sft >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sft);
-      if (lane == 0 && o0 + q < ab) ws[(int64_t)blockIdx.x * ab + o0 + q] = v;
+      for (int q = 0; q < OPT; ++q)
+        if (threadIdx.x + q * 256 < ab) acc[q] = fma(Xs[r * a + oi[q]], Ys[r * b + oj[q]], acc[q]);
     }
   }
+#pragma unroll
+  for (int q = 0; q < OPT; ++q) {
+    const int o = threadIdx.x + q * 256;
+    if (o < ab) ws[(int64_t)blockIdx.x * ab + o] = acc[q];
+  }
+  (void)warp;
+  (void)lane;
+  (void)nw;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
@@ -274,8 +289,18 @@ int tri_solve(Ctx& c, const double* X, int64_t ldx, int64_t m, int64_t b, const 
   if (b > 32) return TTR_ERR_UNSUPPORTED;
   if (m <= 0 || b <= 0) return TTR_OK;
   const unsigned blocks = (unsigned)std::min<int64_t>((m + 255) / 256, 1216);
-  if (b <= 16) tri_solve_kernel<16><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo);
-  else tri_solve_kernel<32><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo);
+  // the substitution is unrolled to BMAX columns, and FP64 instructions cost pipe time even with
+  // their lanes masked off, so BMAX follows b in steps of 4
+  switch ((b + 3) / 4) {
+    case 1: tri_solve_kernel<4><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo); break;
+    case 2: tri_solve_kernel<8><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo); break;
+    case 3: tri_solve_kernel<12><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo); break;
+    case 4: tri_solve_kernel<16><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo); break;
+    case 5: tri_solve_kernel<20><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo); break;
+    case 6: tri_solve_kernel<24><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo); break;
+    case 7: tri_solve_kernel<28><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo); break;
+    default: tri_solve_kernel<32><<<blocks, 256, 0, c.stream>>>(X, ldx, m, (int)b, R, invd, out, ldo); break;
+  }
   return c.check_launch("tri_solve");
 }
 

@@ -85,6 +85,19 @@ def test_fixed_c1(B):
     assert T.left_orth_defect(got) <= 1e-12
 
 
+def test_fixed_c1_orthonormal_every_time(B):
+    """Rank 13 exceeds C1's true rank 10, so every sketch block is numerically rank-deficient and
+    the QR completes it from rounding noise, which varies from run to run (the FP64 products that
+    form M_k sum with atomics).  The completing directions must still be orthonormal, every run."""
+    x = WL.c1()
+    cores = dev(x.cores)
+    for _ in range(12):
+        with B.round_fixed(cores, 13, 31) as y:
+            got = y.to_numpy()
+        assert T.left_orth_defect(got) <= 1e-12
+        assert T.tt_dist(got, x.cores) <= 1e-10 * x.norm
+
+
 def test_fixed_c1_target(B):
     x = WL.c1()
     Y, _ = R.tt_round_fixed(x.cores, 13, seed=31)
