@@ -46,6 +46,9 @@ and the SVD (numpy.linalg.svd).  Readings of points where the paper is silent or
       adaptive counterpart of R6).  Without it an initial block wider than that rank (possible
       with the appendix's b_init = max_i r_k^(i) at the last cores) would sketch an exactly
       rank-deficient matrix.
+  R15 A zero tensor: when ||X|| (given, or estimated by Eq. (3.6)) is 0, the rounding is the zero
+      TT of ranks 1 (there is no subspace to sketch; tau would be 0).  The estimate is 0 only for
+      X = 0, with probability one.
   R13 Sum of TTs, the last core: the appendix writes H(Y_{k+1}) = [Y^(1) ... Y^(s)] for every k.
       For k + 1 = d the summands' last cores share the right bond 1 (the formal sum stacks them
       vertically), so H(Y_d) = sum_i M^(i) H(X_d^(i)); for k + 1 < d the blocks sit side by side
@@ -150,6 +153,17 @@ def residual_sketch(sk: _Sketches, Z: np.ndarray, Q: np.ndarray, k: int, b: int)
     return S - Q @ (Q.T @ S)                                       # Eq. (3.5)
 
 
+def _zero_tt(n) -> list:
+    """The zero TT of ranks 1 with mode sizes n (reading R15)."""
+    return [np.zeros((1, int(v), 1)) for v in n]
+
+
+def _zero_result(n, nrmx, w0, width, extensions):
+    d = len(n)
+    return _zero_tt(n), {"ranks": [1] * (d + 1), "tau": 0.0, "nrmx": nrmx, "estimates": [[] for _ in range(d - 1)],
+                         "width": width, "extensions": extensions, "w0": w0}
+
+
 def right_bound(n, k: int) -> int:
     """prod_{j>k} n_j (1-based k), capped well above any rank (reading R14)."""
     p = 1
@@ -173,6 +187,8 @@ def tt_round_adaptive(cores, tol: float, seed: int, block: int = 0, f_init: floa
     sk = _Sketches(cores, seed, w0)                                # Omega_2..Omega_d, W_2..W_d
     if nrmx is None:
         nrmx = norm_estimate(cores[0], sk.W[2][:, :w0])
+    if nrmx == 0.0:                                                # R15
+        return _zero_result(n, nrmx, w0, sk.width, sk.extensions)
     tau = tol * nrmx / math.sqrt(d - 1)
     Y = [None] * d
     Yk = cores[0].copy()                                           # Y_1 = X_1
@@ -273,6 +289,10 @@ def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_ini
     Yk = np.concatenate([x[0] for x in summands], axis=2)          # Y_1 = [X_1^(1) ... X_1^(s)]
     if nrmx is None:
         nrmx = norm_estimate(Yk, sk.W[2][:, :w0])
+    if nrmx == 0.0:                                                # R15
+        Y, info = _zero_result(n, nrmx, w0, sk.width, sk.extensions)
+        info.update({"b_init": [], "formal_ranks": [1] + [off[k][-1] for k in range(1, d)] + [1]})
+        return Y, info
     tau = tol * nrmx / math.sqrt(d - 1)
     Y = [None] * d
     out_ranks, ests, b_inits = [1], [], []

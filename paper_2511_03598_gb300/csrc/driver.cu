@@ -888,6 +888,38 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
     nrmx = sqrt(ss) / sqrt((double)w0);
     if (!isfinite(nrmx)) return set_error("non-finite norm estimate"), TTR_ERR_NONFINITE;
   }
+  if (nrmx == 0.0) {
+    // X = 0 (the estimate vanishes only then, with probability one): the zero TT of ranks 1
+    // (reading R15)
+    TTR_CHECK(result_alloc(c, X.shape(), out));
+    double* arena = (double*)out->arena;
+    int64_t off = 0;
+    for (int k = 0; k < d; ++k) {
+      out->cores[k] = arena + off;
+      out->ranks[k] = 1;
+      off += X.n[k];
+    }
+    out->ranks[d] = 1;
+    TTR_CUDA(cudaMemsetAsync(arena, 0, sizeof(double) * off, stream));
+    tm.rec(1, stream);
+    tm.rec(2, stream);
+    TTR_CUDA(cudaStreamSynchronize(stream));
+    TTR_CHECK(check_device_flags(c));
+    out->tau = 0.0;
+    out->nrmx = 0.0;
+    out->width = s.width;
+    out->extensions = s.extensions;
+    out->n_estimates = 0;
+    out->estimates = (double*)calloc(1, sizeof(double));
+    out->est_core = (int32_t*)calloc(1, sizeof(int32_t));
+    if (!out->estimates || !out->est_core) return set_error("host allocation"), TTR_ERR_OOM;
+    out->ms_sketch_rl = tm.ms(0, 1);
+    out->ms_total = tm.ms(0, 2);
+    out->kernel_launches = c.launches;
+    c.time_collect(out);
+    disown(c, out->arena);
+    return TTR_OK;
+  }
   const double tau = tol * nrmx / sqrt((double)(d - 1));
   tm.rec(1, stream);
   Sweep w;

@@ -192,3 +192,21 @@ def test_first_block_wider_than_the_last_unfolding():
     Y, info = R.tt_round_adaptive_sum(xs, 1e-10, 3, block=0, nrmx=float(np.linalg.norm(X)))
     assert info["ranks"][4] <= 4 and info["b_init"][3] <= 4
     assert np.linalg.norm(T.full(Y) - X) <= 1e-10 * np.linalg.norm(X)
+
+
+def test_zero_tensor_rounds_to_the_zero_tt():
+    """Reading R15: ||X|| = 0 (estimated here) gives the zero TT of ranks 1, for one TT and a sum."""
+    x = [np.zeros_like(c) for c in WL.random_tt(np.random.default_rng(1), 4, 5, 3)]
+    for Y, info in (R.tt_round_adaptive(x, 1e-6, 3, block=2), R.tt_round_adaptive_sum([x, x], 1e-6, 3, block=0)):
+        assert info["ranks"] == [1, 1, 1, 1, 1] and info["nrmx"] == 0.0
+        assert T.tt_norm(Y) == 0.0 and T.modes(Y) == T.modes(x)
+
+
+def test_two_cores():
+    """d = 2: no partial-contraction step, one sketched core; the sum equals the formal-sum rounding."""
+    xs = summands_of(17, 2, [9, 7], [3, 4], coef=[1.0, 0.5])
+    xf = formal_sum(xs)
+    Ys, infs = R.tt_round_adaptive_sum(xs, 1e-12, 2, block=2)
+    Yf, inff = R.tt_round_adaptive(xf, 1e-12, 2, block=2)
+    assert infs["ranks"] == inff["ranks"] == [1, 7, 1]
+    assert T.tt_dist(Ys, xf) <= 1e-12 * T.tt_norm(xf)

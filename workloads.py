@@ -97,7 +97,10 @@ def block_sum(terms) -> list:
 
 
 def copies_plus_noise(seed: int, d: int, n: int, r: int, copies: int, noise_rank: int, eta: float,
-                      name: str) -> TTInput:
+                      name: str, formal: bool = True) -> TTInput:
+    """Scaled copies of one random TT plus a small random TT.  ``formal=False`` leaves out the
+    block-diagonal formal sum (``cores`` empty) and keeps only the summands, for inputs whose
+    formal sum is too large to build on the host (c5: 25 GB)."""
     rng = np.random.default_rng(seed)
     T = random_tt(rng, d, n, r)
     while True:
@@ -113,7 +116,7 @@ def copies_plus_noise(seed: int, d: int, n: int, r: int, copies: int, noise_rank
     meta = {"seed": seed, "d": d, "n": n, "r": r, "copies": copies, "noise_rank": noise_rank,
             "eta": eta, "coef": c.tolist(), "true_rank": r + noise_rank}
     summands = [[ci * T[0]] + T[1:] for ci, T in ((float(c_), T) for c_ in c)] + [N]
-    return TTInput(name, block_sum(terms), math.sqrt(norm2), meta, summands)
+    return TTInput(name, block_sum(terms) if formal else [], math.sqrt(norm2), meta, summands)
 
 
 def c1(seed: int = 1) -> TTInput:
@@ -124,8 +127,8 @@ def c2(seed: int = 2) -> TTInput:
     return copies_plus_noise(seed, 20, 50, 50, 4, 10, 1e-7, "c2_d20_n50_r50x4+10")
 
 
-def c5(seed: int = 5) -> TTInput:
-    return copies_plus_noise(seed, 50, 100, 200, 4, 10, 1e-8, "c5_d50_n100_r200x4+10")
+def c5(seed: int = 5, formal: bool = True) -> TTInput:
+    return copies_plus_noise(seed, 50, 100, 200, 4, 10, 1e-8, "c5_d50_n100_r200x4+10", formal)
 
 
 def laplace_tt_operator(d: int, n: int) -> list:
