@@ -145,6 +145,38 @@ def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
         srv.close()
 
 
+def sum_round_run(B, x, opts, args, world, stream, barrier, single, out_ranks) -> dict:
+    """The workload as its summands, rounded without forming the formal sum (Remark 3.3, Appendix C):
+    one at a time on one stream, CUDA events around each call as in `single_stream`."""
+    import torch
+    dev_of = {}
+    summands = [[dev_of.setdefault(id(c), torch.from_numpy(np.ascontiguousarray(c)).to("cuda")) for c in part]
+                for part in x.summands]
+    for _ in range(args.warmup):
+        with B.round_adaptive_sum(summands, TOL, BLOCK, SEED, opts) as y:
+            sum_ranks = y.ranks
+    sum_steps = max(3, min(args.steps, 100))
+    barrier()
+    sev = [torch.cuda.Event(enable_timing=True) for _ in range(sum_steps + 1)]
+    sev[0].record(stream)
+    for i in range(sum_steps):
+        y = B.round_adaptive_sum(summands, TOL, BLOCK, SEED, opts)
+        sum_ranks = y.ranks
+        y.free()
+        sev[i + 1].record(stream)
+    barrier()
+    sum_step_ms = [sev[i].elapsed_time(sev[i + 1]) for i in range(sum_steps)]
+    sum_ms = max_over_ranks(sev[0].elapsed_time(sev[-1]), world, "cuda")
+    sum_round = {"roundings_per_s": job_rate(sum_steps, world, sum_ms), "ms_per_rounding": sum_ms / sum_steps,
+                 "p50_ms": float(np.percentile(sum_step_ms, 50)), "p99_ms": float(np.percentile(sum_step_ms, 99)),
+                 "steps": sum_steps, "summands": len(summands), "ranks_out": sum_ranks,
+                 "ranks_equal_formal": sum_ranks == out_ranks,
+                 "speedup_over_formal_single_stream": single["ms_per_rounding"] / (sum_ms / sum_steps),
+                 "note": "tt_round_adaptive_sum on the 4 scaled copies + noise TT (copies share their cores after the "
+                         "first), one stream; compare with single_stream, the formal sum of the same input"}
+    return sum_round
+
+
 def max_over_ranks(ms: float, world: int, device) -> float:
     """The job's time: the largest of the ranks' timed regions (all_reduce MAX when world > 1)."""
     import torch
@@ -421,35 +453,16 @@ def main():
     roof_other = [r for r in cand if r is not roof]
 
     # ---- the same input as its summands, rounded without forming the formal sum (Remark 3.3,
-    # Appendix C): one at a time on one stream, CUDA events around each call as in `single_stream`
-    dev_of = {}
-    summands = [[dev_of.setdefault(id(c), torch.from_numpy(np.ascontiguousarray(c)).to("cuda")) for c in part]
-                for part in x.summands]
-    for _ in range(args.warmup):
-        with B.round_adaptive_sum(summands, TOL, BLOCK, SEED, opts) as y:
-            sum_ranks = y.ranks
-    sum_steps = max(3, min(args.steps, 100))
-    barrier()
-    sev = [torch.cuda.Event(enable_timing=True) for _ in range(sum_steps + 1)]
-    sev[0].record(stream)
-    for i in range(sum_steps):
-        y = B.round_adaptive_sum(summands, TOL, BLOCK, SEED, opts)
-        sum_ranks = y.ranks
-        y.free()
-        sev[i + 1].record(stream)
-    barrier()
-    sum_step_ms = [sev[i].elapsed_time(sev[i + 1]) for i in range(sum_steps)]
-    sum_ms = max_over_ranks(sev[0].elapsed_time(sev[-1]), world, "cuda")
-    sum_round = {"roundings_per_s": job_rate(sum_steps, world, sum_ms), "ms_per_rounding": sum_ms / sum_steps,
-                 "p50_ms": float(np.percentile(sum_step_ms, 50)), "p99_ms": float(np.percentile(sum_step_ms, 99)),
-                 "steps": sum_steps, "summands": len(summands), "ranks_out": sum_ranks,
-                 "ranks_equal_formal": sum_ranks == out_ranks,
-                 "speedup_over_formal_single_stream": single["ms_per_rounding"] / (sum_ms / sum_steps),
-                 "note": "tt_round_adaptive_sum on the 4 scaled copies + noise TT (copies share their cores after the "
-                         "first), one stream; compare with single_stream, the formal sum of the same input"}
-
-    # ---- the serving stream through the library's request server
-    serving = serving_run(B, args.serve_requests, args.streams, 120 << 30) if args.serve_requests > 0 else None
+    # Appendix C), and the serving stream through the library's request server.  Both are reported
+    # beside the headline; a failure in either is recorded in its object, not raised.
+    try:
+        sum_round = sum_round_run(B, x, opts, args, world, stream, barrier, single, out_ranks)
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        sum_round = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        serving = serving_run(B, args.serve_requests, args.streams, 120 << 30) if args.serve_requests > 0 else None
+    except Exception as e:  # noqa: BLE001
+        serving = {"error": f"{type(e).__name__}: {e}"}
 
     # ---- deterministic FP64 TT-rounding on the same GPU (the comparison the metric names)
     det_ms = []
