@@ -25,7 +25,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 // private to this process and this library; it changes no device setting.
 static constexpr uint64_t kPoolKeepBytes = 8ull << 30;
 
-static cudaMemPool_t library_pool(cudaStream_t stream) {
+cudaMemPool_t library_pool(cudaStream_t stream) {
   static std::mutex mu;
   static cudaMemPool_t pools[64] = {};
   int dev = -1;

@@ -111,7 +111,10 @@ void run_request(Request& q, cudaStream_t stream) {
       total += q.r[i][k] * q.n[k] * q.r[i][k + 1];
     }
   double* dev = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&dev, sizeof(double) * std::max<int64_t>(total, 1), stream);
+  const size_t bytes = sizeof(double) * std::max<int64_t>(total, 1);
+  cudaMemPool_t pool = ttr::library_pool(stream);   // keeps the freed input copy for the next request
+  cudaError_t e = pool ? cudaMallocFromPoolAsync((void**)&dev, bytes, pool, stream)
+                       : cudaMallocAsync((void**)&dev, bytes, stream);
   if (e != cudaSuccess) {
     out.status = TTR_ERR_OOM;
     return;

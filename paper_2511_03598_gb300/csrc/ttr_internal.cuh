@@ -13,6 +13,9 @@ namespace ttr {
 
 // ----------------------------------------------------------------------------- errors
 void set_error(const std::string& msg);
+// The library's stream-ordered memory pool of the current device (keeps freed memory for reuse);
+// nullptr if it cannot be made (callers then use the device's default pool).
+cudaMemPool_t library_pool(cudaStream_t stream);
 
 #define TTR_CUDA(call)                                                              \
   do {                                                                              \
