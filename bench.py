@@ -113,7 +113,7 @@ def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
     try:
         # warm-up: the smallest request once (kernel attributes, memory pool)
         small = min(reqs, key=lambda q: q.tt.meta["formal_bytes"])
-        srv.wait(srv.submit(small.tt.summands, small.tol, 0, 7, opts_for(small)))
+        srv.wait(srv.submit(small.tt.summands, small.tol, 0, 7, opts_for(small)), fetch=False)
         out = {}
         for mode in ("closed_loop", "open_loop"):
             t0 = time.perf_counter()
@@ -126,7 +126,7 @@ def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
                 ids.append(srv.submit(q.tt.summands, q.tol, 0, 1000 + q.rid, opts_for(q)))
             lat, ranks_max = [], 0
             for rid in ids:
-                cores, info = srv.wait(rid)
+                _, info = srv.wait(rid, fetch=False)   # result already in host memory (the worker's D2H)
                 lat.append(info["ms_queue"] + info["ms_run"])
                 ranks_max = max(ranks_max, max(info["ranks"]))
             span = time.perf_counter() - t0
@@ -183,13 +183,13 @@ def e2e_server_run(B, host, opts, workers: int, steps: int):
     its result copied back to host memory.  Returns (roundings/s, result bytes, steps)."""
     arrays = [h.numpy() for h in host]                       # views of the pinned buffers
     with B.Server(workers=workers, device_budget=64 << 30) as srv:
-        srv.wait(srv.submit([arrays], TOL, BLOCK, SEED, opts))   # warm-up
+        srv.wait(srv.submit([arrays], TOL, BLOCK, SEED, opts), fetch=False)   # warm-up
         t0 = time.perf_counter()
         ids = [srv.submit([arrays], TOL, BLOCK, SEED, opts) for _ in range(steps)]
         d2h = 0
         for rid in ids:
-            cores, _ = srv.wait(rid)
-            d2h = sum(c.nbytes for c in cores)
+            _, info = srv.wait(rid, fetch=False)   # the worker has copied the result to host memory
+            d2h = info["result_bytes"]
         dt = time.perf_counter() - t0
     return steps / dt, d2h, steps
 

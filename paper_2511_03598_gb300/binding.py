@@ -391,8 +391,10 @@ class Server:
         self._keep[rid.value] = (keep, modes)
         return rid.value
 
-    def wait(self, rid: int):
-        """(cores as numpy arrays, info) of request rid; raises TTRoundError if it failed."""
+    def wait(self, rid: int, fetch: bool = True):
+        """(cores as numpy arrays, info) of request rid; raises TTRoundError if it failed.  The
+        result is already in host memory when the request completes; fetch=False skips copying
+        it into numpy arrays (cores is then None) and just releases it."""
         import numpy as np
         res = ServerResult()
         st = lib().ttr_server_wait(self._h, int(rid), ctypes.byref(res))
@@ -401,13 +403,16 @@ class Server:
             if st != 0:
                 raise TTRoundError(st, f"request {rid}: " + res.message.decode(errors="replace"))
             rk = [int(res.ranks[k]) for k in range(res.d + 1)]
-            cores = []
+            cores = [] if fetch else None
+            nbytes = 0
             for k in range(res.d):
                 cnt = rk[k] * modes[k] * rk[k + 1]
-                a = np.ctypeslib.as_array(res.cores[k], shape=(cnt,)).copy()
-                cores.append(a.reshape(rk[k], modes[k], rk[k + 1]))
+                nbytes += 8 * cnt
+                if fetch:
+                    a = np.ctypeslib.as_array(res.cores[k], shape=(cnt,)).copy()
+                    cores.append(a.reshape(rk[k], modes[k], rk[k + 1]))
             info = {"ranks": rk, "ms_queue": res.ms_queue, "ms_run": res.ms_run, "footprint": int(res.footprint),
-                    "bytes_in": int(res.bytes_in), "admit_order": int(res.admit_order)}
+                    "bytes_in": int(res.bytes_in), "admit_order": int(res.admit_order), "result_bytes": nbytes}
             return cores, info
         finally:
             lib().ttr_server_result_free(ctypes.byref(res))
