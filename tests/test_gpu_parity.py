@@ -255,3 +255,17 @@ def test_bad_arguments_raise(B):
         B.round_adaptive(dev(x.cores), 0.0, 2, 1)
     with pytest.raises(B.TTRoundError):
         B.round_fixed(dev(x.cores), 0, 1)
+
+
+@pytest.mark.parametrize("slices", [3, 4, 5, 6, 7, 8])
+def test_partial_contractions_every_slice_count(B, slices):
+    """The tensor-core issue loop is compiled per slice count; each one against the oracle, within
+    the sliced form's stated error s * 2^(1-7s) of sum |a||b| (sum |a||b| <= 50 max|W| here, with a
+    margin of 10), and at the FP64 floor for the counts that reach it."""
+    cores = WL.random_tt(np.random.default_rng(8), 5, [6, 9, 4, 7, 5], [12, 40, 9, 30])
+    got = B.partial_contractions(dev(cores), 21, 0, 80, precision=1, slices=slices)
+    ref = R.partial_contractions_rl(cores, 21, 0, 80)
+    bound = max(500.0 * slices * 2.0 ** (1 - 7 * slices), 1e-13)
+    for k, Wk in ref.items():
+        err = np.abs(got[k].cpu().numpy() - Wk).max() / np.abs(Wk).max()
+        assert err <= bound, (slices, k, err, bound)
