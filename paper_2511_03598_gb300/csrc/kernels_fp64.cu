@@ -130,11 +130,23 @@ int gram_tn(Ctx& c, const double* X, int64_t ldx, const double* Y, int64_t ldy, 
 // zeroes *zero_out (an accumulator the next kernel adds into).
 constexpr int GRAM_MAX = 1024;
 
+// acc[q] += X(r, oi[q]) Y(r, oj[q]) over the nr staged rows, for the first NQ output slots
+template <int NQ>
+__device__ __forceinline__ void gram_rows(const double* Xs, const double* Ys, int nr, int a, int b, int ab,
+                                          const int (&oi)[GRAM_MAX / 256], const int (&oj)[GRAM_MAX / 256],
+                                          double (&acc)[GRAM_MAX / 256]) {
+  for (int r = 0; r < nr; ++r) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (threadIdx.x + q * 256 < ab) acc[q] = fma(Xs[r * a + oi[q]], Ys[r * b + oj[q]], acc[q]);
+  }
+}
+
 __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                                                            int64_t m, int a, int b, int64_t rpb, double* ws,
                                                            unsigned* ticket, double* C, int64_t ldc, int chol,
                                                            const double* shift, double* R, double* invd, int* bad,
-                                                           double* zero_out) {
+                                                           double* zero_out, int sym) {
   __shared__ double G[GRAM_MAX];
   __shared__ int last;
   const int ab = a * b;
@@ -150,11 +162,27 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* X, int64
   constexpr int OPT = GRAM_MAX / 256;
   int oi[OPT], oj[OPT];
   double acc[OPT];
+  // sym (X == Y, a == b): only the upper triangle i <= j, b (b + 1) / 2 outputs, row by row
+  const int nout = sym ? a * (a + 1) / 2 : ab;
 #pragma unroll
   for (int q = 0; q < OPT; ++q) {
     const int o = threadIdx.x + q * 256;
-    oi[q] = o < ab ? o / b : 0;
-    oj[q] = o < ab ? o % b : 0;
+    int i = 0, j = 0;
+    if (o < nout) {
+      if (sym) {
+        int rem = o;
+        while (rem >= b - i) {
+          rem -= b - i;
+          ++i;
+        }
+        j = i + rem;
+      } else {
+        i = o / b;
+        j = o % b;
+      }
+    }
+    oi[q] = i;
+    oj[q] = j;
     acc[q] = 0.0;
   }
   for (int64_t t0 = r0; t0 < r1; t0 += tr) {
@@ -163,16 +191,19 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* X, int64
     for (int e = threadIdx.x; e < nr * a; e += blockDim.x) Xs[e] = X[(t0 + e / a) * ldx + e % a];
     for (int e = threadIdx.x; e < nr * b; e += blockDim.x) Ys[e] = Y[(t0 + e / b) * ldy + e % b];
     __syncthreads();
-    for (int r = 0; r < nr; ++r) {
-#pragma unroll
-      for (int q = 0; q < OPT; ++q)
-        if (threadIdx.x + q * 256 < ab) acc[q] = fma(Xs[r * a + oi[q]], Ys[r * b + oj[q]], acc[q]);
+    // only the slots that hold outputs in some thread are issued: FP64 instructions with every
+    // lane masked off still take FP64 pipe time on this part
+    switch ((nout + 255) >> 8) {
+      case 1: gram_rows<1>(Xs, Ys, nr, a, b, nout, oi, oj, acc); break;
+      case 2: gram_rows<2>(Xs, Ys, nr, a, b, nout, oi, oj, acc); break;
+      case 3: gram_rows<3>(Xs, Ys, nr, a, b, nout, oi, oj, acc); break;
+      default: gram_rows<4>(Xs, Ys, nr, a, b, nout, oi, oj, acc); break;
     }
   }
 #pragma unroll
   for (int q = 0; q < OPT; ++q) {
     const int o = threadIdx.x + q * 256;
-    if (o < ab) ws[(int64_t)blockIdx.x * ab + o] = acc[q];
+    if (o < nout) ws[(int64_t)blockIdx.x * ab + oi[q] * b + oj[q]] = acc[q];
   }
   (void)warp;
   (void)lane;
@@ -185,15 +216,20 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* X, int64
   __threadfence();
   // the partials of the other CTAs are read through L2 (__ldcg): L1 is not coherent across SMs
   // and the workspace is reused by every reduction of the call
+  // eight independent partial sums keep eight L2 loads in flight per thread
   for (int o = threadIdx.x; o < ab; o += blockDim.x) {
-    double t0 = 0.0, t1 = 0.0;
+    // the symmetric Gram keeps its partials in the upper triangle
+    const int src = (sym && o / b > o % b) ? (o % b) * b + o / b : o;
+    double t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = 0.0;
     unsigned blk = 0;
-    for (; blk + 1 < gridDim.x; blk += 2) {
-      t0 += __ldcg(ws + (int64_t)blk * ab + o);
-      t1 += __ldcg(ws + (int64_t)(blk + 1) * ab + o);
+    for (; blk + 8 <= gridDim.x; blk += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] += __ldcg(ws + (int64_t)(blk + u) * ab + src);
     }
-    if (blk < gridDim.x) t0 += __ldcg(ws + (int64_t)blk * ab + o);
-    const double v = t0 + t1;
+    for (; blk < gridDim.x; ++blk) t[0] += __ldcg(ws + (int64_t)blk * ab + src);
+    const double v = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
     G[o] = v;
     if (C) C[(o / b) * ldc + (o % b)] = v;
   }
@@ -246,8 +282,9 @@ int gram_reduce(Ctx& c, const double* X, int64_t ldx, const double* Y, int64_t l
   int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(128, m / 64));
   const int64_t rpb = (std::max<int64_t>(m, 1) + blocks - 1) / blocks;
   blocks = std::max<int64_t>(1, (m + rpb - 1) / rpb);
+  const int sym = (X == Y && ldx == ldy && a == b) ? 1 : 0;
   gram_reduce_kernel<<<(unsigned)blocks, 256, 0, c.stream>>>(X, ldx, Y, ldy, m, (int)a, (int)b, rpb, c.ws, c.ws_ticket,
-                                                              C, ldc, chol, shift, R, invd, bad, zero_out);
+                                                              C, ldc, chol, shift, R, invd, bad, zero_out, sym);
   return c.check_launch("gram_reduce");
 }
 
