@@ -319,9 +319,16 @@ int ttr_server_wait(ttr_server* S, int64_t id, ttr_server_result* out) {
     auto it = S->all.find(id);
     if (it == S->all.end()) return ttr::set_error("unknown or already collected request id"), TTR_ERR_ARG;
     Request* p = it->second.get();
-    S->cv_done.wait(lock, [&] { return p->done; });
-    q = std::move(it->second);
-    S->all.erase(it);
+    // p stays valid while the entry is in the map; another thread waiting for the same id may
+    // collect it first, so look the entry up again after waking
+    S->cv_done.wait(lock, [&] {
+      auto jt = S->all.find(id);
+      return jt == S->all.end() || jt->second.get() != p || p->done;
+    });
+    auto jt = S->all.find(id);
+    if (jt == S->all.end() || jt->second.get() != p) return ttr::set_error("request collected by another wait"), TTR_ERR_ARG;
+    q = std::move(jt->second);
+    S->all.erase(jt);
   }
   *out = q->res;
   return q->res.status;
