@@ -156,12 +156,17 @@ def sum_round_run(B, x, opts, args, world, stream, barrier, single, out_ranks) -
         with B.round_adaptive_sum(summands, TOL, BLOCK, SEED, opts) as y:
             sum_ranks = y.ranks
     sum_steps = max(3, min(args.steps, 100))
+    topts = B.options(precision=opts.precision, nrmx=opts.nrmx, kernel_timing=True)
+    kt = {"ms_block_loop": 0.0, "ms_rl_kernel": 0.0, "bytes_rl_kernel": 0.0, "n_rl_kernel": 0}
     barrier()
     sev = [torch.cuda.Event(enable_timing=True) for _ in range(sum_steps + 1)]
     sev[0].record(stream)
     for i in range(sum_steps):
-        y = B.round_adaptive_sum(summands, TOL, BLOCK, SEED, opts)
+        y = B.round_adaptive_sum(summands, TOL, BLOCK, SEED, topts)
         sum_ranks = y.ranks
+        res = y.result
+        for key in kt:
+            kt[key] += getattr(res, key)
         y.free()
         sev[i + 1].record(stream)
     barrier()
@@ -172,6 +177,14 @@ def sum_round_run(B, x, opts, args, world, stream, barrier, single, out_ranks) -
                  "steps": sum_steps, "summands": len(summands), "ranks_out": sum_ranks,
                  "ranks_equal_formal": sum_ranks == out_ranks,
                  "speedup_over_formal_single_stream": single["ms_per_rounding"] / (sum_ms / sum_steps),
+                 "share_of_step": {"block_loop": kt["ms_block_loop"] / max(sum_ms, 1e-9),
+                                   "partial_contractions": kt["ms_rl_kernel"] / max(sum_ms, 1e-9)},
+                 "partial_contractions": None if not kt["n_rl_kernel"] else {
+                     "kernel": "grouped partial contractions (one launch per core for all summands)",
+                     "ms_per_launch": kt["ms_rl_kernel"] / kt["n_rl_kernel"],
+                     "achieved_gbs": kt["bytes_rl_kernel"] / (kt["ms_rl_kernel"] / 1e3) / 1e9,
+                     "bytes_per_launch": kt["bytes_rl_kernel"] / kt["n_rl_kernel"],
+                     "hbm_frac": kt["bytes_rl_kernel"] / (kt["ms_rl_kernel"] / 1e3) / 1e9 / peaks()[0]["hbm_gbs"]},
                  "note": "tt_round_adaptive_sum on the 4 scaled copies + noise TT (copies share their cores after the "
                          "first), one stream; compare with single_stream, the formal sum of the same input"}
     return sum_round
