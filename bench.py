@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -207,6 +208,95 @@ def e2e_server_run(B, host, opts, workers: int, steps: int):
     return steps / dt, d2h, steps
 
 
+def configs_table(B, reps: int) -> dict:
+    """Per-configuration timings (the CPU-baseline plan's table): for C1, C2, C3 the GPU
+    deterministic FP64 rounding, the GPU KRP rounding in FP64 and sliced form, the oracle's
+    deterministic and KRP roundings on the host cores, and the sliced result's distance to the
+    oracle's; for C5 (d=50, n=100, formal rank 810, through the sum entry point: its formal sum is
+    25 GB) the GPU KRP roundings and the sliced result's error from FP64 inner products.  GPU times
+    are CUDA-event medians over `reps` calls, host times wall-clock medians."""
+    import torch
+    import workloads as WL
+    from oracle import rounding as OR
+    from oracle import tt as OT
+
+    def gpu_ms(fn, n):
+        # one untimed call, then n timed ones; the last result is copied to the host after its timing
+        st = torch.cuda.current_stream()
+        ts, ranks, res = [], None, None
+        for i in range(n + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            y = fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            ranks = y.ranks
+            if i == n:
+                res = y.to_numpy()
+            y.free()
+            if i > 0:
+                ts.append(a.elapsed_time(b))
+        return float(np.median(ts)), ranks, res
+
+    def cpu_ms(fn, n):
+        ts, out = [], None
+        for _ in range(n):
+            t0 = time.perf_counter()
+            out = fn()
+            ts.append(1e3 * (time.perf_counter() - t0))
+        return float(np.median(ts)), out
+
+    rows = []
+    sl, fp = B.options(precision=B.TTR_PREC_SLICED), B.options(precision=B.TTR_PREC_FP64)
+    for name, x, tol, mode, block in (("c1", WL.c1(), 1e-6, "fixed", 0), ("c2", WL.c2(), 1e-6, "adaptive", 10),
+                                      ("c3", WL.c3(), 1e-8, "adaptive", 0)):
+        cores = [torch.from_numpy(c).to("cuda") for c in x.cores]
+        for o in (sl, fp):
+            o.nrmx = x.norm
+        if mode == "fixed":       # fixed rank 8 from a sketch of 13 (oversampling 5)
+            krp = lambda o: (lambda: B.round_fixed(cores, 13, SEED, target=8, opts=o))
+            oracle_krp = lambda: OR.svd_pass_rl(OR.tt_round_fixed(x.cores, 13, SEED)[0], max_rank=8)
+        else:
+            krp = lambda o: (lambda: B.round_adaptive(cores, tol, block, SEED, o))
+            oracle_krp = lambda: OR.tt_round_adaptive(x.cores, tol, SEED, block=block, nrmx=x.norm)[0]
+        det_n = 2 if name == "c2" else reps
+        g_det, det_ranks, _ = gpu_ms(lambda: B.round_deterministic(cores, tol), det_n)
+        g_fp, fp_ranks, y_fp = gpu_ms(krp(fp), reps)
+        g_sl, sl_ranks, y_sl = gpu_ms(krp(sl), max(reps, 20))
+        c_det, _ = cpu_ms(lambda: OR.tt_round_deterministic(x.cores, tol), 3)
+        c_krp, y_or = cpu_ms(oracle_krp, 5)
+        rows.append({"config": name, "mode": mode, "tol": tol, "cpu_cores": host_cores(),
+                     "oracle_det_ms": c_det, "oracle_krp_ms": c_krp, "gpu_det_fp64_ms": g_det,
+                     "gpu_krp_fp64_ms": g_fp, "gpu_krp_sliced_ms": g_sl, "ranks_krp": sl_ranks,
+                     "ranks_equal_fp64": sl_ranks == fp_ranks, "ranks_det": det_ranks,
+                     "err_sliced_vs_oracle": OT.tt_dist(y_sl, y_or) / OT.tt_norm(y_or),
+                     "err_fp64_vs_oracle": OT.tt_dist(y_fp, y_or) / OT.tt_norm(y_or)})
+        del cores
+    x = WL.c5(formal=False)
+    cache = {}
+    summ = [[cache.setdefault(id(c), torch.from_numpy(np.ascontiguousarray(c)).to("cuda")) for c in part]
+            for part in x.summands]
+    sl.nrmx = fp.nrmx = x.norm
+    g_sl, sl_ranks, _ = gpu_ms(lambda: B.round_adaptive_sum(summ, 1e-6, 0, SEED, sl), 2)
+    g_fp, fp_ranks, _ = gpu_ms(lambda: B.round_adaptive_sum(summ, 1e-6, 0, SEED, fp), 1)
+    y = B.round_adaptive_sum(summ, 1e-6, 0, SEED, sl)
+    Y = y.to_torch()
+    y.free()
+
+    def inner(xs, ys):
+        g = torch.ones((1, 1), dtype=torch.float64, device="cuda")
+        for a, b in zip(xs, ys):
+            g = torch.tensordot(torch.tensordot(g, a, dims=([0], [0])), b, dims=([0, 1], [0, 1]))
+        return float(g.reshape(-1)[0])
+
+    err2 = x.norm ** 2 + inner(Y, Y) - 2.0 * sum(inner(p, Y) for p in summ)
+    rows.append({"config": "c5", "mode": "adaptive, sum of 5 TTs (formal sum not formed)", "tol": 1e-6,
+                 "gpu_krp_fp64_ms": g_fp, "gpu_krp_sliced_ms": g_sl, "ranks_krp_middle": sl_ranks[len(sl_ranks) // 2],
+                 "ranks_equal_fp64": sl_ranks == fp_ranks, "err_sliced_vs_x": math.sqrt(max(err2, 0.0)) / x.norm,
+                 "note": "no oracle or deterministic columns: the formal sum is 25 GB"})
+    return {"configs": rows}
+
+
 def max_over_ranks(ms: float, world: int, device) -> float:
     """The job's time: the largest of the ranks' timed regions (all_reduce MAX when world > 1)."""
     import torch
@@ -377,6 +467,8 @@ def main():
     ap.add_argument("--det-steps", type=int, default=2)
     ap.add_argument("--streams", type=int, default=3, help="roundings in flight at once (one stream each)")
     ap.add_argument("--only-main", action="store_true", help="timed rounding loop only (for profiler runs)")
+    ap.add_argument("--configs", action="store_true",
+                    help="print the per-configuration table (GPU and oracle times) instead of the bench line")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving stream run through the request server (0: skip)")
     args = ap.parse_args()
@@ -397,6 +489,10 @@ def main():
         dist.init_process_group("nccl")
     from paper_2511_03598_gb300 import binding as B
     B.lib()
+    if args.configs:
+        if rank == 0:
+            print(json.dumps(configs_table(B, 5)), flush=True)
+        return
     prec = B.TTR_PREC_SLICED if args.precision == "sliced" else B.TTR_PREC_FP64
     opts = B.options(precision=prec, nrmx=x.norm)
     topts = B.options(precision=prec, nrmx=x.norm, kernel_timing=True)
