@@ -350,7 +350,10 @@ class Server:
     """The library's request server (ttr_server_*): requests are sums of TTs in host memory, admitted
     in arrival order within a device-memory budget and rounded by `workers` threads at once."""
 
-    def __init__(self, workers: int = 3, device_budget: int = 64 << 30, max_sms: int = 0, device: int = 0):
+    def __init__(self, workers: int = 3, device_budget: int = 64 << 30, max_sms: int = 0, device: int | None = None):
+        if device is None:   # the caller's current CUDA device (one server per rank under torchrun)
+            import torch
+            device = torch.cuda.current_device() if torch.cuda.is_available() else 0
         cfg = ServerConfig(int(workers), int(max_sms), int(device_budget), int(device))
         h = ctypes.c_void_p()
         _check(lib().ttr_server_create(ctypes.byref(cfg), ctypes.byref(h)))
