@@ -585,14 +585,18 @@ def main():
         sum_round = sum_round_run(B, x, opts, args, world, stream, barrier, single, out_ranks)
     except Exception as e:  # noqa: BLE001 - reported in the JSON line
         sum_round = {"error": f"{type(e).__name__}: {e}"}
+    # The serving stream and the deterministic baselines repeat one GPU's figures on every rank; with
+    # several ranks (all GPUs held) they run only at N = 1.
+    single_gpu = world == 1
     try:
-        serving = serving_run(B, args.serve_requests, args.streams, 120 << 30) if args.serve_requests > 0 else None
+        serving = (serving_run(B, args.serve_requests, args.streams, 120 << 30)
+                   if args.serve_requests > 0 and single_gpu else None)
     except Exception as e:  # noqa: BLE001
         serving = {"error": f"{type(e).__name__}: {e}"}
 
     # ---- deterministic FP64 TT-rounding on the same GPU (the comparison the metric names)
-    det_ms = []
-    for i in range(args.det_steps + 1):
+    det_ms, det_ranks, tdet_ms, tdet_ranks = [], None, [], None
+    for i in range(args.det_steps + 1 if single_gpu else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with B.round_deterministic(cores, TOL) as z:
@@ -602,8 +606,7 @@ def main():
             det_ms.append(1e3 * (time.perf_counter() - t0))
 
     # ---- the same algorithm on torch's FP64 cuSOLVER QR/SVD, as context for that comparison
-    tdet_ms = []
-    for i in range(max(1, args.det_steps) + 1):
+    for i in range(max(1, args.det_steps) + 1 if single_gpu else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tdet_ranks = torch_deterministic(cores, TOL)
@@ -646,11 +649,12 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else
             f"f64 via bf16 slices (tcgen05)", "data": "synthetic",
             "config": config(x, args.streams), "ranks_out": out_ranks, "sketch_width": w, "extensions": info["extensions"],
-            "det_fp64": {"roundings_per_s": 1e3 / float(np.mean(det_ms)), "ms": float(np.mean(det_ms)),
-                         "ranks_out": det_ranks, "speedup_of_adaptive": value / world / (1e3 / float(np.mean(det_ms)))},
-            "det_torch_cusolver_fp64": {"ms": float(np.mean(tdet_ms)), "roundings_per_s": 1e3 / float(np.mean(tdet_ms)),
-                                        "ranks_out": tdet_ranks,
-                                        "note": "Algorithm 1 on torch.linalg.qr/svd (cuSOLVER), FP64, comparison only"},
+            "det_fp64": None if not det_ms else {
+                "roundings_per_s": 1e3 / float(np.mean(det_ms)), "ms": float(np.mean(det_ms)), "ranks_out": det_ranks,
+                "speedup_of_adaptive": value / world / (1e3 / float(np.mean(det_ms)))},
+            "det_torch_cusolver_fp64": None if not tdet_ms else {
+                "ms": float(np.mean(tdet_ms)), "roundings_per_s": 1e3 / float(np.mean(tdet_ms)), "ranks_out": tdet_ranks,
+                "note": "Algorithm 1 on torch.linalg.qr/svd (cuSOLVER), FP64, comparison only"},
             "roofline": roof, "roofline_other": roof_other[0] if roof_other else None, "gpu_launches": int(launches),
             "max_sms_per_stream": conc["max_sms_per_stream"],
             "e2e": e2e,
