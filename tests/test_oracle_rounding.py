@@ -362,3 +362,17 @@ def test_norm_estimator_spread_grows_with_d():
                       for s in range(400)])
         spreads.append(np.std(np.log(v)))
     assert spreads[0] < spreads[1] < spreads[2]
+
+
+def test_adaptive_rank_bounded_by_the_right_part():
+    """Reading R14: with n_d = 2 and formal rank 6, the last unfolding has rank <= 2, so the last
+    rank stays <= 2 even with blocks of 3, and the error is still within tol of the full tensor."""
+    rng = np.random.default_rng(12)
+    base = WL.random_tt(rng, 4, [4, 3, 3, 2], 3)
+    noise = WL.random_tt(rng, 4, [4, 3, 3, 2], 3)
+    cores = WL.block_sum([(1.0, base), (0.5, noise)])
+    assert T.ranks(cores) == [1, 6, 6, 6, 1]
+    X = T.full(cores)
+    Y, info = R.tt_round_adaptive(cores, 1e-10, seed=4, block=3, nrmx=float(np.linalg.norm(X)))
+    assert info["ranks"][3] <= 2
+    assert np.linalg.norm(T.full(Y) - X) <= 1e-10 * np.linalg.norm(X)

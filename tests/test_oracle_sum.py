@@ -210,3 +210,16 @@ def test_two_cores():
     Yf, inff = R.tt_round_adaptive(xf, 1e-12, 2, block=2)
     assert infs["ranks"] == inff["ranks"] == [1, 7, 1]
     assert T.tt_dist(Ys, xf) <= 1e-12 * T.tt_norm(xf)
+
+
+def test_serving_stream_summands_form_its_sums():
+    """The serving stream's requests as summands reproduce their formal sums (small requests)."""
+    for q in WL.c4_stream(count=200, max_bytes=40e6):
+        f = formal_sum(q.tt.summands)
+        assert T.ranks(f) == T.ranks(q.tt.cores)
+        for a, b in zip(f, q.tt.cores):
+            np.testing.assert_array_equal(a, b)
+        assert len(q.tt.summands) == q.tt.meta["s"]
+        break
+    else:
+        pytest.skip("no small request in the first 200")
