@@ -312,7 +312,7 @@ def job_rate(steps: int, world: int, job_ms: float) -> float:
     return world * steps / (job_ms / 1e3)
 
 
-def concurrent_timed(B, cores, opts_kw, streams: int, rounds: int) -> dict:
+def concurrent_timed(B, cores, opts_kw, streams: int, rounds: int, share: int = 0) -> dict:
     """`streams` host threads, each on its own CUDA stream with 1/streams of the SMs for the block
     loop, round the same resident input `rounds` times each (one step = one round of every
     stream).  The span is taken with CUDA events: a reference event on the current stream after a
@@ -321,7 +321,7 @@ def concurrent_timed(B, cores, opts_kw, streams: int, rounds: int) -> dict:
 
     import torch
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    share = max(1, nsm // streams)
+    share = share if share > 0 else max(1, nsm // streams)
     lat = [[] for _ in range(streams)]
     ends = [None] * streams
     launches = [0] * streams
@@ -467,6 +467,8 @@ def main():
     ap.add_argument("--det-steps", type=int, default=2)
     ap.add_argument("--streams", type=int, default=3, help="roundings in flight at once (one stream each)")
     ap.add_argument("--only-main", action="store_true", help="timed rounding loop only (for profiler runs)")
+    ap.add_argument("--max-sms", type=int, default=0,
+                    help="SMs of each in-flight rounding's block loop (0: SMs / streams)")
     ap.add_argument("--configs", action="store_true",
                     help="print the per-configuration table (GPU and oracle times) instead of the bench line")
     ap.add_argument("--serve-requests", type=int, default=24,
@@ -534,7 +536,7 @@ def main():
 
     # ---- the timed batch: every step rounds the input on each of STREAMS streams at once
     barrier()
-    conc = concurrent_timed(B, cores, {"precision": prec, "nrmx": x.norm}, args.streams, args.steps)
+    conc = concurrent_timed(B, cores, {"precision": prec, "nrmx": x.norm}, args.streams, args.steps, args.max_sms)
     barrier()
     clk.stop()
     total_ms = max_over_ranks(conc["span_ms"], world, "cuda")
