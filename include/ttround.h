@@ -136,8 +136,10 @@ int tt_round_fixed(int32_t d, const int64_t* n, const int64_t* r, const double* 
  *   block  > 0: b_init = b_inc = block; <= 0: b = ceil(f * rbar_k) with opts->f_init/f_inc.
  *   seed   as in tt_round_fixed; the first columns of the sketch are those of the fixed call.
  * The loop at core k stops when ||S_k||_F / sqrt(b_inc) <= tau (Eq. (3.5) residual sketch)
- * or when col(Q_k) reaches rbar_k = min(rows, cols of V(Y_k)).  Output cores 1..d-1 are
- * left-orthonormal unless opts->adap_r is set (then cores 2..d are right-orthonormal). */
+ * or when col(Q_k) reaches rbar_k = min(rows, cols of V(Y_k), prod_{j>k} n_j) (the last factor
+ * bounds the rank of V(Y_k) H(X_{k+1:d})).  Output cores 1..d-1 are left-orthonormal unless
+ * opts->adap_r is set (then cores 2..d are right-orthonormal).  A zero tensor (norm 0, given or
+ * estimated) gives the zero TT of ranks 1. */
 int tt_round_adaptive(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
                       double tol, int64_t block, uint64_t seed, const ttr_options* opts,
                       void* stream, ttr_result* out);
@@ -226,7 +228,9 @@ int ttr_server_submit(ttr_server* srv, int32_t s, int32_t d, const int64_t* n, c
                       const ttr_options* opts, int64_t* id);
 
 /* Block until request `id` is done and hand over its result (release with
- * ttr_server_result_free).  Each id can be waited for once; TTR_ERR_ARG for an unknown id. */
+ * ttr_server_result_free).  Each id can be collected once: TTR_ERR_ARG for an unknown or already
+ * collected id, and for all but one of several threads waiting on the same id.  Returns the
+ * request's own status (its error text is in out->message). */
 int ttr_server_wait(ttr_server* srv, int64_t id, ttr_server_result* out);
 
 void ttr_server_result_free(ttr_server_result* res);
