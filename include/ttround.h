@@ -271,15 +271,15 @@ int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r,
 /* Size of the device array that ttr_partial_contractions_noalloc uses as its scratch. */
 #define TTR_STATIC_SCRATCH_BYTES (32u << 20)
 
-/* ttr_partial_contractions (precision TTR_PREC_FP64) for callers that cannot allocate device
- * memory: a host runtime that owns the whole device through its own pool allocator and forbids
- * side allocations, or a code path where an allocation could fail or block.  The paper has no
- * counterpart; this is a packaging of Algorithm 3 with fixed scratch.
+/* The FP64 form of ttr_partial_contractions with its scratch in a static device array, for callers
+ * that cannot allocate device memory: a host runtime that owns the whole device through its own
+ * pool allocator and forbids side allocations, or a code path where an allocation could fail or
+ * block.  The paper has no counterpart.
  *   Arguments, layout of W and results are those of ttr_partial_contractions with
  *   precision = TTR_PREC_FP64; the caller passes the inputs and the outputs W.
  *   Scratch: a file-scope device array of TTR_STATIC_SCRATCH_BYTES (32 MiB) that every GPU which
  *   loads the library's device code holds until the process exits.  The call needs
- *   8 * (ceil((d-t+1)/32)*32 + ((d-t+1) * max_{k>=t} n_k + max_{t<=k<d} r_{k-1} n_k) * (col1-col0))
+ *   8 * ((d-t+1) * max_{k>=t} n_k + max_{t<=k<d} r_{k-1} n_k) * (col1-col0)
  *   bytes of it and returns TTR_ERR_UNSUPPORTED (message in ttr_last_error) beyond the limit,
  *   before any device work.
  *   Allocates nothing: no cudaMalloc / cudaMallocAsync / cudaFree and no allocating library
@@ -289,8 +289,9 @@ int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r,
  *   All calls share the array and a call leaves its contents behind: calls whose work overlaps
  *   on the GPU (different streams, different host threads) race on it.  Calls ordered on one
  *   stream are safe.
- *   Unlike the other calls it does not synchronize: it returns once the work is enqueued on
- *   `stream`, and W is ready when the stream reaches that point. */
+ *   Unlike the other calls it does not synchronize and copies nothing between host and device:
+ *   the mode sizes reach the kernels as kernel parameters.  It returns once its kernels are
+ *   enqueued on `stream`, and W is ready when the stream reaches that point. */
 int ttr_partial_contractions_noalloc(int32_t d, const int64_t* n, const int64_t* r,
                                      const double* const* cores, uint64_t seed, int64_t col0,
                                      int64_t col1, int32_t t, double* const* W, void* stream);

@@ -318,13 +318,27 @@ def partial_contractions_noalloc(cores, seed: int, col0: int, col1: int, t: int 
                                  stream=None) -> dict:
     """FP64 Algorithm 3 through ttr_partial_contractions_noalloc: the library allocates no device
     memory (its scratch is a fixed static array); the outputs {k: W_k} are the caller's, given in
-    `out` or created here.  Enqueued on `stream` without synchronizing."""
+    `out` or created here on the cores' device.  Enqueued on `stream` without synchronizing.
+
+    The C side cannot check buffer sizes, so a given `out` must hold, for k = t..d, a contiguous
+    float64 tensor of shape (r_{k-1}, col1 - col0) on the cores' device (ValueError otherwise)."""
     import torch
     d, n, r, p = _tt_args(cores)
     w = col1 - col0
-    bufs = out if out is not None else {k: torch.empty((r[k - 1], w), dtype=torch.float64, device="cuda")
-                                        for k in range(t, d + 1)}
-    ptrs = (ctypes.c_void_p * d)(*[bufs[k + 1].data_ptr() if (k + 1) in bufs else 0 for k in range(d)])
+    device = cores[0].device
+    if out is None:
+        bufs = {k: torch.empty((r[k - 1], w), dtype=torch.float64, device=device) for k in range(t, d + 1)}
+    else:
+        bufs = out
+        for k in range(t, d + 1):
+            b = bufs.get(k)
+            if not isinstance(b, torch.Tensor):
+                raise ValueError(f"out[{k}] is missing or not a tensor")
+            if b.dtype != torch.float64 or not b.is_contiguous() or b.device != device:
+                raise ValueError(f"out[{k}] must be a contiguous float64 tensor on {device}")
+            if tuple(b.shape) != (r[k - 1], w):
+                raise ValueError(f"out[{k}] has shape {tuple(b.shape)}, expected {(r[k - 1], w)}")
+    ptrs = (ctypes.c_void_p * d)(*[bufs[k + 1].data_ptr() if t <= k + 1 <= d else 0 for k in range(d)])
     _check(lib().ttr_partial_contractions_noalloc(d, n, r, p, ctypes.c_uint64(seed), col0, col1, t, ptrs,
                                                   _stream_handle(stream)))
     return bufs

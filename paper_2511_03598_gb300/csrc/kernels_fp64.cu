@@ -424,17 +424,47 @@ int omega_fill(Ctx& c, uint64_t seed, int32_t k_lo, int32_t k_hi, const int64_t*
   return c.check_launch("omega_fill");
 }
 
-// As omega_fill, with the mode sizes n_k (k = k_lo..k_lo+nc-1) already in device memory and
-// their maximum given: allocates nothing and copies nothing.
-int omega_fill_dev(Ctx& c, uint64_t seed, int32_t k_lo, int32_t nc, const int64_t* nk_dev, int64_t nmax,
-                   int64_t col0, int64_t col1, double* dst, int64_t ostride, int64_t ld) {
+// Mode sizes of up to kOmegaByValue cores, passed to the kernel by value (kernel parameter space),
+// so that filling Omega needs no device copy of them.
+constexpr int kOmegaByValue = 256;
+struct ModeSizes {
+  int64_t n[kOmegaByValue];
+};
+
+__global__ void omega_kernel_byval(uint64_t seed, int32_t k_lo, ModeSizes nk, int64_t col0, int64_t w, double* dst,
+                                   int64_t ostride, int64_t ld) {
+  const int32_t kk = blockIdx.y;                       // core offset within this launch
+  const int64_t n = nk.n[kk];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * w;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / w, j = e % w;
+    const int32_t q = omega_int(seed, (uint32_t)(k_lo + kk), (uint32_t)i, (uint32_t)(col0 + j));
+    dst[kk * ostride + i * ld + j] = (double)q * (1.0 / kOmegaScale);
+  }
+}
+
+// As omega_fill without dst_int, with the mode sizes n_host[0..nc-1] of cores k_lo..k_lo+nc-1 read
+// on the host and handed to the kernels by value (kOmegaByValue cores per launch): allocates nothing
+// and copies nothing.
+int omega_fill_byval(Ctx& c, uint64_t seed, int32_t k_lo, int32_t nc, const int64_t* n_host, int64_t col0,
+                     int64_t col1, double* dst, int64_t ostride, int64_t ld) {
   const int64_t w = col1 - col0;
   if (nc <= 0 || w <= 0) return TTR_OK;
-  const int64_t per = nmax * w;
-  unsigned bx = (unsigned)((per + 255) / 256);
-  if (bx > 1024) bx = 1024;
-  omega_kernel<<<dim3(bx, nc), 256, 0, c.stream>>>(seed, k_lo, nk_dev, col0, w, dst, nullptr, ostride, ld);
-  return c.check_launch("omega_fill");
+  for (int32_t c0 = 0; c0 < nc; c0 += kOmegaByValue) {
+    const int32_t cn = std::min<int32_t>(kOmegaByValue, nc - c0);
+    ModeSizes ms;
+    int64_t nmax = 0;
+    for (int32_t i = 0; i < kOmegaByValue; ++i) ms.n[i] = i < cn ? n_host[c0 + i] : 0;
+    for (int32_t i = 0; i < cn; ++i) nmax = std::max(nmax, ms.n[i]);
+    const int64_t per = nmax * w;
+    unsigned bx = (unsigned)((per + 255) / 256);
+    if (bx > 1024) bx = 1024;
+    if (bx == 0) bx = 1;
+    omega_kernel_byval<<<dim3(bx, cn), 256, 0, c.stream>>>(seed, k_lo + c0, ms, col0, w, dst + (int64_t)c0 * ostride,
+                                                          ostride, ld);
+    TTR_CHECK(c.check_launch("omega_fill"));
+  }
+  return TTR_OK;
 }
 
 // ----------------------------------------------------------------------------- Omega reduction

@@ -75,7 +75,7 @@ int ttr_partial_contractions_noalloc(int32_t d, const int64_t* n, const int64_t*
     if (!W[k - 1] || reinterpret_cast<uintptr_t>(W[k - 1]) % 8 != 0)
       return set_error("W buffers must be non-null and 8-byte aligned"), TTR_ERR_ARG;
 
-  // scratch layout (doubles): [n_t..n_d as int64, padded to 256 B] [Omega_t..Omega_d] [T]
+  // scratch layout (doubles): [Omega_t..Omega_d] [T]
   const int64_t w = col1 - col0;
   const int32_t nc = d - t + 1;
   int64_t nmax = 1;
@@ -85,9 +85,8 @@ int ttr_partial_contractions_noalloc(int32_t d, const int64_t* n, const int64_t*
     const __int128 rows = (__int128)r[k - 1] * n[k - 1];
     if (k < d && rows > rowsmax) rowsmax = rows;
   }
-  const int64_t hdr = ((int64_t)nc + 31) / 32 * 32;
   const bool huge = rowsmax > kScratchDoubles || nmax > kScratchDoubles || w > kScratchDoubles;
-  const __int128 need = huge ? ((__int128)1 << 62) : (__int128)hdr + ((__int128)nc * nmax + rowsmax) * w;
+  const __int128 need = huge ? ((__int128)1 << 62) : ((__int128)nc * nmax + rowsmax) * w;
   if (need > kScratchDoubles) {
     const __int128 bytes = need * 8;
     set_error("ttr_partial_contractions_noalloc needs " +
@@ -99,20 +98,16 @@ int ttr_partial_contractions_noalloc(int32_t d, const int64_t* n, const int64_t*
 
   double* base = nullptr;
   TTR_CHECK(scratch_base(&base));
-  int64_t* nk = reinterpret_cast<int64_t*>(base);
-  double* Om = base + hdr;
+  double* Om = base;
   const int64_t ostride = nmax * w;
   double* T = Om + (int64_t)nc * ostride;   // (max r_{k-1} n_k) x w
 
   Ctx c;   // no allocation below: every device buffer is the caller's or the static scratch
   c.stream = (cudaStream_t)stream;
-  // Pageable stack copy: cudaMemcpyAsync has consumed it by the time it returns.
-  int64_t nh[TTR_MAX_D];
-  for (int32_t i = 0; i < nc; ++i) nh[i] = n[t - 1 + i];
-  TTR_CUDA(cudaMemcpyAsync(nk, nh, sizeof(int64_t) * nc, cudaMemcpyHostToDevice, c.stream));
-  // Every scratch element read below is written earlier in this call (Omega by omega_fill_dev,
-  // T by a non-accumulating GEMM), so nothing left by a previous call needs clearing.
-  TTR_CHECK(omega_fill_dev(c, seed, t, nc, nk, nmax, col0, col1, Om, ostride, w));
+  // The mode sizes go to the Omega kernels as kernel parameters (no host-to-device copy).  Every
+  // scratch element read below is written earlier in this call (Omega by omega_fill_byval, T by a
+  // non-accumulating GEMM), so nothing left by a previous call needs clearing.
+  TTR_CHECK(omega_fill_byval(c, seed, t, nc, n + (t - 1), col0, col1, Om, ostride, w));
   {  // W_d = H(X_d) Omega_d   (Eq. (3.2))
     Gemm g;
     g.M = r[d - 1]; g.N = w; g.K = n[d - 1];

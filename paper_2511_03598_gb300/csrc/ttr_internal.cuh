@@ -130,10 +130,10 @@ int tri_solve(Ctx& c, const double* X, int64_t ldx, int64_t m, int64_t b, const 
 int omega_fill(Ctx& c, uint64_t seed, int32_t k_lo, int32_t k_hi, const int64_t* n_host,
                int64_t col0, int64_t col1, double* dst, int* dst_int, int64_t ostride, int64_t ld);
 
-// omega_fill for cores k_lo..k_lo+nc-1 whose mode sizes are already on the device (nk_dev,
-// maximum nmax); no dst_int.  Allocates nothing.
-int omega_fill_dev(Ctx& c, uint64_t seed, int32_t k_lo, int32_t nc, const int64_t* nk_dev, int64_t nmax,
-                   int64_t col0, int64_t col1, double* dst, int64_t ostride, int64_t ld);
+// omega_fill (no dst_int) for cores k_lo..k_lo+nc-1 with mode sizes n_host[0..nc-1] (host), which
+// reach the kernels as kernel parameters: allocates nothing and copies nothing.
+int omega_fill_byval(Ctx& c, uint64_t seed, int32_t k_lo, int32_t nc, const int64_t* n_host, int64_t col0,
+                     int64_t col1, double* dst, int64_t ostride, int64_t ld);
 
 // W_k(a, j) = sum_i T(a*n + i, j) * Omega(i, j) for a < r0, j < w  (Algorithm 3 epilogue)
 int omega_reduce(Ctx& c, const double* T, int64_t ldt, const double* Om, int64_t ldo, int64_t r0,

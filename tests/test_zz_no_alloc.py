@@ -59,6 +59,21 @@ def test_noalloc_same_call_twice_into_the_same_outputs(B):
         _close(out, ref)
 
 
+@pytest.mark.gpu
+def test_noalloc_checks_caller_outputs(B):
+    """The C side cannot check buffer sizes: the binding refuses a wrong `out` before any call."""
+    cores = _dev(WL.c3(d=4, n=8, r=5).cores)
+    good = {k: torch.empty((c.shape[0], 16), dtype=torch.float64, device="cuda") for k, c in
+            zip(range(2, 5), cores[1:])}
+    for k, bad in [(3, torch.empty((good[3].shape[0] + 1, 16), dtype=torch.float64, device="cuda")),
+                   (4, torch.empty(good[4].shape, dtype=torch.float32, device="cuda")),
+                   (2, torch.empty((16, good[2].shape[0]), dtype=torch.float64, device="cuda").t())]:
+        with pytest.raises(ValueError):
+            B.partial_contractions_noalloc(cores, 1, 0, 16, 2, out={**good, k: bad})
+    with pytest.raises(ValueError):
+        B.partial_contractions_noalloc(cores, 1, 0, 16, 2, out={k: v for k, v in good.items() if k != 3})
+
+
 def test_noalloc_rejects_shapes_beyond_the_static_limit(B):
     """Host-side check, before any device work: runs without a GPU."""
     L = B.lib()
