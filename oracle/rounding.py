@@ -12,7 +12,7 @@ Contents (paper sections / algorithms):
 * ``norm_estimate``            - Remark 3.1, Eq. (3.6)
 * ``svd_pass_rl``              - Remark 3.2 (the "Adap-R" compression pass, right to left)
 * ``partial_contractions_rl_sum`` / ``tt_round_adaptive_sum``
-                               - Remark 3.3 and Appendix C (the algorithms for a sum of TT
+                               - Remark 3.3 and Appendix D (the algorithms for a sum of TT
                                  tensors): every summand sketched with the shared Omega, the
                                  sum never formed
 * ``tt_round_deterministic``   - Algorithm 1 (TT-Rounding, Oseledets)
@@ -49,6 +49,16 @@ and the SVD (numpy.linalg.svd).  Readings of points where the paper is silent or
   R15 A zero tensor: when ||X|| (given, or estimated by Eq. (3.6)) is 0, the rounding is the zero
       TT of ranks 1 (there is no subspace to sketch; tau would be 0).  The estimate is 0 only for
       X = 0, with probability one.
+  R16 Estimator width and safety factor (Sec. 3.4, Theorem 3.3 and its Corollary): the residual
+      estimate of Algorithm 6 may use more KRP columns than the block it appends, and the stop may
+      compare it with tau / beta.  With ``est_min`` = p the residual sketch has max(b_inc, p) columns
+      (Eqs. (3.4)-(3.5)) and est = ||S||_F / sqrt(max(b_inc, p)); the new directions still come from
+      its first min(b_inc, rbar - col(Q)) columns, and the next residual sketch starts after them.
+      With ``est_safety`` = beta the loop stops when est <= tau / beta.  The Corollary bounds the
+      estimate from below by ||A_k||_F / sqrt(zeta) with a sample count growing like ln^(d-k)(2/delta):
+      few columns and many remaining modes (the operator-applied vector, d = 16, b_inc = 3) leave the
+      estimate far below the residual, and the oracle then ends above tol.  Defaults p = 0, beta = 1
+      are Algorithm 6 as printed.
   R13 Sum of TTs, the last core: the appendix writes H(Y_{k+1}) = [Y^(1) ... Y^(s)] for every k.
       For k + 1 = d the summands' last cores share the right bond 1 (the formal sum stacks them
       vertically), so H(Y_d) = sum_i M^(i) H(X_d^(i)); for k + 1 < d the blocks sit side by side
@@ -174,11 +184,12 @@ def right_bound(n, k: int) -> int:
 
 def tt_round_adaptive(cores, tol: float, seed: int, block: int = 0, f_init: float = 0.1,
                       f_inc: float = 0.05, nrmx: float | None = None, adap_r: bool = False,
-                      adap_r_tau: float | None = None):
+                      adap_r_tau: float | None = None, est_min: int = 0, est_safety: float = 1.0):
     """Algorithm 6: adaptive-rank randomize-then-orthogonalize with KRP sketches.
 
     ``nrmx`` is ||X|| if known; otherwise Eq. (3.6) estimates it (Remark 3.1).  ``adap_r``
-    appends the right-to-left compression pass of Remark 3.2.  Returns (Y cores, info).
+    appends the right-to-left compression pass of Remark 3.2.  ``est_min`` and ``est_safety``
+    are the estimator width and safety factor of reading R16.  Returns (Y cores, info).
     """
     d = len(cores)
     r, n = ranks(cores), modes(cores)
@@ -202,12 +213,13 @@ def tt_round_adaptive(cores, tol: float, seed: int, block: int = 0, f_init: floa
         Q, _ = np.linalg.qr(S)
         Hn = (Q.T @ Z) @ H(cores[k])                               # H(Y_{k+1}) = M_k H(X_{k+1})
         b_inc = block_size(rbar, block, f_inc)
+        b_est = max(b_inc, est_min)                                # R16: estimator columns
         est_k = []
         while Q.shape[1] < rbar:                                   # R4
-            S = residual_sketch(sk, Z, Q, k, b_inc)
-            est = float(np.linalg.norm(S) / math.sqrt(b_inc))
+            S = residual_sketch(sk, Z, Q, k, b_est)
+            est = float(np.linalg.norm(S) / math.sqrt(b_est))
             est_k.append(est)
-            if not est > tau:
+            if not est > tau / est_safety:                         # R16: tau / beta
                 break
             bb = min(b_inc, rbar - Q.shape[1])                     # R4: last block clamped
             Qn, _ = np.linalg.qr(S[:, :bb])
@@ -255,7 +267,7 @@ def partial_contractions_rl_sum(summands, seed: int, col0: int, col1: int, t: in
 
 
 def project_summands(Mq: np.ndarray, summands, off, k: int) -> list:
-    """Rows of H(Y_{k+1}) for the directions Mq = Q^T V(Y_k), one block per summand (Appendix C):
+    """Rows of H(Y_{k+1}) for the directions Mq = Q^T V(Y_k), one block per summand (Appendix D):
     [M^(1) ... M^(s)] = Mq split at the bond-k offsets, block i = M^(i) H(X_{k+1}^(i))."""
     return [Mq[:, off[k][i]:off[k][i + 1]] @ H(x[k]) for i, x in enumerate(summands)]
 
@@ -270,14 +282,14 @@ def next_core_of_sum(parts, lk: int, n_next: int, right_ranks, last: bool) -> np
 
 def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_init: float = 0.1,
                           f_inc: float = 0.05, nrmx: float | None = None, adap_r: bool = False,
-                          adap_r_tau: float | None = None):
+                          adap_r_tau: float | None = None, est_min: int = 0, est_safety: float = 1.0):
     """Adaptive-rank rounding of X = X^(1) + ... + X^(s) without forming the formal sum
-    (Appendix C: the sum forms of Algorithms 5 and 6; readings R12, R13).
+    (Appendix D: the sum forms of Algorithms 5 and 6; readings R12, R13).
 
     Y_1 = [X_1^(1) ... X_1^(s)] (first cores side by side); at core k the sketch is
     V(Y_k) [W_{k+1}^(1); ...; W_{k+1}^(s)], and the next core is projected summand by summand,
-    M^(i) H(X_{k+1}^(i)) with [M^(1) ... M^(s)] = Q_k^T V(Y_k).  ``f_init`` is unused (R12).
-    Returns (Y cores, info).
+    M^(i) H(X_{k+1}^(i)) with [M^(1) ... M^(s)] = Q_k^T V(Y_k).  ``f_init`` is unused (R12);
+    ``est_min`` and ``est_safety`` as in ``tt_round_adaptive`` (R16).  Returns (Y cores, info).
     """
     d, n = _check_summands(summands)
     rs = [ranks(x) for x in summands]
@@ -307,12 +319,13 @@ def tt_round_adaptive_sum(summands, tol: float, seed: int, block: int = 0, f_ini
         Q, _ = np.linalg.qr(S)
         parts = project_summands(Q.T @ Z, summands, off, k)
         b_inc = block_size(rbar, block, f_inc)
+        b_est = max(b_inc, est_min)                                # R16
         est_k = []
         while Q.shape[1] < rbar:                                   # R4
-            S = residual_sketch(sk, Z, Q, k, b_inc)                # stacked W: the sum form of Alg. 5
-            est = float(np.linalg.norm(S) / math.sqrt(b_inc))
+            S = residual_sketch(sk, Z, Q, k, b_est)                # stacked W: the sum form of Alg. 5
+            est = float(np.linalg.norm(S) / math.sqrt(b_est))
             est_k.append(est)
-            if not est > tau:
+            if not est > tau / est_safety:                         # R16
                 break
             bb = min(b_inc, rbar - Q.shape[1])
             Qn, _ = np.linalg.qr(S[:, :bb])

@@ -1,4 +1,4 @@
-"""Pins for the oracle's rounding of a sum of TTs (Remark 3.3, Appendix C), each against
+"""Pins for the oracle's rounding of a sum of TTs (Remark 3.3, Appendix D), each against
 something other than the sum code itself.
 
 * Stacked per-summand partial contractions equal Algorithm 3 on the explicit block-diagonal
@@ -72,14 +72,16 @@ def test_stacked_partial_contractions_equal_formal_sum(d, n, ranks):
     dict(d=5, n=4, ranks=[3, 2, 4], block=2, tol=1e-2),
     dict(d=4, n=5, ranks=[2, 2], block=1, tol=1e-3),
     dict(d=6, n=3, ranks=[2, 3, 1, 2], block=3, tol=1e-1),
+    dict(d=5, n=4, ranks=[3, 2, 4], block=2, tol=1e-3, est_min=5, est_safety=4.0),   # reading R16
 ])
 @pytest.mark.parametrize("given_norm", [False, True])
 def test_block_mode_equals_adaptive_on_formal_sum(case, given_norm):
     xs = summands_of(7, case["d"], case["n"], case["ranks"], coef=[1.0, -0.7, 0.4, 1.3][:len(case["ranks"])])
     xf = formal_sum(xs)
     nrmx = T.tt_norm(xf) if given_norm else None
-    Ys, infs = R.tt_round_adaptive_sum(xs, case["tol"], 5, block=case["block"], nrmx=nrmx)
-    Yf, inff = R.tt_round_adaptive(xf, case["tol"], 5, block=case["block"], nrmx=nrmx)
+    est = dict(est_min=case.get("est_min", 0), est_safety=case.get("est_safety", 1.0))
+    Ys, infs = R.tt_round_adaptive_sum(xs, case["tol"], 5, block=case["block"], nrmx=nrmx, **est)
+    Yf, inff = R.tt_round_adaptive(xf, case["tol"], 5, block=case["block"], nrmx=nrmx, **est)
     assert infs["ranks"] == inff["ranks"]
     assert infs["formal_ranks"] == T.ranks(xf)
     assert math.isclose(infs["tau"], inff["tau"], rel_tol=1e-12)
