@@ -147,7 +147,7 @@ def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
 
 
 def sum_round_run(B, x, opts, args, world, stream, barrier, single, out_ranks) -> dict:
-    """The workload as its summands, rounded without forming the formal sum (Remark 3.3, Appendix C):
+    """The workload as its summands, rounded without forming the formal sum (Remark 3.3, Appendix D):
     one at a time on one stream, CUDA events around each call as in `single_stream`."""
     import torch
     dev_of = {}
@@ -581,7 +581,7 @@ def main():
     roof_other = [r for r in cand if r is not roof]
 
     # ---- the same input as its summands, rounded without forming the formal sum (Remark 3.3,
-    # Appendix C), and the serving stream through the library's request server.  Both are reported
+    # Appendix D), and the serving stream through the library's request server.  Both are reported
     # beside the headline; a failure in either is recorded in its object, not raised.
     try:
         sum_round = sum_round_run(B, x, opts, args, world, stream, barrier, single, out_ranks)

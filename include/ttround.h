@@ -85,6 +85,15 @@ typedef struct {
   int32_t max_sms;        /* largest number of SMs the persistent block-loop kernel (one CTA per
                              SM, all resident at once) may take; 0 = all.  Lets calls on different
                              streams run side by side: e.g. two calls with half the SMs each */
+  int32_t est_min;        /* adaptive only: the residual estimate of each block uses
+                             max(b_inc, est_min) sketch columns, while b_inc columns are appended
+                             (0 = b_inc, Algorithm 6 as printed; 0..4096) */
+  double est_safety;      /* adaptive only: the block loop stops when the estimate is <= tau /
+                             est_safety (1 = Algorithm 6 as printed; >= 1).  Sec. 3.4: a KRP
+                             estimate from few columns over many remaining modes can fall far below
+                             the residual it estimates; est_min = 10 with est_safety = 10 keeps the
+                             result within tol on the operator-applied vector (d = 16, tol 1e-8),
+                             where the printed rule ends at ~7 tol */
 } ttr_options;
 
 typedef struct {
@@ -98,7 +107,7 @@ typedef struct {
   int64_t width;          /* final number of sketch columns of W_2..W_d */
   int32_t extensions;     /* times Algorithm 5 appended columns to the partial contractions */
   int32_t n_estimates;    /* number of entries in estimates */
-  double* estimates;      /* host: residual estimates ||S_k||_F / sqrt(b_inc) in sweep order */
+  double* estimates;      /* host: residual estimates ||S_k||_F / sqrt(b_e) in sweep order */
   int32_t* est_core;      /* host: core index k (1-based) of each estimate */
   float ms_sketch_rl;     /* device time of the right-to-left partial contractions */
   float ms_sweep_lr;      /* device time of the left-to-right sweep */
@@ -115,7 +124,8 @@ typedef struct {
 } ttr_result;
 
 /* Fill `opts` with defaults: FP64, adap_r off, scale 1, nrmx 0 (estimate), f_init 0.1,
- * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0, max_sms 0. */
+ * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0, max_sms 0, est_min 0,
+ * est_safety 1. */
 void ttr_default_options(ttr_options* opts);
 
 /* Algorithm 4 (Sec. 3.2): fixed-rank randomize-then-orthogonalize with a KRP sketch.
@@ -135,8 +145,8 @@ int tt_round_fixed(int32_t d, const int64_t* n, const int64_t* r, const double* 
  *   tol    relative Frobenius tolerance eps > 0; per-core threshold tau = eps*nrmx/sqrt(d-1).
  *   block  > 0: b_init = b_inc = block; <= 0: b = ceil(f * rbar_k) with opts->f_init/f_inc.
  *   seed   as in tt_round_fixed; the first columns of the sketch are those of the fixed call.
- * The loop at core k stops when ||S_k||_F / sqrt(b_inc) <= tau (Eq. (3.5) residual sketch)
- * or when col(Q_k) reaches rbar_k = min(rows, cols of V(Y_k), prod_{j>k} n_j) (the last factor
+ * The loop at core k stops when ||S_k||_F / sqrt(b_e) <= tau / opts->est_safety (Eq. (3.5)
+ * residual sketch S_k of b_e = max(b_inc, opts->est_min) columns) or when col(Q_k) reaches rbar_k = min(rows, cols of V(Y_k), prod_{j>k} n_j) (the last factor
  * bounds the rank of V(Y_k) H(X_{k+1:d})).  Output cores 1..d-1 are left-orthonormal unless
  * opts->adap_r is set (then cores 2..d are right-orthonormal).  A zero tensor (norm 0, given or
  * estimated) gives the zero TT of ranks 1. */
@@ -145,7 +155,7 @@ int tt_round_adaptive(int32_t d, const int64_t* n, const int64_t* r, const doubl
                       void* stream, ttr_result* out);
 
 /* Adaptive-rank rounding of a sum X = X^(1) + ... + X^(s) of TT tensors without forming the
- * block-diagonal formal sum (Remark 3.3; the sum forms of Algorithms 5 and 6 in Appendix C).
+ * block-diagonal formal sum (Remark 3.3; the sum forms of Algorithms 5 and 6 in Appendix D).
  *   s      number of summands, 1 <= s <= TTR_MAX_SUMMANDS.
  *   d, n   shared by every summand (n: host array of d mode sizes).
  *   r      host array of s pointers; r[i] points to the d+1 ranks of summand i (r[i][0] =

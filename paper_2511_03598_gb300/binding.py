@@ -25,7 +25,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("slices", ctypes.c_int32), ("adap_r", ctypes.c_int32),
                 ("adap_r_tau_scale", ctypes.c_double), ("nrmx", ctypes.c_double), ("f_init", ctypes.c_double),
                 ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64), ("kernel_timing", ctypes.c_int32),
-                ("max_sms", ctypes.c_int32)]
+                ("max_sms", ctypes.c_int32), ("est_min", ctypes.c_int32), ("est_safety", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -134,13 +134,14 @@ def _tt_args(cores):
 
 def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = False, adap_r_tau_scale: float = 1.0,
             nrmx: float = 0.0, f_init: float = 0.1, f_inc: float = 0.05, width_hint: int = 0,
-            kernel_timing: bool = False, max_sms: int = 0) -> Options:
+            kernel_timing: bool = False, max_sms: int = 0, est_min: int = 0, est_safety: float = 1.0) -> Options:
     o = Options()
     lib().ttr_default_options(ctypes.byref(o))
     o.precision, o.slices, o.adap_r = precision, slices, int(adap_r)
     o.adap_r_tau_scale, o.nrmx, o.f_init, o.f_inc, o.width_hint = adap_r_tau_scale, nrmx, f_init, f_inc, width_hint
     o.kernel_timing = int(kernel_timing)
     o.max_sms = int(max_sms)
+    o.est_min, o.est_safety = int(est_min), float(est_safety)
     return o
 
 

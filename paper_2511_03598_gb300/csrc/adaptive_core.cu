@@ -3,9 +3,11 @@
 //
 // Given the sketch S_all = V(Y_k) W_{k+1}(:, 0:width) (computed on the tensor cores), the loop
 //   Q = qr(S_all(:, 0:b_init))
-//   repeat: S = S_all(:, c:c+b_inc) - Q (Q^T S_all(:, c:c+b_inc))          (Eqs. (3.4)-(3.5))
-//           est = ||S||_F / sqrt(b_inc); stop if est <= tau or c = rbar
+//   repeat: S = S_all(:, c:c+b_e) - Q (Q^T S_all(:, c:c+b_e))              (Eqs. (3.4)-(3.5))
+//           est = ||S||_F / sqrt(b_e); stop if est <= tau or c = rbar
 //           Q_new = qr(S(:, 1:bb)); Q_new = qr(Q_new - Q (Q^T Q_new)); Q = [Q, Q_new]
+// with b_e = max(b_inc, est_min) estimator columns and bb = min(b_inc, rbar - c) appended ones
+// (b_e = b_inc in Algorithm 6 as printed).
 // is a chain of small dependent FP64 steps.  On GB300 FP64 runs at ~1.2 TFLOP/s, so every step is
 // spread over all SMs (each CTA owns a block of rows) and the steps are separated by a grid
 // barrier instead of kernel launches; the stopping decision is taken on the device, and the
@@ -50,6 +52,7 @@ struct Args {
   int64_t qcols;        // columns of Q kept per row in shared memory (>= rbar)
   int rpc;              // rows per CTA
   int b0, bi, rbar, width;
+  int ba;               // columns appended per block (<= bi, the residual sketch's width)
   int cc0;              // columns of Q already final on entry (0: phase 1 still to do)
   double tau;
   unsigned* bar;        // [0] arrival counter, [1] generation
@@ -696,7 +699,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     sub_qp<A>(Rs, bi, Qs, ldq, cc, Ps, ldp, bi, nr);
     tmr.mark(PH_RESIDUAL);
     // reduction B: ||S||_F^2 and the Gram matrix of the candidate block S(:, 0:bb)
-    const int bb = min(bi, a.rbar - cc);
+    const int bb = min(a.ba, a.rbar - cc);
     {
       double* eb = red_buf(rd);
       sumsq_acc<A>(Rs, bi, bi, nr, eb);
@@ -707,10 +710,10 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     if (threadIdx.x == 0) est_s = __ldcg(bufB);
     __syncthreads();
     const double ss = est_s;                               // ||S||_F^2
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.est_out[nest] = mul_pow2(ss, -2 * a.sshift);   // host: sqrt(ss / b_inc)
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.est_out[nest] = mul_pow2(ss, -2 * a.sshift);   // host: sqrt(ss / b_e)
     ++nest;
     tmr.mark(PH_REDUCE_B);
-    // est = sqrt(ss / b_inc) > tau  <=>  ss > tau^2 b_inc  (the square root is left to the host)
+    // est = sqrt(ss / b_e) > tau  <=>  ss > tau^2 b_e  (the square root is left to the host)
     const double tau_s = mul_pow2(a.tau, a.sshift);
     if (!(ss > tau_s * tau_s * (double)bi)) return finish(ST_DONE);
     // new directions (Algorithm 6): Q_new = qr(S(:, 0:bb)); Q_new -= Q (Q^T Q_new); Q_new = qr(Q_new).
@@ -784,9 +787,10 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
 // (ST_DONE, ST_EXTEND: more sketch columns are needed, ST_BREAKDOWN: a CholeskyQR pivot failed
 // at column *cc), or TTR_ERR_UNSUPPORTED when this path does not apply.
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
-                  int bi, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status, int* cc,
-                  int* nest, bool double_float, double scale, int max_sms) {
+                  int bi, int ba, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status,
+                  int* cc, int* nest, bool double_float, double scale, int max_sms) {
   if (b0 > ac::BMAX || bi > ac::BMAX || (int64_t)rbar * bi > ac::ACC || m <= 0) return TTR_ERR_UNSUPPORTED;
+  if (ba < 1 || ba > bi) return set_error("adaptive loop: appended block wider than the residual sketch"), TTR_ERR_ARG;
   int dev = 0;
   TTR_CUDA(cudaGetDevice(&dev));
   // device properties and the kernel's shared-memory limit, looked up once per device
@@ -855,7 +859,8 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * used, c.stream));
   ac::Args a{};
   a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;
-  a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.rbar = rbar; a.width = width; a.cc0 = cc0; a.tau = tau;
+  a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.ba = ba; a.rbar = rbar; a.width = width; a.cc0 = cc0;
+  a.tau = tau;
   a.bar = c.ac_bar; a.err = c.d_flags; a.est_out = reinterpret_cast<double*>(c.ac_io + 4); a.io = c.ac_io;
   // double-float keeps binary32 exponents: hold the sketch scaled so that ||X|| maps near 1
   a.sshift = 0;
@@ -876,7 +881,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   TTR_CUDA(cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(ac::NT), params, dyn, c.stream));
   TTR_CHECK(c.check_launch("adaptive_core"));
   // one launch makes at most one estimate per block it runs
-  const int est_max = std::min(cap, (rbar - cc0) / std::max(1, bi) + 3);
+  const int est_max = std::min(cap, (rbar - cc0) / std::max(1, ba) + 3);
   std::vector<unsigned char> back(16 + sizeof(double) * (size_t)est_max);
   TTR_CUDA(cudaMemcpyAsync(back.data(), c.ac_io, back.size(), cudaMemcpyDeviceToHost, c.stream));
   TTR_CUDA(cudaStreamSynchronize(c.stream));
@@ -903,7 +908,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
       f += 2.0 * M * cur * bi;
     }
     for (int i = 0; i < *nest && cur < rbar; ++i) {
-      const int bb = std::min(bi, rbar - cur);
+      const int bb = std::min(ba, rbar - cur);
       f += 2.0 * M * cur * bi + 2.0 * M * bi + 2.0 * M * bb * bb;
       if (i + 1 < *nest || *status != ac::ST_DONE) {
         f += M * bb * bb + 4.0 * M * cur * bb + 2.0 * M * bb * bb + 2.0 * M * (cur + bb) * bi + M * bb * bb;

@@ -587,7 +587,7 @@ static int sweep_alloc(Ctx& c, const TT& X, int64_t bcap, Sweep& s) {
 // M = Q^T Z  (c x cols), then Ynext = M H(X_{k+1})  (c x n r).  For a sum of TTs, M splits into
 // the column blocks M^(i) of the summands and the next core is projected summand by summand:
 // M^(i) H(X_{k+1}^(i)) fills the columns of summand i in the right bond of Ynext, and at the last
-// core (shared right bond 1) the summands' products add up (Appendix C).
+// core (shared right bond 1) the summands' products add up (Appendix D).
 // Zd: for a sum, the summands' last cores stacked (R_{d-1} x n_d, the formal sum's last core)
 static int project_next(Ctx& c, const Engine& E, const Sweep& s, const double* Z, int64_t rows, int64_t cols,
                         int64_t ccols, const SumTT& X, int k, double* Ynext, const double* Zd = nullptr) {
@@ -814,13 +814,15 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
 }
 
 // ----------------------------------------------------------------------------- adaptive
-// appendix_blocks: the block rule of the sum algorithm in Appendix C when block <= 0 (b_init =
+// appendix_blocks: the block rule of the sum algorithm in Appendix D when block <= 0 (b_init =
 // max_i r_k^(i), initial sketch width max_{i,k} r_k^(i)) instead of the fractions f_init of Sec. 3.3.
 static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t seed, const ttr_options& o,
                           cudaStream_t stream, ttr_result* out, bool appendix_blocks = false) {
   if (!(tol > 0.0) || !isfinite(tol)) return set_error("tol must be positive and finite"), TTR_ERR_ARG;
   if (block <= 0 && !((appendix_blocks || (o.f_init > 0.0 && o.f_init < 1.0)) && o.f_inc > 0.0 && o.f_inc < 1.0))
     return set_error("f_init and f_inc must lie in (0, 1)"), TTR_ERR_ARG;
+  if (o.est_min < 0 || o.est_min > 4096) return set_error("est_min must lie in [0, 4096]"), TTR_ERR_ARG;
+  if (!(o.est_safety >= 1.0) || !isfinite(o.est_safety)) return set_error("est_safety must be finite and >= 1"), TTR_ERR_ARG;
   Ctx c;
   c.stream = stream;
   c.prof_begin();
@@ -838,7 +840,9 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
                                                     : appendix ? rpart : (int64_t)ceil((double)rmax * o.f_init - 1e-9));
   const int64_t binc_max = block > 0 ? std::min(block, rmax) : block_size(rmax, 0, o.f_inc);
   const int64_t binit_max = block > 0 ? std::min(block, rmax) : appendix ? rpart : block_size(rmax, 0, o.f_init);
-  const int64_t wcap = std::max(w0, rmax + binc_max);
+  // residual sketches hold max(b_inc, est_min) columns (reading R16), past col(Q) <= rmax
+  const int64_t best_max = std::max<int64_t>(binc_max, o.est_min);
+  const int64_t wcap = std::max(w0, rmax + best_max);
   Engine E;
   TTR_CHECK(E.init(c, o.precision, o.slices, tol));
   Sketch s;
@@ -850,7 +854,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   if (o.width_hint > 0) wdev = std::min(wcap, std::max(w0, o.width_hint));
   TTR_CHECK(rl_pass(c, E, X, seed, 0, wdev, 2, s));
   s.width = wdev;
-  // V(Y_1): the first core, or for a sum the summands' first cores side by side (Appendix C)
+  // V(Y_1): the first core, or for a sum the summands' first cores side by side (Appendix D)
   const double* Z1 = X.parts[0].cores[0];
   if (!X.single()) {
     double* z = nullptr;
@@ -921,9 +925,10 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
     return TTR_OK;
   }
   const double tau = tol * nrmx / sqrt((double)(d - 1));
+  const double tau_stop = tau / o.est_safety;   // reading R16: the loop stops at est <= tau / beta
   tm.rec(1, stream);
   Sweep w;
-  TTR_CHECK(sweep_alloc(c, X.shape(), std::max(binc_max, binit_max), w));
+  TTR_CHECK(sweep_alloc(c, X.shape(), std::max(best_max, binit_max), w));
   if (!X.single()) {
     int64_t ymax = 1;
     for (int k = 1; k < d; ++k) ymax = std::max(ymax, X.n[k] * X.part_rank_max(k + 1));
@@ -988,7 +993,8 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
     for (int j = k; j < d && right < rows; ++j) right = std::min<int64_t>(right * X.n[j], (int64_t)1 << 62);
     const int64_t rbar = std::min(std::min(rows, cols), right);
     const int64_t b0 = appendix ? std::min(rbar, X.part_rank_max(k)) : block_size(rbar, block, o.f_init);
-    const int64_t bi = block_size(rbar, block, o.f_inc);
+    const int64_t ba = block_size(rbar, block, o.f_inc);   // columns appended per block
+    const int64_t bi = std::max<int64_t>(ba, o.est_min);   // columns of each residual sketch (R16)
     sk_cols = 0;
     TTR_CHECK(ensure(k, std::min(rbar, b0) + bi, rows, cols));
     int64_t cc = 0;
@@ -1000,8 +1006,8 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
       while (!done) {
         if (++guard > 4 * (int)rbar + 16) return set_error("adaptive loop did not terminate"), TTR_ERR_TIMEOUT;
         int status = 0, ccn = 0, nest = 0;
-        st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)b0, (int)bi, (int)rbar, (int)sk_cols, (int)cc, tau,
-                           hest.data(), (int)hest.size(), &status, &ccn, &nest,
+        st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)b0, (int)bi, (int)ba, (int)rbar, (int)sk_cols,
+                           (int)cc, tau_stop, hest.data(), (int)hest.size(), &status, &ccn, &nest,
                            E.precision == TTR_PREC_SLICED && E.slices <= 6, nrmx, o.max_sms);
         if (st == TTR_ERR_UNSUPPORTED) break;
         if (st != TTR_OK) return st;
@@ -1023,7 +1029,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
             TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
             cc = b0;
           } else {
-            const int64_t bb = std::min(bi, rbar - cc);
+            const int64_t bb = std::min(ba, rbar - cc);
             TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
             TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
             TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
@@ -1048,7 +1054,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
       TTR_CHECK(copy2d(c, w.S, bi, Sall + cc, wcap, rows, bi));
       TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.S, bi, bi, w.P, &dprobe->ss));
       // speculative next block: Q_new = qr(S(:, :bb)), re-orthogonalized against Q, qr again
-      const int64_t bb = std::min(bi, rbar - cc);
+      const int64_t bb = std::min(ba, rbar - cc);
       TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
       TTR_CHECK(qr_try(w.Q + cc, w.qcap, rows, bb));
       TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
@@ -1069,7 +1075,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
       if (!isfinite(est)) return set_error("non-finite residual estimate"), TTR_ERR_NONFINITE;
       ests.push_back(est);
       est_core.push_back(k);
-      if (!(est > tau)) break;                   // the speculative block is dropped
+      if (!(est > tau_stop)) break;              // the speculative block is dropped
       if (hp.flag) {
         // CholeskyQR broke down on the new block: redo it with the robust fallbacks
         TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
@@ -1329,6 +1335,8 @@ void ttr_default_options(ttr_options* o) {
   o->width_hint = 0;
   o->kernel_timing = 0;
   o->max_sms = 0;
+  o->est_min = 0;
+  o->est_safety = 1.0;
 }
 
 static int finish(int st, ttr_result* out, cudaStream_t s) {

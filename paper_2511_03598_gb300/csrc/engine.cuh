@@ -51,10 +51,11 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
 // the sliced form with at most 6 slices, whose contractions already err by ~3e-12, never where
 // FP64 accuracy is promised); scale: a value of the order of the sketch entries (the input norm).
 // The estimates (||S||_F^2 of each residual block, in order) come back in est_host (host, room for
-// est_cap values; *nest of them are written).
+// est_cap values; *nest of them are written).  bi: columns of each residual sketch (the estimate's
+// width); ba <= bi: columns appended per block; tau: the stopping threshold.
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
-                  int bi, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status, int* cc,
-                  int* nest, bool double_float, double scale, int max_sms);
+                  int bi, int ba, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status,
+                  int* cc, int* nest, bool double_float, double scale, int max_sms);
 
 // Widest tensor-core tile (UMMA N) usable with s slices.
 int tile_width(int s);

@@ -1,4 +1,4 @@
-"""GPU parity of the rounding of a sum of TTs (tt_round_adaptive_sum, Remark 3.3 / Appendix C)
+"""GPU parity of the rounding of a sum of TTs (tt_round_adaptive_sum, Remark 3.3 / Appendix D)
 against the oracle's sum algorithm on the same seeded inputs.
 
 Bars as for the single-TT adaptive rounding: FP64 form identical ranks, represented tensors within
@@ -166,8 +166,10 @@ def test_host_driven_block_loop(B, prec, monkeypatch):
     for x, c in zip(wide, (1.0, -0.5, 0.7)):
         x[0] = x[0] * c
     x1 = WL.c1()
-    for xs, tol, block, nrmx in ((x1.summands, 1e-6, 2, x1.norm), (wide, 1e-4, 30, None)):
-        ref, info = R.tt_round_adaptive_sum(xs, tol, 5, block=block, nrmx=nrmx)
-        with B.round_adaptive_sum(dev_summands(xs), tol, block, 5, B.options(precision=prec, nrmx=nrmx or 0.0)) as y:
+    for xs, tol, block, nrmx, em, beta in ((x1.summands, 1e-6, 2, x1.norm, 0, 1.0), (wide, 1e-4, 30, None, 0, 1.0),
+                                           (x1.summands, 1e-6, 2, x1.norm, 6, 4.0)):   # the last: reading R16
+        ref, info = R.tt_round_adaptive_sum(xs, tol, 5, block=block, nrmx=nrmx, est_min=em, est_safety=beta)
+        with B.round_adaptive_sum(dev_summands(xs), tol, block, 5,
+                                  B.options(precision=prec, nrmx=nrmx or 0.0, est_min=em, est_safety=beta)) as y:
             assert y.info["ranks"] == info["ranks"]
             assert rel(y.to_numpy(), ref) <= (1e-10 if prec == 0 else max(1e-8, 1e-3 * tol))
