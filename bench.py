@@ -616,6 +616,32 @@ def main():
         if i > 0:
             tdet_ms.append(1e3 * (time.perf_counter() - t0))
 
+    # ---- precision forms beside the headline's (6 slices, double-float block loop): the same
+    # single-stream rounding with the block loop in FP64, and at 8 slices (FP64-accurate contractions)
+    forms = {}
+    if prec == B.TTR_PREC_SLICED:
+        for name, kw in (("sliced6_fp64_block_loop", {"block_loop_fp64": True}), ("sliced8_fp64", {"slices": 8})):
+            fo = B.options(precision=prec, nrmx=x.norm, **kw)
+            for _ in range(2):
+                B.round_adaptive(cores, TOL, BLOCK, SEED, fo).free()
+            nf = max(3, min(args.steps, 30))
+            fe = [torch.cuda.Event(enable_timing=True) for _ in range(nf + 1)]
+            fe[0].record(stream)
+            franks = None
+            for i in range(nf):
+                y = B.round_adaptive(cores, TOL, BLOCK, SEED, fo)
+                franks = y.ranks
+                y.free()
+                fe[i + 1].record(stream)
+            torch.cuda.synchronize()
+            fms = [fe[i].elapsed_time(fe[i + 1]) for i in range(nf)]
+            forms[name] = {"roundings_per_s": 1e3 * nf / fe[0].elapsed_time(fe[-1]),
+                           "p50_ms": float(np.percentile(fms, 50)), "p99_ms": float(np.percentile(fms, 99)),
+                           "steps": nf, "ranks_equal_headline": franks == out_ranks,
+                           "what": ("6 slices, CholeskyQR2 / Gram / estimator of the block loop in FP64"
+                                    if "6" in name else "8 slices (contractions FP64-accurate), FP64 block loop"),
+                           "measured": "one rounding at a time on one stream (compare single_stream)"}
+
     # ---- end to end through host buffers: H2D of the cores, rounding, D2H of the result
     host = [torch.from_numpy(c).pin_memory() for c in x.cores]
     h2d = sum(c.nbytes for c in x.cores)
@@ -653,7 +679,11 @@ def main():
             "config": config(x, args.streams), "ranks_out": out_ranks, "sketch_width": w, "extensions": info["extensions"],
             "det_fp64": None if not det_ms else {
                 "roundings_per_s": 1e3 / float(np.mean(det_ms)), "ms": float(np.mean(det_ms)), "ranks_out": det_ranks,
-                "speedup_of_adaptive": value / world / (1e3 / float(np.mean(det_ms)))},
+                "speedup_of_adaptive": value / world / (1e3 / float(np.mean(det_ms))),
+                "note": "this library's Algorithm 1: Householder QR and multi-CTA one-sided Jacobi SVD, FP64"},
+            "speedup_vs_fastest_deterministic": None if not (det_ms and tdet_ms) else
+                value / world / (1e3 / min(float(np.mean(det_ms)), float(np.mean(tdet_ms)))),
+            "precision_forms": forms or None,
             "det_torch_cusolver_fp64": None if not tdet_ms else {
                 "ms": float(np.mean(tdet_ms)), "roundings_per_s": 1e3 / float(np.mean(tdet_ms)), "ranks_out": tdet_ranks,
                 "note": "Algorithm 1 on torch.linalg.qr/svd (cuSOLVER), FP64, comparison only"},

@@ -66,8 +66,12 @@ typedef enum {
  * TTR_PREC_SLICED: the large contractions run on the BF16 tensor cores (tcgen05) on
  *   fixed-point slices of the FP64 operands with exact FP32 accumulation, recombined in
  *   integer/FP64 arithmetic; `slices` sets the number of 7-bit slices per operand (3..8);
- *   8 slices reproduce FP64 results to about 1e-15 relative.  QR, Gram matrices, the
- *   estimator and all truncation decisions stay FP64. */
+ *   8 slices reproduce FP64 results to about 1e-15 relative, s slices to about s 2^(1-7s) of
+ *   sum |a||b| per product.  The host-driven block loop, the Remark 3.2 pass, the truncation SVDs
+ *   and every cross-CTA sum are FP64.  The persistent device block loop of Algorithm 6 (its
+ *   CholeskyQR2 Gram matrices, block Gram-Schmidt and residual norms) is FP64 at 7 and 8 slices;
+ *   at 3..6 slices its per-CTA arithmetic is double-float (pairs of binary32, about 2^-48 relative,
+ *   on the FP32 pipe) unless ttr_options::block_loop_fp64 is set. */
 typedef enum { TTR_PREC_FP64 = 0, TTR_PREC_SLICED = 1 } ttr_precision;
 
 typedef struct {
@@ -94,6 +98,15 @@ typedef struct {
                              the residual it estimates; est_min = 10 with est_safety = 10 keeps the
                              result within tol on the operator-applied vector (d = 16, tol 1e-8),
                              where the printed rule ends at ~7 tol */
+  int32_t rl_percore;     /* right-to-left partial contractions (Algorithm 3): 0 = the chain of
+                             per-core contractions (default); 1 = the per-core-parallel form of the
+                             Conclusion (Sec. 5): every G_k(:, :, j) = sum_i X_k(:, i, :) Omega_k(i, j)
+                             in one launch, then W_k(:, j) = G_k(:, :, j) W_{k+1}(:, j) column by
+                             column in another (FP64; scratch 8 sum_k r_{k-1} r_k w bytes); 2 = the
+                             per-core form when that scratch is at most 32 MiB, else the chain */
+  int32_t block_loop_fp64;/* TTR_PREC_SLICED with 3..6 slices: 1 = keep the device block loop in FP64
+                             (CholeskyQR2, Gram matrices and estimator FP64 at any slice count);
+                             0 = its per-CTA arithmetic in double-float (default) */
 } ttr_options;
 
 typedef struct {
@@ -125,7 +138,7 @@ typedef struct {
 
 /* Fill `opts` with defaults: FP64, adap_r off, scale 1, nrmx 0 (estimate), f_init 0.1,
  * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0, max_sms 0, est_min 0,
- * est_safety 1. */
+ * est_safety 1, rl_percore 0, block_loop_fp64 0. */
 void ttr_default_options(ttr_options* opts);
 
 /* Algorithm 4 (Sec. 3.2): fixed-rank randomize-then-orthogonalize with a KRP sketch.
@@ -176,6 +189,28 @@ int tt_round_adaptive(int32_t d, const int64_t* n, const int64_t* r, const doubl
 int tt_round_adaptive_sum(int32_t s, int32_t d, const int64_t* n, const int64_t* const* r,
                           const double* const* const* cores, double tol, int64_t block,
                           uint64_t seed, const ttr_options* opts, void* stream, ttr_result* out);
+
+/* Adaptive-rank rounding (Algorithm 6, as tt_round_adaptive) of an operator-applied TT vector
+ * y = A x, the rounding after each operator application in TT-GMRES (Sec. 4.3), without forming the
+ * cores of y in the right-to-left pass (the MPO-MPS product structure named in the Introduction and
+ * the Conclusion).
+ *   n      HOST array of d output mode sizes (the modes of y).
+ *   m      HOST array of d input mode sizes (the modes of x).
+ *   p      HOST array of d+1 operator ranks, p[0] = p[d] = 1.
+ *   A      HOST array of d DEVICE pointers; operator core k is p[k] x n[k] x m[k] x p[k+1] doubles,
+ *          row-major [a][i][j][g] with i the output and j the input index:
+ *          A(i_1..i_d; j_1..j_d) = A_1(i_1, j_1) ... A_d(i_d, j_d).
+ *   r, x   ranks (d+1, r[0] = r[d] = 1) and DEVICE cores (r[k] x m[k] x r[k+1], [b][j][c]) of x.
+ *   tol, block, seed, opts, stream, out   as in tt_round_adaptive (opts->rl_percore must be 0).
+ * y has ranks p[k] r[k] with cores y_k((a, b), i, (g, c)) = sum_j A_k(a, i, j, g) x_k(b, j, c); the
+ * result is that of tt_round_adaptive on those cores with the same seed, up to rounding.  Per core,
+ * the partial contraction contracts Omega_k into A_k first, then V(x_k) with each operator-rank block
+ * of W_{k+1}, then the two over (j, g); the left-to-right sweep forms one core of y at a time for the
+ * projection of the next core.  Errors as tt_round_adaptive. */
+int tt_round_adaptive_matvec(int32_t d, const int64_t* n, const int64_t* m, const int64_t* p,
+                             const double* const* A, const int64_t* r, const double* const* x, double tol,
+                             int64_t block, uint64_t seed, const ttr_options* opts, void* stream,
+                             ttr_result* out);
 
 /* Algorithm 1 (Sec. 2.3, Oseledets' TT-Rounding), FP64: right-to-left orthogonalization,
  * tau = ||Y_1|| tol / sqrt(d-1), left-to-right tau-truncated SVDs (smallest rank whose
@@ -277,6 +312,32 @@ int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r,
                              const double* const* cores, uint64_t seed, int64_t col0,
                              int64_t col1, int32_t t, int32_t precision, int32_t slices,
                              double* const* W, void* stream);
+
+/* Self-test of the reciprocal square root the block loop's Cholesky factors use (a binary32 seed
+ * refined by one third-order Newton-Householder step, in place of an FP64 division and square
+ * root): out[i] = 1/sqrt(x[i]) for `count` positive finite doubles, both DEVICE buffers.  No
+ * counterpart in the paper; for tests of that arithmetic against a correctly rounded reference. */
+int ttr_selftest_rsqrt(const double* x, double* out, int64_t count, void* stream);
+
+/* The partial contractions of ttr_partial_contractions (arguments, layout of W and results alike,
+ * FP64) in the per-core-parallel form of the Conclusion (Sec. 5; ttr_options::rl_percore = 1):
+ * all G_k(:, :, j) = sum_i X_k(:, i, :) Omega_k(i, j) for k = t..d in one launch, then
+ * W_d(:, j) = G_d(:, 0, j) and W_k(:, j) = G_k(:, :, j) W_{k+1}(:, j) in a second launch with one
+ * CTA per sketch column.  Scratch: 8 sum_{k=t..d} r_{k-1} r_k (col1 - col0) bytes (stream-ordered);
+ * TTR_ERR_UNSUPPORTED when a rank exceeds 12800 (the chain keeps two vectors per CTA in shared
+ * memory).  Synchronizes `stream` before returning. */
+int ttr_partial_contractions_percore(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
+                                     uint64_t seed, int64_t col0, int64_t col1, int32_t t, double* const* W,
+                                     void* stream);
+
+/* The partial contractions of Algorithm 3 on the product y = A x (arguments of the operator and the
+ * vector as in tt_round_adaptive_matvec; seed, col0, col1, t, precision, slices, stream as in
+ * ttr_partial_contractions), computed without forming y's cores: W[k-1] (k = t..d) are DEVICE buffers
+ * of p[k-1] r[k-1] x (col1 - col0) doubles, rows (a, b) = a r[k-1] + b.  Synchronizes `stream`. */
+int ttr_partial_contractions_matvec(int32_t d, const int64_t* n, const int64_t* m, const int64_t* p,
+                                    const double* const* A, const int64_t* r, const double* const* x,
+                                    uint64_t seed, int64_t col0, int64_t col1, int32_t t, int32_t precision,
+                                    int32_t slices, double* const* W, void* stream);
 
 /* Size of the device array that ttr_partial_contractions_noalloc uses as its scratch. */
 #define TTR_STATIC_SCRATCH_BYTES (32u << 20)

@@ -6,6 +6,8 @@ It shares no code with the CUDA path; both sides only share the seeded input gen
 
 Contents (paper sections / algorithms):
 * ``partial_contractions_rl``  - Algorithm 3 (KRP-PartialContractionsRL), Eqs. (3.1)-(3.3)
+* ``partial_contractions_percore`` - the same W_k through the per-core contractions with Omega that
+                                 the Conclusion (Sec. 5) notes can be done in parallel over the cores
 * ``tt_round_fixed``           - Algorithm 4 (fixed-rank Rand-Orth with KRP), Sec. 3.2
 * ``residual_sketch``          - Algorithm 5 (GenerateResidualSketch), Eqs. (3.4)-(3.5)
 * ``tt_round_adaptive``        - Algorithm 6 (adaptive-rank Rand-Orth with KRP), Sec. 3.3
@@ -16,6 +18,8 @@ Contents (paper sections / algorithms):
                                  tensors): every summand sketched with the shared Omega, the
                                  sum never formed
 * ``tt_round_deterministic``   - Algorithm 1 (TT-Rounding, Oseledets)
+* ``tt_round_adaptive_matvec`` - Algorithm 6 applied to y = A x (the operator application of
+                                 TT-GMRES, Sec. 4.3), from its definition: y formed explicitly
 
 Library primitives used as single steps: matrix product, Householder QR (numpy.linalg.qr)
 and the SVD (numpy.linalg.svd).  Readings of points where the paper is silent or garbled:
@@ -71,7 +75,7 @@ import math
 import numpy as np
 
 from .philox import omega
-from .tt import H, V, modes, orthogonalize_rl, ranks, truncation_rank
+from .tt import H, V, modes, orthogonalize_rl, ranks, truncation_rank, tt_matvec
 
 
 def block_size(rbar: int, block: int, frac: float) -> int:
@@ -94,6 +98,26 @@ def partial_contractions_rl(cores, seed: int, col0: int, col1: int, t: int = 2):
         wn = W[k + 1]                                              # r_k x w
         krp = (om[:, None, :] * wn[None, :, :]).reshape(-1, wn.shape[1])   # rows (i, c), c fastest
         W[k] = H(cores[k - 1]) @ krp
+    return W
+
+
+def partial_contractions_percore(cores, seed: int, col0: int, col1: int, t: int = 2):
+    """Algorithm 3's W_k on sketch columns [col0, col1) for k = d..t, from per-core pieces.
+
+    Each core is contracted with its own Gaussian block first, independently of the others (the
+    parallelism over cores noted in the Conclusion, Sec. 5):
+        G_k(:, :, j) = sum_i X_k(:, i, :) Omega_k(i, j)            (r_{k-1} x r_k for each column j)
+    and the right-to-left dependency is left to one small matrix-vector product per core and column:
+        W_d(:, j) = G_d(:, 0, j),   W_k(:, j) = G_k(:, :, j) W_{k+1}(:, j).
+    By Eq. (3.3) read by index (R1), W_k(a, j) = sum_c [sum_i X_k(a,i,c) Omega_k(i,j)] W_{k+1}(c, j).
+    """
+    d = len(cores)
+    n = modes(cores)
+    G = {k: np.einsum("aic,ij->jac", cores[k - 1], omega(seed, k, n[k - 1], col0, col1))
+         for k in range(t, d + 1)}                                 # G[k][j] = G_k(:, :, j)
+    W = {d: G[d][:, :, 0].T.copy()}                                # r_d = 1
+    for k in range(d - 1, t - 1, -1):
+        W[k] = np.einsum("jac,cj->aj", G[k], W[k + 1])
     return W
 
 
@@ -385,3 +409,11 @@ def tt_round_deterministic(cores, tol: float):
         q0, qn, q1 = Y[k + 1].shape
         Y[k + 1] = ((s[:rp, None] * Vt[:rp]) @ H(Y[k + 1])).reshape(rp, qn, q1)   # H(Y_{k+1}) = S V^T H(Y_{k+1})
     return Y, {"ranks": ranks(Y), "tau": tau}
+
+
+def tt_round_adaptive_matvec(op, x, tol: float, seed: int, **kw):
+    """Algorithm 6 on y = A x (Sec. 4.3: the rounding after an operator application in TT-GMRES):
+    the product formed by its definition (``oracle.tt.tt_matvec``), then ``tt_round_adaptive`` with
+    the same arguments.  The fused GPU form, which never forms y's cores in its right-to-left
+    pass, must agree with this up to rounding."""
+    return tt_round_adaptive(tt_matvec(op, x), tol, seed, **kw)

@@ -104,6 +104,36 @@ def tt_inner(x, y) -> float:
     return float(g[0, 0])
 
 
+def tt_matvec(op, x):
+    """y = A x for a TT operator A and a TT vector x (the operator application of TT-GMRES,
+    Sec. 4.3; the MPO-MPS product of the Introduction and Conclusion).
+
+    Operator cores are A_k in R^{p_{k-1} x n_k x n_k x p_k}, [a][i][j][g] with i the output and
+    j the input index, so that A(i_1..i_d; j_1..j_d) = A_1(i_1, j_1) ... A_d(i_d, j_d).  The
+    product's cores are y_k((a, b), i, (g, c)) = sum_j A_k(a, i, j, g) x_k(b, j, c), with the
+    operator's bond index the slower one in each bond of y (ranks p_k r_k).
+    """
+    out = []
+    for A, X in zip(op, x):
+        p0, n, m, p1 = A.shape
+        r0, m2, r1 = X.shape
+        if m != m2:
+            raise ValueError("operator input size must match the vector's mode size")
+        y = np.einsum("aijg,bjc->abigc", A, X).reshape(p0 * r0, n, p1 * r1)
+        out.append(np.ascontiguousarray(y))
+    return out
+
+
+def full_operator(op) -> np.ndarray:
+    """The N x N matrix of a TT operator (N = prod n_k), rows (i_1..i_d) and columns (j_1..j_d) in
+    C order; small operators only."""
+    M = np.ones((1, 1, 1))                    # (rows, cols, bond)
+    for A in op:
+        p0, n, m, p1 = A.shape
+        M = np.einsum("rca,aijg->ricjg", M, A).reshape(M.shape[0] * n, M.shape[1] * m, p1)
+    return M[:, :, 0]
+
+
 def truncation_rank(sigma: np.ndarray, tau: float) -> int:
     """Smallest r' >= 1 whose discarded tail sqrt(sum_{i>r'} sigma_i^2) is <= tau.
 

@@ -25,7 +25,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("slices", ctypes.c_int32), ("adap_r", ctypes.c_int32),
                 ("adap_r_tau_scale", ctypes.c_double), ("nrmx", ctypes.c_double), ("f_init", ctypes.c_double),
                 ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64), ("kernel_timing", ctypes.c_int32),
-                ("max_sms", ctypes.c_int32), ("est_min", ctypes.c_int32), ("est_safety", ctypes.c_double)]
+                ("max_sms", ctypes.c_int32), ("est_min", ctypes.c_int32), ("est_safety", ctypes.c_double),
+                ("rl_percore", ctypes.c_int32), ("block_loop_fp64", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -88,6 +89,12 @@ def lib():
         L.ttr_sketch_omega.argtypes = [u64, i32, i64, i64, i64, vp, vp]
         L.ttr_partial_contractions.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, i32, i32, PP, vp]
         L.ttr_partial_contractions_noalloc.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, PP, vp]
+        L.ttr_selftest_rsqrt.argtypes = [vp, vp, i64, vp]
+        L.ttr_partial_contractions_percore.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, PP, vp]
+        L.tt_round_adaptive_matvec.argtypes = [i32, P64, P64, P64, PP, P64, PP, dbl, i64, u64,
+                                               ctypes.POINTER(Options), vp, ctypes.POINTER(Result)]
+        L.ttr_partial_contractions_matvec.argtypes = [i32, P64, P64, P64, PP, P64, PP, u64, i64, i64, i32, i32, i32,
+                                                      PP, vp]
         L.tt_round_adaptive_sum.argtypes = [i32, i32, P64, ctypes.POINTER(P64), ctypes.POINTER(PP), dbl, i64, u64,
                                             ctypes.POINTER(Options), vp, ctypes.POINTER(Result)]
         L.ttr_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
@@ -134,7 +141,8 @@ def _tt_args(cores):
 
 def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = False, adap_r_tau_scale: float = 1.0,
             nrmx: float = 0.0, f_init: float = 0.1, f_inc: float = 0.05, width_hint: int = 0,
-            kernel_timing: bool = False, max_sms: int = 0, est_min: int = 0, est_safety: float = 1.0) -> Options:
+            kernel_timing: bool = False, max_sms: int = 0, est_min: int = 0, est_safety: float = 1.0,
+            rl_percore: int = 0, block_loop_fp64: bool = False) -> Options:
     o = Options()
     lib().ttr_default_options(ctypes.byref(o))
     o.precision, o.slices, o.adap_r = precision, slices, int(adap_r)
@@ -142,6 +150,8 @@ def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = Fals
     o.kernel_timing = int(kernel_timing)
     o.max_sms = int(max_sms)
     o.est_min, o.est_safety = int(est_min), float(est_safety)
+    o.rl_percore = int(rl_percore)
+    o.block_loop_fp64 = int(block_loop_fp64)
     return o
 
 
@@ -315,6 +325,64 @@ def partial_contractions(cores, seed: int, col0: int, col1: int, t: int = 2, pre
     return bufs
 
 
+def partial_contractions_percore(cores, seed: int, col0: int, col1: int, t: int = 2, stream=None) -> dict:
+    """Algorithm 3's W_k in the per-core-parallel form (ttr_partial_contractions_percore), FP64."""
+    import torch
+    d, n, r, p = _tt_args(cores)
+    w = col1 - col0
+    bufs = {k: torch.empty((r[k - 1], w), dtype=torch.float64, device=cores[0].device) for k in range(t, d + 1)}
+    ptrs = (ctypes.c_void_p * d)(*[bufs[k + 1].data_ptr() if (k + 1) in bufs else 0 for k in range(d)])
+    _check(lib().ttr_partial_contractions_percore(d, n, r, p, ctypes.c_uint64(seed), col0, col1, t, ptrs,
+                                                  _stream_handle(stream)))
+    return bufs
+
+
+def _op_args(op, x):
+    import torch
+    d = len(op)
+    if len(x) != d:
+        raise ValueError("operator and vector must have the same number of cores")
+    for a in op:
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.dim() == 4
+                and a.is_contiguous()):
+            raise ValueError("operator cores must be contiguous CUDA float64 tensors of shape (p0, n, m, p1)")
+    dx, m, r, px = _tt_args(x)
+    # the C side cannot check device buffer sizes: the operator cores must chain and match x's modes
+    for k, a in enumerate(op):
+        if int(a.shape[2]) != int(m[k]):
+            raise ValueError(f"operator core {k} has input size {int(a.shape[2])}, x has mode size {int(m[k])}")
+        if k > 0 and int(a.shape[0]) != int(op[k - 1].shape[3]):
+            raise ValueError(f"operator ranks do not chain at core {k}")
+    n = (ctypes.c_int64 * d)(*[int(a.shape[1]) for a in op])
+    p = (ctypes.c_int64 * (d + 1))(*([int(op[0].shape[0])] + [int(a.shape[3]) for a in op]))
+    pa = (ctypes.c_void_p * d)(*[a.data_ptr() for a in op])
+    return d, n, m, p, pa, r, px
+
+
+def round_adaptive_matvec(op, x, tol: float, block: int, seed: int, opts: Options | None = None,
+                          stream=None) -> Rounded:
+    """Algorithm 6 on y = A x without forming y (tt_round_adaptive_matvec); op: cores (p0, n, m, p1)."""
+    d, n, m, p, pa, r, px = _op_args(op, x)
+    res = Result()
+    s = _stream_handle(stream)
+    st = lib().tt_round_adaptive_matvec(d, n, m, p, pa, r, px, float(tol), int(block), ctypes.c_uint64(seed),
+                                        ctypes.byref(opts) if opts else None, s, ctypes.byref(res))
+    return _finish(res, st, s, list(n))
+
+
+def partial_contractions_matvec(op, x, seed: int, col0: int, col1: int, t: int = 2, precision: int = TTR_PREC_FP64,
+                                slices: int = 0, stream=None) -> dict:
+    """Algorithm 3 on y = A x without forming y (ttr_partial_contractions_matvec): {k: W_k}."""
+    import torch
+    d, n, m, p, pa, r, px = _op_args(op, x)
+    w = col1 - col0
+    bufs = {k: torch.empty((p[k - 1] * r[k - 1], w), dtype=torch.float64, device=x[0].device) for k in range(t, d + 1)}
+    ptrs = (ctypes.c_void_p * d)(*[bufs[k + 1].data_ptr() if (k + 1) in bufs else 0 for k in range(d)])
+    _check(lib().ttr_partial_contractions_matvec(d, n, m, p, pa, r, px, ctypes.c_uint64(seed), col0, col1, t,
+                                                 precision, slices, ptrs, _stream_handle(stream)))
+    return bufs
+
+
 def partial_contractions_noalloc(cores, seed: int, col0: int, col1: int, t: int = 2, out: dict | None = None,
                                  stream=None) -> dict:
     """FP64 Algorithm 3 through ttr_partial_contractions_noalloc: the library allocates no device
@@ -343,6 +411,17 @@ def partial_contractions_noalloc(cores, seed: int, col0: int, col1: int, t: int 
     _check(lib().ttr_partial_contractions_noalloc(d, n, r, p, ctypes.c_uint64(seed), col0, col1, t, ptrs,
                                                   _stream_handle(stream)))
     return bufs
+
+
+def selftest_rsqrt(x, stream=None):
+    """The block loop's reciprocal square root applied to the CUDA float64 tensor x (ttr_selftest_rsqrt)."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous CUDA float64 tensor")
+    out = torch.empty_like(x)
+    _check(lib().ttr_selftest_rsqrt(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
+                                    _stream_handle(stream)))
+    return out
 
 
 @dataclass

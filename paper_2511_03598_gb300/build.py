@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libttround.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["kernels_fp64.cu", "engine.cu", "ozaki_tc.cu", "adaptive_core.cu", "driver.cu", "noalloc.cu", "server.cu"]
+SOURCES = ["kernels_fp64.cu", "engine.cu", "ozaki_tc.cu", "adaptive_core.cu", "householder.cu", "jacobi.cu",
+           "percore.cu", "matvec.cu", "driver.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

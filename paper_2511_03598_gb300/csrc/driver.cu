@@ -232,9 +232,20 @@ static int validate(const TT& X) {
 // share d and the mode sizes, never formed (Remark 3.3).  R are the ranks of the formal sum, and
 // off[i][k] is the first index of summand i in bond k of the formal sum (its rows of W_{k+1}, its
 // columns of V(Y_k)); the outer bonds (k = 0, d) are shared.
+// An operator-applied TT vector y = A x never formed (matvec.cu): operator cores A_k
+// (p_{k-1} x n_k x m_k x p_k, [a][i][j][g]) and vector cores x_k (r_{k-1} x m_k x r_k).
+struct Matvec {
+  const int64_t* m = nullptr;        // input mode sizes (d)
+  const int64_t* p = nullptr;        // operator ranks (d+1)
+  const double* const* A = nullptr;  // operator cores (device)
+  const int64_t* r = nullptr;        // vector ranks (d+1)
+  const double* const* x = nullptr;  // vector cores (device)
+};
+
 struct SumTT {
   int d = 0;
   const int64_t* n = nullptr;
+  const Matvec* mv = nullptr;        // set: the input is y = A x (parts empty, R = p r)
   std::vector<TT> parts;
   std::vector<int64_t> R;
   std::vector<std::vector<int64_t>> off;
@@ -282,6 +293,30 @@ static int make_sum(int32_t s, int32_t d, const int64_t* n, const int64_t* const
   }
   for (int k = 0; k < d; ++k)
     if ((double)S.R[k] * (double)n[k] * (double)S.R[k + 1] > 9.0e15) return set_error("formal sum too large"), TTR_ERR_ARG;
+  return TTR_OK;
+}
+
+// The operator-applied input y = A x: checks the operator and vector cores and sets the ranks of y.
+static int make_matvec(int32_t d, const int64_t* n, const int64_t* m, const int64_t* p, const double* const* A,
+                       const int64_t* r, const double* const* x, Matvec& mv, SumTT& S) {
+  if (d < 2 || d > TTR_MAX_D) return set_error("d must be in [2, TTR_MAX_D]"), TTR_ERR_ARG;
+  if (!n || !m || !p || !A || !r || !x) return set_error("null operator or vector argument"), TTR_ERR_ARG;
+  if (p[0] != 1 || p[d] != 1 || r[0] != 1 || r[d] != 1)
+    return set_error("outer operator and vector ranks must be 1"), TTR_ERR_ARG;
+  for (int k = 0; k < d; ++k) {
+    if (n[k] < 1 || m[k] < 1 || p[k + 1] < 1 || r[k + 1] < 1) return set_error("sizes and ranks must be >= 1"), TTR_ERR_ARG;
+    if (!A[k] || !x[k] || (((uintptr_t)A[k]) & 7) || (((uintptr_t)x[k]) & 7))
+      return set_error("core pointers must be non-null and 8-byte aligned"), TTR_ERR_ARG;
+    const double big = (double)p[k] * r[k] * (double)n[k] * (double)p[k + 1] * r[k + 1];
+    if (big > 9.0e15 || (double)p[k] * n[k] * (double)m[k] * p[k + 1] > 9.0e15) return set_error("core too large"), TTR_ERR_ARG;
+  }
+  mv = Matvec{m, p, A, r, x};
+  S = SumTT{};
+  S.d = d;
+  S.n = n;
+  S.mv = &mv;
+  S.R.assign(d + 1, 1);
+  for (int k = 1; k < d; ++k) S.R[k] = p[k] * r[k];
   return TTR_OK;
 }
 
@@ -418,7 +453,89 @@ struct Sketch {
   double* T = nullptr;      // (max r_{k-1} n_k) x ldw scratch
   int extensions = 0;
   std::vector<BPlanes> wplanes;   // digit planes of W_{k+1}(:, 0:width) made by the first pass (index k)
+  bool percore = false;           // per-core-parallel form of the pass (rl_percore)
 };
+
+// rl_percore = 2 takes the per-core form up to this much scratch
+static constexpr double kPercoreAutoBytes = 32.0 * 1024 * 1024;
+
+// Scratch bytes of the per-core-parallel pass on w columns for cores t..d of every summand.
+static double percore_bytes(const SumTT& X, int t, int64_t w) {
+  double tot = 0.0;
+  for (const TT& P : X.parts)
+    for (int k = t; k <= X.d; ++k) tot += 8.0 * (double)P.r[k - 1] * (double)P.r[k] * (double)w;
+  return tot;
+}
+
+// Algorithm 3 on y = A x without forming y's cores (matvec.cu), columns [col0, col1), Omega already
+// in s.Om: per core, Ahat = Omega contracted into A_k, Z_g = V(x_k) W_{k+1}(g-th row block), and
+// W_k = the (j, g) contraction of the two.
+static int rl_pass_matvec(Ctx& c, const Engine& E, const SumTT& X, int64_t col0, int64_t col1, int t, Sketch& s) {
+  const Matvec& v = *X.mv;
+  const int d = X.d;
+  const int64_t w = col1 - col0;
+  int64_t amax = 1, zmax = 1;
+  for (int k = t; k <= d; ++k) {
+    amax = std::max(amax, v.p[k - 1] * v.m[k - 1] * v.p[k] * w);
+    zmax = std::max(zmax, v.p[k] * v.r[k - 1] * v.m[k - 1] * w);
+  }
+  double *Ahat = nullptr, *Z = nullptr;
+  TTR_CHECK(c.alloc_t(&Ahat, amax));
+  TTR_CHECK(c.alloc_t(&Z, zmax));
+  for (int k = d; k >= t; --k) {
+    const int64_t p0 = v.p[k - 1], p1 = v.p[k], r0 = v.r[k - 1], r1 = v.r[k], n = X.n[k - 1], m = v.m[k - 1];
+    const double* Om = s.Om + (int64_t)(k - 1) * s.om_stride;
+    for (int64_t a = 0; a < p0; ++a) {   // Ahat(a, (j, g), l) = sum_i A_k(a, i, (j, g)) Omega_k(i, l)
+      Gemm g;
+      g.M = m * p1; g.N = w; g.K = n;
+      g.A = v.A[k - 1] + a * n * m * p1; g.sam = 1; g.sak = m * p1;
+      g.B = Om; g.sbk = s.ldom; g.sbn = 1;
+      g.C = Ahat + a * m * p1 * w; g.scm = w; g.scn = 1;
+      TTR_CHECK(E.small_gemm(c, g));
+    }
+    if (k == d) {
+      TTR_CHECK(mv_reduce(c, Ahat, nullptr, v.x[d - 1], p0, r0, m, 1, w, s.W[d - 1] + col0, s.ldw));
+      continue;
+    }
+    for (int64_t gi = 0; gi < p1; ++gi) {   // Z_g = V(x_k) W_{k+1}(g r_k : (g+1) r_k, :)
+      Gemm z;
+      z.M = r0 * m; z.N = w; z.K = r1;
+      z.A = v.x[k - 1]; z.sam = r1; z.sak = 1;
+      z.B = s.W[k] + col0 + gi * r1 * s.ldw; z.sbk = s.ldw; z.sbn = 1;
+      z.C = Z + gi * r0 * m * w; z.scm = w; z.scn = 1;
+      TTR_CHECK(E.sketch(c, z));
+    }
+    TTR_CHECK(mv_reduce(c, Ahat, Z, nullptr, p0, r0, m, p1, w, s.W[k - 1] + col0, s.ldw));
+  }
+  return TTR_OK;
+}
+
+// The per-core-parallel form (Conclusion, Sec. 5) of Algorithm 3 on columns [col0, col1), FP64:
+// all G_k in one launch, then the column-wise chain in another.
+static int rl_pass_percore(Ctx& c, const SumTT& X, int64_t col0, int64_t col1, int t, Sketch& s) {
+  const int d = X.d;
+  const int64_t w = col1 - col0;
+  const int ns = (int)X.parts.size();
+  double* G = nullptr;
+  TTR_CHECK(c.alloc_t(&G, (int64_t)ceil(percore_bytes(X, t, w) / 8.0)));
+  std::vector<PcCore> tab;
+  tab.reserve((size_t)ns * (d - t + 1));
+  int64_t goff = 0;
+  for (int p = 0; p < ns; ++p) {
+    const TT& P = X.parts[p];
+    for (int k = t; k <= d; ++k) {
+      PcCore e;
+      e.X = P.cores[k - 1];
+      e.r0 = P.r[k - 1]; e.n = X.n[k - 1]; e.r1 = P.r[k];
+      e.Om = s.Om + (int64_t)(k - 1) * s.om_stride; e.ldom = s.ldom;
+      e.G = G + goff;
+      e.W = s.W[k - 1] + X.off[p][k - 1] * s.ldw + col0; e.ldw = s.ldw;
+      goff += e.r0 * e.r1 * w;
+      tab.push_back(e);
+    }
+  }
+  return rl_percore(c, tab, ns, w);
+}
 
 static int rl_pass(Ctx& c, const Engine& E, const SumTT& X, uint64_t seed, int64_t col0, int64_t col1, int t,
                    Sketch& s) {
@@ -427,6 +544,8 @@ static int rl_pass(Ctx& c, const Engine& E, const SumTT& X, uint64_t seed, int64
   if (w <= 0) return TTR_OK;
   TTR_CHECK(omega_fill(c, seed, t, d, X.n, col0, col1, s.Om + (int64_t)(t - 1) * s.om_stride,
                        s.Omi + (int64_t)(t - 1) * s.om_stride, s.om_stride, s.ldom));
+  if (X.mv) return rl_pass_matvec(c, E, X, col0, col1, t, s);
+  if (s.percore) return rl_pass_percore(c, X, col0, col1, t, s);
   // digit planes of W_{k+1} (all summands' rows) are kept for the sketch
   const bool keep = col0 == 0;
   if (keep) s.wplanes.assign(d + 1, BPlanes{});
@@ -555,6 +674,7 @@ struct Sweep {
   double* P = nullptr;                 // rmax x bcap
   double* M = nullptr;                 // rmax x rmax
   double* ytmp = nullptr;              // one summand's block of the next core (sums only)
+  double* ycore = nullptr;             // one formed core of y = A x (operator-applied input only)
   int64_t bcap = 0;
   QrWork qr;
 };
@@ -593,6 +713,12 @@ static int project_next(Ctx& c, const Engine& E, const Sweep& s, const double* Z
                         int64_t ccols, const SumTT& X, int k, double* Ynext, const double* Zd = nullptr) {
   TTR_CHECK(E.left_project(c, s.Q, s.qcap, Z, rows, cols, ccols, s.M));
   const int64_t nk = X.n[k];
+  if (X.mv) {
+    // one core of y = A x at a time: y_{k+1} into scratch, then M y_{k+1}
+    const Matvec& v = *X.mv;
+    TTR_CHECK(mv_form(c, v.A[k], v.p[k], nk, v.m[k], v.p[k + 1], v.x[k], v.r[k], v.r[k + 1], s.ycore));
+    return E.project(c, s.M, cols, ccols, cols, s.ycore, nk * X.R[k + 1], Ynext);
+  }
   if (X.single()) {
     // H(X_{k+1}) is cols x (n_{k+1} r_{k+2}), row-major
     return E.project(c, s.M, cols, ccols, cols, X.parts[0].cores[k], nk * X.parts[0].r[k + 1], Ynext);
@@ -694,7 +820,10 @@ static int svd_pass_rl(Ctx& c, const Engine& E, ttr_result* out, const int64_t* 
     // SVD of R^T = U S Vt: Jacobi on R^T (transpose R into U's storage first)
     TTR_CHECK(E.transpose(c, R, r0, r0, tmp));                // tmp = R^T (r0 x r0)
     TTR_CUDA(cudaMemsetAsync(w.dflag, 0, sizeof(int), c.stream));
-    TTR_CHECK(jacobi_svd(c, tmp, r0, r0, sig, U, Vt, w.dflag));
+    if (r0 >= kJacobiMultiFrom)
+      TTR_CHECK(jacobi_svd_multi(c, tmp, r0, r0, sig, U, Vt, w.dflag));
+    else
+      TTR_CHECK(jacobi_svd(c, tmp, r0, r0, sig, U, Vt, w.dflag));
     TTR_CUDA(cudaMemcpyAsync(hs.data(), sig, sizeof(double) * r0, cudaMemcpyDeviceToHost, c.stream));
     TTR_CUDA(cudaStreamSynchronize(c.stream));
     int64_t rp = r0;
@@ -756,8 +885,10 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   TTR_CHECK(E.init(c, o.precision, o.slices, 0.0));
   const int d = X.d;
   const SumTT XS = single_sum(X);
+  if (o.rl_percore < 0 || o.rl_percore > 2) return set_error("rl_percore must be 0, 1 or 2"), TTR_ERR_ARG;
   Sketch s;
   TTR_CHECK(sketch_alloc(c, X, ell, s));
+  s.percore = o.rl_percore == 1 || (o.rl_percore == 2 && percore_bytes(XS, 2, ell) <= kPercoreAutoBytes);
   TTR_CHECK(rl_pass(c, E, XS, seed, 0, ell, 2, s));
   s.width = ell;
   tm.rec(1, stream);
@@ -845,8 +976,10 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   const int64_t wcap = std::max(w0, rmax + best_max);
   Engine E;
   TTR_CHECK(E.init(c, o.precision, o.slices, tol));
+  if (o.rl_percore < 0 || o.rl_percore > 2) return set_error("rl_percore must be 0, 1 or 2"), TTR_ERR_ARG;
   Sketch s;
   TTR_CHECK(sketch_alloc(c, X.shape(), wcap, s));
+  s.percore = o.rl_percore == 1 || (o.rl_percore == 2 && percore_bytes(X, 2, wcap) <= kPercoreAutoBytes);
   // Columns of W are a prefix of one counter-based stream, so how many are drawn up front (and how
   // the rest are appended) never changes a result; draw one tensor-core tile width up front and
   // grow geometrically, which keeps the number of right-to-left passes small.
@@ -855,8 +988,15 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   TTR_CHECK(rl_pass(c, E, X, seed, 0, wdev, 2, s));
   s.width = wdev;
   // V(Y_1): the first core, or for a sum the summands' first cores side by side (Appendix D)
-  const double* Z1 = X.parts[0].cores[0];
-  if (!X.single()) {
+  const double* Z1 = X.mv ? nullptr : X.parts[0].cores[0];
+  if (X.mv) {
+    // V(Y_1) = the first core of y = A x (1 x n_1 x p_1 r_1), formed
+    double* z = nullptr;
+    TTR_CHECK(c.alloc_t(&z, X.n[0] * X.R[1]));
+    const Matvec& v = *X.mv;
+    TTR_CHECK(mv_form(c, v.A[0], 1, X.n[0], v.m[0], v.p[1], v.x[0], 1, v.r[1], z));
+    Z1 = z;
+  } else if (!X.single()) {
     double* z = nullptr;
     TTR_CHECK(c.alloc_t(&z, X.n[0] * X.R[1]));
     for (size_t p = 0; p < X.parts.size(); ++p)
@@ -865,7 +1005,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   }
   // for a sum, the last cores stacked: the formal sum's last core, projected in one product
   double* Zd = nullptr;
-  if (!X.single()) {
+  if (!X.single() && !X.mv) {
     TTR_CHECK(c.alloc_t(&Zd, X.R[d - 1] * X.n[d - 1]));
     for (size_t p = 0; p < X.parts.size(); ++p)
       TTR_CUDA(cudaMemcpyAsync(Zd + X.off[p][d - 1] * X.n[d - 1], X.parts[p].cores[d - 1],
@@ -929,7 +1069,11 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   tm.rec(1, stream);
   Sweep w;
   TTR_CHECK(sweep_alloc(c, X.shape(), std::max(best_max, binit_max), w));
-  if (!X.single()) {
+  if (X.mv) {
+    int64_t ymax = 1;
+    for (int k = 1; k < d; ++k) ymax = std::max(ymax, X.R[k] * X.n[k] * X.R[k + 1]);
+    TTR_CHECK(c.alloc_t(&w.ycore, ymax));
+  } else if (!X.single()) {
     int64_t ymax = 1;
     for (int k = 1; k < d; ++k) ymax = std::max(ymax, X.n[k] * X.part_rank_max(k + 1));
     TTR_CHECK(c.alloc_t(&w.ytmp, w.qcap * ymax));
@@ -1008,7 +1152,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
         int status = 0, ccn = 0, nest = 0;
         st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)b0, (int)bi, (int)ba, (int)rbar, (int)sk_cols,
                            (int)cc, tau_stop, hest.data(), (int)hest.size(), &status, &ccn, &nest,
-                           E.precision == TTR_PREC_SLICED && E.slices <= 6, nrmx, o.max_sms);
+                           E.precision == TTR_PREC_SLICED && E.slices <= 6 && !o.block_loop_fp64, nrmx, o.max_sms);
         if (st == TTR_ERR_UNSUPPORTED) break;
         if (st != TTR_OK) return st;
         for (int q = 0; q < nest; ++q) {
@@ -1135,28 +1279,47 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
 }
 
 // ----------------------------------------------------------------------------- deterministic
-// Algorithm 1.  QR and SVD of the (possibly rank-deficient) unfoldings of a formal sum are taken
-// through the Gram matrix: A^T A = V diag(lambda) V^T by one-sided Jacobi, sigma = sqrt(lambda),
-// U = A V_r diag(1/sigma_r) re-orthonormalized by CholeskyQR2.  Directions with
-// sigma < 1e-7 * sigma_max are dropped from the QR of the orthogonalization phase (they are
-// below the FP64 resolution of a Gram matrix); the represented tensor changes by less than that.
-static int gram_svd(Ctx& c, const Engine& E, const double* A, int64_t sam, int64_t sak, int64_t m, int64_t b,
-                    double* G, double* U, double* Vt, double* sig, int* flag, std::vector<double>& hsig) {
-  TTR_CHECK(fill_zero(c, G, b * b));
-  Gemm g;
-  g.M = b; g.N = b; g.K = m;
-  g.A = A; g.sam = sak; g.sak = sam;
-  g.B = A; g.sbk = sam; g.sbn = sak;
-  g.C = G; g.scm = b; g.scn = 1;
-  g.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, m / 256), 128);
-  TTR_CHECK(E.small_gemm(c, g));
-  TTR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
-  TTR_CHECK(jacobi_svd(c, G, b, b, sig, U, Vt, flag));
-  hsig.resize(b);
-  TTR_CUDA(cudaMemcpyAsync(hsig.data(), sig, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
+// Algorithm 1 in FP64.  Every QR is a Householder QR (householder.cu), backward stable also on the
+// exactly rank-deficient unfoldings of a formal sum, and every SVD is one-sided Jacobi on the small
+// triangular factor R (no Gram matrix, so singular values down to about u ||A|| are resolved and no
+// direction is dropped before the truncation).
+
+// SVD of the rows x cols row-major A (rows >= cols) through its R factor: A is overwritten by the
+// Householder reflectors, and on return R = U S V^T with sig (device, cols, descending) and its
+// host copy hsig, U in sw.U and V^T in sw.Vt (cols x cols each).  The left factor Q U of A is then
+// householder_apply(A, E = U(:, :rp)).
+struct SvdWork {
+  double* R = nullptr;
+  double* U = nullptr;
+  double* Vt = nullptr;
+  double* sig = nullptr;
+  int* flag = nullptr;
+};
+
+static int svd_tall(Ctx& c, HhWork& hw, double* A, int64_t rows, int64_t cols, const SvdWork& sw,
+                    std::vector<double>& hsig) {
+  TTR_CHECK(householder_qr(c, hw, A, cols, rows, cols, sw.R, cols));
+  TTR_CUDA(cudaMemsetAsync(sw.flag, 0, sizeof(int), c.stream));
+  if (cols >= kJacobiMultiFrom)
+    TTR_CHECK(jacobi_svd_multi(c, sw.R, cols, cols, sw.sig, sw.U, sw.Vt, sw.flag));
+  else
+    TTR_CHECK(jacobi_svd(c, sw.R, cols, cols, sw.sig, sw.U, sw.Vt, sw.flag));
+  hsig.resize(cols);
+  int bad = 0;
+  TTR_CUDA(cudaMemcpyAsync(hsig.data(), sw.sig, sizeof(double) * cols, cudaMemcpyDeviceToHost, c.stream));
+  TTR_CUDA(cudaMemcpyAsync(&bad, sw.flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   TTR_CUDA(cudaStreamSynchronize(c.stream));
-  for (auto& v : hsig) v = sqrt(std::max(v, 0.0));   // eigenvalues of the Gram -> singular values
+  if (bad) return set_error("deterministic rounding: non-finite singular values"), TTR_ERR_NONFINITE;
   return TTR_OK;
+}
+
+static int64_t tail_rank(const std::vector<double>& s, int64_t n, double tau) {
+  // smallest rp >= 1 with sqrt(sum_{i >= rp} s_i^2) <= tau (the truncated SVD of Algorithm 1)
+  std::vector<double> tail(n + 1, 0.0);
+  for (int64_t i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + s[i] * s[i];
+  for (int64_t q = 1; q <= n; ++q)
+    if (sqrt(tail[q]) <= tau) return q;
+  return n;
 }
 
 static int round_deterministic(const TT& X, double tol, cudaStream_t stream, ttr_result* out) {
@@ -1167,15 +1330,13 @@ static int round_deterministic(const TT& X, double tol, cudaStream_t stream, ttr
   Timer tm;
   tm.rec(0, stream);
   Engine E;
-  ttr_options o;
-  ttr_default_options(&o);
   TTR_CHECK(E.init(c, TTR_PREC_FP64, 0, tol));
   const int d = X.d;
   std::vector<int64_t> r(X.r, X.r + d + 1);
   int64_t cmax = 1, rmax = 1;
   for (int k = 0; k < d; ++k) {
     cmax = std::max(cmax, X.r[k] * X.n[k] * X.r[k + 1]);
-    rmax = std::max(rmax, X.r[k + 1]);
+    rmax = std::max(rmax, std::max(X.r[k + 1], X.r[k]));
   }
   std::vector<double*> Y(d);
   for (int k = 0; k < d; ++k) {
@@ -1183,66 +1344,47 @@ static int round_deterministic(const TT& X, double tol, cudaStream_t stream, ttr
     TTR_CHECK(c.alloc_t(&Y[k], sz));
     TTR_CUDA(cudaMemcpyAsync(Y[k], X.cores[k], sizeof(double) * sz, cudaMemcpyDeviceToDevice, stream));
   }
-  double *G, *U, *Vt, *sig, *tmp, *Rm;
-  int* flag;
-  TTR_CHECK(c.alloc_t(&G, rmax * rmax));
-  TTR_CHECK(c.alloc_t(&U, rmax * rmax));
-  TTR_CHECK(c.alloc_t(&Vt, rmax * rmax));
-  TTR_CHECK(c.alloc_t(&sig, rmax));
+  double *tmp, *tmp2;
   TTR_CHECK(c.alloc_t(&tmp, cmax));
-  TTR_CHECK(c.alloc_t(&Rm, rmax * rmax));
-  TTR_CHECK(c.alloc_t(&flag, 4));
-  QrWork qw;
-  TTR_CHECK(c.alloc_t(&qw.tmp, cmax));
-  TTR_CHECK(c.alloc_t(&qw.save, cmax));
-  TTR_CHECK(c.alloc_t(&qw.G, rmax * rmax));
-  TTR_CHECK(c.alloc_t(&qw.Rinv, rmax * rmax));
-  TTR_CHECK(c.alloc_t(&qw.dscal, 8));
-  TTR_CHECK(c.alloc_t(&qw.dflag, 4));
-  std::vector<double> hs;
-  // ---- OrthogonalizeRL: H(Y_k)^T = Q R (rank-revealing through the Gram), H(Y_k) <- Q^T,
-  //      V(Y_{k-1}) <- V(Y_{k-1}) R^T
+  TTR_CHECK(c.alloc_t(&tmp2, cmax));
+  SvdWork sw;
+  TTR_CHECK(c.alloc_t(&sw.R, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&sw.U, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&sw.Vt, rmax * rmax));
+  TTR_CHECK(c.alloc_t(&sw.sig, rmax));
+  TTR_CHECK(c.alloc_t(&sw.flag, 4));
+  HhWork hw;
+  // ---- OrthogonalizeRL: H(Y_k)^T = Q R, H(Y_k) <- Q^T, V(Y_{k-1}) <- V(Y_{k-1}) R^T
   for (int k = d - 1; k >= 1; --k) {
     const int64_t r0 = r[k], nk = X.n[k], r1 = r[k + 1], m = nk * r1;
-    // A = H(Y_k)^T: A(row, a) = Y[a*m + row]  -> sam = 1, sak = m
-    TTR_CHECK(gram_svd(c, E, Y[k], 1, m, m, r0, G, U, Vt, sig, flag, hs));
-    int64_t q = 0;
-    while (q < r0 && q < m && hs[q] > 1e-7 * hs[0]) ++q;
-    if (q < 1) q = 1;
-    // Qt = diag(1/s) Vt[:q] H(Y_k)   (q x m) -> orthonormal rows, then CholQR2 on its transpose
-    TTR_CHECK(E.scale_rows_inv(c, Vt, r0, q, r0, sig));   // Vt[j,:] /= sqrt(lambda_j)
-    Gemm g;
-    g.M = q; g.N = m; g.K = r0;
-    g.A = Vt; g.sam = r0; g.sak = 1;
-    g.B = Y[k]; g.sbk = m; g.sbn = 1;
-    g.C = tmp; g.scm = m; g.scn = 1;
-    TTR_CHECK(E.small_gemm(c, g));
-    // tmp (q x m) rows ~ orthonormal; make them exactly so: QR of tmp^T (m x q)
-    TTR_CHECK(E.transpose(c, tmp, q, m, qw.tmp));          // qw.tmp = tmp^T (m x q)
-    // qr_inplace uses qw.tmp as scratch, so copy to another buffer first
-    TTR_CHECK(copy2d(c, tmp, q, qw.tmp, q, m, q));          // tmp = Qhat (m x q, ld q)
-    TTR_CHECK(qr_inplace(c, E, tmp, q, m, q, qw));
-    // R = Q^T H(Y_k)^T (q x r0) : R(j, a) = sum_row Q(row, j) Y[a*m + row]
-    TTR_CHECK(fill_zero(c, Rm, q * r0));
-    Gemm h;
-    h.M = q; h.N = r0; h.K = m;
-    h.A = tmp; h.sam = 1; h.sak = q;
-    h.B = Y[k]; h.sbk = 1; h.sbn = m;
-    h.C = Rm; h.scm = r0; h.scn = 1;
-    h.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, m / 256), 128);
-    TTR_CHECK(E.small_gemm(c, h));
-    // new core k: H(Y_k) = Q^T  (q x m)
-    TTR_CHECK(E.transpose(c, tmp, m, q, Y[k]));
-    // V(Y_{k-1}) <- V(Y_{k-1}) R^T  ((r_{k-1} n_{k-1}) x r0)(r0 x q)
     const int64_t rows = r[k - 1] * X.n[k - 1];
+    if (r0 > m) {
+      // the rows of H(Y_k) span at most R^m: H(Y_k) = H(Y_k) I_m, so H(Y_k) <- I_m (orthonormal
+      // rows) and V(Y_{k-1}) <- V(Y_{k-1}) H(Y_k) (the rank drops to m, the tensor is unchanged)
+      Gemm v;
+      v.M = rows; v.N = m; v.K = r0;
+      v.A = Y[k - 1]; v.sam = r0; v.sak = 1;
+      v.B = Y[k]; v.sbk = m; v.sbn = 1;
+      v.C = tmp; v.scm = m; v.scn = 1;
+      TTR_CHECK(E.small_gemm(c, v));
+      TTR_CUDA(cudaMemcpyAsync(Y[k - 1], tmp, sizeof(double) * rows * m, cudaMemcpyDeviceToDevice, stream));
+      TTR_CHECK(E.identity(c, Y[k], m));
+      r[k] = m;
+      continue;
+    }
+    TTR_CHECK(E.transpose(c, Y[k], r0, m, tmp));            // tmp = H(Y_k)^T  (m x r0)
+    TTR_CHECK(householder_qr(c, hw, tmp, r0, m, r0, sw.R, r0));   // reflectors in tmp, R (r0 x r0)
+    TTR_CHECK(E.identity(c, sw.U, r0));
+    TTR_CHECK(householder_apply(c, hw, tmp, r0, m, r0, sw.U, r0, r0, tmp2, r0));   // tmp2 = Q (m x r0)
+    TTR_CHECK(E.transpose(c, tmp2, m, r0, Y[k]));           // H(Y_k) = Q^T  (r0 x m)
+    // V(Y_{k-1}) <- V(Y_{k-1}) R^T  ((r_{k-1} n_{k-1}) x r0)(r0 x r0)
     Gemm v;
-    v.M = rows; v.N = q; v.K = r0;
+    v.M = rows; v.N = r0; v.K = r0;
     v.A = Y[k - 1]; v.sam = r0; v.sak = 1;
-    v.B = Rm; v.sbk = 1; v.sbn = r0;
-    v.C = tmp; v.scm = q; v.scn = 1;
+    v.B = sw.R; v.sbk = 1; v.sbn = r0;
+    v.C = tmp; v.scm = r0; v.scn = 1;
     TTR_CHECK(E.small_gemm(c, v));
-    TTR_CUDA(cudaMemcpyAsync(Y[k - 1], tmp, sizeof(double) * rows * q, cudaMemcpyDeviceToDevice, stream));
-    r[k] = q;
+    TTR_CUDA(cudaMemcpyAsync(Y[k - 1], tmp, sizeof(double) * rows * r0, cudaMemcpyDeviceToDevice, stream));
   }
   // ---- tau = ||Y_1|| tol / sqrt(d-1)
   double* dsc;
@@ -1253,44 +1395,45 @@ static int round_deterministic(const TT& X, double tol, cudaStream_t stream, ttr
   const double nrm = sqrt(dsync_read(c, dsc, &st));
   if (st != TTR_OK) return st;
   const double tau = nrm * tol / sqrt((double)(d - 1));
-  // ---- compression: SVD of V(Y_k) truncated at tau; V(Y_k) <- U, H(Y_{k+1}) <- S Vt H(Y_{k+1})
+  // ---- compression: [Q, R] = QR(V(Y_k)), [U, S, V] = SVD(R, tau), V(Y_k) <- Q U,
+  //      H(Y_{k+1}) <- S V^T H(Y_{k+1})
+  std::vector<double> hs;
   for (int k = 0; k < d - 1; ++k) {
     const int64_t rows = r[k] * X.n[k], cols = r[k + 1];
-    TTR_CHECK(gram_svd(c, E, Y[k], cols, 1, rows, cols, G, U, Vt, sig, flag, hs));
-    std::vector<double> tail(cols + 1, 0.0);
-    for (int64_t i = cols - 1; i >= 0; --i) tail[i] = tail[i + 1] + hs[i] * hs[i];
-    int64_t rp = cols;
-    for (int64_t q = 1; q <= cols; ++q)
-      if (sqrt(tail[q]) <= tau) {
-        rp = q;
-        break;
-      }
-    // U_Y = V(Y_k) V[:, :rp] diag(1/s)  -> then CholQR2 for exact orthonormality
-    Gemm g;
-    g.M = rows; g.N = rp; g.K = cols;
-    g.A = Y[k]; g.sam = cols; g.sak = 1;
-    g.B = Vt; g.sbk = 1; g.sbn = cols;                      // V = Vt^T
-    g.C = tmp; g.scm = rp; g.scn = 1;
-    TTR_CHECK(E.small_gemm(c, g));
-    TTR_CHECK(qr_inplace(c, E, tmp, rp, rows, rp, qw));
-    // coefficient C = U_Y^T V(Y_k)  (rp x cols) = S V^T up to the re-orthonormalization
-    TTR_CHECK(fill_zero(c, Rm, rp * cols));
-    Gemm h;
-    h.M = rp; h.N = cols; h.K = rows;
-    h.A = tmp; h.sam = 1; h.sak = rp;
-    h.B = Y[k]; h.sbk = cols; h.sbn = 1;
-    h.C = Rm; h.scm = cols; h.scn = 1;
-    h.split_k = (int)std::min<int64_t>(std::max<int64_t>(1, rows / 256), 128);
-    TTR_CHECK(E.small_gemm(c, h));
-    TTR_CUDA(cudaMemcpyAsync(Y[k], tmp, sizeof(double) * rows * rp, cudaMemcpyDeviceToDevice, stream));
-    // H(Y_{k+1}) <- C H(Y_{k+1})  (rp x cols)(cols x n r)
     const int64_t ncol = X.n[k + 1] * r[k + 2];
-    Gemm v;
-    v.M = rp; v.N = ncol; v.K = cols;
-    v.A = Rm; v.sam = cols; v.sak = 1;
-    v.B = Y[k + 1]; v.sbk = ncol; v.sbn = 1;
-    v.C = tmp; v.scm = ncol; v.scn = 1;
-    TTR_CHECK(E.small_gemm(c, v));
+    int64_t rp = 0;
+    if (rows >= cols) {
+      TTR_CHECK(copy2d(c, tmp2, cols, Y[k], cols, rows, cols));
+      TTR_CHECK(svd_tall(c, hw, tmp2, rows, cols, sw, hs));            // reflectors of V(Y_k) in tmp2
+      rp = tail_rank(hs, cols, tau);
+      // V(Y_k) <- Q U(:, :rp)
+      TTR_CHECK(householder_apply(c, hw, tmp2, cols, rows, cols, sw.U, cols, rp, Y[k], rp));
+      // H(Y_{k+1}) <- diag(s) V^T(:rp, :) H(Y_{k+1})
+      TTR_CHECK(E.scale_rows(c, sw.Vt, cols, rp, cols, sw.sig));
+      Gemm v;
+      v.M = rp; v.N = ncol; v.K = cols;
+      v.A = sw.Vt; v.sam = cols; v.sak = 1;
+      v.B = Y[k + 1]; v.sbk = ncol; v.sbn = 1;
+      v.C = tmp; v.scm = ncol; v.scn = 1;
+      TTR_CHECK(E.small_gemm(c, v));
+    } else {
+      // wide: V(Y_k)^T (cols x rows, tall) = Q2 R2, R2 = U2 S V2^T, so V(Y_k) = V2 S (Q2 U2)^T
+      TTR_CHECK(E.transpose(c, Y[k], rows, cols, tmp));                 // tmp = V(Y_k)^T  (cols x rows)
+      TTR_CHECK(svd_tall(c, hw, tmp, cols, rows, sw, hs));              // reflectors in tmp
+      rp = tail_rank(hs, rows, tau);
+      // V(Y_k) <- V2(:, :rp)  (rows x rp): V2 = Vt^T
+      TTR_CHECK(E.transpose(c, sw.Vt, rows, rows, sw.R));               // R = V2 (rows x rows)
+      TTR_CHECK(copy2d(c, Y[k], rp, sw.R, rows, rows, rp));
+      // H(Y_{k+1}) <- diag(s) (Q2 U2(:, :rp))^T H(Y_{k+1})
+      TTR_CHECK(householder_apply(c, hw, tmp, rows, cols, rows, sw.U, rows, rp, tmp2, rp));   // P = Q2 U2 (cols x rp)
+      TTR_CHECK(E.scale_cols(c, tmp2, rp, rp, cols, sw.sig));           // P diag(s)
+      Gemm v;                                                           // (P diag(s))^T H(Y_{k+1})
+      v.M = rp; v.N = ncol; v.K = cols;
+      v.A = tmp2; v.sam = 1; v.sak = rp;
+      v.B = Y[k + 1]; v.sbk = ncol; v.sbn = 1;
+      v.C = tmp; v.scm = ncol; v.scn = 1;
+      TTR_CHECK(E.small_gemm(c, v));
+    }
     TTR_CUDA(cudaMemcpyAsync(Y[k + 1], tmp, sizeof(double) * rp * ncol, cudaMemcpyDeviceToDevice, stream));
     r[k + 1] = rp;
   }
@@ -1306,6 +1449,7 @@ static int round_deterministic(const TT& X, double tol, cudaStream_t stream, ttr
   for (int k = 0; k <= d; ++k) out->ranks[k] = r[k];
   tm.rec(2, stream);
   TTR_CUDA(cudaStreamSynchronize(stream));
+  TTR_CHECK(check_device_flags(c));
   out->tau = tau;
   out->nrmx = nrm;
   out->ms_total = tm.ms(0, 2);
@@ -1337,6 +1481,8 @@ void ttr_default_options(ttr_options* o) {
   o->max_sms = 0;
   o->est_min = 0;
   o->est_safety = 1.0;
+  o->rl_percore = 0;
+  o->block_loop_fp64 = 0;
 }
 
 static int finish(int st, ttr_result* out, cudaStream_t s) {
@@ -1388,6 +1534,21 @@ int tt_round_adaptive_sum(int32_t s, int32_t d, const int64_t* n, const int64_t*
   return finish(st, out, (cudaStream_t)stream);
 }
 
+int tt_round_adaptive_matvec(int32_t d, const int64_t* n, const int64_t* m, const int64_t* p,
+                             const double* const* A, const int64_t* r, const double* const* x, double tol,
+                             int64_t block, uint64_t seed, const ttr_options* opts, void* stream, ttr_result* out) {
+  if (!out) return set_error("out must be non-null"), TTR_ERR_ARG;
+  result_zero(out);
+  ttr_options o;
+  if (opts) o = *opts; else ttr_default_options(&o);
+  Matvec mv;
+  SumTT X;
+  int st = make_matvec(d, n, m, p, A, r, x, mv, X);
+  if (st == TTR_OK && o.rl_percore != 0) st = (set_error("rl_percore applies to plain TTs and sums, not to y = A x"), TTR_ERR_ARG);
+  if (st == TTR_OK) st = round_adaptive(X, tol, block, seed, o, (cudaStream_t)stream, out);
+  return finish(st, out, (cudaStream_t)stream);
+}
+
 int tt_round_deterministic(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores, double tol,
                            void* stream, ttr_result* out) {
   if (!out) return set_error("out must be non-null"), TTR_ERR_ARG;
@@ -1432,6 +1593,66 @@ int ttr_sketch_omega(uint64_t seed, int32_t k, int64_t n_k, int64_t col0, int64_
     if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
   }
   return st;
+}
+
+int ttr_partial_contractions_percore(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
+                                     uint64_t seed, int64_t col0, int64_t col1, int32_t t, double* const* W,
+                                     void* stream) {
+  TT X{d, n, r, cores};
+  int st = validate(X);
+  if (st != TTR_OK) return st;
+  if (!W || t < 2 || t > d || col1 <= col0 || col0 < 0) return set_error("bad partial-contraction arguments"), TTR_ERR_ARG;
+  for (int k = t; k <= d; ++k)
+    if (!W[k - 1]) return set_error("null W buffer"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = (cudaStream_t)stream;
+  Engine E;
+  TTR_CHECK(E.init(c, TTR_PREC_FP64, 0, 0.0));
+  const int64_t w = col1 - col0;
+  Sketch s;
+  TTR_CHECK(sketch_alloc(c, X, w, s));
+  for (int k = t; k <= d; ++k) s.W[k - 1] = W[k - 1] - col0;   // caller buffers: [a][j - col0], ld w
+  s.ldw = w;
+  s.percore = true;
+  TTR_CHECK(rl_pass(c, E, single_sum(X), seed, col0, col1, t, s));
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
+  return check_device_flags(c);
+}
+
+int ttr_partial_contractions_matvec(int32_t d, const int64_t* n, const int64_t* m, const int64_t* p,
+                                    const double* const* A, const int64_t* r, const double* const* x, uint64_t seed,
+                                    int64_t col0, int64_t col1, int32_t t, int32_t precision, int32_t slices,
+                                    double* const* W, void* stream) {
+  Matvec mv;
+  SumTT X;
+  TTR_CHECK(make_matvec(d, n, m, p, A, r, x, mv, X));
+  if (!W || t < 2 || t > d || col1 <= col0 || col0 < 0) return set_error("bad partial-contraction arguments"), TTR_ERR_ARG;
+  for (int k = t; k <= d; ++k)
+    if (!W[k - 1]) return set_error("null W buffer"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = (cudaStream_t)stream;
+  Engine E;
+  TTR_CHECK(E.init(c, precision, slices, 0.0));
+  const int64_t w = col1 - col0;
+  Sketch s;
+  TTR_CHECK(sketch_alloc(c, X.shape(), w, s));
+  for (int k = t; k <= d; ++k) s.W[k - 1] = W[k - 1] - col0;   // caller buffers: [(a, b)][j - col0], ld w
+  s.ldw = w;
+  TTR_CHECK(rl_pass(c, E, X, seed, col0, col1, t, s));
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
+  return check_device_flags(c);
+}
+
+int ttr_selftest_rsqrt(const double* x, double* out, int64_t count, void* stream) {
+  if (!x || !out || count < 0) return set_error("bad self-test arguments"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = (cudaStream_t)stream;
+  TTR_CHECK(rsqrt_selftest(c, x, out, count));
+  const cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
+  return TTR_OK;
 }
 
 int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,

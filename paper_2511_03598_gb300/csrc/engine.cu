@@ -40,20 +40,29 @@ int scale_cols_f64(Ctx& c, double* U, int64_t ld, int64_t ncols, int64_t rows, c
   return c.check_launch("scale_cols");
 }
 
-__global__ void scale_rows_rsqrt_kernel(double* Vt, int64_t ld, int64_t nrows, int64_t ncols, const double* lam) {
+__global__ void scale_rows_kernel(double* A, int64_t ld, int64_t nrows, int64_t ncols, const double* s) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrows * ncols; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / ncols, j = e % ncols;
-    const double l = lam[i];
-    Vt[i * ld + j] = (l > 0.0) ? Vt[i * ld + j] / sqrt(l) : 0.0;
+    A[i * ld + j] *= s[i];
   }
 }
 
-int scale_rows_rsqrt_f64(Ctx& c, double* Vt, int64_t ld, int64_t nrows, int64_t ncols, const double* lam) {
+int scale_rows_f64(Ctx& c, double* A, int64_t ld, int64_t nrows, int64_t ncols, const double* s) {
   const int64_t tot = nrows * ncols;
   if (tot <= 0) return TTR_OK;
-  scale_rows_rsqrt_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, c.stream>>>(Vt, ld, nrows,
-                                                                                                        ncols, lam);
-  return c.check_launch("scale_rows_rsqrt");
+  scale_rows_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, c.stream>>>(A, ld, nrows, ncols, s);
+  return c.check_launch("scale_rows");
+}
+
+__global__ void identity_kernel(double* A, int64_t m) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += (int64_t)gridDim.x * blockDim.x)
+    A[e] = (e / m == e % m) ? 1.0 : 0.0;
+}
+
+int identity_f64(Ctx& c, double* A, int64_t m) {
+  if (m <= 0) return TTR_OK;
+  identity_kernel<<<(unsigned)std::min<int64_t>((m * m + 255) / 256, 4096), 256, 0, c.stream>>>(A, m);
+  return c.check_launch("identity");
 }
 
 }  // namespace ttr

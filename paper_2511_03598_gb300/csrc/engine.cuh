@@ -57,13 +57,61 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
                   int bi, int ba, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status,
                   int* cc, int* nest, bool double_float, double scale, int max_sms);
 
+// Householder QR of a tall row-major m x b matrix (householder.cu), for the deterministic rounding.
+// householder_qr overwrites A with the reflectors and R (R also copied to R, b x b, ld ldr, if
+// given); householder_apply then writes Q E (m x nq, ld ldq) for a b x nq matrix E (E = I gives the
+// thin Q).  The workspace keeps the reflector scalars of the last factorization.
+struct HhWork {
+  double* buf = nullptr;
+  int cap = 0;
+  unsigned* bar = nullptr;
+  double* vjj = nullptr;
+  double* beta = nullptr;
+  int bcap = 0;
+};
+int householder_qr(Ctx& c, HhWork& w, double* A, int64_t lda, int64_t m, int64_t b, double* R, int64_t ldr);
+int householder_apply(Ctx& c, HhWork& w, const double* A, int64_t lda, int64_t m, int64_t b, const double* E,
+                      int64_t lde, int64_t nq, double* Q, int64_t ldq);
+
+// Jacobi SVD of a b x b row-major A (ld) spread over the SMs (jacobi.cu), same outputs as
+// jacobi_svd (sigma descending, U, Vt with ld); A is read only.
+int jacobi_svd_multi(Ctx& c, const double* A, int64_t b, int64_t ld, double* sigma, double* U, double* Vt, int* bad);
+// b from which the multi-CTA Jacobi is used
+constexpr int64_t kJacobiMultiFrom = 48;
+
+// Per-core-parallel partial contractions (percore.cu): one entry per core k = t..d of each summand
+// (summand-major, cores in increasing k); G is that core's r0 x r1 x w scratch, W its rows of W_k
+// (column 0 = the first sketch column of the call, leading dimension ldw), Om its Omega block.
+struct PcCore {
+  const double* X;
+  int64_t r0, n, r1;
+  const double* Om;
+  int64_t ldom;
+  double* G;
+  double* W;
+  int64_t ldw;
+};
+int rl_percore(Ctx& c, const std::vector<PcCore>& cores, int nsum, int64_t w);
+
+// Operator-applied TT vectors (matvec.cu).  mv_form: the core y_k (p0 r0 x n x p1 r1) of y = A x from
+// A_k (p0 x n x m x p1) and x_k (r0 x m x r1).  mv_reduce: W_k((a, b), l) = sum_{j,g} Ahat(a, j, g, l)
+// Z_g((b, j), l) (Ahat p0 x m x p1 x w, Z p1 x (r0 m) x w); with xb, Z_0((b, j), l) = xb(b, j).
+int mv_form(Ctx& c, const double* A, int64_t p0, int64_t n, int64_t m, int64_t p1, const double* X, int64_t r0,
+            int64_t r1, double* Y);
+int mv_reduce(Ctx& c, const double* Ahat, const double* Z, const double* xb, int64_t p0, int64_t r0, int64_t m,
+              int64_t p1, int64_t w, double* W, int64_t ldw);
+
+// out[i] = the block loop's reciprocal square root of x[i] (positive, finite), for its self-test.
+int rsqrt_selftest(Ctx& c, const double* x, double* out, int64_t n);
+
 // Widest tensor-core tile (UMMA N) usable with s slices.
 int tile_width(int s);
 
 // Small helper kernels (engine.cu)
 int transpose_f64(Ctx& c, const double* A, int64_t rows, int64_t cols, double* out);
 int scale_cols_f64(Ctx& c, double* U, int64_t ld, int64_t ncols, int64_t rows, const double* s);
-int scale_rows_rsqrt_f64(Ctx& c, double* Vt, int64_t ld, int64_t nrows, int64_t ncols, const double* lam);
+int scale_rows_f64(Ctx& c, double* A, int64_t ld, int64_t nrows, int64_t ncols, const double* s);   // row i *= s[i]
+int identity_f64(Ctx& c, double* A, int64_t m);                                                      // A = I (m x m)
 
 // rows x cc x bcols of a block projection from which the sliced form uses the tensor cores
 constexpr double kSlicedProjectWork = 1 << 24;
@@ -254,9 +302,10 @@ struct Engine {
   int scale_cols(Ctx& c, double* U, int64_t ld, int64_t ncols, int64_t rows, const double* s) const {
     return scale_cols_f64(c, U, ld, ncols, rows, s);
   }
-  int scale_rows_inv(Ctx& c, double* Vt, int64_t ld, int64_t nrows, int64_t ncols, const double* lam) const {
-    return scale_rows_rsqrt_f64(c, Vt, ld, nrows, ncols, lam);
+  int scale_rows(Ctx& c, double* A, int64_t ld, int64_t nrows, int64_t ncols, const double* s) const {
+    return scale_rows_f64(c, A, ld, nrows, ncols, s);
   }
+  int identity(Ctx& c, double* A, int64_t m) const { return identity_f64(c, A, m); }
 };
 
 }  // namespace ttr

@@ -642,18 +642,41 @@ int fill_zero(Ctx& c, double* p, int64_t count) {
 
 // ----------------------------------------------------------------------------- Jacobi SVD
 // One-sided (Hestenes) Jacobi on the columns of a b x b matrix A, one CTA, b <= 1024.
-// Round-robin pair ordering: in round r, position i pairs with position b2-1-i where
-// positions hold players (0, 1+((i-1+r) mod (b2-1))).  One warp per pair.
+// The columns are rotated as the rows of A^T, which lives in U's storage during the sweeps, so a
+// warp reads and writes each column it rotates as one contiguous run; V accumulates the same
+// rotations on the rows of Vt.  Round-robin pair ordering: in round r, position i pairs with
+// position b2-1-i where positions hold players (0, 1+((i-1+r) mod (b2-1))).  One warp per pair.
+// A pair is rotated when |a_p^T a_q| > 1e-15 ||a_p|| ||a_q||, unless both columns are below the
+// rounding level b u ||A||_F of the factor A came from (their rotations change nothing above it).
+// Singular values come out to about u ||A|| absolute (no Gram matrix is formed).
 __global__ void __launch_bounds__(1024) jacobi_svd_kernel(double* A, int64_t b, int64_t ld, double* sigma,
                                                           double* U, double* Vt, int* bad) {
   extern __shared__ int sh_idx[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int64_t b2 = (b + 1) & ~1LL;
-  // V := I  (stored transposed as Vt rows = columns of V)
-  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) Vt[(e / b) * ld + (e % b)] = ((e / b) == (e % b)) ? 1.0 : 0.0;
+  double* At = U;                                    // row j of At = column j of A
+  __shared__ double s_part[32];
   __shared__ int rotated;
+  double nrm2 = 0.0;
+  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int64_t i = e / b, j = e % b;
+    const double v = A[i * ld + j];
+    At[j * ld + i] = v;
+    nrm2 = fma(v, v, nrm2);
+    Vt[i * ld + j] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+  if (lane == 0) s_part[warp] = nrm2;
   __syncthreads();
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nwarps; ++w) t += s_part[w];
+    s_part[0] = t;
+  }
+  __syncthreads();
+  const double floor_ = (double)b * 2.220446049250313e-16;
+  const double tiny = floor_ * floor_ * s_part[0];   // squared column norm of the rounding level
+  for (int sweep = 0; sweep < 60; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int64_t r = 0; r < b2 - 1; ++r) {
@@ -662,9 +685,11 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(double* A, int64_t b, 
         const int64_t p = (i1 == 0) ? 0 : 1 + ((i1 - 1 + r) % (b2 - 1));
         const int64_t q = (i2 == 0) ? 0 : 1 + ((i2 - 1 + r) % (b2 - 1));
         if (p >= b || q >= b) continue;
+        double* xp = At + p * ld;
+        double* xq = At + q * ld;
         double al = 0, be = 0, ga = 0;
         for (int64_t i = lane; i < b; i += 32) {
-          const double x = A[i * ld + p], y = A[i * ld + q];
+          const double x = xp[i], y = xq[i];
           al = fma(x, x, al);
           be = fma(y, y, be);
           ga = fma(x, y, ga);
@@ -674,31 +699,33 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(double* A, int64_t b, 
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
+        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al) * sqrt(be) && !(al <= tiny && be <= tiny)) {
           const double zeta = (be - al) / (2.0 * ga);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
           const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          double* vp = Vt + p * ld;
+          double* vq = Vt + q * ld;
           for (int64_t i = lane; i < b; i += 32) {
-            const double x = A[i * ld + p], y = A[i * ld + q];
-            A[i * ld + p] = cs * x - sn * y;
-            A[i * ld + q] = sn * x + cs * y;
-            const double vx = Vt[p * ld + i], vy = Vt[q * ld + i];
-            Vt[p * ld + i] = cs * vx - sn * vy;
-            Vt[q * ld + i] = sn * vx + cs * vy;
+            const double x = xp[i], y = xq[i];
+            xp[i] = cs * x - sn * y;
+            xq[i] = sn * x + cs * y;
+            const double vx = vp[i], vy = vq[i];
+            vp[i] = cs * vx - sn * vy;
+            vq[i] = sn * vx + cs * vy;
           }
           if (lane == 0) rotated = 1;
         }
       }
       __syncthreads();
     }
+    const int any = rotated;
     __syncthreads();
-    if (!rotated) break;
-    __syncthreads();
+    if (!any) break;
   }
-  // sigma_j = ||a_j||, U_j = a_j / sigma_j; sort descending (selection sort by thread 0)
+  // sigma_j = ||a_j||; sort descending (selection sort by thread 0)
   for (int64_t j = warp; j < b; j += nwarps) {
     double s = 0;
-    for (int64_t i = lane; i < b; i += 32) s = fma(A[i * ld + j], A[i * ld + j], s);
+    for (int64_t i = lane; i < b; i += 32) s = fma(At[j * ld + i], At[j * ld + i], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) sigma[j] = sqrt(s);
   }
@@ -715,21 +742,29 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(double* A, int64_t b, 
     }
   }
   __syncthreads();
-  // U(:, j) = A(:, idx[j]) / sigma[idx[j]]; Vt row j = old Vt row idx[j]  (A and old Vt still intact)
-  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int64_t i = e / b, j = e % b;
-    const int src = sh_idx[j];
-    const double s = sigma[src];
-    U[i * ld + j] = (s > 0.0) ? A[i * ld + src] / s : ((i == j) ? 1.0 : 0.0);
-  }
-  __syncthreads();
-  // permute Vt rows through A (A is free now) and sigma
+  // A (free now) <- the permuted rows of Vt
   for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int64_t j = e / b, i = e % b;
     A[j * ld + i] = Vt[(int64_t)sh_idx[j] * ld + i];
   }
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) Vt[(e / b) * ld + (e % b)] = A[(e / b) * ld + (e % b)];
+  // Vt's storage <- U(:, j) = a_{idx[j]} / sigma[idx[j]] (row-major U), read from At
+  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int64_t i = e / b, j = e % b;
+    const int src = sh_idx[j];
+    const double s = sigma[src];
+    Vt[i * ld + j] = (s > 0.0) ? At[(int64_t)src * ld + i] / s : ((i == j) ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int64_t i = e / b, j = e % b;
+    U[i * ld + j] = Vt[i * ld + j];
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int64_t i = e / b, j = e % b;
+    Vt[i * ld + j] = A[i * ld + j];
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int64_t j = 0; j < b; ++j) A[j] = sigma[sh_idx[j]];

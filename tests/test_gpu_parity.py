@@ -253,15 +253,23 @@ def test_adaptive_estimator_reading_parity(B, name, make, tol, block, est_min, b
 
 
 # ------------------------------------------------------------------ Algorithm 1
-@pytest.mark.parametrize("tol", [1e-2, 1e-6])
-def test_deterministic_c1(B, tol):
-    x = WL.c1()
+@pytest.mark.parametrize("name,make,tol", [("c1", lambda: WL.c1(), 1e-2), ("c1", lambda: WL.c1(), 1e-6),
+                                           ("c1", lambda: WL.c1(), 1e-9),
+                                           ("c3", lambda: WL.c3(), 1e-8), ("c2", lambda: WL.c2(), 1e-6),
+                                           ("ragged", lambda: WL.copies_plus_noise(8, 5, 7, 5, 3, 2, 1e-6, "r"), 1e-5)])
+def test_deterministic_fp64(B, name, make, tol):
+    """Algorithm 1 in FP64 against the oracle's LAPACK QR/SVD form: identical ranks, the represented
+    tensors within 1e-10, the tolerance met.  The formal sums (c1, c2, ragged) have numerically
+    rank-deficient unfoldings; the operator-applied vector (c3) is truncated at 1e-8, where a Gram
+    matrix could not resolve the discarded singular values."""
+    x = make()
     ref, info = R.tt_round_deterministic(x.cores, tol)
     with B.round_deterministic(dev(x.cores), tol) as y:
-        assert y.ranks == info["ranks"]
+        assert y.ranks == info["ranks"], (y.ranks, info["ranks"])
         got = y.to_numpy()
-    assert T.tt_dist(got, x.cores) <= tol * x.norm
-    assert rel_tensor_diff(got, ref) <= 1e-7
+        assert math.isclose(y.info["tau"], info["tau"], rel_tol=1e-10)
+    assert T.tt_dist(got, x.cores) <= tol * x.norm * (1 + 1e-9)
+    assert rel_tensor_diff(got, ref) <= 1e-10
 
 
 # ------------------------------------------------------------------ edge cases and errors
@@ -293,3 +301,42 @@ def test_partial_contractions_every_slice_count(B, slices):
     for k, Wk in ref.items():
         err = np.abs(got[k].cpu().numpy() - Wk).max() / np.abs(Wk).max()
         assert err <= bound, (slices, k, err, bound)
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-4])
+def test_adaptive_sliced_at_the_tolerance_chosen_slice_count(B, tol):
+    """The bench workload (d=20, n=50, formal rank 210, block 10) in sliced form with the slice count
+    the tolerance chooses: 4 slices at 1e-3 (each product exact to ~4 * 2^-27 = 3e-8 of sum |a||b|)
+    and 5 at 1e-4 (~3e-10), with the double-float block loop.  Stated bar for these loose forms: ranks
+    identical to the FP64 oracle's, the represented tensor within max(1e-8, 1e-3 tol) of the oracle's,
+    and the tolerance met."""
+    x = WL.c2()
+    ref, info = R.tt_round_adaptive(x.cores, tol, seed=2024, block=10, nrmx=x.norm)
+    with B.round_adaptive(dev(x.cores), tol, 10, 2024, B.options(precision=B.TTR_PREC_SLICED, nrmx=x.norm)) as y:
+        assert y.ranks == info["ranks"]
+        got = y.to_numpy()
+    assert rel_tensor_diff(got, ref) <= max(1e-8, 1e-3 * tol)
+    assert T.tt_dist(got, x.cores) <= tol * x.norm
+
+
+def test_adaptive_sliced_default_with_fp64_block_loop(B):
+    """The bench configuration (6 slices at tol 1e-6) with the block loop kept in FP64
+    (block_loop_fp64): the same bars as the default sliced form, whose block loop is double-float."""
+    x = WL.c2()
+    ref, info = R.tt_round_adaptive(x.cores, 1e-6, seed=2024, block=10, nrmx=x.norm)
+    with B.round_adaptive(dev(x.cores), 1e-6, 10, 2024,
+                          B.options(precision=B.TTR_PREC_SLICED, nrmx=x.norm, block_loop_fp64=True)) as y:
+        assert y.ranks == info["ranks"]
+        got = y.to_numpy()
+    assert rel_tensor_diff(got, ref) <= 1e-8
+    assert T.tt_dist(got, x.cores) <= 1e-6 * x.norm
+
+
+def test_adaptive_adap_r_sliced(B):
+    """The Remark 3.2 pass after the sliced rounding (8 slices): ranks and tensor as the oracle's."""
+    x = WL.c1()
+    ref, info = R.tt_round_adaptive(x.cores, 1e-6, seed=5, block=2, nrmx=x.norm, adap_r=True)
+    with B.round_adaptive(dev(x.cores), 1e-6, 2, 5, B.options(precision=B.TTR_PREC_SLICED, slices=8, nrmx=x.norm,
+                                                               adap_r=True)) as y:
+        assert y.ranks == info["ranks"]
+        assert rel_tensor_diff(y.to_numpy(), ref) <= 1e-10

@@ -75,3 +75,47 @@ def test_server_budget_admits_one_at_a_time(B):
     assert st["peak_in_use"] <= biggest
     # first come, first served: requests are admitted in the order they were submitted
     assert [i["admit_order"] for i in infos] == list(range(len(reqs)))
+
+
+def serving_requests(ids):
+    return [q for q in WL.c4_stream(count=max(ids) + 1, formal=False) if q.rid in ids]
+
+
+def test_server_serving_stream_requests_alone_and_in_the_mix(B):
+    """Two requests of the serving stream at their configured sizes (request 12: 2 summands of ranks
+    93 and 31, d = 31, n = 112; request 16: ranks 98 and 77, d = 16, n = 75; both tol 1e-6, formal
+    ranks 124 and 175), in the precision the serving measurement uses (sliced, slices from tol: 6,
+    ~2.7e-12 per product), against the oracle's rounding of the same sum: identical ranks, the
+    represented tensor within 1e-8 of the oracle's.  Each is rounded alone (one worker) and again in a
+    mix with the small requests on three workers; the two results agree within the same bar (the
+    block loop's SM share, hence its reduction order, differs)."""
+    big = serving_requests({12, 16})
+    opts = B.options(precision=B.TTR_PREC_SLICED)
+    alone = {}
+    with B.Server(workers=1, device_budget=16 << 30) as srv:
+        for q in big:
+            alone[q.rid] = srv.wait(srv.submit(q.tt.summands, q.tol, 0, 1000 + q.rid, opts))
+    for q in big:
+        got, info = alone[q.rid]
+        ref, rinfo = R.tt_round_adaptive_sum(q.tt.summands, q.tol, 1000 + q.rid, block=0)
+        assert info["ranks"] == rinfo["ranks"], (q.rid, info["ranks"], rinfo["ranks"])
+        assert T.tt_dist(got, ref) <= 1e-8 * T.tt_norm(ref), q.rid
+    small = requests()
+    with B.Server(workers=3, device_budget=16 << 30) as srv:
+        ids = []
+        for i, q in enumerate(big):
+            ids.append(("big", q, srv.submit(q.tt.summands, q.tol, 0, 1000 + q.rid, opts)))
+            for xs, tol, block, seed, prec in small[3 * i:3 * i + 3]:
+                ids.append(("small", (xs, tol, block, seed, prec),
+                            srv.submit(xs, tol, block, seed, B.options(precision=prec, slices=8))))
+        for kind, q, rid in ids:
+            got, info = srv.wait(rid)
+            if kind == "big":
+                ref, rinfo = alone[q.rid]
+                assert info["ranks"] == rinfo["ranks"]
+                assert T.tt_dist(got, ref) <= 1e-8 * T.tt_norm(ref), q.rid
+            else:
+                xs, tol, block, seed, prec = q
+                ref, rinfo = R.tt_round_adaptive_sum(xs, tol, seed, block=block)
+                assert info["ranks"] == rinfo["ranks"]
+                assert T.tt_dist(got, ref) <= (1e-10 if prec == 0 else 1e-9) * T.tt_norm(ref)

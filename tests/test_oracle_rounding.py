@@ -78,6 +78,39 @@ def test_partial_contractions_column_chunks_append():
         assert np.allclose(full[k], np.concatenate([a[k], b[k]], axis=1), rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("d,n,r", [(4, 3, 2), (5, [2, 3, 4, 2, 3], 3), (3, 4, [2, 5])])
+def test_percore_contractions_equal_definition(d, n, r):
+    """The per-core form (Conclusion, Sec. 5) gives Algorithm 3's W_k: against the explicit
+    H(X_{k:d}) times the explicit Kronecker columns, and against the chain itself."""
+    cores = tiny_tt(10 + d, d, n, r)
+    nn = T.modes(cores)
+    W = R.partial_contractions_percore(cores, 31, 2, 9)
+    Wc = R.partial_contractions_rl(cores, 31, 2, 9)
+    for k in range(2, d + 1):
+        Rk = right_part(cores, k)                                       # C order: i_d fastest
+        ref = Rk.reshape(Rk.shape[0], -1) @ krp_columns(31, list(range(k, d + 1)), nn, 2, 9)
+        assert np.allclose(W[k], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+        assert np.allclose(W[k], Wc[k], rtol=0, atol=1e-13 * np.abs(ref).max())
+    Wt = R.partial_contractions_percore(cores, 31, 5, 9, t=3)          # column chunk and t > 2
+    for k in range(3, d + 1):
+        assert np.allclose(Wt[k], W[k][:, 3:], rtol=0, atol=1e-14 * np.abs(W[k]).max())
+
+
+def test_planted_percore_transpose_mistake_is_caught(monkeypatch):
+    """G_k(:, :, j) applied transposed (a plausible index slip) no longer matches the definition."""
+    cores = tiny_tt(14, 4, 3, 3)
+    real = np.einsum
+
+    def wrong(spec, *ops, **kw):
+        return real("jca,cj->aj" if spec == "jac,cj->aj" else spec, *ops, **kw)
+
+    monkeypatch.setattr(R.np, "einsum", wrong)
+    W = R.partial_contractions_percore(cores, 31, 0, 6)
+    monkeypatch.setattr(R.np, "einsum", real)
+    ref = R.partial_contractions_rl(cores, 31, 0, 6)
+    assert not np.allclose(W[2], ref[2], rtol=0, atol=1e-10 * np.abs(ref[2]).max())
+
+
 def test_planted_krp_order_mistake_is_caught(monkeypatch):
     cores = tiny_tt(4, 4, 3, 2)
     nn = T.modes(cores)
@@ -435,3 +468,40 @@ def test_adaptive_rank_bounded_by_the_right_part():
     Y, info = R.tt_round_adaptive(cores, 1e-10, seed=4, block=3, nrmx=float(np.linalg.norm(X)))
     assert info["ranks"][3] <= 2
     assert np.linalg.norm(T.full(Y) - X) <= 1e-10 * np.linalg.norm(X)
+
+
+# ------------------------------------------------------------------ operator application (Sec. 4.3)
+def test_tt_matvec_equals_the_dense_product():
+    rng = np.random.default_rng(21)
+    d, n = 4, [3, 2, 4, 3]
+    p = [1, 2, 3, 2, 1]
+    op = [rng.standard_normal((p[k], n[k], n[k], p[k + 1])) for k in range(d)]
+    x = WL.random_tt(rng, d, n, 3)
+    y = T.tt_matvec(op, x)
+    assert T.ranks(y) == [1, 6, 9, 6, 1]
+    dense = T.full_operator(op) @ T.full(x).reshape(-1)
+    assert np.allclose(T.full(y).reshape(-1), dense, rtol=0, atol=1e-13 * np.abs(dense).max())
+
+
+def test_laplacian_operator_is_the_kronecker_sum():
+    """The rank-2 TT operator of the operator-applied workload is sum_m I x .. x L x .. x I with
+    L = tridiag(-1, 2, -1): its dense matrix built term by term with numpy.kron."""
+    d, n = 4, 5
+    op = WL.laplace_tt_operator(d, n)
+    L = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    ref = np.zeros((n ** d, n ** d))
+    for m in range(d):
+        term = np.ones((1, 1))
+        for k in range(d):
+            term = np.kron(term, L if k == m else np.eye(n))
+        ref += term
+    assert np.array_equal(T.full_operator(op), ref)
+
+
+def test_adaptive_matvec_rounds_the_product():
+    op = WL.laplace_tt_operator(5, 6)              # y = A x, formal rank 8
+    rng = np.random.default_rng(4)
+    xv = WL.random_tt(rng, 5, 6, 4)
+    Y, info = R.tt_round_adaptive_matvec(op, xv, 1e-10, seed=3, block=2)
+    dense = T.full_operator(op) @ T.full(xv).reshape(-1)
+    assert np.linalg.norm(T.full(Y).reshape(-1) - dense) <= 1e-10 * np.linalg.norm(dense) * (1 + 1e-9)
