@@ -620,7 +620,7 @@ def main():
     # single-stream rounding with the block loop in FP64, and at 8 slices (FP64-accurate contractions)
     forms = {}
     if prec == B.TTR_PREC_SLICED:
-        for name, kw in (("sliced6_fp64_block_loop", {"block_loop_fp64": True}), ("sliced8_fp64", {"slices": 8})):
+        for name, kw in (("sliced6_df_block_loop", {"block_loop_df": True}), ("sliced8_fp64", {"slices": 8})):
             fo = B.options(precision=prec, nrmx=x.norm, **kw)
             for _ in range(2):
                 B.round_adaptive(cores, TOL, BLOCK, SEED, fo).free()
@@ -638,7 +638,7 @@ def main():
             forms[name] = {"roundings_per_s": 1e3 * nf / fe[0].elapsed_time(fe[-1]),
                            "p50_ms": float(np.percentile(fms, 50)), "p99_ms": float(np.percentile(fms, 99)),
                            "steps": nf, "ranks_equal_headline": franks == out_ranks,
-                           "what": ("6 slices, CholeskyQR2 / Gram / estimator of the block loop in FP64"
+                           "what": ("6 slices, the block loop's per-CTA arithmetic in double-float (FP32 pipe)"
                                     if "6" in name else "8 slices (contractions FP64-accurate), FP64 block loop"),
                            "measured": "one rounding at a time on one stream (compare single_stream)"}
 

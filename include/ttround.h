@@ -69,10 +69,24 @@ typedef enum {
  *   8 slices reproduce FP64 results to about 1e-15 relative, s slices to about s 2^(1-7s) of
  *   sum |a||b| per product.  The host-driven block loop, the Remark 3.2 pass, the truncation SVDs
  *   and every cross-CTA sum are FP64.  The persistent device block loop of Algorithm 6 (its
- *   CholeskyQR2 Gram matrices, block Gram-Schmidt and residual norms) is FP64 at 7 and 8 slices;
- *   at 3..6 slices its per-CTA arithmetic is double-float (pairs of binary32, about 2^-48 relative,
- *   on the FP32 pipe) unless ttr_options::block_loop_fp64 is set. */
-typedef enum { TTR_PREC_FP64 = 0, TTR_PREC_SLICED = 1 } ttr_precision;
+ *   CholeskyQR2 Gram matrices, block Gram-Schmidt and residual norms) is FP64 as well, unless
+ *   ttr_options::block_loop_df asks for double-float at 3..6 slices.
+ * TTR_PREC_TF32_SKETCH, TTR_PREC_BF16_SKETCH: the reduced-precision sketch forms.  Only the
+ *   right-to-left partial contractions (the W chain, Algorithm 3, with its extensions) and the sketch
+ *   S_k = V(Y_k) W_{k+1} take reduced-precision operands: TF32 (each operand rounded to FP32, then to
+ *   TF32's 11 significant bits, and multiplied as an exact BF16 head + tail, three BF16 products) or
+ *   BF16 (8 significant bits), with FP32 accumulation on the tensor cores and the Omega weighting and
+ *   slab sums in FP64.  The next-core projections, QR, Gram matrices, estimator, truncations and
+ *   Remark 3.2 pass stay FP64-accurate (8 slices for the large products, FP64 elsewhere).  A
+ *   reduced-precision sketch captures the range of X up to a perturbation of about u_low ||X||
+ *   (u_low = 2^-11 TF32, 2^-8 BF16), so at tolerances below that the block loop grows the ranks
+ *   toward rbar_k; opts->adap_r then truncates the FP64-accurate result. */
+typedef enum {
+  TTR_PREC_FP64 = 0,
+  TTR_PREC_SLICED = 1,
+  TTR_PREC_TF32_SKETCH = 2,
+  TTR_PREC_BF16_SKETCH = 3
+} ttr_precision;
 
 typedef struct {
   int32_t precision;      /* ttr_precision */
@@ -103,10 +117,12 @@ typedef struct {
                              Conclusion (Sec. 5): every G_k(:, :, j) = sum_i X_k(:, i, :) Omega_k(i, j)
                              in one launch, then W_k(:, j) = G_k(:, :, j) W_{k+1}(:, j) column by
                              column in another (FP64; scratch 8 sum_k r_{k-1} r_k w bytes); 2 = the
-                             per-core form when that scratch is at most 32 MiB, else the chain */
-  int32_t block_loop_fp64;/* TTR_PREC_SLICED with 3..6 slices: 1 = keep the device block loop in FP64
-                             (CholeskyQR2, Gram matrices and estimator FP64 at any slice count);
-                             0 = its per-CTA arithmetic in double-float (default) */
+                             per-core form when that scratch is at most 32 MiB in FP64 precision, 2 MiB
+                             in sliced precision, else the chain */
+  int32_t block_loop_df;  /* TTR_PREC_SLICED with 3..6 slices: 1 = the device block loop's per-CTA
+                             arithmetic in double-float (pairs of binary32, about 2^-48 relative, on
+                             the FP32 pipe; cross-CTA sums stay FP64); 0 = FP64 (default: CholeskyQR2,
+                             the Gram matrices and the estimator FP64 at every slice count) */
 } ttr_options;
 
 typedef struct {
@@ -138,7 +154,7 @@ typedef struct {
 
 /* Fill `opts` with defaults: FP64, adap_r off, scale 1, nrmx 0 (estimate), f_init 0.1,
  * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0, max_sms 0, est_min 0,
- * est_safety 1, rl_percore 0, block_loop_fp64 0. */
+ * est_safety 1, rl_percore 0, block_loop_df 0. */
 void ttr_default_options(ttr_options* opts);
 
 /* Algorithm 4 (Sec. 3.2): fixed-rank randomize-then-orthogonalize with a KRP sketch.

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libttround.so")
 
 TTR_PREC_FP64 = 0
 TTR_PREC_SLICED = 1
+TTR_PREC_TF32_SKETCH = 2
+TTR_PREC_BF16_SKETCH = 3
 STATUS = {0: "TTR_OK", 1: "TTR_ERR_ARG", 2: "TTR_ERR_OOM", 3: "TTR_ERR_NONFINITE", 4: "TTR_ERR_QR_BREAKDOWN",
           5: "TTR_ERR_TIMEOUT", 6: "TTR_ERR_CUDA", 7: "TTR_ERR_UNSUPPORTED"}
 
@@ -26,7 +28,7 @@ class Options(ctypes.Structure):
                 ("adap_r_tau_scale", ctypes.c_double), ("nrmx", ctypes.c_double), ("f_init", ctypes.c_double),
                 ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64), ("kernel_timing", ctypes.c_int32),
                 ("max_sms", ctypes.c_int32), ("est_min", ctypes.c_int32), ("est_safety", ctypes.c_double),
-                ("rl_percore", ctypes.c_int32), ("block_loop_fp64", ctypes.c_int32)]
+                ("rl_percore", ctypes.c_int32), ("block_loop_df", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -142,7 +144,7 @@ def _tt_args(cores):
 def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = False, adap_r_tau_scale: float = 1.0,
             nrmx: float = 0.0, f_init: float = 0.1, f_inc: float = 0.05, width_hint: int = 0,
             kernel_timing: bool = False, max_sms: int = 0, est_min: int = 0, est_safety: float = 1.0,
-            rl_percore: int = 0, block_loop_fp64: bool = False) -> Options:
+            rl_percore: int = 0, block_loop_df: bool = False) -> Options:
     o = Options()
     lib().ttr_default_options(ctypes.byref(o))
     o.precision, o.slices, o.adap_r = precision, slices, int(adap_r)
@@ -151,7 +153,7 @@ def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = Fals
     o.max_sms = int(max_sms)
     o.est_min, o.est_safety = int(est_min), float(est_safety)
     o.rl_percore = int(rl_percore)
-    o.block_loop_fp64 = int(block_loop_fp64)
+    o.block_loop_df = int(block_loop_df)
     return o
 
 

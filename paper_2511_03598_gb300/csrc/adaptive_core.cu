@@ -35,7 +35,7 @@ namespace ttr {
 namespace ac {
 
 constexpr int NT = 256;
-constexpr int BMAX = 32;                          // largest block handled here
+constexpr int BMAX = kBlockLoopMaxBlock;          // largest block handled here
 constexpr long long BAR_CYCLES = 4000000000LL;   // ~2 s
 
 enum Status { ST_DONE = 0, ST_EXTEND = 1, ST_BREAKDOWN = 2, ST_TIMEOUT = 3 };
@@ -62,6 +62,8 @@ struct Args {
   int* io;              // [0] status, [1] cc, [2] number of estimates
   unsigned long long* prof;   // optional: SM cycles per phase, seen by CTA 0 (null: off)
   int sshift;           // the sketch is held scaled by 2^sshift (double-float range; 0 in FP64)
+  double* gwork;        // null: the CTA's rows live in shared memory; else in this global buffer,
+  int64_t gstride;      //   gstride doubles per CTA (rows too wide for shared memory)
 };
 
 // Phase timer of CTA 0 (launch-timeline profiling only): cycles since the previous mark are
@@ -82,7 +84,7 @@ struct Timer {
 // the CTA's copy of Args::prof, for grid_sync
 __shared__ unsigned long long* s_barrier_prof;
 
-constexpr int ACC = 8192;                         // doubles per accumulation buffer (>= rbar * BMAX)
+constexpr int ACC = 8192;                         // doubles per accumulation buffer allocated up front
 
 __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
   __syncthreads();
@@ -200,9 +202,10 @@ struct DF {
   }
 };
 
-// Each CTA keeps its own rows resident in shared memory:
+// Each CTA keeps its own rows resident in shared memory (or, for rows too wide, in its own region
+// of a global buffer, with the same layout):
 //   Qs  [nr][ldq]  rows of Q,    Ss [nr][ldw] rows of the sketch S_all,   Rs [nr][bi] residual block.
-// buf[i*b + j] += sum_{own rows} X(r, i) Y(r, j), i < a, j < b   (X, Y in shared memory)
+// buf[i*b + j] += sum_{own rows} X(r, i) Y(r, j), i < a, j < b   (X, Y the CTA's own rows)
 template <class A>
 __device__ void gram_acc(const typename A::T* X, int ldx, const typename A::T* Y, int ldy, int a, int b, int nr,
                          double* buf) {
@@ -614,7 +617,8 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   const int nr = (int)(hi - lo);
   const int ldq = (int)a.qcols, ldw = a.width, bi = a.bi;
   static_assert(sizeof(T) == sizeof(double), "the shared-memory layout assumes 8-byte elements");
-  T* Qs = reinterpret_cast<T*>(sm);                  // [rpc][ldq]   own rows of Q
+  double* base = a.gwork ? a.gwork + (int64_t)blockIdx.x * a.gstride : sm;
+  T* Qs = reinterpret_cast<T*>(base);                // [rpc][ldq]   own rows of Q
   T* Ss = Qs + (size_t)a.rpc * ldq;                  // [rpc][ldw]   own rows of the sketch S_all (x 2^sshift)
   T* Rs = Ss + (size_t)a.rpc * ldw;                  // [rpc][bi]    residual block (x 2^sshift)
   T* Tb = Rs + (size_t)a.rpc * bi;                   // [rpc][BMAX]  staging for X R^{-1}
@@ -797,13 +801,30 @@ int rsqrt_selftest(Ctx& c, const double* x, double* out, int64_t n) {
   return c.check_launch("rsqrt_selftest");
 }
 
+// Whether the block loop's rows for these sizes fit in shared memory (else they would live in
+// global memory); the same sizing as adaptive_core.
+bool adaptive_core_rows_fit(int64_t m, int b0, int bi, int rbar, int width, int max_sms) {
+  int dev = 0, nsm = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  const int sms = (max_sms > 0 && max_sms < nsm) ? max_sms : nsm;
+  const int nblocks = (int)std::min<int64_t>(sms, m);
+  if (nblocks < 1) return false;
+  const int rpc = (int)((m + nblocks - 1) / nblocks);
+  const int64_t qcols = std::min(rbar, width);
+  const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
+                                        2 * (size_t)qcols * (size_t)std::max(b0, bi));
+  return dyn + 48 * 1024 <= (size_t)optin;
+}
+
 // Host side: runs the adaptive loop of one core on the device.  Returns TTR_OK with *status set
 // (ST_DONE, ST_EXTEND: more sketch columns are needed, ST_BREAKDOWN: a CholeskyQR pivot failed
 // at column *cc), or TTR_ERR_UNSUPPORTED when this path does not apply.
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
                   int bi, int ba, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status,
-                  int* cc, int* nest, bool double_float, double scale, int max_sms) {
-  if (b0 > ac::BMAX || bi > ac::BMAX || (int64_t)rbar * bi > ac::ACC || m <= 0) return TTR_ERR_UNSUPPORTED;
+                  int* cc, int* nest, bool double_float, double scale, int max_sms, bool host_if_global) {
+  if (b0 > ac::BMAX || bi > ac::BMAX || m <= 0) return TTR_ERR_UNSUPPORTED;
   if (ba < 1 || ba > bi) return set_error("adaptive loop: appended block wider than the residual sketch"), TTR_ERR_ARG;
   int dev = 0;
   TTR_CUDA(cudaGetDevice(&dev));
@@ -832,11 +853,24 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
                                         2 * (size_t)qcols * (size_t)std::max(b0, bi));
   const size_t static_bytes = 48 * 1024;   // G, R^{-1} (FP64 and working type), [G | I], pivot buffers (about 44 KB)
-  if (dyn + static_bytes > (size_t)smem_optin) return TTR_ERR_UNSUPPORTED;
+  // rows that do not fit in shared memory live in a global buffer, one region per CTA (same layout)
+  const bool global_rows = dyn + static_bytes > (size_t)smem_optin;
+  if (global_rows && host_if_global) return TTR_ERR_UNSUPPORTED;
   const void* kern = double_float ? (const void*)ac::adaptive_core_kernel<ac::DF>
                                   : (const void*)ac::adaptive_core_kernel<ac::F64>;
   const int ki = double_float ? 1 : 0;
-  {
+  double* gwork = nullptr;
+  const int64_t gstride = (int64_t)((dyn / sizeof(double) + 31) / 32 * 32);
+  if (global_rows) {
+    const size_t need = sizeof(double) * (size_t)gstride * (size_t)nblocks;
+    if (c.ac_gwork_bytes < need) {
+      void* p = nullptr;
+      TTR_CHECK(c.alloc(&p, need));
+      c.ac_gwork = static_cast<double*>(p);
+      c.ac_gwork_bytes = need;
+    }
+    gwork = c.ac_gwork;
+  } else {
     // the limit belongs to the kernel, shared by every thread that calls it: only ever raise it
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -848,10 +882,17 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
       di.raised[ki] = (int)dyn;
     }
   }
-  if (!c.ac_part) {
-    TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * (ac::ACC + 64)));   // 3 buffers of up to ACC + 33 doubles
+  // largest reduction: first block (b0^2 + b0 bi) or the second one of a block ((cc + bb)(bb + bi)
+  // <= 2 rbar bi); the estimate's (1 + bi^2) and fresh coefficients (rbar bi) are smaller
+  const int used = (std::max(b0 * b0 + b0 * bi, 1 + 2 * rbar * bi) + 1 + 31) / 32 * 32;
+  if (!c.ac_bar) {
     TTR_CHECK(c.alloc_t(&c.ac_bar, 4));
     TTR_CUDA(cudaMemsetAsync(c.ac_bar, 0, 4 * sizeof(unsigned), c.stream));
+  }
+  if (c.ac_part_cap < used) {
+    const int cap = std::max(used, ac::ACC + 64);
+    TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * cap));   // 3 rotating accumulation buffers
+    c.ac_part_cap = cap;
   }
   // status words and the estimates share one device buffer, read back by a single copy:
   // [status, cc, count, -] ints, then up to est_cap doubles
@@ -866,16 +907,13 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
     TTR_CHECK(c.alloc_t(&c.d_flags, 4));
     TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
   }
-  // largest reduction: first block (b0^2 + b0 bi) or the second one of a block ((cc + bb)(bb + bi)
-  // <= 2 rbar bi); the estimate's (1 + bi^2) and fresh coefficients (rbar bi) are smaller
-  const int used = (std::max(b0 * b0 + b0 * bi, 1 + 2 * rbar * bi) + 1 + 31) / 32 * 32;
-  if (used > ac::ACC + 64) return TTR_ERR_UNSUPPORTED;
   TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * used, c.stream));
   ac::Args a{};
   a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;
   a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.ba = ba; a.rbar = rbar; a.width = width; a.cc0 = cc0;
   a.tau = tau;
   a.bar = c.ac_bar; a.err = c.d_flags; a.est_out = reinterpret_cast<double*>(c.ac_io + 4); a.io = c.ac_io;
+  a.gwork = gwork; a.gstride = gstride;
   // double-float keeps binary32 exponents: hold the sketch scaled so that ||X|| maps near 1
   a.sshift = 0;
   if (double_float && scale > 0.0 && isfinite(scale)) {
@@ -892,7 +930,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   }
   void* params[] = {&a};
   c.time_begin(Ctx::KT_BLOCK_LOOP);
-  TTR_CUDA(cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(ac::NT), params, dyn, c.stream));
+  TTR_CUDA(cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(ac::NT), params, global_rows ? 0 : dyn, c.stream));
   TTR_CHECK(c.check_launch("adaptive_core"));
   // one launch makes at most one estimate per block it runs
   const int est_max = std::min(cap, (rbar - cc0) / std::max(1, ba) + 3);

@@ -456,8 +456,15 @@ struct Sketch {
   bool percore = false;           // per-core-parallel form of the pass (rl_percore)
 };
 
-// rl_percore = 2 takes the per-core form up to this much scratch
-static constexpr double kPercoreAutoBytes = 32.0 * 1024 * 1024;
+// rl_percore = 2 takes the per-core form up to this much scratch: in FP64 form, where it replaces a
+// chain of FP64 GEMM launches; in sliced form only for small shapes, where launch latency dominates
+// the chain of tensor-core launches (measured: 2x faster on the 6-core workload, slower from the
+// operator-applied vector up)
+static constexpr double kPercoreAutoBytesFp64 = 32.0 * 1024 * 1024;
+static constexpr double kPercoreAutoBytesSliced = 2.0 * 1024 * 1024;
+static bool percore_auto(const Engine& E, double bytes) {
+  return bytes <= (E.precision == TTR_PREC_FP64 ? kPercoreAutoBytesFp64 : kPercoreAutoBytesSliced);
+}
 
 // Scratch bytes of the per-core-parallel pass on w columns for cores t..d of every summand.
 static double percore_bytes(const SumTT& X, int t, int64_t w) {
@@ -485,14 +492,8 @@ static int rl_pass_matvec(Ctx& c, const Engine& E, const SumTT& X, int64_t col0,
   for (int k = d; k >= t; --k) {
     const int64_t p0 = v.p[k - 1], p1 = v.p[k], r0 = v.r[k - 1], r1 = v.r[k], n = X.n[k - 1], m = v.m[k - 1];
     const double* Om = s.Om + (int64_t)(k - 1) * s.om_stride;
-    for (int64_t a = 0; a < p0; ++a) {   // Ahat(a, (j, g), l) = sum_i A_k(a, i, (j, g)) Omega_k(i, l)
-      Gemm g;
-      g.M = m * p1; g.N = w; g.K = n;
-      g.A = v.A[k - 1] + a * n * m * p1; g.sam = 1; g.sak = m * p1;
-      g.B = Om; g.sbk = s.ldom; g.sbn = 1;
-      g.C = Ahat + a * m * p1 * w; g.scm = w; g.scn = 1;
-      TTR_CHECK(E.small_gemm(c, g));
-    }
+    // Ahat(a, (j, g), l) = sum_i A_k(a, i, (j, g)) Omega_k(i, l)
+    TTR_CHECK(mv_ahat(c, v.A[k - 1], p0, n, m, p1, Om, s.ldom, w, Ahat));
     if (k == d) {
       TTR_CHECK(mv_reduce(c, Ahat, nullptr, v.x[d - 1], p0, r0, m, 1, w, s.W[d - 1] + col0, s.ldw));
       continue;
@@ -888,7 +889,7 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   if (o.rl_percore < 0 || o.rl_percore > 2) return set_error("rl_percore must be 0, 1 or 2"), TTR_ERR_ARG;
   Sketch s;
   TTR_CHECK(sketch_alloc(c, X, ell, s));
-  s.percore = o.rl_percore == 1 || (o.rl_percore == 2 && percore_bytes(XS, 2, ell) <= kPercoreAutoBytes);
+  s.percore = o.rl_percore == 1 || (o.rl_percore == 2 && percore_auto(E, percore_bytes(XS, 2, ell)));
   TTR_CHECK(rl_pass(c, E, XS, seed, 0, ell, 2, s));
   s.width = ell;
   tm.rec(1, stream);
@@ -979,7 +980,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   if (o.rl_percore < 0 || o.rl_percore > 2) return set_error("rl_percore must be 0, 1 or 2"), TTR_ERR_ARG;
   Sketch s;
   TTR_CHECK(sketch_alloc(c, X.shape(), wcap, s));
-  s.percore = o.rl_percore == 1 || (o.rl_percore == 2 && percore_bytes(X, 2, wcap) <= kPercoreAutoBytes);
+  s.percore = o.rl_percore == 1 || (o.rl_percore == 2 && percore_auto(E, percore_bytes(X, 2, wcap)));
   // Columns of W are a prefix of one counter-based stream, so how many are drawn up front (and how
   // the rest are appended) never changes a result; draw one tensor-core tile width up front and
   // grow geometrically, which keeps the number of right-to-left passes small.
@@ -1144,15 +1145,29 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
     int64_t cc = 0;
     bool done = false;
     if (device_loop) {
-      // the whole block loop on the device; the host steps in only to append sketch columns or to
-      // redo a block whose CholeskyQR broke down
+      // the whole block loop on the device; the host steps in only to append sketch columns, to
+      // factor a first block wider than the device loop's factors, or to redo a block whose
+      // CholeskyQR broke down
+      // blocks whose projections the host-driven loop puts on the tensor cores (sliced form): there
+      // a block loop with its rows in global memory (FP64 pipe) is slower than the host-driven one
+      const bool wide_tc = E.sliced() && (double)rows * rbar * bi >= kSlicedProjectWork;
+      const bool device_runs = !wide_tc || adaptive_core_rows_fit(rows, (int)std::min<int64_t>(b0, bi), (int)bi,
+                                                                  (int)rbar, (int)wcap, o.max_sms);
+      if (device_runs && b0 > kBlockLoopMaxBlock && bi <= kBlockLoopMaxBlock) {
+        TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
+        TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+        cc = b0;
+        if (cc >= rbar) done = true;
+      }
       int guard = 0;
       while (!done) {
         if (++guard > 4 * (int)rbar + 16) return set_error("adaptive loop did not terminate"), TTR_ERR_TIMEOUT;
         int status = 0, ccn = 0, nest = 0;
-        st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)b0, (int)bi, (int)ba, (int)rbar, (int)sk_cols,
-                           (int)cc, tau_stop, hest.data(), (int)hest.size(), &status, &ccn, &nest,
-                           E.precision == TTR_PREC_SLICED && E.slices <= 6 && !o.block_loop_fp64, nrmx, o.max_sms);
+        st = adaptive_core(c, Sall, wcap, w.Q, w.qcap, w.S, rows, (int)(cc > 0 ? std::min(b0, bi) : b0), (int)bi,
+                           (int)ba, (int)rbar, (int)sk_cols, (int)cc, tau_stop, hest.data(), (int)hest.size(), &status,
+                           &ccn, &nest,
+                           E.precision == TTR_PREC_SLICED && E.slices <= 6 && o.block_loop_df, nrmx, o.max_sms,
+                           wide_tc);
         if (st == TTR_ERR_UNSUPPORTED) break;
         if (st != TTR_OK) return st;
         for (int q = 0; q < nest; ++q) {
@@ -1482,7 +1497,7 @@ void ttr_default_options(ttr_options* o) {
   o->est_min = 0;
   o->est_safety = 1.0;
   o->rl_percore = 0;
-  o->block_loop_fp64 = 0;
+  o->block_loop_df = 0;
 }
 
 static int finish(int st, ttr_result* out, cudaStream_t s) {

@@ -44,6 +44,12 @@ int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M
                      int64_t ldb, int64_t N, double* C, int64_t ldc, const BPlanes* reuse = nullptr);
 int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn,
                int64_t ncol, double* Y);
+// Reduced-precision sketch forms (fs = 2: TF32 operands as BF16 head + tail; fs = 1: BF16 operands;
+// FP32 accumulation): the partial-contraction step with FP64 Omega, and a row-major product.
+int tc_rl_step_flt(Ctx& c, int fs, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
+                   const double* Om, int64_t ldo, int64_t w, double* Wout, int64_t ldwo);
+int tc_gemm_rowmajor_flt(Ctx& c, int fs, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
+                         int64_t ldb, int64_t N, double* C, int64_t ldc);
 
 // Persistent cooperative kernel for the adaptive block loop of one core (adaptive_core.cu).
 // *status: 0 done, 1 needs more sketch columns, 2 CholeskyQR breakdown at column *cc.
@@ -52,10 +58,16 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
 // FP64 accuracy is promised); scale: a value of the order of the sketch entries (the input norm).
 // The estimates (||S||_F^2 of each residual block, in order) come back in est_host (host, room for
 // est_cap values; *nest of them are written).  bi: columns of each residual sketch (the estimate's
-// width); ba <= bi: columns appended per block; tau: the stopping threshold.
+// width); ba <= bi: columns appended per block; tau: the stopping threshold.  Rows that do not fit in
+// shared memory live in global memory; host_if_global returns TTR_ERR_UNSUPPORTED instead (the
+// caller's host-driven loop, whose wide block projections run on the tensor cores, is faster there).
+bool adaptive_core_rows_fit(int64_t m, int b0, int bi, int rbar, int width, int max_sms);
+// widest block (b_init or the residual sketch) the device block loop factors itself; a wider first
+// block is factored on the host side before the loop starts at col(Q) = b_init
+constexpr int kBlockLoopMaxBlock = 32;
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
                   int bi, int ba, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status,
-                  int* cc, int* nest, bool double_float, double scale, int max_sms);
+                  int* cc, int* nest, bool double_float, double scale, int max_sms, bool host_if_global);
 
 // Householder QR of a tall row-major m x b matrix (householder.cu), for the deterministic rounding.
 // householder_qr overwrites A with the reflectors and R (R also copied to R, b x b, ld ldr, if
@@ -100,6 +112,9 @@ int mv_form(Ctx& c, const double* A, int64_t p0, int64_t n, int64_t m, int64_t p
             int64_t r1, double* Y);
 int mv_reduce(Ctx& c, const double* Ahat, const double* Z, const double* xb, int64_t p0, int64_t r0, int64_t m,
               int64_t p1, int64_t w, double* W, int64_t ldw);
+// Ahat(a, (j, g), l) = sum_i A_k(a, i, (j, g)) Omega_k(i, l), one launch (Omega n x w, leading dimension ldom)
+int mv_ahat(Ctx& c, const double* A, int64_t p0, int64_t n, int64_t m, int64_t p1, const double* Om, int64_t ldom,
+            int64_t w, double* Ahat);
 
 // out[i] = the block loop's reciprocal square root of x[i] (positive, finite), for its self-test.
 int rsqrt_selftest(Ctx& c, const double* x, double* out, int64_t n);
@@ -119,14 +134,26 @@ constexpr double kSlicedProjectWork = 1 << 24;
 struct Engine {
   int precision = TTR_PREC_FP64;
   int slices = 0;
+  int fs = 0;      // reduced-precision sketch forms: planes per operand of the W chain and the sketch
+
+  // the sliced tensor-core products run the contractions that are not sketches: every precision but
+  // FP64 (the reduced-precision forms keep their projections FP64-accurate at 8 slices)
+  bool sliced() const { return precision != TTR_PREC_FP64; }
+  bool reduced() const { return fs > 0; }
 
   int init(Ctx& c, int prec, int sl, double tol) {
     (void)c;
-    if (prec != TTR_PREC_FP64 && prec != TTR_PREC_SLICED) {
+    if (prec != TTR_PREC_FP64 && prec != TTR_PREC_SLICED && prec != TTR_PREC_TF32_SKETCH &&
+        prec != TTR_PREC_BF16_SKETCH) {
       set_error("unknown precision");
       return TTR_ERR_ARG;
     }
     precision = prec;
+    if (prec == TTR_PREC_TF32_SKETCH || prec == TTR_PREC_BF16_SKETCH) {
+      fs = prec == TTR_PREC_TF32_SKETCH ? 2 : 1;
+      slices = 8;
+      return TTR_OK;
+    }
     if (prec == TTR_PREC_SLICED) {
       if (sl == 0) {
         // enough 7-bit slices that the contraction error sits well below the tolerance:
@@ -148,14 +175,14 @@ struct Engine {
   int small_gemm(Ctx& c, const Gemm& g) const { return gemm_f64(c, g); }
 
   // sketch columns worth drawing up front: one tensor-core tile in sliced mode
-  int64_t natural_width() const { return precision == TTR_PREC_SLICED ? tile_width(slices) : 64; }
+  int64_t natural_width() const { return sliced() ? tile_width(slices) : 64; }
 
   // S = Z W(:, cols): A row-major (sak == 1), B row-major (sbn == 1), C row-major (scn == 1);
   // `reuse`: planes of W kept by the right-to-left pass
   int sketch(Ctx& c, const Gemm& g, const BPlanes* reuse = nullptr) const {
-    if (precision == TTR_PREC_SLICED && g.sak == 1 && g.sbn == 1 && g.scn == 1 && g.split_k <= 1 &&
-        g.alpha == 1.0 && g.beta == 0.0) {
-      int st = tc_gemm_rowmajor(c, slices, g.A, g.sam, g.M, g.K, g.B, g.sbk, g.N, g.C, g.scm, reuse);
+    if (sliced() && g.sak == 1 && g.sbn == 1 && g.scn == 1 && g.split_k <= 1 && g.alpha == 1.0 && g.beta == 0.0) {
+      int st = reduced() ? tc_gemm_rowmajor_flt(c, fs, g.A, g.sam, g.M, g.K, g.B, g.sbk, g.N, g.C, g.scm)
+                         : tc_gemm_rowmajor(c, slices, g.A, g.sam, g.M, g.K, g.B, g.sbk, g.N, g.C, g.scm, reuse);
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
     return gemm_f64(c, g);
@@ -165,7 +192,10 @@ struct Engine {
   int rl_step(Ctx& c, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
               const double* Om, const int* Omi, int64_t ldom, int64_t w, double* Wout, int64_t ldwo, double* T,
               BPlanes* keep = nullptr) const {
-    if (precision == TTR_PREC_SLICED) {
+    if (reduced()) {
+      int st = tc_rl_step_flt(c, fs, Xk, r0, n, r1, Wn, ldw, Om, ldom, w, Wout, ldwo);
+      if (st != TTR_ERR_UNSUPPORTED) return st;
+    } else if (sliced()) {
       int st = tc_rl_step(c, slices, Xk, r0, n, r1, Wn, ldw, Omi, ldom, w, Wout, ldwo, keep);
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
@@ -182,7 +212,22 @@ struct Engine {
   // Omega_d (n_d x w, leading dimension ldo), into C[g] (leading dimension ldc)
   int last_core_group(Ctx& c, int ng, const double* const* A, const int64_t* M, int64_t n, const double* Om,
                       int64_t ldo, int64_t w, double* const* C, int64_t ldc) const {
-    if (precision == TTR_PREC_SLICED) {
+    if (reduced()) {
+      for (int g = 0; g < ng; ++g) {
+        int st = tc_gemm_rowmajor_flt(c, fs, A[g], n, M[g], n, Om, ldo, w, C[g], ldc);
+        if (st == TTR_ERR_UNSUPPORTED) {
+          Gemm q;
+          q.M = M[g]; q.N = w; q.K = n;
+          q.A = A[g]; q.sam = n; q.sak = 1;
+          q.B = Om; q.sbk = ldo; q.sbn = 1;
+          q.C = C[g]; q.scm = ldc; q.scn = 1;
+          st = gemm_f64(c, q);
+        }
+        TTR_CHECK(st);
+      }
+      return TTR_OK;
+    }
+    if (sliced()) {
       int64_t lda[kMaxGroup];
       for (int g = 0; g < ng; ++g) lda[g] = n;
       int st = tc_gemm_shared_b(c, slices, ng, A, M, lda, n, Om, ldo, w, C, ldc);
@@ -205,7 +250,7 @@ struct Engine {
                     const double* Wn, int64_t ldw, int64_t Kall, const int64_t* off_n, const double* Om,
                     const int* Omi, int64_t ldom, int64_t w, double* Wout, int64_t ldwo, const int64_t* off_out,
                     double* T, BPlanes* keep = nullptr) const {
-    if (precision == TTR_PREC_SLICED) {
+    if (sliced() && !reduced()) {
       int st = tc_rl_step_grouped(c, slices, ng, Xk, r0, n, r1, Wn, ldw, Kall, off_n, Omi, ldom, w, Wout, ldwo,
                                   off_out, keep);
       if (st != TTR_ERR_UNSUPPORTED) return st;
@@ -219,7 +264,7 @@ struct Engine {
   // Y = M H(X_{k+1}):  (L x K)(K x ncol), all row-major; M has leading dimension ldm >= K
   int project(Ctx& c, const double* Mk, int64_t ldm, int64_t L, int64_t K, const double* Xn, int64_t ncol,
               double* Y) const {
-    if (precision == TTR_PREC_SLICED) {
+    if (sliced()) {
       int st = tc_project(c, slices, Mk, ldm, L, K, Xn, ncol, Y);
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
@@ -240,7 +285,7 @@ struct Engine {
       TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
       return sumsq(c, S, rows, bcols, lds, 1, sumsq_out);
     }
-    if (precision == TTR_PREC_SLICED && (double)rows * cc * bcols >= kSlicedProjectWork) {
+    if (sliced() && (double)rows * cc * bcols >= kSlicedProjectWork) {
       // wide blocks (the host-driven loop): both products on the tensor cores, each exact to the
       // sliced form's stated error, instead of FP64 at 2 FMA per clock per SM
       int st = tc_gemm_tn(c, slices, Q, ldq, rows, cc, S, lds, bcols, P, bcols, 1);   // P = Q^T S
@@ -276,7 +321,7 @@ struct Engine {
   // M (ccols x cols, ld cols) = Q(:, :ccols)^T Z   (M_k = Q_k^T V(Y_k))
   int left_project(Ctx& c, const double* Q, int64_t ldq, const double* Z, int64_t rows, int64_t cols, int64_t ccols,
                    double* M) const {
-    if (precision == TTR_PREC_SLICED) {
+    if (sliced()) {
       // M^T = Z^T Q: big operand Z^T (column-major view), rows split over CTAs
       int st = tc_gemm_tn(c, slices, Z, cols, rows, cols, Q, ldq, ccols, M, 1, cols);
       if (st != TTR_ERR_UNSUPPORTED) return st;
@@ -290,7 +335,7 @@ struct Engine {
   int project_group(Ctx& c, int ng, const double* M, int64_t ldm, int64_t L, int64_t Kall, const int64_t* koff,
                     const int64_t* K, const double* const* Xn, int64_t n, const int64_t* rn, double* Ynext, int64_t R,
                     const int64_t* yoff) const {
-    if (precision != TTR_PREC_SLICED) return TTR_ERR_UNSUPPORTED;
+    if (!sliced()) return TTR_ERR_UNSUPPORTED;
     int64_t ncol[kMaxGroup];
     for (int g = 0; g < ng; ++g) ncol[g] = n * rn[g];
     return tc_project_grouped(c, slices, ng, M, ldm, L, Kall, koff, K, Xn, ncol, rn, Ynext, n * R, R, yoff);

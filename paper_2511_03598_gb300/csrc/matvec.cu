@@ -44,13 +44,79 @@ __global__ void mv_form_kernel(const double* A, int64_t p0, int64_t n, int64_t m
   }
 }
 
+// The same product with the operands staged: one CTA per (b, (a, g)) holds A_k(a, :, :, g) (n x m)
+// and x_k(b, :, :) (m x r1) in shared memory and writes y_k((a, b), :, (g, :)).
+__global__ void __launch_bounds__(256) mv_form_tiled_kernel(const double* A, int64_t p0, int64_t n, int64_t m,
+                                                            int64_t p1, const double* X, int64_t r0, int64_t r1,
+                                                            double* Y) {
+  extern __shared__ double sm[];
+  double* As = sm;               // [n][m]
+  double* Xs = sm + n * m;       // [m][r1]
+  const int64_t b = blockIdx.x, ag = blockIdx.y;
+  const int64_t a = ag / p1, g = ag - a * p1;
+  for (int64_t e = threadIdx.x; e < n * m; e += blockDim.x) {
+    const int64_t i = e / m, j = e - i * m;
+    As[e] = A[((a * n + i) * m + j) * p1 + g];
+  }
+  for (int64_t e = threadIdx.x; e < m * r1; e += blockDim.x) Xs[e] = X[b * m * r1 + e];
+  __syncthreads();
+  const int64_t R1 = p1 * r1;
+  for (int64_t e = threadIdx.x; e < n * r1; e += blockDim.x) {
+    const int64_t i = e / r1, cc = e - i * r1;
+    const double* ar = As + i * m;
+    double s0 = 0.0, s1 = 0.0;
+    int64_t j = 0;
+    for (; j + 1 < m; j += 2) {
+      s0 = fma(ar[j], Xs[j * r1 + cc], s0);
+      s1 = fma(ar[j + 1], Xs[(j + 1) * r1 + cc], s1);
+    }
+    if (j < m) s0 = fma(ar[j], Xs[j * r1 + cc], s0);
+    Y[((a * r0 + b) * n + i) * R1 + g * r1 + cc] = s0 + s1;
+  }
+}
+
 int mv_form(Ctx& c, const double* A, int64_t p0, int64_t n, int64_t m, int64_t p1, const double* X, int64_t r0,
             int64_t r1, double* Y) {
   const int64_t tot = p0 * r0 * n * p1 * r1;
   if (tot <= 0) return TTR_OK;
+  const size_t smem = sizeof(double) * (size_t)(n * m + m * r1);
+  if (smem <= 48 * 1024 && r0 <= 0x7fffffff && p0 * p1 <= 65535) {
+    mv_form_tiled_kernel<<<dim3((unsigned)r0, (unsigned)(p0 * p1)), 256, smem, c.stream>>>(A, p0, n, m, p1, X, r0, r1,
+                                                                                        Y);
+    return c.check_launch("mv_form");
+  }
   const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 16);
   mv_form_kernel<<<blocks, 256, 0, c.stream>>>(A, p0, n, m, p1, X, r0, r1, Y);
   return c.check_launch("mv_form");
+}
+
+// Ahat(a, (j, g), l) = sum_i A_k(a, i, (j, g)) Omega_k(i, l): the sketch block contracted into the
+// operator core (p0 x (m p1) x w, l fastest)
+__global__ void mv_ahat_kernel(const double* A, int64_t p0, int64_t n, int64_t mp1, const double* Om, int64_t ldom,
+                               int64_t w, double* Ahat) {
+  const int64_t tot = p0 * mp1 * w;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e % w, rest = e / w;
+    const int64_t jg = rest % mp1, a = rest / mp1;
+    const double* ap = A + a * n * mp1 + jg;      // A_k(a, i, (j, g)) at ap[i mp1]
+    double s0 = 0.0, s1 = 0.0;
+    int64_t i = 0;
+    for (; i + 1 < n; i += 2) {
+      s0 = fma(ap[i * mp1], Om[i * ldom + l], s0);
+      s1 = fma(ap[(i + 1) * mp1], Om[(i + 1) * ldom + l], s1);
+    }
+    if (i < n) s0 = fma(ap[i * mp1], Om[i * ldom + l], s0);
+    Ahat[e] = s0 + s1;
+  }
+}
+
+int mv_ahat(Ctx& c, const double* A, int64_t p0, int64_t n, int64_t m, int64_t p1, const double* Om, int64_t ldom,
+            int64_t w, double* Ahat) {
+  const int64_t tot = p0 * m * p1 * w;
+  if (tot <= 0) return TTR_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+  mv_ahat_kernel<<<blocks, 256, 0, c.stream>>>(A, p0, n, m * p1, Om, ldom, w, Ahat);
+  return c.check_launch("mv_ahat");
 }
 
 // W_k((a, b), l) = sum_{j, g} Ahat(a, j, g, l) Z_g((b, j), l); with xb (the last core, p1 = r1 = 1)

@@ -24,6 +24,13 @@
 // Truncating the digits and the diagonals at s leaves a relative error of about s*2^(1-7s)
 // of the row/column scales: 8 slices reach FP64 accuracy, 5 slices ~1e-10.
 //
+// The same kernels also run the reduced-precision sketch forms (Args::flt): each operand value is
+// stored as one BF16 plane (its BF16 rounding), or as two (the BF16 head and tail of its TF32
+// rounding, so that head*head + head*tail + tail*head on two FP32 accumulators reproduces a TF32
+// product with FP32 accumulation); no exponent scan, and the epilogue converts the FP32
+// accumulators to FP64 and, for partial contractions, weights by the FP64 sketch entries and sums
+// each slab in FP64.
+//
 // Operands are staged by the CTA's threads into shared memory in the canonical K-major,
 // no-swizzle UMMA layout (8x16-byte core matrices; the leading byte offset steps along K,
 // the stride byte offset along M/N), double-buffered across K-chunks of 32; one thread issues
@@ -82,6 +89,8 @@ struct Args {
   // plain mode: output row m lands at row (m / rp) * rstride + m % rp of C (rp = 0: at row m), which
   // places the columns (i, c) of one summand's block of H(Y_{k+1}) inside the stacked right bond
   int64_t rp, rstride;
+  int flt;                            // reduced-precision operands: s = 1 BF16, s = 2 TF32 (head, tail)
+  const double* Omd;                  // flt partial contractions: Omega(i, j) [i * ldo + j]
 };
 
 // Up to MAXG independent products of one grouped launch (the summands of a sum of TTs): each
@@ -173,6 +182,41 @@ __device__ __forceinline__ void store_digits(const double* v, int E, uint16_t* p
 #pragma unroll
   for (int p = 0; p < S; ++p)
     *reinterpret_cast<uint4*>(planes + (size_t)p * plane_stride + idx) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+
+// Reduced-precision forms: the BF16 rounding of 8 values (s = 1), or the BF16 head and tail of
+// their TF32 rounding (s = 2; TF32 keeps 11 significant bits, the head 8, so the tail is exact).
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float tf32_round(float x) {
+  const uint32_t u = __float_as_uint(x);
+  if (((u >> 23) & 0xFF) == 0xFF) return x;                  // inf / nan unchanged
+  return __uint_as_float((u + 0xFFFu + ((u >> 13) & 1u)) & ~0x1FFFu);
+}
+__device__ __forceinline__ void store_float_s(int s, const double* v, uint16_t* planes, size_t plane_stride, int idx) {
+  uint16_t hbits[8], tbits[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float f = __double2float_rn(v[q]);
+    if (s == 1) {
+      hbits[q] = bf16_bits(f);
+    } else {
+      const float t = tf32_round(f);
+      const __nv_bfloat16 h = __float2bfloat16_rn(t);
+      hbits[q] = __bfloat16_as_ushort(h);
+      tbits[q] = bf16_bits(t - __bfloat162float(h));
+    }
+  }
+  uint4 hw, tw;
+  hw.x = hbits[0] | ((uint32_t)hbits[1] << 16); hw.y = hbits[2] | ((uint32_t)hbits[3] << 16);
+  hw.z = hbits[4] | ((uint32_t)hbits[5] << 16); hw.w = hbits[6] | ((uint32_t)hbits[7] << 16);
+  *reinterpret_cast<uint4*>(planes + idx) = hw;
+  if (s == 2) {
+    tw.x = tbits[0] | ((uint32_t)tbits[1] << 16); tw.y = tbits[2] | ((uint32_t)tbits[3] << 16);
+    tw.z = tbits[4] | ((uint32_t)tbits[5] << 16); tw.w = tbits[6] | ((uint32_t)tbits[7] << 16);
+    *reinterpret_cast<uint4*>(planes + plane_stride + idx) = tw;
+  }
 }
 
 __device__ __forceinline__ void store_digits_s(int s, const double* v, int E, uint16_t* planes, size_t plane_stride,
@@ -272,7 +316,7 @@ __device__ __forceinline__ void issue_chunk(uint64_t da0, uint64_t db0, uint32_t
 }
 
 // 17 warps: one SM sub-partition holds 5 of them, so its 16K registers cap a thread at 96.
-template <int MODE, bool AKFAST, bool GROUPED>
+template <int MODE, bool AKFAST, bool GROUPED, bool FLT>
 __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Groups gr) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // this CTA's product: the launch's, or that of its group (tiles numbered within the group)
@@ -356,8 +400,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
   mark(TP_SETUP);
 
   // ---- pass 1: exponent scale of every row over this K segment (many loads in flight)
-  if (warp >= NWP) {
-    // the MMA warp takes no part in the scan
+  if (warp >= NWP || FLT) {
+    // the MMA warp takes no part in the scan; the reduced-precision forms need no scale
   } else if (AKFAST) {
     // row-major A: a warp scans 8 rows; each step loads one value of each row per lane
     constexpr int RPW = TM / NWP;
@@ -430,6 +474,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
         const uint64_t da0 = umma_desc(abase, (TM / 8) * 128, 128);
         const uint64_t db0 = umma_desc(bbase, s * (tn / 8) * 128, 128);
         switch (s) {
+          case 1: issue_chunk<1>(da0, db0, tmem, tn, idesc0, c == 0); break;
+          case 2: issue_chunk<2>(da0, db0, tmem, tn, idesc0, c == 0); break;
           case 3: issue_chunk<3>(da0, db0, tmem, tn, idesc0, c == 0); break;
           case 4: issue_chunk<4>(da0, db0, tmem, tn, idesc0, c == 0); break;
           case 5: issue_chunk<5>(da0, db0, tmem, tn, idesc0, c == 0); break;
@@ -499,7 +545,8 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
         // (A grouped launch writes every position: its B chunks may hold other groups' rows.)
         if (!GROUPED && c >= 2 && (row >= rows || c * KC + grp * 8 >= kseg_len)) continue;
         const int idx = ((grp * (TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;   // bf16 index in a plane
-        store_digits_s(s, vc[i], rowE[row], Ap, PLANE_A, idx);
+        if (FLT) store_float_s(s, vc[i], Ap, PLANE_A, idx);
+        else store_digits_s(s, vc[i], rowE[row], Ap, PLANE_A, idx);
       }
 #pragma unroll
       for (int i = 0; i < TASKS; ++i)
@@ -534,8 +581,11 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
         // Vl (shifts 0..28) < 2^56 and Vh (shifts 35..49, less 35) < 2^41.  The accumulators are
         // integer-valued binary32 values, so the float-to-int32 conversion is exact.
         long long Vh[16], Vl[16];
+        double Vd[FLT ? 16 : 1];              // reduced-precision forms: sum of the FP32 accumulators
 #pragma unroll
         for (int j = 0; j < 16; ++j) Vh[j] = Vl[j] = 0;
+#pragma unroll
+        for (int j = 0; j < (FLT ? 16 : 1); ++j) Vd[j] = 0.0;
 #pragma unroll 1
         for (int t = 0; t < s; ++t) {
           uint32_t r[16];
@@ -546,6 +596,11 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (FLT) {
+#pragma unroll
+            for (int j = 0; j < (FLT ? 16 : 1); ++j) Vd[j] += (double)__uint_as_float(r[j]);
+            continue;
+          }
           const int shift = 7 * (s - 1 - t);
           if (shift >= 35) {
             const long long mul = 1LL << (shift - 35);
@@ -576,8 +631,13 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
             for (int j = 0; j < 16; ++j) {
               const int64_t n = n0 + j;
               if (n < a.N) {
-                const int X = e_row + max(1, a.Fmax[n]) - 2044 - 7 * s - 7;
-                const double out = v64 ? i64_to_double(Vh[j] * (1LL << 35) + Vl[j], X) : i128_to_double(V[j], X);
+                double out;
+                if (FLT) {
+                  out = Vd[FLT ? j : 0];
+                } else {
+                  const int X = e_row + max(1, a.Fmax[n]) - 2044 - 7 * s - 7;
+                  out = v64 ? i64_to_double(Vh[j] * (1LL << 35) + Vl[j], X) : i128_to_double(V[j], X);
+                }
                 double* cp = a.C + maddr * a.scm + n * a.scn;
                 if (MODE == ATOMIC) atomicAdd(cp, out);
                 else *cp = out;
@@ -585,13 +645,24 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
             }
           }
         } else {
-          // weight by the integer sketch entry 2^20 Omega(i, n); summed over i below
+          // weight by the integer sketch entry 2^20 Omega(i, n); summed over i below (the
+          // reduced-precision forms: by Omega(i, n) in FP64, into the same slots as doubles)
           const int i = row % (int)a.nmode;
+          if (FLT) {
+            double* PD = reinterpret_cast<double*>(P);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int64_t n = n0 + j;
-            const int om = (row < rows && n < a.N) ? a.Omint[i * a.ldo + n] : 0;
-            P[row * PB + (((cg - blk0) * 16 + j) ^ (row & 7))] = V[j] * (__int128)om;
+            for (int j = 0; j < 16; ++j) {
+              const int64_t n = n0 + j;
+              const double om = (row < rows && n < a.N) ? a.Omd[i * a.ldo + n] : 0.0;
+              PD[row * PB + (((cg - blk0) * 16 + j) ^ (row & 7))] = Vd[FLT ? j : 0] * om;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int64_t n = n0 + j;
+              const int om = (row < rows && n < a.N) ? a.Omint[i * a.ldo + n] : 0;
+              P[row * PB + (((cg - blk0) * 16 + j) ^ (row & 7))] = V[j] * (__int128)om;
+            }
           }
         }
       }
@@ -603,14 +674,25 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
           const int sl = task / bcols, j = task % bcols;
           const int64_t n = (int64_t)nc * tn + blk0 * 16 + j;
           if (n >= a.N) continue;
-          __int128 acc = 0;
-          for (int ii = 0; ii < (int)a.nmode; ++ii) {
-            const int r = sl * (int)a.nmode + ii;
-            acc += P[r * PB + (j ^ (r & 7))];
-          }
-          const int e_slab = rowE[sl * (int)a.nmode];
           const int64_t aidx = bx * a.g + sl;
-          const double out = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
+          double out;
+          if (FLT) {
+            const double* PD = reinterpret_cast<const double*>(P);
+            double accd = 0.0;
+            for (int ii = 0; ii < (int)a.nmode; ++ii) {
+              const int r = sl * (int)a.nmode + ii;
+              accd += PD[r * PB + (j ^ (r & 7))];
+            }
+            out = accd;
+          } else {
+            __int128 acc = 0;
+            for (int ii = 0; ii < (int)a.nmode; ++ii) {
+              const int r = sl * (int)a.nmode + ii;
+              acc += P[r * PB + (j ^ (r & 7))];
+            }
+            const int e_slab = rowE[sl * (int)a.nmode];
+            out = i128_to_double(acc, e_slab + max(1, a.Fmax[n]) - 2044 - 7 * s - 7 - 20);
+          }
           if (a.watomic) atomicAdd(a.W + aidx * a.ldw + n, out);
           else a.W[aidx * a.ldw + n] = out;
         }
@@ -776,6 +858,26 @@ __global__ void __launch_bounds__(256) prep_b_fused_kernel(const double* B, int6
   }
 }
 
+// Reduced-precision forms: B(k, n) as s = 1 (BF16) or 2 (TF32 head and tail) planes in the layout of
+// b_digit_index; no column scales.
+__global__ void __launch_bounds__(256) slice_b_float_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K,
+                                                            int64_t N, int s, int tn, int kchunks, uint4* planes) {
+  const int nc = blockIdx.x, kcn = blockIdx.y;
+  const int plane_b = tn * KC;
+  uint4* blk = planes + ((size_t)nc * kchunks + kcn) * (size_t)s * (plane_b / 8);
+  for (int u = threadIdx.x; u < tn * (KC / 8); u += blockDim.x) {
+    const int j = u % tn, grp = u / tn;
+    const int64_t n = (int64_t)nc * tn + j;
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)kcn * KC + grp * 8 + q;
+      v[q] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0;
+    }
+    store_float_s(s, v, reinterpret_cast<uint16_t*>(blk), tn * 8, b_digit_index(grp, j, s, tn));
+  }
+}
+
 static size_t smem_bytes(int s, int tn, int mode) {
   size_t need = 2 * (size_t)s * (PLANE_A + tn * KC) * 2;
   if (mode == RLM) need = std::max(need, (size_t)TM * PB * sizeof(__int128));
@@ -798,17 +900,19 @@ static int launch(Ctx& c, const Args& a_in, dim3 grid, const char* name, const G
     a.prof = c.tc_prof;
   }
   const size_t sm = smem_bytes(a.s, a.tn, MODE);
-  auto kern = groups ? sliced_kernel<MODE, AKFAST, true> : sliced_kernel<MODE, AKFAST, false>;
+  if (groups && a.flt) return set_error("grouped reduced-precision products are not built"), TTR_ERR_UNSUPPORTED;
+  auto kern = groups ? sliced_kernel<MODE, AKFAST, true, false>
+                     : (a.flt ? sliced_kernel<MODE, AKFAST, false, true> : sliced_kernel<MODE, AKFAST, false, false>);
   // the shared-memory limit belongs to the kernel and every calling thread shares it: raise it per
   // device to the largest size requested so far, never lower it
   constexpr int MAXDEV = 64;
-  static int raised[2][MAXDEV] = {};           // [grouped kernel][device]
+  static int raised[3][MAXDEV] = {};           // [plain, grouped, reduced-precision kernel][device]
   static std::mutex mu;
   int dev = 0;
   TTR_CUDA(cudaGetDevice(&dev));
   {
     std::lock_guard<std::mutex> lock(mu);
-    int* slot = (dev >= 0 && dev < MAXDEV) ? &raised[groups ? 1 : 0][dev] : nullptr;
+    int* slot = (dev >= 0 && dev < MAXDEV) ? &raised[groups ? 1 : (a.flt ? 2 : 0)][dev] : nullptr;
     const int have = slot ? *slot : 0;
     if (have < (int)sm) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -918,6 +1022,26 @@ static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, 
     keep->N = N;
   }
   return TTR_OK;
+}
+
+static int prep_b_float(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int s, BPrep& p) {
+  const int tmax = tile_width(s);
+  p.nchunks = (int)((N + tmax - 1) / tmax);
+  const int64_t per = (N + p.nchunks - 1) / p.nchunks;
+  p.tn = (int)std::min<int64_t>(tmax, std::max<int64_t>(16, (per + 15) / 16 * 16));
+  p.kchunks = (int)((K + KC - 1) / KC);
+  const size_t need = ((size_t)p.nchunks * p.kchunks * s * p.tn * KC * 2 + 255) / 256 * 256;
+  if (c.bprep_bytes < need) {
+    void* ws = nullptr;
+    TTR_CHECK(c.alloc(&ws, std::max(need, (size_t)2 * c.bprep_bytes)));
+    c.bprep = ws;
+    c.bprep_bytes = std::max(need, (size_t)2 * c.bprep_bytes);
+  }
+  p.planes = static_cast<uint4*>(c.bprep);
+  p.Fmax = nullptr;
+  slice_b_float_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, s, p.tn,
+                                                                                             p.kchunks, p.planes);
+  return c.check_launch("prep_b_float");
 }
 
 // K per CTA for `tiles` output tiles: the fewest K-chunks per CTA that keep the grid within one
@@ -1147,6 +1271,54 @@ int tc_project_grouped(Ctx& c, int slices, int ng, const double* M, int64_t ldm,
   gr.tile0[ng] = tiles;
   dim3 grid((unsigned)tiles, (unsigned)bp.nchunks, 1);
   return launch<PLAIN, false>(c, a, grid, "tc_project", &gr);
+}
+
+// ---- reduced-precision sketch forms (TF32 / BF16 operands, FP32 accumulation): fs = 2 or 1 planes
+
+int tc_rl_step_flt(Ctx& c, int fs, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
+                   const double* Om, int64_t ldo, int64_t w, double* Wout, int64_t ldwo) {
+  if (n > TM || (fs != 1 && fs != 2) || !Om) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b_float(c, Wn, ldw, 1, r1, w, fs, bp));
+  Args a{};
+  a.A = Xk; a.M = r0 * n; a.K = r1; a.sam = r1; a.sak = 1;
+  a.Bp = bp.planes; a.Fmax = nullptr; a.N = w; a.kchunks = bp.kchunks; a.s = fs; a.tn = bp.tn;
+  a.Omd = Om; a.ldo = ldo; a.nmode = n; a.g = (int)(TM / n); a.slabs = r0; a.W = Wout; a.ldw = ldwo;
+  a.err = c.d_flags; a.flt = 1;
+  const int64_t tiles = (r0 + a.g - 1) / a.g * bp.nchunks;
+  a.kseg = kseg_for(tiles, r1);
+  const unsigned ksplit = (unsigned)((r1 + a.kseg - 1) / a.kseg);
+  if (ksplit > 1) {
+    a.watomic = 1;
+    TTR_CUDA(cudaMemset2DAsync(Wout, ldwo * sizeof(double), 0, w * sizeof(double), r0, c.stream));
+  }
+  dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, ksplit);
+  c.time_begin(Ctx::KT_RL);
+  TTR_CHECK((launch<RLM, true>(c, a, grid, "tc_rl_step_flt")));
+  c.time_end(8.0 * ((double)r0 * n * r1 + (double)r1 * w + (double)r0 * w));
+  return TTR_OK;
+}
+
+int tc_gemm_rowmajor_flt(Ctx& c, int fs, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
+                         int64_t ldb, int64_t N, double* C, int64_t ldc) {
+  if ((fs != 1 && fs != 2) || M <= 0 || N <= 0 || K <= 0) return TTR_ERR_UNSUPPORTED;
+  TTR_CHECK(ensure_err(c));
+  BPrep bp;
+  TTR_CHECK(prep_b_float(c, B, ldb, 1, K, N, fs, bp));
+  Args a{};
+  a.A = A; a.M = M; a.K = K; a.sam = lda; a.sak = 1;
+  a.Bp = bp.planes; a.Fmax = nullptr; a.N = N; a.kchunks = bp.kchunks; a.s = fs; a.tn = bp.tn;
+  a.C = C; a.scm = ldc; a.scn = 1; a.err = c.d_flags; a.flt = 1;
+  const int64_t tiles = (M + TM - 1) / TM * bp.nchunks;
+  a.kseg = kseg_for(tiles, K);
+  const unsigned ksplit = (unsigned)((K + a.kseg - 1) / a.kseg);
+  dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
+  if (ksplit > 1) {
+    TTR_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, N * sizeof(double), M, c.stream));
+    return launch<ATOMIC, true>(c, a, grid, "tc_sketch_flt");
+  }
+  return launch<PLAIN, true>(c, a, grid, "tc_sketch_flt");
 }
 
 }  // namespace ttr

@@ -90,6 +90,7 @@ uint64_t footprint_of(int32_t s, int32_t d, const int64_t* n, const int64_t* con
   dbl += (double)d * nmax * wcap * 1.5;                   // Omega and its integer copy
   dbl += 4.0 * rmax * rmax + rmax * nmax * rpart + 2.0 * nmax * rmax;
   dbl += 2.0 * rowsmax * rmax;                            // digit planes of the largest tensor-core B operand
+  dbl += rowsmax * (rmax + wcap + 64.0);                  // the block loop's rows when they live in global memory
   *bytes_in = (uint64_t)(8.0 * in);
   return (uint64_t)(8.0 * dbl) + (64ull << 20);
 }

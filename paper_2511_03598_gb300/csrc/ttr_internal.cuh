@@ -42,7 +42,10 @@ struct Ctx {
   int* d_flags = nullptr;          // device status flags (0 = ok); bounded waits write here
   double* ws = nullptr;            // reduction workspace (128 x 1024 doubles) for gram_reduce
   unsigned* ws_ticket = nullptr;   // its completion counter (kept at zero between kernels)
-  double* ac_part = nullptr;       // adaptive_core: per-CTA partial sums (two buffers)
+  double* ac_part = nullptr;       // adaptive_core: rotating accumulation buffers (three)
+  int ac_part_cap = 0;             // doubles per buffer
+  double* ac_gwork = nullptr;      // adaptive_core: the CTAs' rows when they do not fit in shared memory
+  size_t ac_gwork_bytes = 0;
   double* ac_red = nullptr;        // adaptive_core: reduced projection coefficients
   unsigned* ac_bar = nullptr;      // adaptive_core: grid barrier counter/generation
   int* ac_io = nullptr;            // adaptive_core: status, column count, estimate count, estimates

@@ -173,3 +173,20 @@ def test_host_driven_block_loop(B, prec, monkeypatch):
                                   B.options(precision=prec, nrmx=nrmx or 0.0, est_min=em, est_safety=beta)) as y:
             assert y.info["ranks"] == info["ranks"]
             assert rel(y.to_numpy(), ref) <= (1e-10 if prec == 0 else max(1e-8, 1e-3 * tol))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_wide_ranks_device_block_loop(B, prec):
+    """A full-rank sum whose block loop rows do not fit in shared memory (three summands of rank 60,
+    n = 40: rows up to 180 x 40 = 7200, sketch widths near 200) and whose first block (the appendix's
+    b_init = 60) is wider than the device loop factors: the first block is factored on the host side,
+    the rest of the loop runs on the device with its rows in global memory.  Against the oracle."""
+    rng = np.random.default_rng(91)
+    xs = [WL.random_tt(rng, 6, 40, 60) for _ in range(3)]
+    for x, c in zip(xs, (1.0, -0.6, 0.8)):
+        x[0] = x[0] * c
+    ref, info = R.tt_round_adaptive_sum(xs, 1e-6, 7, block=0)
+    assert max(info["ranks"]) == 180
+    with B.round_adaptive_sum(dev_summands(xs), 1e-6, 0, 7, B.options(precision=prec, slices=8)) as y:
+        assert y.info["ranks"] == info["ranks"]
+        assert rel(y.to_numpy(), ref) <= (1e-10 if prec == 0 else 1e-9)
