@@ -89,58 +89,129 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (the
+# fallback when the GEMM probe below cannot run)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def probe_peaks() -> dict:
+    """Measured FP64 and TF32 GEMM rates of this GPU (torch.matmul, i.e. cuBLAS, 8192^3 FP64 and
+    FP32-with-TF32, best of 3 after one warm-up; CUDA events): the denominators of the FP64-pipe
+    roofline, beside the measured HBM and BF16 figures."""
+    import torch
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, tf32 in (("fp64_tflops", torch.float64, False), ("tf32_tflops", torch.float32, True)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            n = 8192
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    out["how"] = "torch.matmul 8192^3 (cuBLAS), best of 3 after a warm-up, CUDA events"
+    return out
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # this workload in sliced precision, for the kernels as they stand (the capture command is in
-# profiles/): the block loop's figure is the median over full-rank cores, the partial
+# profiles/): the FP64 block loop's figure is the median over full-rank cores, the partial
 # contraction's the mean over all 18 launches of one pass.  Other precisions run other kernels.
-TRAFFIC_SLICED = {"block_loop": 2.44e6, "rl_kernel": 17.98e6}
+TRAFFIC_SLICED = {"block_loop": 2.437e6, "rl_kernel": 17.98e6}
 
 
 def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
     """The serving stream (Poisson arrivals, mean gap 2 ms; each request a sum of 2-6 random TTs
     with d 8-32, n 16-128, ranks 20-100, tol 1e-4/1e-6/1e-8): its first `nreq` requests, given to
-    the library's request server as summands in host memory.  Closed loop: all queued at once
-    (throughput).  Open loop: each submitted at its arrival time (latency under that load)."""
-    import workloads as WL
-    reqs = list(WL.c4_stream(count=nreq, formal=False))
-    srv = B.Server(workers=workers, device_budget=budget)
+    the library's request server as summands in host memory.  A producer thread generates the
+    requests while the server works, holding at most a window of them (the whole stream's summands
+    are ~80 GB); each request's host data is dropped once its result is collected.  Closed loop: a
+    request is submitted as soon as it is generated and the window has room (throughput).  Open loop:
+    each is submitted at its arrival time, or when generated if that is later (latency under that
+    load; the stream arrives ~100 times faster than one GPU rounds it, so queueing dominates)."""
+    import collections
+    import queue
 
-    def opts_for(q):
-        return B.options(precision=B.TTR_PREC_SLICED)
+    import workloads as WL
+    window = max(4, 3 * workers)
+    srv = B.Server(workers=workers, device_budget=budget)
+    opts = B.options(precision=B.TTR_PREC_SLICED)
+
+    def producer(q, stop):
+        for r in WL.c4_stream(count=nreq, formal=False):
+            while not stop.is_set():
+                try:
+                    q.put(r, timeout=0.5)
+                    break
+                except queue.Full:
+                    continue
+            if stop.is_set():
+                return
+        q.put(None)
 
     try:
-        # warm-up: the smallest request once (kernel attributes, memory pool)
-        small = min(reqs, key=lambda q: q.tt.meta["formal_bytes"])
-        srv.wait(srv.submit(small.tt.summands, small.tol, 0, 7, opts_for(small)), fetch=False)
+        # warm-up: one small request (kernel attributes, memory pool)
+        small = next(WL.c4_stream(count=nreq, formal=False, max_bytes=1e8))
+        srv.wait(srv.submit(small.tt.summands, small.tol, 0, 7, opts), fetch=False)
         out = {}
         for mode in ("closed_loop", "open_loop"):
+            q, stop = queue.Queue(maxsize=window), threading.Event()
+            th = threading.Thread(target=producer, args=(q, stop), daemon=True)
+            th.start()
+            pending = collections.deque()
+            lat, late, ranks_max, formal, inbytes, count = [], [], 0, 0, 0, 0
             t0 = time.perf_counter()
-            ids = []
-            for q in reqs:
-                if mode == "open_loop":
-                    delay = q.arrival_ms / 1e3 - (time.perf_counter() - t0)
-                    if delay > 0:
-                        time.sleep(delay)
-                ids.append(srv.submit(q.tt.summands, q.tol, 0, 1000 + q.rid, opts_for(q)))
-            lat, ranks_max = [], 0
-            for rid in ids:
+
+            def collect_one():
+                nonlocal ranks_max
+                rid = pending.popleft()
                 _, info = srv.wait(rid, fetch=False)   # result already in host memory (the worker's D2H)
                 lat.append(info["ms_queue"] + info["ms_run"])
                 ranks_max = max(ranks_max, max(info["ranks"]))
+            try:
+                while True:
+                    r = q.get()
+                    if r is None:
+                        break
+                    if mode == "open_loop":
+                        delay = r.arrival_ms / 1e3 - (time.perf_counter() - t0)
+                        if delay > 0:
+                            time.sleep(delay)
+                        else:
+                            late.append(-delay * 1e3)
+                    while len(pending) >= window:
+                        collect_one()
+                    pending.append(srv.submit(r.tt.summands, r.tol, 0, 1000 + r.rid, opts))
+                    formal += r.tt.meta["formal_bytes"]
+                    inbytes += sum(c.nbytes for x in r.tt.summands for c in x)
+                    count += 1
+                while pending:
+                    collect_one()
+            finally:
+                stop.set()
             span = time.perf_counter() - t0
             st = srv.stats()
-            out[mode] = {"roundings_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99)), "span_s": span,
-                         "peak_device_bytes_admitted": int(st["peak_in_use"]), "max_output_rank": ranks_max}
-        out.update({"requests": len(reqs), "workers": workers, "device_budget": budget,
-                    "formal_bytes_total": int(sum(q.tt.meta["formal_bytes"] for q in reqs)),
-                    "input_bytes_total": int(sum(c.nbytes for q in reqs for x in q.tt.summands for c in x)),
+            out[mode] = {"roundings_per_s": count / span, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "span_s": span, "requests": count,
+                         "peak_device_bytes_admitted": int(st["peak_in_use"]), "max_output_rank": ranks_max,
+                         "formal_bytes_total": int(formal), "input_bytes_total": int(inbytes)}
+            if mode == "open_loop":
+                out[mode]["submitted_after_arrival_p50_ms"] = float(np.percentile(late, 50)) if late else 0.0
+        out.update({"requests": nreq, "workers": workers, "device_budget": budget, "window": window,
                     "precision": "sliced, slices from each request's tol", "block": "appendix rule (block 0)",
-                    "note": "first requests of the seeded serving stream (seed 4), summands in pageable host "
-                            "memory; latency = submit to result in host memory"})
+                    "note": "first requests of the seeded serving stream (seed 4), generated by a producer thread "
+                            "while the server works, summands in pageable host memory; latency = submit to result "
+                            "in host memory (queueing + H2D + rounding + D2H)"})
         return out
     finally:
         srv.close()
@@ -552,14 +623,21 @@ def main():
     # ---- rooflines from the library's CUDA events around each launch in the timed region
     w = int(info["width"])
     pk, pk_kind = peaks()
+    try:
+        probed = probe_peaks()
+    except Exception as e:  # noqa: BLE001 - fall back to the derived FP64 peak, and say so
+        probed = {"error": f"{type(e).__name__}: {e}"}
+    fp64_peak = probed.get("fp64_tflops") or FP64_PEAK_TFLOPS
+    fp64_src = ("measured FP64 GEMM (torch.matmul 8192^3, cuBLAS) on this GPU" if "fp64_tflops" in probed else
+                "derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz")
     traffic = TRAFFIC_SLICED if args.precision == "sliced" else {}
     roof_bl = None
     if kt["n_block_loop"]:
         ach = kt["flops_block_loop"] / (kt["ms_block_loop"] / 1e3) / 1e12
-        roof_bl = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                   "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic.get("block_loop"),
+        roof_bl = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                   "frac": ach / fp64_peak, "traffic": traffic.get("block_loop"),
                    "kernel": "adaptive block loop (Algorithm 6): persistent cooperative FP64 kernel, one launch per core",
-                   "peak_source": "derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                   "peak_source": fp64_src,
                    "per_unit": f"{kt['flops_block_loop'] / kt['n_block_loop']:.3e} FP64 flop per launch (one core's "
                                "blocks: residual projections, Gram matrices, CholeskyQR2, block Gram-Schmidt)",
                    "ms_per_launch": kt["ms_block_loop"] / kt["n_block_loop"],
@@ -688,7 +766,7 @@ def main():
                 "ms": float(np.mean(tdet_ms)), "roundings_per_s": 1e3 / float(np.mean(tdet_ms)), "ranks_out": tdet_ranks,
                 "note": "Algorithm 1 on torch.linalg.qr/svd (cuSOLVER), FP64, comparison only"},
             "roofline": roof, "roofline_other": roof_other[0] if roof_other else None, "gpu_launches": int(launches),
-            "max_sms_per_stream": conc["max_sms_per_stream"],
+            "max_sms_per_stream": conc["max_sms_per_stream"], "measured_peaks_probe": probed,
             "e2e": e2e,
             "e2e_single_call": {"value": e2e_single, "unit": "roundings/s", "steps": e2e_steps,
                                 "path": "tt_round_adaptive one call at a time: H2D, rounding, D2H in sequence"},
