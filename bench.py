@@ -318,9 +318,11 @@ def configs_table(B, reps: int) -> dict:
         return float(np.median(ts)), out
 
     rows = []
-    sl, fp = B.options(precision=B.TTR_PREC_SLICED), B.options(precision=B.TTR_PREC_FP64)
     for name, x, tol, mode, block in (("c1", WL.c1(), 1e-6, "fixed", 0), ("c2", WL.c2(), 1e-6, "adaptive", 10),
                                       ("c3", WL.c3(), 1e-8, "adaptive", 0)):
+        # the operator-applied vector runs with the estimator reading R16 (10 columns, stop at tau / 10)
+        est = dict(est_min=10, est_safety=10.0) if name == "c3" else {}
+        sl, fp = B.options(precision=B.TTR_PREC_SLICED, **est), B.options(precision=B.TTR_PREC_FP64, **est)
         cores = [torch.from_numpy(c).to("cuda") for c in x.cores]
         for o in (sl, fp):
             o.nrmx = x.norm
@@ -329,19 +331,30 @@ def configs_table(B, reps: int) -> dict:
             oracle_krp = lambda: OR.svd_pass_rl(OR.tt_round_fixed(x.cores, 13, SEED)[0], max_rank=8)
         else:
             krp = lambda o: (lambda: B.round_adaptive(cores, tol, block, SEED, o))
-            oracle_krp = lambda: OR.tt_round_adaptive(x.cores, tol, SEED, block=block, nrmx=x.norm)[0]
+            oracle_krp = lambda: OR.tt_round_adaptive(x.cores, tol, SEED, block=block, nrmx=x.norm, **est)[0]
         det_n = 2 if name == "c2" else reps
         g_det, det_ranks, _ = gpu_ms(lambda: B.round_deterministic(cores, tol), det_n)
         g_fp, fp_ranks, y_fp = gpu_ms(krp(fp), reps)
         g_sl, sl_ranks, y_sl = gpu_ms(krp(sl), max(reps, 20))
         c_det, _ = cpu_ms(lambda: OR.tt_round_deterministic(x.cores, tol), 3)
         c_krp, y_or = cpu_ms(oracle_krp, 5)
-        rows.append({"config": name, "mode": mode, "tol": tol, "cpu_cores": host_cores(),
-                     "oracle_det_ms": c_det, "oracle_krp_ms": c_krp, "gpu_det_fp64_ms": g_det,
-                     "gpu_krp_fp64_ms": g_fp, "gpu_krp_sliced_ms": g_sl, "ranks_krp": sl_ranks,
-                     "ranks_equal_fp64": sl_ranks == fp_ranks, "ranks_det": det_ranks,
-                     "err_sliced_vs_oracle": OT.tt_dist(y_sl, y_or) / OT.tt_norm(y_or),
-                     "err_fp64_vs_oracle": OT.tt_dist(y_fp, y_or) / OT.tt_norm(y_or)})
+        row = {"config": name, "mode": mode, "tol": tol, "cpu_cores": host_cores(),
+               "oracle_det_ms": c_det, "oracle_krp_ms": c_krp, "gpu_det_fp64_ms": g_det,
+               "gpu_krp_fp64_ms": g_fp, "gpu_krp_sliced_ms": g_sl, "ranks_krp": sl_ranks,
+               "ranks_equal_fp64": sl_ranks == fp_ranks, "ranks_det": det_ranks,
+               "err_sliced_vs_oracle": OT.tt_dist(y_sl, y_or) / OT.tt_norm(y_or),
+               "err_fp64_vs_oracle": OT.tt_dist(y_fp, y_or) / OT.tt_norm(y_or),
+               "rel_err_sliced_vs_x": OT.tt_dist(y_sl, x.cores) / x.norm,
+               "estimator": "R16 (est_min 10, est_safety 10)" if est else "Algorithm 6 as printed"}
+        if name == "c3":
+            # the same rounding from the operator and the vector, y never formed in the right-to-left pass
+            op, xv = WL.c3_factors()
+            opd = [torch.from_numpy(np.ascontiguousarray(c)).to("cuda") for c in op]
+            xvd = [torch.from_numpy(np.ascontiguousarray(c)).to("cuda") for c in xv]
+            g_mv, mv_ranks, y_mv = gpu_ms(lambda: B.round_adaptive_matvec(opd, xvd, tol, block, SEED, sl), reps)
+            row.update({"gpu_krp_sliced_matvec_fused_ms": g_mv, "ranks_matvec_equal": mv_ranks == sl_ranks,
+                        "err_matvec_vs_oracle": OT.tt_dist(y_mv, y_or) / OT.tt_norm(y_or)})
+        rows.append(row)
         del cores
     x = WL.c5(formal=False)
     cache = {}

@@ -28,20 +28,8 @@ def dev(cores):
 
 
 def c3_parts(d=16, n=64, r=30, seed=3):
-    """The operator-applied workload's factors: the Laplacian TT operator and the vector x, built
-    as workloads.c3 builds them (x left-orthonormal with bond weights 2^-(i-1))."""
-    rng = np.random.default_rng(seed)
-    w = 2.0 ** -np.arange(r)
-    x = []
-    rk = [1] + [r] * (d - 1) + [1]
-    for k in range(d):
-        g = rng.standard_normal((rk[k] * n, rk[k + 1]))
-        if k < d - 1:
-            q, _ = np.linalg.qr(g)
-            x.append((q * w[None, :]).reshape(rk[k], n, rk[k + 1]))
-        else:
-            x.append(g.reshape(rk[k], n, 1) / np.sqrt(n * r))
-    return WL.laplace_tt_operator(d, n), x
+    """The operator-applied workload's factors: the Laplacian TT operator and the vector x."""
+    return WL.c3_factors(seed, d, n, r)
 
 
 def random_op(rng, d, n, m, p):

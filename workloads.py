@@ -152,7 +152,8 @@ def tt_matvec(op, x) -> list:
     return out
 
 
-def c3(seed: int = 3, d: int = 16, n: int = 64, r: int = 30) -> TTInput:
+def c3_factors(seed: int = 3, d: int = 16, n: int = 64, r: int = 30):
+    """The factors of the operator-applied vector: (the Laplacian TT operator, the rank-r TT x)."""
     rng = np.random.default_rng(seed)
     w = 2.0 ** -np.arange(r)
     x = []
@@ -164,7 +165,12 @@ def c3(seed: int = 3, d: int = 16, n: int = 64, r: int = 30) -> TTInput:
             x.append((q * w[None, :]).reshape(rk[k], n, rk[k + 1]))
         else:
             x.append(g.reshape(rk[k], n, 1) / math.sqrt(n * r))
-    y = tt_matvec(laplace_tt_operator(d, n), x)
+    return laplace_tt_operator(d, n), x
+
+
+def c3(seed: int = 3, d: int = 16, n: int = 64, r: int = 30) -> TTInput:
+    op, x = c3_factors(seed, d, n, r)
+    y = tt_matvec(op, x)
     norm = math.sqrt(max(_gram_inner(y, y), 0.0))
     return TTInput(f"c3_d{d}_n{n}_Ax_r{r}x2", y, norm, {"seed": seed, "d": d, "n": n, "r": r})
 
