@@ -375,9 +375,30 @@ struct QrWork {
   int* dflag = nullptr;
 };
 
+// out (m x b) = X R^{-1} for R^{-1} upper triangular (b x b, leading dimension b).  Wide, tall
+// products in sliced form run on the tensor cores at 8 slices, whose error bound is that of an FP64
+// product (below 64 columns the FP64 kernel is the faster one).
+static int apply_rinv(Ctx& c, const Engine& E, const double* X, int64_t ldx, int64_t m, int64_t b, const double* Rinv,
+                      double* out, int64_t ldo) {
+  if (E.sliced() && b > 64 && (double)m * b * b >= kSlicedProjectWork) {
+    const int st = tc_gemm_rowmajor(c, kMaxSlices, X, ldx, m, b, Rinv, b, b, out, ldo);
+    if (st != TTR_ERR_UNSUPPORTED) return st;
+  }
+  return gemm_nn_small(c, X, ldx, Rinv, b, m, b, b, out, ldo, 1.0, 0.0);
+}
+
 static int chol_pass(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m, int64_t b, double* out,
                      int64_t ldo, const QrWork& w, const double* shift) {
-  (void)E;
+  if (E.sliced() && b > 32 && (double)m * b * b >= kSlicedProjectWork) {
+    // wide, tall blocks in sliced form: the Gram matrix (and X R^{-1}, see apply_rinv) on the tensor
+    // cores at 8 slices (FP64-accurate products); the Cholesky factorization itself stays FP64
+    const int st = tc_gemm_tn(c, kMaxSlices, X, ldx, m, b, X, ldx, b, w.G, b, 1);
+    if (st == TTR_OK) {
+      TTR_CHECK(chol_inv(c, w.G, b, b, shift, w.Rinv, w.dflag));
+      return apply_rinv(c, E, X, ldx, m, b, w.Rinv, out, ldo);
+    }
+    if (st != TTR_ERR_UNSUPPORTED) return st;
+  }
   if (b <= 32) {
     // Gram, Cholesky and 1/diag in one kernel (w.G holds R, w.Rinv the inverse diagonal), then
     // a row-parallel triangular solve
@@ -386,7 +407,7 @@ static int chol_pass(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m,
   }
   TTR_CHECK(gram_tn(c, X, ldx, X, ldx, m, b, b, w.G, b));                 // G = X^T X
   TTR_CHECK(chol_inv(c, w.G, b, b, shift, w.Rinv, w.dflag));
-  return gemm_nn_small(c, X, ldx, w.Rinv, b, m, b, b, out, ldo, 1.0, 0.0);  // out = X R^{-1}
+  return apply_rinv(c, E, X, ldx, m, b, w.Rinv, out, ldo);                 // out = X R^{-1}
 }
 
 static int qr_inplace(Ctx& c, const Engine& E, double* X, int64_t ldx, int64_t m, int64_t b, const QrWork& w) {
@@ -1090,6 +1111,12 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   };
   Probe* dprobe = nullptr;                      // residual sum of squares + QR breakdown flag
   TTR_CHECK(c.alloc(reinterpret_cast<void**>(&dprobe), sizeof(Probe)));
+  struct HostLoop {                             // buffers of the host-driven loop (made on first use)
+    double* T = nullptr;                        // [Q, Q1]^T [Q1, S_next]
+    double* Mn = nullptr;                       // Q1^T S_next - C^T Q^T S_next
+    double* Pn = nullptr;                       // the next block's coefficients on Q_new
+    double* Bt[2] = {nullptr, nullptr};         // [Q1, S_next] of alternate blocks
+  } hl;
   std::vector<double> ests;
   std::vector<int32_t> est_core;
   double* arena = (double*)out->arena;
@@ -1200,33 +1227,60 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
       }
     }
     if (!done) {
-    cc = 0;
-    // host-driven loop (blocks wider than the device loop supports)
+    // Host-driven loop (blocks wider than the device loop supports), with the device loop's algebra:
+    // after the first CholeskyQR pass Q1 of a residual block, one product [Q, Q1]^T [Q1, S_next]
+    // gives C = Q^T Q1, the Gram matrix Q1^T Q1 - C^T C of Q1 - Q C (the second pass) and the next
+    // block's coefficients, and one product Q [C, Q^T S_next] applies both, so each block reads Q
+    // twice.  The residual of the next block is S_next - Q (Q^T S_next) - Q_new P_new with
+    // P_new = R2^{-T} (Q1^T S_next - C^T Q^T S_next).  A CholeskyQR breakdown (seen at the next host
+    // read) redoes that block with the robust fallbacks.
     TTR_CUDA(cudaMemsetAsync(dprobe, 0, sizeof(Probe), stream));
     TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
     TTR_CHECK(qr_try(w.Q, w.qcap, rows, b0));
-    bool phase1_checked = false;
     cc = b0;
-    while (cc < rbar) {
+    if (!hl.T) {
+      const int64_t bmax = w.bcap;
+      TTR_CHECK(c.alloc_t(&hl.T, (w.qcap + bmax) * 2 * bmax));
+      TTR_CHECK(c.alloc_t(&hl.Mn, bmax * bmax));
+      TTR_CHECK(c.alloc_t(&hl.Pn, bmax * bmax));
+      TTR_CHECK(c.alloc_t(&hl.Bt[0], rowsmax * 2 * bmax));
+      TTR_CHECK(c.alloc_t(&hl.Bt[1], rowsmax * 2 * bmax));
+    }
+    QrWork q1 = w.qr;
+    q1.dflag = &dprobe->flag;
+    double* Rcur = w.S;              // residual sketch of the block at cc (rows x bi)
+    int64_t ldr = bi;
+    const double* Rprev = nullptr;   // that of the block appended last (for a fallback)
+    int64_t ldp = 0, prev_bb = 0;
+    bool phase1_checked = false, pending = true;
+    int buf = 0;
+    auto residual = [&]() -> int {   // Rcur = S_all(:, cc:cc+bi) - Q Q^T S_all(:, cc:cc+bi)
       TTR_CHECK(ensure(k, cc + bi, rows, cols));
-      // residual sketch S = (I - Q Q^T) Z W_{k+1}(:, cc:cc+bi)   (Eqs. (3.4)-(3.5))
-      TTR_CHECK(copy2d(c, w.S, bi, Sall + cc, wcap, rows, bi));
-      TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.S, bi, bi, w.P, &dprobe->ss));
-      // speculative next block: Q_new = qr(S(:, :bb)), re-orthogonalized against Q, qr again
-      const int64_t bb = std::min(ba, rbar - cc);
-      TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
-      TTR_CHECK(qr_try(w.Q + cc, w.qcap, rows, bb));
-      TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
-      TTR_CHECK(qr_try(w.Q + cc, w.qcap, rows, bb));
+      TTR_CHECK(copy2d(c, Rcur, ldr, Sall + cc, wcap, rows, bi));
+      return E.project_out(c, w.Q, w.qcap, rows, cc, Rcur, ldr, bi, w.P, &dprobe->ss);
+    };
+    if (cc < rbar) TTR_CHECK(residual());
+    while (cc < rbar) {
       Probe hp;
       TTR_CUDA(cudaMemcpyAsync(&hp, dprobe, sizeof(Probe), cudaMemcpyDeviceToHost, stream));
       TTR_CUDA(cudaStreamSynchronize(stream));
-      if (hp.flag && !phase1_checked) {
-        // the phase-1 factor may be the broken one: redo it robustly, then this iteration
+      pending = false;
+      if (hp.flag) {
+        // a CholeskyQR pass of the last factorization broke down: redo it robustly, then the
+        // residual of the current block
         TTR_CUDA(cudaMemsetAsync(dprobe, 0, sizeof(Probe), stream));
-        TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
-        TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+        if (!phase1_checked) {
+          TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
+          TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+        } else {
+          const int64_t c0 = cc - prev_bb;
+          TTR_CHECK(copy2d(c, w.Q + c0, w.qcap, Rprev, ldp, rows, prev_bb));
+          TTR_CHECK(qr_inplace(c, E, w.Q + c0, w.qcap, rows, prev_bb, w.qr));
+          TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, c0, w.Q + c0, w.qcap, prev_bb, w.P));
+          TTR_CHECK(qr_inplace(c, E, w.Q + c0, w.qcap, rows, prev_bb, w.qr));
+        }
         phase1_checked = true;
+        TTR_CHECK(residual());
         continue;
       }
       phase1_checked = true;
@@ -1234,25 +1288,54 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
       if (!isfinite(est)) return set_error("non-finite residual estimate"), TTR_ERR_NONFINITE;
       ests.push_back(est);
       est_core.push_back(k);
-      if (!(est > tau_stop)) break;              // the speculative block is dropped
-      if (hp.flag) {
-        // CholeskyQR broke down on the new block: redo it with the robust fallbacks
-        TTR_CHECK(copy2d(c, w.Q + cc, w.qcap, w.S, bi, rows, bb));
-        TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
-        TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, cc, w.Q + cc, w.qcap, bb, w.P));
-        TTR_CHECK(qr_inplace(c, E, w.Q + cc, w.qcap, rows, bb, w.qr));
+      if (!(est > tau_stop)) break;
+      const int64_t bb = std::min(ba, rbar - cc), nxt = cc + bb;
+      const bool want = nxt < rbar;
+      if (want) TTR_CHECK(ensure(k, nxt + bi, rows, cols));
+      const int64_t bn = want ? bi : 0, tw = bb + bn;
+      // first pass: Q1 = Rcur(:, :bb) R1^{-1} into Q(:, cc:cc+bb)
+      TTR_CHECK(chol_pass(c, E, Rcur, ldr, rows, bb, w.Q + cc, w.qcap, q1, nullptr));
+      // [Q1, S_next] side by side, then T = [Q, Q1]^T [Q1, S_next]
+      double* Bt = hl.Bt[buf];
+      TTR_CHECK(copy2d(c, Bt, tw, w.Q + cc, w.qcap, rows, bb));
+      if (want) TTR_CHECK(copy2d(c, Bt + bb, tw, Sall + nxt, wcap, rows, bi));
+      TTR_CHECK(E.tn_product(c, w.Q, w.qcap, rows, cc + bb, Bt, tw, tw, hl.T, tw));
+      // G2 = Q1^T Q1 - C^T C (into the QR workspace), Mn = Q1^T S_next - C^T Q^T S_next
+      TTR_CHECK(block_step_gram(c, hl.T, tw, cc, bb, bn, w.qr.G, hl.Mn));
+      TTR_CHECK(chol_inv(c, w.qr.G, bb, bb, nullptr, w.qr.Rinv, &dprobe->flag));
+      // [Q1 - Q C, S_next - Q Q^T S_next] in one pass over Q, then Q_new = (Q1 - Q C) R2^{-1}
+      TTR_CHECK(E.sub_product(c, w.Q, w.qcap, rows, cc, hl.T, tw, tw, Bt, tw));
+      TTR_CHECK(apply_rinv(c, E, Bt, tw, rows, bb, w.qr.Rinv, w.Q + cc, w.qcap));
+      Rprev = Rcur;
+      ldp = ldr;
+      prev_bb = bb;
+      cc = nxt;
+      pending = true;
+      if (want) {
+        // residual of the next block: S_next - Q Q^T S_next - Q_new P_new, with its sum of squares
+        TTR_CHECK(tri_t_mul(c, w.qr.Rinv, bb, hl.Mn, bb, bi, hl.Pn));
+        TTR_CHECK(E.sub_product(c, w.Q + cc - bb, w.qcap, rows, bb, hl.Pn, bi, bi, Bt + bb, tw, &dprobe->ss));
+        Rcur = Bt + bb;
+        ldr = tw;
+        buf ^= 1;
       }
-      TTR_CUDA(cudaMemsetAsync(&dprobe->flag, 0, sizeof(int), stream));
-      cc += bb;
     }
-    if (!phase1_checked) {
-      // the loop never ran (b_init already reached rbar): check the phase-1 factorization
+    if (pending) {
+      // the last factorization was never checked: a breakdown there is redone robustly
       Probe hp;
       TTR_CUDA(cudaMemcpyAsync(&hp, dprobe, sizeof(Probe), cudaMemcpyDeviceToHost, stream));
       TTR_CUDA(cudaStreamSynchronize(stream));
       if (hp.flag) {
-        TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
-        TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+        if (!phase1_checked) {
+          TTR_CHECK(copy2d(c, w.Q, w.qcap, Sall, wcap, rows, b0));
+          TTR_CHECK(qr_inplace(c, E, w.Q, w.qcap, rows, b0, w.qr));
+        } else {
+          const int64_t c0 = cc - prev_bb;
+          TTR_CHECK(copy2d(c, w.Q + c0, w.qcap, Rprev, ldp, rows, prev_bb));
+          TTR_CHECK(qr_inplace(c, E, w.Q + c0, w.qcap, rows, prev_bb, w.qr));
+          TTR_CHECK(E.project_out(c, w.Q, w.qcap, rows, c0, w.Q + c0, w.qcap, prev_bb, w.P));
+          TTR_CHECK(qr_inplace(c, E, w.Q + c0, w.qcap, rows, prev_bb, w.qr));
+        }
       }
     }
     }

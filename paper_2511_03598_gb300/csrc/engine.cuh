@@ -130,6 +130,8 @@ int identity_f64(Ctx& c, double* A, int64_t m);                                 
 
 // rows x cc x bcols of a block projection from which the sliced form uses the tensor cores
 constexpr double kSlicedProjectWork = 1 << 24;
+// Most slices per operand of the tensor-core products: at 8, a product's error bound matches FP64's.
+constexpr int kMaxSlices = 8;
 
 struct Engine {
   int precision = TTR_PREC_FP64;
@@ -276,46 +278,54 @@ struct Engine {
     return gemm_f64(c, g);
   }
 
-  // P = Q(:, :cc)^T S;  S <- S - Q(:, :cc) P     (Eq. (3.5) / block Gram-Schmidt), FP64
-  // With sumsq_out, ||S||_F^2 of the result is accumulated there (it is zeroed in here first).
-  int project_out(Ctx& c, const double* Q, int64_t ldq, int64_t rows, int64_t cc, double* S, int64_t lds,
-                  int64_t bcols, double* P, double* sumsq_out = nullptr) const {
-    if (cc <= 0) {
-      if (!sumsq_out) return TTR_OK;
-      TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
-      return sumsq(c, S, rows, bcols, lds, 1, sumsq_out);
-    }
-    if (sliced() && (double)rows * cc * bcols >= kSlicedProjectWork) {
-      // wide blocks (the host-driven loop): both products on the tensor cores, each exact to the
-      // sliced form's stated error, instead of FP64 at 2 FMA per clock per SM
-      int st = tc_gemm_tn(c, slices, Q, ldq, rows, cc, S, lds, bcols, P, bcols, 1);   // P = Q^T S
-      if (st == TTR_OK) {
-        const size_t need = sizeof(double) * (size_t)rows * bcols;
-        if (c.ptmp_bytes < need) {
-          void* t = nullptr;
-          TTR_CHECK(c.alloc(&t, std::max(need, 2 * c.ptmp_bytes)));
-          c.ptmp = static_cast<double*>(t);
-          c.ptmp_bytes = std::max(need, 2 * c.ptmp_bytes);
-        }
-        TTR_CHECK(tc_gemm_rowmajor(c, slices, Q, ldq, rows, cc, P, bcols, bcols, c.ptmp, bcols));  // Q P
-        if (sumsq_out) TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
-        return sub2d(c, S, lds, c.ptmp, bcols, rows, bcols, sumsq_out);
-      }
+  // T (a x b, leading dimension ldt) = Q(:, :a)^T B(:, :b) over `rows` rows.  Wide products (the
+  // host-driven loop) go on the tensor cores in sliced form, each exact to the form's stated error,
+  // instead of FP64 at 2 FMA per clock per SM.
+  int tn_product(Ctx& c, const double* Q, int64_t ldq, int64_t rows, int64_t a, const double* Bm, int64_t ldb,
+                 int64_t b, double* T, int64_t ldt) const {
+    if (a <= 0 || b <= 0) return TTR_OK;
+    if (sliced() && (double)rows * a * b >= kSlicedProjectWork) {
+      int st = tc_gemm_tn(c, slices, Q, ldq, rows, a, Bm, ldb, b, T, ldt, 1);
       if (st != TTR_ERR_UNSUPPORTED) return st;
     }
-    int st = gram_reduce(c, Q, ldq, S, lds, rows, cc, bcols, P, bcols, 0, nullptr, nullptr, nullptr, nullptr, sumsq_out);
-    if (st == TTR_ERR_UNSUPPORTED) {
-      TTR_CHECK(gram_tn(c, Q, ldq, S, lds, rows, cc, bcols, P, bcols));
-      if (sumsq_out) TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
-    } else if (st != TTR_OK) {
-      return st;
+    int st = gram_reduce(c, Q, ldq, Bm, ldb, rows, a, b, T, ldt, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (st != TTR_ERR_UNSUPPORTED) return st;
+    return gram_tn(c, Q, ldq, Bm, ldb, rows, a, b, T, ldt);
+  }
+
+  // S (rows x n, leading dimension lds) <- S - Q(:, :k) P with P k x n (leading dimension ldp); with
+  // sumsq_out, ||S||_F^2 of the result is stored there.
+  int sub_product(Ctx& c, const double* Q, int64_t ldq, int64_t rows, int64_t k, const double* P, int64_t ldp,
+                  int64_t n, double* S, int64_t lds, double* sumsq_out = nullptr) const {
+    if (n <= 0) return TTR_OK;
+    if (sumsq_out) TTR_CUDA(cudaMemsetAsync(sumsq_out, 0, sizeof(double), c.stream));
+    if (k <= 0) return sumsq_out ? sumsq(c, S, rows, n, lds, 1, sumsq_out) : TTR_OK;
+    if (sliced() && (double)rows * k * n >= kSlicedProjectWork) {
+      const size_t need = sizeof(double) * (size_t)rows * n;
+      if (c.ptmp_bytes < need) {
+        void* t = nullptr;
+        TTR_CHECK(c.alloc(&t, std::max(need, 2 * c.ptmp_bytes)));
+        c.ptmp = static_cast<double*>(t);
+        c.ptmp_bytes = std::max(need, 2 * c.ptmp_bytes);
+      }
+      int st = tc_gemm_rowmajor(c, slices, Q, ldq, rows, k, P, ldp, n, c.ptmp, n);   // Q P
+      if (st == TTR_OK) return sub2d(c, S, lds, c.ptmp, n, rows, n, sumsq_out);
+      if (st != TTR_ERR_UNSUPPORTED) return st;
     }
-    st = gemm_nn_small(c, Q, ldq, P, bcols, rows, cc, bcols, S, lds, -1.0, 1.0, sumsq_out);
+    int st = gemm_nn_small(c, Q, ldq, P, ldp, rows, k, n, S, lds, -1.0, 1.0, sumsq_out);
     if (st == TTR_ERR_UNSUPPORTED && sumsq_out) {
-      TTR_CHECK(gemm_nn_small(c, Q, ldq, P, bcols, rows, cc, bcols, S, lds, -1.0, 1.0, nullptr));
-      return sumsq(c, S, rows, bcols, lds, 1, sumsq_out);
+      TTR_CHECK(gemm_nn_small(c, Q, ldq, P, ldp, rows, k, n, S, lds, -1.0, 1.0, nullptr));
+      return sumsq(c, S, rows, n, lds, 1, sumsq_out);
     }
     return st;
+  }
+
+  // P = Q(:, :cc)^T S;  S <- S - Q(:, :cc) P     (Eq. (3.5) / block Gram-Schmidt)
+  // With sumsq_out, ||S||_F^2 of the result is stored there.
+  int project_out(Ctx& c, const double* Q, int64_t ldq, int64_t rows, int64_t cc, double* S, int64_t lds,
+                  int64_t bcols, double* P, double* sumsq_out = nullptr) const {
+    if (cc > 0) TTR_CHECK(tn_product(c, Q, ldq, rows, cc, S, lds, bcols, P, bcols));
+    return sub_product(c, Q, ldq, rows, cc, P, bcols, bcols, S, lds, sumsq_out);
   }
 
   // M (ccols x cols, ld cols) = Q(:, :ccols)^T Z   (M_k = Q_k^T V(Y_k))

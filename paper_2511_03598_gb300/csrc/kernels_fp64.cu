@@ -7,6 +7,7 @@
 
 #include "gaussian.cuh"
 #include "ttr_internal.cuh"
+#include "rsqrt.cuh"
 
 namespace ttr {
 
@@ -564,59 +565,132 @@ int add_gaussian(Ctx& c, double* X, int64_t m, int64_t b, int64_t ld, const doub
 
 // ----------------------------------------------------------------------------- Cholesky + inverse
 // One CTA.  Upper factor R (G = R^T R) overwrites the upper triangle of G; Rinv = R^{-1}.
+// Right-looking: step j takes the pivot, scales row j and updates the trailing upper triangle
+// with one independent FMA per element, so the critical path is a few FP64 operations per column
+// (not a dot product of length j); R^{-1} likewise, by rows from the last, each finished row of
+// R^{-1} subtracted from the rows above it at once.  Pivots come from one reciprocal square root
+// (r = 1/sqrt(d), R_jj = d r), with no FP64 square root or division.  inv (dynamic shared memory,
+// b doubles) keeps the r_j for the inverse.
 __global__ void __launch_bounds__(1024) chol_inv_kernel(double* G, int64_t b, int64_t ld, const double* shift,
                                                         double* Rinv, int* bad) {
-  __shared__ double piv;
+  extern __shared__ double inv[];
   __shared__ int fail;
-  if (threadIdx.x == 0) fail = 0;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  if (tid == 0) fail = 0;
   const double sh = shift ? *shift : 0.0;
+  for (int64_t j = tid; j < b; j += nt) G[j * ld + j] += sh;
   __syncthreads();
-  __shared__ double red[32];
+  __shared__ double rs;
   for (int64_t j = 0; j < b; ++j) {
-    // R[j][c] = (G[j][c] + sh*[c==j] - sum_{p<j} R[p][j] R[p][c]) / R[j][j], c >= j
-    double part = 0.0;
-    for (int64_t p = threadIdx.x; p < j; p += blockDim.x) part = fma(G[p * ld + j], G[p * ld + j], part);
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double ssum = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ssum += red[w];
-      double d = G[j * ld + j] + sh - ssum;
+    // thread 0 takes pivot j (R_jj = d r, r = 1/sqrt(d)); the others scale row j - 1 by r_{j-1},
+    // which no later update reads unscaled
+    if (tid == 0) {
+      double d = G[j * ld + j];
       if (!(d > 0.0) || !isfinite(d)) {
         fail = 1;
         d = 1.0;
       }
-      piv = sqrt(d);
-      G[j * ld + j] = piv;
+      const double r = rsqrt_full(d);
+      rs = r;
+      inv[j] = r;
+      G[j * ld + j] = d * r;
+    }
+    if (j > 0) {
+      const double rp = inv[j - 1];
+      for (int64_t col = j + tid; col < b; col += nt) G[(j - 1) * ld + col] *= rp;
     }
     __syncthreads();
-    for (int64_t col = j + 1 + threadIdx.x; col < b; col += blockDim.x) {
-      double v = G[j * ld + col];
-      for (int64_t p = 0; p < j; ++p) v -= G[p * ld + j] * G[p * ld + col];
-      G[j * ld + col] = v / piv;
+    // G[p][q] -= R[j][p] R[j][q] = G[j][p] G[j][q] r^2 for j < p <= q: warps over rows p, lanes over q
+    const double r2 = rs * rs;
+    for (int64_t p = j + 1 + warp; p < b; p += nw) {
+      const double t = G[j * ld + p] * r2;
+      for (int64_t q = p + lane; q < b; q += 32) G[p * ld + q] = fma(-t, G[j * ld + q], G[p * ld + q]);
     }
     __syncthreads();
   }
-  // Rinv: column c by back substitution, one thread per column.
-  for (int64_t col = threadIdx.x; col < b; col += blockDim.x) {
-    for (int64_t i = b - 1; i >= 0; --i) {
-      if (i > col) {
-        Rinv[i * ld + col] = 0.0;
-        continue;
-      }
-      double v = (i == col) ? 1.0 : 0.0;
-      for (int64_t p = i + 1; p <= col; ++p) v -= G[i * ld + p] * Rinv[p * ld + col];
-      Rinv[i * ld + col] = v / G[i * ld + i];
-    }
+  // Rinv starts as the identity (upper part); for p = b-1 .. 0: row p *= 1/R[p][p], then
+  // Rinv[i][c] -= R[i][p] Rinv[p][c] for i < p, c >= p.
+  for (int64_t e = tid; e < b * b; e += nt) {
+    const int64_t i = e / b, col = e % b;
+    Rinv[i * ld + col] = (i == col) ? 1.0 : 0.0;
   }
-  if (threadIdx.x == 0 && fail) *bad = 1;
+  __syncthreads();
+  for (int64_t pr = b - 1; pr >= 0; --pr) {
+    const double ip = inv[pr];
+    for (int64_t col = pr + tid; col < b; col += nt) Rinv[pr * ld + col] *= ip;
+    __syncthreads();
+    for (int64_t i = warp; i < pr; i += nw) {
+      const double rip = G[i * ld + pr];
+      for (int64_t col = pr + lane; col < b; col += 32)
+        Rinv[i * ld + col] = fma(-rip, Rinv[pr * ld + col], Rinv[i * ld + col]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && fail) *bad = 1;
 }
 
 int chol_inv(Ctx& c, double* G, int64_t b, int64_t ld, const double* shift_dev, double* Rinv, int* bad) {
   if (b <= 0) return TTR_OK;
-  chol_inv_kernel<<<1, 256, 0, c.stream>>>(G, b, ld, shift_dev, Rinv, bad);
+  if (b > 6144) return set_error("chol_inv: block wider than 6144 columns"), TTR_ERR_UNSUPPORTED;
+  const int threads = b <= 64 ? 256 : 1024;
+  const size_t smem = sizeof(double) * (size_t)b;
+  if (smem > 48 * 1024)
+    TTR_CUDA(cudaFuncSetAttribute((const void*)chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  chol_inv_kernel<<<1, threads, smem, c.stream>>>(G, b, ld, shift_dev, Rinv, bad);
   return c.check_launch("chol_inv");
+}
+
+// ----------------------------------------------------------------------------- host-driven block step
+// From T = [Q, Q1]^T [Q1, S] ((cc + bb) x (bb + bn), leading dimension ldt) with C = T[:cc, :bb]:
+//   G2 = T[cc:, :bb] - C^T C            (bb x bb, leading dimension bb)
+//   Mn = T[cc:, bb:] - C^T T[:cc, bb:]  (bb x bn, leading dimension bn)
+// One warp per output; the lanes split the sum over the cc rows of T.
+__global__ void __launch_bounds__(256) block_step_gram_kernel(const double* T, int64_t ldt, int64_t cc, int64_t bb,
+                                                              int64_t bn, double* G2, double* Mn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wcols = bb + bn;
+  const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (o >= bb * wcols) return;
+  const int64_t i = o / wcols, j = o % wcols;
+  double s0 = 0.0, s1 = 0.0;
+  int64_t p = lane;
+  for (; p + 32 < cc; p += 64) {
+    s0 = fma(T[p * ldt + i], T[p * ldt + j], s0);
+    s1 = fma(T[(p + 32) * ldt + i], T[(p + 32) * ldt + j], s1);
+  }
+  if (p < cc) s0 = fma(T[p * ldt + i], T[p * ldt + j], s0);
+  double s = s0 + s1;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) {
+    const double v = T[(cc + i) * ldt + j] - s;
+    if (j < bb) G2[i * bb + j] = v;
+    else Mn[i * bn + (j - bb)] = v;
+  }
+}
+
+int block_step_gram(Ctx& c, const double* T, int64_t ldt, int64_t cc, int64_t bb, int64_t bn, double* G2,
+                    double* Mn) {
+  if (bb <= 0) return TTR_OK;
+  const int64_t warps = bb * (bb + bn);
+  block_step_gram_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, c.stream>>>(T, ldt, cc, bb, bn, G2, Mn);
+  return c.check_launch("block_step_gram");
+}
+
+// out (b x n) = Rinv^T M for Rinv = R^{-1} upper triangular (b x b, leading dimension ldr)
+__global__ void tri_t_mul_kernel(const double* Rinv, int64_t ldr, const double* M, int64_t b, int64_t n, double* out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    double v = 0.0;
+    for (int64_t p = 0; p <= i; ++p) v = fma(Rinv[p * ldr + i], M[p * n + j], v);
+    out[e] = v;
+  }
+}
+
+int tri_t_mul(Ctx& c, const double* Rinv, int64_t ldr, const double* M, int64_t b, int64_t n, double* out) {
+  if (b <= 0 || n <= 0) return TTR_OK;
+  tri_t_mul_kernel<<<(unsigned)std::min<int64_t>((b * n + 255) / 256, 1024), 256, 0, c.stream>>>(Rinv, ldr, M, b, n,
+                                                                                                  out);
+  return c.check_launch("tri_t_mul");
 }
 
 // ----------------------------------------------------------------------------- copies
@@ -629,6 +703,16 @@ __global__ void copy2d_kernel(double* dst, int64_t ldd, const double* src, int64
 
 int copy2d(Ctx& c, double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows, int64_t cols) {
   if (rows <= 0 || cols <= 0) return TTR_OK;
+  if (ldd == cols && lds == cols) {
+    TTR_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)(rows * cols), cudaMemcpyDeviceToDevice, c.stream));
+    return TTR_OK;
+  }
+  if (cols < 64) {
+    // narrow strided rows (the block columns of the adaptive loop): one coalesced kernel pass
+    const unsigned blocks = (unsigned)std::min<int64_t>((rows * cols + 255) / 256, 152 * 16);
+    copy2d_kernel<<<blocks, 256, 0, c.stream>>>(dst, ldd, src, lds, rows, cols);
+    return c.check_launch("copy2d");
+  }
   TTR_CUDA(cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double), cols * sizeof(double), rows,
                              cudaMemcpyDeviceToDevice, c.stream));
   return TTR_OK;

@@ -52,7 +52,7 @@ constexpr int TNMAX = 256;            // largest UMMA N; the tile width tn is ch
 constexpr int PB = 64;                // partial-contraction epilogue: columns per staging block
 constexpr int KC = 32;                // K per shared-memory chunk (two UMMA K-steps of 16)
 constexpr int KSEG = 256;             // largest K per CTA: bound for exact FP32 accumulation
-constexpr int MAXS = 8;               // slices per operand
+constexpr int MAXS = kMaxSlices;      // slices per operand
 constexpr int PLANE_A = TM * KC;      // bf16 per A digit plane per chunk (8 KB)
 
 constexpr int NP = 512;               // producer threads: slicing, then the epilogue (4 warps per TMEM lane quarter)
@@ -718,49 +718,46 @@ __host__ __device__ __forceinline__ int b_digit_index(int grp, int j, int s, int
 
 // ---- B operand preparation: column exponent scales, then digit planes in the shared-memory
 // image.  B(k, n) = B[k*sbk + n*sbn], K x N.
-// Pass 1: grid (N-chunks, K-chunks of 32 rows); each CTA writes the largest exponent of each of its
-// tn columns over its 32 rows to Fpart[kchunk][column] (plain stores: nothing to clear first).
+// Pass 1: grid (N-chunks, up to 128 CTAs along K); each CTA takes the largest exponent of each of
+// its tn columns over the K-chunks of 32 rows y, y + gridDim.y, ... and folds it into Fmax[column]
+// with one integer atomic maximum per column (Fmax is zeroed before the launch; every exponent
+// field is at least 1).
 __global__ void __launch_bounds__(256) colmax_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
-                                                       int tn, int64_t npad, int* Fpart) {
+                                                       int tn, int* Fmax) {
   __shared__ int cm[TNMAX];
   const int nc = blockIdx.x;
   for (int j = threadIdx.x; j < tn; j += blockDim.x) cm[j] = 1;
   __syncthreads();
+  const int64_t kchunks = (K + KC - 1) / KC;
   // a task reads 8 rows of one column (all loads in flight)
-  for (int u = threadIdx.x; u < tn * (KC / 8); u += blockDim.x) {
-    const int j = u % tn, grp = u / tn;
-    const int64_t n = (int64_t)nc * tn + j;
-    if (n >= N) continue;
-    double v[8];
+  for (int64_t y = blockIdx.y; y < kchunks; y += gridDim.y) {
+    for (int u = threadIdx.x; u < tn * (KC / 8); u += blockDim.x) {
+      const int j = u % tn, grp = u / tn;
+      const int64_t n = (int64_t)nc * tn + j;
+      if (n >= N) continue;
+      double v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int64_t k = (int64_t)blockIdx.y * KC + grp * 8 + q;
-      v[q] = (k < K) ? B[k * sbk + n * sbn] : 0.0;
+      for (int q = 0; q < 8; ++q) {
+        const int64_t k = y * KC + grp * 8 + q;
+        v[q] = (k < K) ? B[k * sbk + n * sbn] : 0.0;
+      }
+      int e = 1;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) e = max(e, exp_field(v[q]));
+      atomicMax(&cm[j], e);
     }
-    int e = 1;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) e = max(e, exp_field(v[q]));
-    atomicMax(&cm[j], e);
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < tn; j += blockDim.x) Fpart[(int64_t)blockIdx.y * npad + (int64_t)nc * tn + j] = cm[j];
+  for (int j = threadIdx.x; j < tn; j += blockDim.x) atomicMax(Fmax + (int64_t)nc * tn + j, cm[j]);
 }
 
-// Pass 2: one CTA per (tn-column chunk, 32-row K chunk).  The column scales are the maxima of the
-// pass-1 partials (CTA (nc, 0) also stores them to Fmax); tasks (column, group of 8 k) then write
-// the s digit planes.
+// Pass 2: one CTA per (tn-column chunk, 32-row K chunk), after pass 1 has completed Fmax (the
+// column scales); tasks (column, group of 8 k) write the s digit planes.
 __global__ void __launch_bounds__(256) slice_b_kernel(const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
-                                                      int s, int tn, int kchunks, int64_t npad, const int* Fpart,
-                                                      int* Fmax, uint4* planes) {
+                                                      int s, int tn, int kchunks, const int* Fmax, uint4* planes) {
   __shared__ int E[TNMAX];
   const int nc = blockIdx.x, kcn = blockIdx.y;
-  for (int j = threadIdx.x; j < tn; j += blockDim.x) {
-    int e = 1;
-    const int* fp = Fpart + (int64_t)nc * tn + j;
-    for (int q = 0; q < kchunks; ++q) e = max(e, __ldg(fp + (int64_t)q * npad));
-    E[j] = e;
-    if (kcn == 0) Fmax[(int64_t)nc * tn + j] = e;
-  }
+  for (int j = threadIdx.x; j < tn; j += blockDim.x) E[j] = max(1, __ldg(Fmax + (int64_t)nc * tn + j));
   __syncthreads();
   const int plane_b = tn * KC;
   uint4* blk = planes + ((size_t)nc * kchunks + kcn) * (size_t)s * (plane_b / 8);
@@ -1002,11 +999,12 @@ static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, 
                                          dim3(256), params, 0, c.stream));
     TTR_CHECK(c.check_launch("prep_b"));
   } else {
-    colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(B, sbk, sbn, K, N, p.tn,
-                                                                                        npad, Fpart);
+    TTR_CUDA(cudaMemsetAsync(p.Fmax, 0, sizeof(int) * (size_t)npad, c.stream));
+    colmax_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)std::min(p.kchunks, 128)), 256, 0, c.stream>>>(
+        B, sbk, sbn, K, N, p.tn, p.Fmax);
     TTR_CHECK(c.check_launch("colmax_b"));
     slice_b_kernel<<<dim3((unsigned)p.nchunks, (unsigned)p.kchunks), 256, 0, c.stream>>>(
-        B, sbk, sbn, K, N, s, p.tn, p.kchunks, npad, Fpart, p.Fmax, p.planes);
+        B, sbk, sbn, K, N, s, p.tn, p.kchunks, p.Fmax, p.planes);
     TTR_CHECK(c.check_launch("slice_b"));
   }
   if (keep) {

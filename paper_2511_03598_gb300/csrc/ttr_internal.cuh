@@ -153,6 +153,14 @@ int sub2d(Ctx& c, double* S, int64_t lds, const double* T, int64_t ldt, int64_t 
 int chol_inv(Ctx& c, double* G, int64_t b, int64_t ld, const double* shift_dev, double* Rinv,
              int* bad);
 
+// One block of the host-driven adaptive loop, from T = [Q, Q1]^T [Q1, S] ((cc + bb) x (bb + bn),
+// leading dimension ldt), C = T[:cc, :bb]:  G2 = T[cc:, :bb] - C^T C (bb x bb) and
+// Mn = T[cc:, bb:] - C^T T[:cc, bb:] (bb x bn).
+int block_step_gram(Ctx& c, const double* T, int64_t ldt, int64_t cc, int64_t bb, int64_t bn, double* G2,
+                    double* Mn);
+// out (b x n) = Rinv^T M for upper-triangular Rinv (b x b, leading dimension ldr), M b x n.
+int tri_t_mul(Ctx& c, const double* Rinv, int64_t ldr, const double* M, int64_t b, int64_t n, double* out);
+
 // X += (*scale_dev) * G with G an m x b standard Gaussian matrix drawn from `seed`.
 int add_gaussian(Ctx& c, double* X, int64_t m, int64_t b, int64_t ld, const double* scale_dev, uint64_t seed);
 

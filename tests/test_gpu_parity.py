@@ -128,7 +128,7 @@ def test_adaptive_parity(B, name, make, tol, block, prec):
     assert yi["ranks"] == info["ranks"]
     flat = [e for es in info["estimates"] for e in es]
     assert len(flat) == len(yi["estimates"])
-    assert np.allclose(yi["estimates"], flat, rtol=1e-8, atol=1e-14 * x.norm)
+    assert np.allclose(yi["estimates"], flat, rtol=1e-8, atol=1e-13 * x.norm)
     assert rel_tensor_diff(got, ref) <= 1e-10
     assert T.tt_dist(got, x.cores) <= tol * x.norm * (1 + 1e-9)
 
@@ -238,7 +238,10 @@ def test_adaptive_c3_full_size(B, prec):
 ])
 def test_adaptive_estimator_reading_parity(B, name, make, tol, block, est_min, beta):
     """Reading R16 on the device loop: residual sketches wider than the appended block and the stop
-    at tau / beta, against the oracle with the same settings (FP64 bars)."""
+    at tau / beta, against the oracle with the same settings (FP64 bars).  The estimate of a block
+    whose residual vanishes exactly (the rank of the unfolding is used up) is rounding noise of
+    order u ||X|| times the entries summed, whose value depends on the summation order (the device
+    reductions add in no fixed order): estimates are compared to 1e-13 ||X|| absolute."""
     x = make()
     ref, info = R.tt_round_adaptive(x.cores, tol, seed=5, block=block, nrmx=x.norm, est_min=est_min, est_safety=beta)
     with B.round_adaptive(dev(x.cores), tol, block, 5, B.options(nrmx=x.norm, est_min=est_min, est_safety=beta)) as y:
@@ -247,7 +250,7 @@ def test_adaptive_estimator_reading_parity(B, name, make, tol, block, est_min, b
     assert yi["ranks"] == info["ranks"]
     flat = [e for es in info["estimates"] for e in es]
     assert len(flat) == len(yi["estimates"])
-    assert np.allclose(yi["estimates"], flat, rtol=1e-8, atol=1e-14 * x.norm)
+    assert np.allclose(yi["estimates"], flat, rtol=1e-8, atol=1e-13 * x.norm)
     assert rel_tensor_diff(got, ref) <= 1e-10
     assert T.tt_dist(got, x.cores) <= tol * x.norm * (1 + 1e-9)
 
