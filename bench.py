@@ -130,28 +130,33 @@ def probe_peaks() -> dict:
 TRAFFIC_SLICED = {"block_loop": 2.437e6, "rl_kernel": 17.98e6}
 
 
-def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
+def serving_run(B, nreq: int, workers: int, budget: int, nreq_open: int | None = None) -> dict:
     """The serving stream (Poisson arrivals, mean gap 2 ms; each request a sum of 2-6 random TTs
-    with d 8-32, n 16-128, ranks 20-100, tol 1e-4/1e-6/1e-8): its first `nreq` requests, given to
-    the library's request server as summands in host memory.  A producer thread generates the
-    requests while the server works, holding at most a window of them (the whole stream's summands
-    are ~80 GB); each request's host data is dropped once its result is collected.  Closed loop: a
+    with d 8-32, n 16-128, ranks 20-100, tol 1e-4/1e-6/1e-8): its first `nreq` requests (closed
+    loop) and its first `nreq_open` (open loop; default `nreq`), given to
+    the library's request server as summands in host memory.  A producer generates the requests
+    (on a pool of host threads, each request from a generator of its own) while the server works,
+    holding at most a window of them (the whole stream's summands are ~80 GB); each request's host
+    data is dropped once its result is collected.  Closed loop: a
     request is submitted as soon as it is generated and the window has room (throughput).  Open loop:
     each is submitted at its arrival time, or when generated if that is later (latency under that
     load; the stream arrives ~100 times faster than one GPU rounds it, so queueing dominates)."""
     import collections
     import queue
+    from concurrent.futures import ThreadPoolExecutor
 
     import workloads as WL
     window = max(4, 3 * workers)
+    gen_threads = max(1, min(8, (os.cpu_count() or 4) // 2))
     srv = B.Server(workers=workers, device_budget=budget)
     opts = B.options(precision=B.TTR_PREC_SLICED)
 
-    def producer(q, stop):
-        for r in WL.c4_stream(count=nreq, formal=False):
+    def producer(q, stop, pool, count):
+        for spec in WL.c4_specs(count=count):
+            fut = pool.submit(WL.c4_request, spec, 4, False)
             while not stop.is_set():
                 try:
-                    q.put(r, timeout=0.5)
+                    q.put(fut, timeout=0.5)
                     break
                 except queue.Full:
                     continue
@@ -161,12 +166,16 @@ def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
 
     try:
         # warm-up: one small request (kernel attributes, memory pool)
-        small = next(WL.c4_stream(count=nreq, formal=False, max_bytes=1e8))
+        small = next(WL.c4_stream(count=512, formal=False, max_bytes=1e8))
         srv.wait(srv.submit(small.tt.summands, small.tol, 0, 7, opts), fetch=False)
         out = {}
+        counts = {"closed_loop": nreq, "open_loop": nreq if nreq_open is None else nreq_open}
         for mode in ("closed_loop", "open_loop"):
+            if counts[mode] <= 0:
+                continue
             q, stop = queue.Queue(maxsize=window), threading.Event()
-            th = threading.Thread(target=producer, args=(q, stop), daemon=True)
+            pool = ThreadPoolExecutor(max_workers=gen_threads)
+            th = threading.Thread(target=producer, args=(q, stop, pool, counts[mode]), daemon=True)
             th.start()
             pending = collections.deque()
             lat, late, ranks_max, formal, inbytes, count = [], [], 0, 0, 0, 0
@@ -180,9 +189,10 @@ def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
                 ranks_max = max(ranks_max, max(info["ranks"]))
             try:
                 while True:
-                    r = q.get()
-                    if r is None:
+                    fut = q.get()
+                    if fut is None:
                         break
+                    r = fut.result()
                     if mode == "open_loop":
                         delay = r.arrival_ms / 1e3 - (time.perf_counter() - t0)
                         if delay > 0:
@@ -199,6 +209,7 @@ def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
                     collect_one()
             finally:
                 stop.set()
+                pool.shutdown(wait=True, cancel_futures=True)
             span = time.perf_counter() - t0
             st = srv.stats()
             out[mode] = {"roundings_per_s": count / span, "p50_ms": float(np.percentile(lat, 50)),
@@ -207,11 +218,12 @@ def serving_run(B, nreq: int, workers: int, budget: int) -> dict:
                          "formal_bytes_total": int(formal), "input_bytes_total": int(inbytes)}
             if mode == "open_loop":
                 out[mode]["submitted_after_arrival_p50_ms"] = float(np.percentile(late, 50)) if late else 0.0
-        out.update({"requests": nreq, "workers": workers, "device_budget": budget, "window": window,
+        out.update({"requests": counts, "workers": workers, "device_budget": budget, "window": window,
+                    "generator_threads": gen_threads,
                     "precision": "sliced, slices from each request's tol", "block": "appendix rule (block 0)",
-                    "note": "first requests of the seeded serving stream (seed 4), generated by a producer thread "
-                            "while the server works, summands in pageable host memory; latency = submit to result "
-                            "in host memory (queueing + H2D + rounding + D2H)"})
+                    "note": "requests of the seeded serving stream (seed 4), generated on host threads while the "
+                            "server works, summands in pageable host memory; latency = submit to result in host "
+                            "memory (queueing + H2D + rounding + D2H)"})
         return out
     finally:
         srv.close()
@@ -585,7 +597,10 @@ def main():
     ap.add_argument("--configs", action="store_true",
                     help="print the per-configuration table (GPU and oracle times) instead of the bench line")
     ap.add_argument("--serve-requests", type=int, default=24,
-                    help="requests of the serving stream run through the request server (0: skip)")
+                    help="requests of the serving stream in the closed-loop run (0: skip)")
+    ap.add_argument("--serve-open-requests", type=int, default=512,
+                    help="requests of the serving stream in the open-loop run at their arrival times "
+                         "(512: the whole configured stream; 0: skip)")
     args = ap.parse_args()
 
     import workloads as WL
@@ -711,8 +726,8 @@ def main():
     # several ranks (all GPUs held) they run only at N = 1.
     single_gpu = world == 1
     try:
-        serving = (serving_run(B, args.serve_requests, args.streams, 120 << 30)
-                   if args.serve_requests > 0 and single_gpu else None)
+        serving = (serving_run(B, args.serve_requests, args.streams, 120 << 30, args.serve_open_requests)
+                   if (args.serve_requests > 0 or args.serve_open_requests > 0) and single_gpu else None)
     except Exception as e:  # noqa: BLE001
         serving = {"error": f"{type(e).__name__}: {e}"}
 

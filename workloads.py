@@ -183,14 +183,11 @@ class Request:
     tt: TTInput
 
 
-def c4_stream(seed: int = 4, count: int = 512, mean_gap_ms: float = 2.0, max_bytes: float | None = None,
-              formal: bool = True):
-    """Serving stream: Poisson arrivals; each request is a sum of s in [2, 6] random TTs with d in
-    [8, 32], n in [16, 128], component ranks in [20, 100] (all bonds of a summand equal), coefficients
-    N(0, 1) on the first cores, and tol in {1e-4, 1e-6, 1e-8}.  Yields requests lazily (the whole
-    stream is larger than host or device memory).  Each request carries its summands; with
-    ``formal`` it also carries the block-diagonal formal sum as ``cores`` (costly for large
-    requests), else ``cores`` is empty.  ``max_bytes`` skips requests whose formal sum is larger."""
+def c4_specs(seed: int = 4, count: int = 512, mean_gap_ms: float = 2.0, max_bytes: float | None = None):
+    """The serving stream's request parameters in arrival order (cheap; no tensor data): Poisson
+    arrivals; each request a sum of s in [2, 6] random TTs with d in [8, 32], n in [16, 128],
+    component ranks in [20, 100] (all bonds of a summand equal) and tol in {1e-4, 1e-6, 1e-8}.
+    ``max_bytes`` skips requests whose formal sum is larger."""
     rng = np.random.default_rng(seed)
     t = 0.0
     for rid in range(count):
@@ -204,11 +201,27 @@ def c4_stream(seed: int = 4, count: int = 512, mean_gap_ms: float = 2.0, max_byt
         nb = 8 * (2 * n * R + (d - 2) * n * R * R)
         if max_bytes is not None and nb > max_bytes:
             continue
-        sub = np.random.default_rng([seed, rid])
-        terms = [(float(sub.standard_normal()), random_tt(sub, d, n, rc)) for rc in comp]
-        summands = []
-        for c, x in terms:
-            summands.append([c * x[0]] + x[1:])
-        cores = block_sum(terms) if formal else []
-        yield Request(rid, t, tol, TTInput(f"c4_req{rid}", cores, float("nan"),
-                                           {"s": s, "d": d, "n": n, "ranks": comp, "formal_bytes": nb}, summands))
+        yield {"rid": rid, "arrival_ms": t, "tol": tol, "s": s, "d": d, "n": n, "ranks": comp, "formal_bytes": nb}
+
+
+def c4_request(spec: dict, seed: int = 4, formal: bool = True) -> Request:
+    """The request of one spec of ``c4_specs``: coefficients N(0, 1) on the first cores of its random
+    summands, drawn from a generator of its own (so requests can be made in any order or in
+    parallel).  With ``formal`` it also carries the block-diagonal formal sum as ``cores``."""
+    rid, d, n, comp = spec["rid"], spec["d"], spec["n"], spec["ranks"]
+    sub = np.random.default_rng([seed, rid])
+    terms = [(float(sub.standard_normal()), random_tt(sub, d, n, rc)) for rc in comp]
+    summands = [[c * x[0]] + x[1:] for c, x in terms]
+    cores = block_sum(terms) if formal else []
+    meta = {"s": spec["s"], "d": d, "n": n, "ranks": comp, "formal_bytes": spec["formal_bytes"]}
+    return Request(rid, spec["arrival_ms"], spec["tol"], TTInput(f"c4_req{rid}", cores, float("nan"), meta, summands))
+
+
+def c4_stream(seed: int = 4, count: int = 512, mean_gap_ms: float = 2.0, max_bytes: float | None = None,
+              formal: bool = True):
+    """Serving stream: the requests of ``c4_specs`` in arrival order, made lazily (the whole stream
+    is larger than host or device memory).  Each request carries its summands; with ``formal`` it
+    also carries the block-diagonal formal sum as ``cores`` (costly for large requests), else
+    ``cores`` is empty."""
+    for spec in c4_specs(seed, count, mean_gap_ms, max_bytes):
+        yield c4_request(spec, seed, formal)
