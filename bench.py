@@ -756,9 +756,12 @@ def main():
     # (FP64-accurate contractions)
     forms = {}
     what = {"sliced6_df_block_loop": "6 slices, the block loop's per-CTA arithmetic in double-float (FP32 pipe)",
-            "sliced8_fp64": "8 slices (contractions FP64-accurate), FP64 block loop"}
+            "sliced8_fp64": "8 slices (contractions FP64-accurate), FP64 block loop",
+            "adap_r": "the headline form followed by the Remark 3.2 right-to-left compression pass (threshold tau), "
+                      "which truncates the over-estimated ranks toward the deterministic rounding's"}
     if prec == B.TTR_PREC_SLICED:
-        for name, kw in (("sliced6_df_block_loop", {"block_loop_df": True}), ("sliced8_fp64", {"slices": 8})):
+        for name, kw in (("sliced6_df_block_loop", {"block_loop_df": True}), ("sliced8_fp64", {"slices": 8}),
+                         ("adap_r", {"adap_r": True})):
             fo = B.options(precision=prec, nrmx=x.norm, **kw)
             for _ in range(2):
                 B.round_adaptive(cores, TOL, BLOCK, SEED, fo).free()
@@ -776,7 +779,7 @@ def main():
             forms[name] = {"roundings_per_s": 1e3 * nf / fe[0].elapsed_time(fe[-1]),
                            "p50_ms": float(np.percentile(fms, 50)), "p99_ms": float(np.percentile(fms, 99)),
                            "steps": nf, "ranks_equal_headline": franks == out_ranks,
-                           "what": what[name],
+                           "max_rank": max(franks), "what": what[name],
                            "measured": "one rounding at a time on one stream (compare single_stream)"}
 
     # ---- end to end through host buffers: H2D of the cores, rounding, D2H of the result

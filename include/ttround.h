@@ -123,6 +123,13 @@ typedef struct {
                              arithmetic in double-float (pairs of binary32, about 2^-48 relative, on
                              the FP32 pipe; cross-CTA sums stay FP64); 0 = FP64 (default: CholeskyQR2,
                              the Gram matrices and the estimator FP64 at every slice count) */
+  int32_t block_loop_tc;  /* TTR_PREC_SLICED, FP64 block loop: 1 = its per-row products (the block
+                             Gram-Schmidt coefficients, the Gram matrices of the second CholeskyQR
+                             pass and the updates X - Q P) on the tensor cores as 8-slice products,
+                             whose error bound is that of an FP64 product; 0 = FP64 FMA (default:
+                             with K <= 256 per CTA these products are short, and the FMA form is
+                             the faster one on the measured workloads).  The small factorizations,
+                             the residual norms and every decision stay FP64 either way. */
 } ttr_options;
 
 typedef struct {
@@ -154,7 +161,7 @@ typedef struct {
 
 /* Fill `opts` with defaults: FP64, adap_r off, scale 1, nrmx 0 (estimate), f_init 0.1,
  * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0, max_sms 0, est_min 0,
- * est_safety 1, rl_percore 0, block_loop_df 0. */
+ * est_safety 1, rl_percore 0, block_loop_df 0, block_loop_tc 0. */
 void ttr_default_options(ttr_options* opts);
 
 /* Algorithm 4 (Sec. 3.2): fixed-rank randomize-then-orthogonalize with a KRP sketch.

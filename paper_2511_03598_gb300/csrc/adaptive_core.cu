@@ -31,6 +31,7 @@
 
 #include "engine.cuh"
 #include "rsqrt.cuh"
+#include "sliced_mma.cuh"
 
 namespace ttr {
 namespace ac {
@@ -65,12 +66,16 @@ struct Args {
   int sshift;           // the sketch is held scaled by 2^sshift (double-float range; 0 in FP64)
   double* gwork;        // null: the CTA's rows live in shared memory; else in this global buffer,
   int64_t gstride;      //   gstride doubles per CTA (rows too wide for shared memory)
+  int tc_off;           // tensor-core products: byte offset of their planes in dynamic shared memory
+  int tc_cols;          //   and the TMEM columns they take (256 or 512)
 };
 
 // Phase timer of CTA 0 (launch-timeline profiling only): cycles since the previous mark are
 // added to prof[phase]; prof[PH_BARRIER] collects the cycles spent waiting in grid barriers.
 enum Phase { PH_STAGE = 0, PH_FIRST_QR, PH_COEFF, PH_RESIDUAL, PH_REDUCE_B, PH_QR1, PH_REORTH, PH_REDUCE_A,
-             PH_FINISH, PH_BARRIER, PH_COUNT };
+             PH_FINISH, PH_BARRIER,
+             // parts of the phases above (each mark closes the part before it)
+             PH_B_LOCAL, PH_QR1_FACTOR, PH_RO_LOCAL, PH_RO_REDUCE, PH_RO_FIX, PH_QR2_FACTOR, PH_QR2_P, PH_COUNT };
 struct Timer {
   unsigned long long* p;
   long long t;
@@ -202,6 +207,176 @@ struct DF {
     return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
   }
 };
+
+// ---- tensor-core products of the block loop (sliced form).  The per-row products of a block --
+// the coefficients and Gram matrices [Q, Q_new]^T [Q_new, S_next] and Q^T S, and the updates
+// X <- X - Q P -- run on the BF16 tensor cores as 8-slice products (the error bound of an FP64
+// product; FP64 retires two FMAs per clock per SM on this part).  Each CTA multiplies its own
+// rows: K (the rows for a Gram product, the columns of Q for an update) is at most 256, so the
+// low digit diagonals accumulate exactly in FP32; operands are cut into digits in shared memory
+// one 16-deep K-chunk at a time, one thread issues the MMAs of the chunk into TMEM and waits on an
+// mbarrier (bounded), and the epilogue recombines the diagonals in integers as the contraction
+// kernels do.  C(m, n) = sum_k A(m, k) B(k, n) with m < M (tiles of 128), n < N <= 64, k < K.
+constexpr int TKC = 16;                            // K per chunk: one UMMA K-step
+constexpr int TSL = kMaxSlices;                    // slices per operand
+constexpr int TNB = 64;                            // widest N
+constexpr int TMAXK = 256;                         // K bound for exact low diagonals
+constexpr int TROWS = 512;                         // largest M (row scales kept in shared memory)
+constexpr int TPA = tc::TM * TKC;                  // bf16 per A digit plane
+constexpr int TPB = TNB * TKC;                     // bf16 per B digit plane (widest)
+constexpr size_t TC_BYTES = (size_t)TSL * (TPA + TPB) * 2;    // 48 KB of dynamic shared memory
+
+struct Tc {
+  uint16_t* ap;          // A digit planes (TSL x TPA), K-major UMMA layout
+  uint16_t* bp;          // B digit planes, layout of b_digit_index
+  uint32_t tmem;         // TMEM base: TSL diagonals x NB columns
+  uint64_t* bar;         // MMA completion
+  uint32_t* phase;       // parity of the next wait on bar (shared)
+  int* rowE;             // biased exponent scale of each A row m (TROWS)
+  int* colE;             // of each B column n (TNB)
+  int* err;
+};
+
+// rowE[m] = max_k exponent field of A(m, k), colE[n] = that of B(k, n) (at least 1)
+template <class FA, class FB>
+__device__ __forceinline__ void tc_scales(const Tc& t, int M, int N, int K, FA a_at, FB b_at) {
+  for (int m = threadIdx.x; m < M; m += NT) t.rowE[m] = 1;
+  for (int n = threadIdx.x; n < N; n += NT) t.colE[n] = 1;
+  __syncthreads();
+  for (int e = threadIdx.x; e < M * K; e += NT) {
+    const int m = e / K, k = e - m * K;
+    atomicMax(&t.rowE[m], tc::exp_field(a_at(m, k)));
+  }
+  for (int e = threadIdx.x; e < K * N; e += NT) {
+    const int k = e / N, n = e - k * N;
+    atomicMax(&t.colE[n], tc::exp_field(b_at(k, n)));
+  }
+  __syncthreads();
+}
+
+// digits of the chunk k0 .. k0 + 15 of rows m0 .. m0 + 127 of A (rows below M; entries past K are 0)
+// and of columns n < N of B, into the planes; the rows >= M and columns >= N of the planes are
+// left as they are (they reach only outputs that are dropped)
+template <class FA, class FB>
+__device__ __forceinline__ void tc_slice(const Tc& t, int m0, int M, int N, int K, int k0, int NB, FA a_at, FB b_at) {
+  for (int task = threadIdx.x; task < tc::TM * (TKC / 8); task += NT) {
+    const int row = task >> 1, grp = task & 1, m = m0 + row;
+    if (m >= M) continue;
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + grp * 8 + q;
+      v[q] = (k < K) ? a_at(m, k) : 0.0;
+    }
+    const int idx = ((grp * (tc::TM / 8)) + (row >> 3)) * 64 + (row & 7) * 8;
+    tc::store_digits<TSL>(v, t.rowE[m], t.ap, TPA, idx);
+  }
+  for (int task = threadIdx.x; task < N * (TKC / 8); task += NT) {
+    const int n = task % N, grp = task / N;
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + grp * 8 + q;
+      v[q] = (k < K) ? b_at(k, n) : 0.0;
+    }
+    tc::store_digits<TSL>(v, t.colE[n], t.bp, (size_t)NB * 8, tc::b_digit_index(grp, n, TSL, NB));
+  }
+}
+
+// The MMAs of one chunk (one 16-deep K-step): for each A plane p, the B planes q = 0 .. TSL-1-p,
+// adjacent along N in the b_digit_index layout, go to diagonals p + q in one MMA per group of
+// floor(256 / NB) planes.  The first chunk's p = 0 MMAs write every diagonal first.
+__device__ __forceinline__ void tc_issue(const Tc& t, int NB, bool first) {
+  const uint64_t da0 = tc::umma_desc(tc::smem_u32(t.ap), (tc::TM / 8) * 128, 128);
+  const uint64_t db0 = tc::umma_desc(tc::smem_u32(t.bp), TSL * (NB / 8) * 128, 128);
+  constexpr uint32_t PA = (TPA * 2) >> 4;
+  const uint32_t pb = (uint32_t)((NB / 8) * 128) >> 4;
+  const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tc::TM >> 4) << 24);
+  const int G = 256 / NB;
+#pragma unroll
+  for (int p = 0; p < TSL; ++p) {
+    const uint64_t da = da0 + (uint64_t)(p * PA);
+    for (int q0 = 0; q0 < TSL - p; q0 += G) {
+      const int nq = min(G, TSL - p - q0);
+      const uint64_t db = db0 + (uint64_t)((uint32_t)q0 * pb);
+      const uint32_t idesc = idesc0 | ((uint32_t)((nq * NB) >> 3) << 17);
+      const uint32_t accum = (first && p == 0) ? 0u : 1u;
+      asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                   "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(t.tmem + (uint32_t)((p + q0) * NB)),
+                   "l"(da), "l"(db), "r"(idesc), "r"(accum));
+    }
+  }
+}
+
+// C = A B (see above), out(m, n, value) for m < M, n < N.  Returns false when a wait ran out (the
+// error flag is set).  All threads of the CTA call it.
+template <class FA, class FB, class FO>
+__device__ bool tc_product(const Tc& t, int M, int N, int K, FA a_at, FB b_at, FO out) {
+  __shared__ int ok_s;
+  const int NB = N <= 32 ? 32 : 64;                 // TSL * NB TMEM columns (256 or 512)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  tc_scales(t, M, N, K, a_at, b_at);
+  if (threadIdx.x == 0) ok_s = 1;
+  for (int m0 = 0; m0 < M; m0 += tc::TM) {
+    for (int k0 = 0; k0 < K; k0 += TKC) {
+      tc_slice(t, m0, M, N, K, k0, NB, a_at, b_at);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        tc_issue(t, NB, k0 == 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            tc::smem_u32(t.bar)));
+        if (!tc::mbar_wait(tc::smem_u32(t.bar), *t.phase, t.err)) ok_s = 0;
+        *t.phase ^= 1u;
+      }
+      __syncthreads();
+      if (!ok_s) return false;
+    }
+    // epilogue: warp w reads TMEM lane quarter w % 4 (rows), the two warps of a quarter take
+    // alternate groups of 16 columns; V = sum_t acc_t 2^(7(TSL-1-t)) in integers (as in the
+    // contraction kernels: Vh carries the shifts >= 35), then one rounding to FP64
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int quarter = warp & 3, half = warp >> 2, row = quarter * 32 + lane, m = m0 + row;
+    for (int cg = half; cg < NB / 16; cg += NT / 128) {
+      long long Vh[16], Vl[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) Vh[j] = Vl[j] = 0;
+#pragma unroll 1
+      for (int d = 0; d < TSL; ++d) {
+        uint32_t r[16];
+        const uint32_t taddr = t.tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * NB + cg * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int shift = 7 * (TSL - 1 - d);
+        if (shift >= 35) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) Vh[j] += (long long)__float2int_rz(__uint_as_float(r[j])) << (shift - 35);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) Vl[j] += (long long)__float2int_rz(__uint_as_float(r[j])) << shift;
+        }
+      }
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = cg * 16 + j;
+          if (n < N) {
+            const __int128 V = (__int128)Vh[j] * ((__int128)1 << 35) + (__int128)Vl[j];
+            out(m, n, tc::i128_to_double(V, t.rowE[m] + t.colE[n] - 2044 - 7 * TSL - 7));
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  return true;
+}
 
 // Each CTA keeps its own rows resident in shared memory (or, for rows too wide, in its own region
 // of a global buffer, with the same layout):
@@ -570,10 +745,10 @@ __device__ void mul_rinv_t_left(const double* C, int b, int n, const double* Ri,
   __syncthreads();
 }
 
-template <class A>
+template <class A, bool TCP>
 __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   using T = typename A::T;
-  extern __shared__ __align__(16) double sm[];
+  extern __shared__ __align__(128) double sm[];
   __shared__ T RiT[BMAX * BMAX];
   __shared__ double G[BMAX * BMAX];
   __shared__ double Ri[BMAX * BMAX];
@@ -609,6 +784,37 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   Red rd{a.acc, 0, a.acc_used};
   Timer tmr{a.prof, clock64()};
   if (threadIdx.x == 0) s_barrier_prof = (blockIdx.x == 0) ? a.prof : nullptr;
+  // tensor-core products: TMEM, the completion barrier and the scales
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t tc_bar;
+  __shared__ uint32_t tc_phase;
+  __shared__ int tc_rowE[TROWS];
+  __shared__ int tc_colE[TNB];
+  Tc tcx{};
+  if constexpr (TCP) {
+    unsigned char* tb = reinterpret_cast<unsigned char*>(sm) + a.tc_off;
+    tcx.ap = reinterpret_cast<uint16_t*>(tb);
+    tcx.bp = reinterpret_cast<uint16_t*>(tb + (size_t)TSL * TPA * 2);
+    tcx.bar = &tc_bar;
+    tcx.phase = &tc_phase;
+    tcx.rowE = tc_rowE;
+    tcx.colE = tc_colE;
+    tcx.err = a.err;
+    if ((threadIdx.x >> 5) == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_slot)),
+                   "r"(a.tc_cols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&tc_bar)));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+      tc_phase = 0u;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    tcx.tmem = tmem_slot;
+  }
   // stage the own rows: sketch columns, and the part of Q that is already final
   for (int e = threadIdx.x; e < nr * ldw; e += NT)
     Ss[e] = A::from(mul_pow2(a.Sall[(lo + e / ldw) * a.lds + e % ldw], a.sshift));
@@ -626,6 +832,13 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
       a.io[0] = timeout ? ST_TIMEOUT : status;
       a.io[1] = cc;
       a.io[2] = nest;
+    }
+    if constexpr (TCP) {
+      // every MMA of this CTA has completed (each product waits for its own): release TMEM
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcx.tmem), "r"(a.tc_cols));
     }
   };
   // one cross-CTA reduction: everything accumulated into red_buf(rd) before the call is summed
@@ -671,7 +884,19 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   while (cc < a.rbar) {
     if (cc + bi > a.width) return finish(ST_EXTEND);
     if (!have_p) {
-      gram_acc<A>(Qs, ldq, Ss + cc, ldw, cc, bi, nr, red_buf(rd));
+      if (TCP && nr > 0) {
+        double* eb = red_buf(rd);
+        const T* sc_ = Ss + cc;
+        if (!tc_product(
+                tcx, cc, bi, nr, [&](int m, int k) { return A::to(Qs[k * ldq + m]); },
+                [&](int k, int n) { return A::to(sc_[k * ldw + n]); },
+                [&](int m, int n, double v) { atomicAdd(eb + m * bi + n, v); })) {
+          timeout = true;
+          return finish(ST_TIMEOUT);
+        }
+      } else {
+        gram_acc<A>(Qs, ldq, Ss + cc, ldw, cc, bi, nr, red_buf(rd));
+      }
       double* buf = reduce();
       if (!buf) return finish(ST_TIMEOUT);
       read_totals_t<A>(buf, cc * bi, Ps);
@@ -680,7 +905,17 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     // residual sketch of the next block (Eqs. (3.4)-(3.5)): S = S_all(:, cc:cc+bi) - Q P
     for (int e = threadIdx.x; e < nr * bi; e += NT) Rs[e] = Ss[(e / bi) * ldw + cc + e % bi];
     __syncthreads();
-    sub_qp<A>(Rs, bi, Qs, ldq, cc, Ps, ldp, bi, nr);
+    if (TCP && cc > 0 && cc <= TMAXK && nr > 0) {
+      if (!tc_product(
+              tcx, nr, bi, cc, [&](int m, int k) { return A::to(Qs[m * ldq + k]); },
+              [&](int k, int n) { return A::to(Ps[k * ldp + n]); },
+              [&](int m, int n, double v) { Rs[m * bi + n] = A::from(A::to(Rs[m * bi + n]) - v); })) {
+        timeout = true;
+        return finish(ST_TIMEOUT);
+      }
+    } else {
+      sub_qp<A>(Rs, bi, Qs, ldq, cc, Ps, ldp, bi, nr);
+    }
     tmr.mark(PH_RESIDUAL);
     // reduction B: ||S||_F^2 and the Gram matrix of the candidate block S(:, 0:bb)
     const int bb = min(a.ba, a.rbar - cc);
@@ -689,6 +924,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
       sumsq_acc<A>(Rs, bi, bi, nr, eb);
       gram_acc<A>(Rs, bi, Rs, bi, bb, bb, nr, eb + 1);
     }
+    tmr.mark(PH_B_LOCAL);
     double* bufB = reduce();
     if (!bufB) return finish(ST_TIMEOUT);
     if (threadIdx.x == 0) est_s = __ldcg(bufB);
@@ -705,6 +941,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     // the first pass leaves Q_new orthonormal to ~u cond(S)^2, the second to ~u).
     read_totals(bufB + 1, bb * bb, G);
     if (!factor1(bb)) return finish(ST_BREAKDOWN);
+    tmr.mark(PH_QR1_FACTOR);
     T* Qn = Qs + cc;
     for (int e = threadIdx.x; e < nr * bb; e += NT) Qn[(e / bb) * ldq + e % bb] = Rs[(e / bb) * bi + e % bb];
     __syncthreads();
@@ -721,12 +958,29 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     const bool want = nxt < a.rbar && nxt + bi <= a.width;
     {
       double* eb = red_buf(rd);
-      gram_acc<A>(Qs, ldq, Qn, ldq, nxt, bb, nr, eb);                                  // (cc + bb) x bb
-      if (want) gram_acc<A>(Qs, ldq, Ss + nxt, ldw, nxt, bi, nr, eb + nxt * bb);      // (cc + bb) x bi
+      if (TCP && nr > 0) {
+        const T* sn = Ss + nxt;
+        const int nb = bb + (want ? bi : 0);
+        if (!tc_product(
+                tcx, nxt, nb, nr, [&](int m, int k) { return A::to(Qs[k * ldq + m]); },
+                [&](int k, int n) { return n < bb ? A::to(Qn[k * ldq + n]) : A::to(sn[k * ldw + (n - bb)]); },
+                [&](int m, int n, double v) {
+                  if (n < bb) atomicAdd(eb + m * bb + n, v);
+                  else atomicAdd(eb + nxt * bb + m * bi + (n - bb), v);
+                })) {
+          timeout = true;
+          return finish(ST_TIMEOUT);
+        }
+      } else {
+        gram_acc<A>(Qs, ldq, Qn, ldq, nxt, bb, nr, eb);                                  // (cc + bb) x bb
+        if (want) gram_acc<A>(Qs, ldq, Ss + nxt, ldw, nxt, bi, nr, eb + nxt * bb);      // (cc + bb) x bi
+      }
     }
+    tmr.mark(PH_RO_LOCAL);
     double* bufA = reduce();
     if (!bufA) return finish(ST_TIMEOUT);
     if (cc > 0) read_totals_t<A>(bufA, cc * bb, Cs);
+    tmr.mark(PH_RO_REDUCE);
     for (int o = threadIdx.x; o < bb * bb; o += NT) {
       const int i = o / bb, j = o % bb;
       T t = A::zero();
@@ -734,9 +988,21 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
       G[o] = __ldcg(bufA + (cc + i) * bb + j) - A::to(t);
     }
     __syncthreads();
-    if (cc > 0) sub_qp<A>(Qn, ldq, Qs, ldq, cc, Cs, bb, bb, nr);
+    tmr.mark(PH_RO_FIX);
+    if (TCP && cc > 0 && cc <= TMAXK && nr > 0) {
+      if (!tc_product(
+              tcx, nr, bb, cc, [&](int m, int k) { return A::to(Qs[m * ldq + k]); },
+              [&](int k, int n) { return A::to(Cs[k * bb + n]); },
+              [&](int m, int n, double v) { Qn[m * ldq + n] = A::from(A::to(Qn[m * ldq + n]) - v); })) {
+        timeout = true;
+        return finish(ST_TIMEOUT);
+      }
+    } else if (cc > 0) {
+      sub_qp<A>(Qn, ldq, Qs, ldq, cc, Cs, bb, bb, nr);
+    }
     tmr.mark(PH_REORTH);
     if (!factor2(bb)) return finish(ST_BREAKDOWN);
+    tmr.mark(PH_QR2_FACTOR);
     if (want) {
       // P = [Q^T S_next; R2^{-T} (Q_new^T S_next - C^T Q^T S_next)]; the middle term goes through M
       const double* pb = bufA + nxt * bb;
@@ -756,6 +1022,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
       }
       __syncthreads();
     }
+    tmr.mark(PH_QR2_P);
     to_arith<A>(Ri, bb * bb, RiT);
     apply_rinv<A>(Qn, ldq, bb, RiT, nr, Tb);
     have_p = want;
@@ -801,7 +1068,8 @@ bool adaptive_core_rows_fit(int64_t m, int b0, int bi, int rbar, int width, int 
 // at column *cc), or TTR_ERR_UNSUPPORTED when this path does not apply.
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
                   int bi, int ba, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status,
-                  int* cc, int* nest, bool double_float, double scale, int max_sms, bool host_if_global) {
+                  int* cc, int* nest, bool double_float, double scale, int max_sms, bool host_if_global,
+                  bool tensor_products) {
   if (b0 > ac::BMAX || bi > ac::BMAX || m <= 0) return TTR_ERR_UNSUPPORTED;
   if (ba < 1 || ba > bi) return set_error("adaptive loop: appended block wider than the residual sketch"), TTR_ERR_ARG;
   int dev = 0;
@@ -809,7 +1077,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   // device properties and the kernel's shared-memory limit, looked up once per device
   constexpr int MAXDEV = 64;
   struct DevInfo {
-    int nsm, coop, smem_optin, raised[2];
+    int nsm, coop, smem_optin, raised[3], static_bytes[3];
   };
   static DevInfo info[MAXDEV] = {};
   DevInfo local{};
@@ -830,13 +1098,32 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   const int64_t qcols = std::min(rbar, width);     // columns of Q never exceed the sketch width
   const size_t dyn = sizeof(double) * ((size_t)rpc * (size_t)(qcols + width + bi + ac::BMAX) +
                                         2 * (size_t)qcols * (size_t)std::max(b0, bi));
-  const size_t static_bytes = 48 * 1024;   // G, R^{-1} (FP64 and working type), [G | I], pivot buffers (about 44 KB)
+  // the kernels' static shared memory (G, R^{-1}, [G | I], pivot buffers, the product scales)
+  const void* kerns[3] = {(const void*)ac::adaptive_core_kernel<ac::F64, false>,
+                          (const void*)ac::adaptive_core_kernel<ac::DF, false>,
+                          (const void*)ac::adaptive_core_kernel<ac::F64, true>};
+  if (di.static_bytes[0] == 0) {
+    for (int q = 0; q < 3; ++q) {
+      cudaFuncAttributes fa{};
+      TTR_CUDA(cudaFuncGetAttributes(&fa, kerns[q]));
+      di.static_bytes[q] = (int)fa.sharedSizeBytes + 1024;
+    }
+  }
   // rows that do not fit in shared memory live in a global buffer, one region per CTA (same layout)
-  const bool global_rows = dyn + static_bytes > (size_t)smem_optin;
+  const bool global_rows = dyn + (size_t)di.static_bytes[double_float ? 1 : 0] > (size_t)smem_optin;
   if (global_rows && host_if_global) return TTR_ERR_UNSUPPORTED;
-  const void* kern = double_float ? (const void*)ac::adaptive_core_kernel<ac::DF>
-                                  : (const void*)ac::adaptive_core_kernel<ac::F64>;
-  const int ki = double_float ? 1 : 0;
+  // tensor-core products (sliced form, FP64 arithmetic): K of every product within the exact bound,
+  // the widths within the TMEM columns, and their digit planes beside the rows in shared memory
+  const size_t tc_off = global_rows ? 0 : (dyn + 127) / 128 * 128;
+  const bool use_tc = tensor_products && !double_float && rpc <= ac::TMAXK && rbar <= ac::TROWS &&
+                      ba + bi <= ac::TNB &&
+                      tc_off + ac::TC_BYTES + (size_t)di.static_bytes[2] <= (size_t)smem_optin;
+  const int ki = use_tc ? 2 : (double_float ? 1 : 0);
+  const void* kern = kerns[ki];
+  size_t dyn_launch = use_tc ? tc_off + ac::TC_BYTES : (global_rows ? 0 : dyn);
+  // a CTA that takes all 512 TMEM columns must have its SM to itself (a second one would wait for
+  // them while the first waits for it at a grid barrier): ask for more than half the shared memory
+  if (use_tc && ba + bi > 32) dyn_launch = std::max(dyn_launch, (size_t)smem_optin / 2 + 1024);
   double* gwork = nullptr;
   const int64_t gstride = (int64_t)((dyn / sizeof(double) + 31) / 32 * 32);
   if (global_rows) {
@@ -848,16 +1135,17 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
       c.ac_gwork_bytes = need;
     }
     gwork = c.ac_gwork;
-  } else {
+  }
+  if (dyn_launch > 0) {
     // the limit belongs to the kernel, shared by every thread that calls it: only ever raise it
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
-    if (di.raised[ki] < (int)dyn) {
-      TTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    if (di.raised[ki] < (int)dyn_launch) {
+      TTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_launch));
       int per_sm = 0;
-      TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ac::NT, dyn));
+      TTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ac::NT, dyn_launch));
       if (per_sm < 1) return TTR_ERR_UNSUPPORTED;
-      di.raised[ki] = (int)dyn;
+      di.raised[ki] = (int)dyn_launch;
     }
   }
   // largest reduction: first block (b0^2 + b0 bi) or the second one of a block ((cc + bb)(bb + bi)
@@ -892,6 +1180,8 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   a.tau = tau;
   a.bar = c.ac_bar; a.err = c.d_flags; a.est_out = reinterpret_cast<double*>(c.ac_io + 4); a.io = c.ac_io;
   a.gwork = gwork; a.gstride = gstride;
+  a.tc_off = (int)tc_off;
+  a.tc_cols = (ba + bi <= 32) ? 256 : 512;
   // double-float keeps binary32 exponents: hold the sketch scaled so that ||X|| maps near 1
   a.sshift = 0;
   if (double_float && scale > 0.0 && isfinite(scale)) {
@@ -908,7 +1198,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   }
   void* params[] = {&a};
   c.time_begin(Ctx::KT_BLOCK_LOOP);
-  TTR_CUDA(cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(ac::NT), params, global_rows ? 0 : dyn, c.stream));
+  TTR_CUDA(cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(ac::NT), params, dyn_launch, c.stream));
   TTR_CHECK(c.check_launch("adaptive_core"));
   // one launch makes at most one estimate per block it runs
   const int est_max = std::min(cap, (rbar - cc0) / std::max(1, ba) + 3);

@@ -105,15 +105,18 @@ void Ctx::prof_report() {
             a.second.ms, 100.0 * a.second.ms / std::max(total, 1e-9), 1e3 * a.second.ms / a.second.n);
   if (ac_prof) {
     static const char* names[] = {"stage rows", "first block QR", "fresh Q^T S", "residual (local)",
-                                  "reduce B + estimate", "QR pass 1", "reduce A + reorth", "QR 2 + next P",
-                                  "write back", "(barrier waits)"};
-    unsigned long long cyc[10] = {};
+                                  "reduce B + estimate", "QR 1 (copy, apply)", "reorth (local sub)",
+                                  "QR 2 (apply)", "write back", "(barrier waits)", "reduce B (local sums)",
+                                  "QR 1 (factor)", "reorth (local Gram)", "reorth (reduction)",
+                                  "reorth (G - C^T C)", "QR 2 (factor)", "QR 2 (next P)"};
+    constexpr int NPH = (int)(sizeof(names) / sizeof(names[0]));
+    unsigned long long cyc[NPH] = {};
     cudaMemcpy(cyc, ac_prof, sizeof(cyc), cudaMemcpyDeviceToHost);
     int dev = 0, khz = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
     const double mhz = khz > 0 ? khz / 1e3 : 2070.0;
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < NPH; ++i)
       fprintf(stderr, "[ttr profile]   adaptive_core %-22s %9.3f ms (CTA 0, %.0f MHz)\n", names[i], cyc[i] / mhz / 1e3,
               mhz);
   }
@@ -1194,7 +1197,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
                            (int)ba, (int)rbar, (int)sk_cols, (int)cc, tau_stop, hest.data(), (int)hest.size(), &status,
                            &ccn, &nest,
                            E.precision == TTR_PREC_SLICED && E.slices <= 6 && o.block_loop_df, nrmx, o.max_sms,
-                           wide_tc);
+                           wide_tc, E.sliced() && o.block_loop_tc != 0);
         if (st == TTR_ERR_UNSUPPORTED) break;
         if (st != TTR_OK) return st;
         for (int q = 0; q < nest; ++q) {
@@ -1581,6 +1584,7 @@ void ttr_default_options(ttr_options* o) {
   o->est_safety = 1.0;
   o->rl_percore = 0;
   o->block_loop_df = 0;
+  o->block_loop_tc = 0;
 }
 
 static int finish(int st, ttr_result* out, cudaStream_t s) {

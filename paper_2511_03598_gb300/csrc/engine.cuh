@@ -61,13 +61,16 @@ int tc_gemm_rowmajor_flt(Ctx& c, int fs, const double* A, int64_t lda, int64_t M
 // width); ba <= bi: columns appended per block; tau: the stopping threshold.  Rows that do not fit in
 // shared memory live in global memory; host_if_global returns TTR_ERR_UNSUPPORTED instead (the
 // caller's host-driven loop, whose wide block projections run on the tensor cores, is faster there).
+// tensor_products: the FP64 loop's per-row products as 8-slice tensor-core products where their
+// shapes allow (at most 256 rows per CTA, rbar <= 512, ba + bi <= 64, room in shared memory).
 bool adaptive_core_rows_fit(int64_t m, int b0, int bi, int rbar, int width, int max_sms);
 // widest block (b_init or the residual sketch) the device block loop factors itself; a wider first
 // block is factored on the host side before the loop starts at col(Q) = b_init
 constexpr int kBlockLoopMaxBlock = 32;
 int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ldq, double* S, int64_t m, int b0,
                   int bi, int ba, int rbar, int width, int cc0, double tau, double* est_host, int est_cap, int* status,
-                  int* cc, int* nest, bool double_float, double scale, int max_sms, bool host_if_global);
+                  int* cc, int* nest, bool double_float, double scale, int max_sms, bool host_if_global,
+                  bool tensor_products = false);
 
 // Householder QR of a tall row-major m x b matrix (householder.cu), for the deterministic rounding.
 // householder_qr overwrites A with the reflectors and R (R also copied to R, b x b, ld ldr, if

@@ -339,6 +339,25 @@ def test_adaptive_sliced_default_with_double_float_block_loop(B):
     assert T.tt_dist(got, x.cores) <= 1e-6 * x.norm
 
 
+@pytest.mark.parametrize("name,make,tol,block,slices,bar", [
+    ("c2", lambda: WL.c2(), 1e-6, 10, 0, 1e-8),
+    ("c3_small", lambda: WL.c3(d=6, n=16, r=10), 1e-7, 0, 8, 1e-10),
+    ("ragged", lambda: WL.copies_plus_noise(8, 5, 7, 5, 3, 2, 1e-6, "ragged"), 1e-5, 3, 8, 1e-10),
+])
+def test_adaptive_block_loop_tensor_core_products(B, name, make, tol, block, slices, bar):
+    """The block loop's per-row products on the tensor cores (block_loop_tc, 8-slice products with
+    the error bound of FP64 products): the oracle's ranks, and the tensor within the bar of the
+    sliced form at that slice count (tolerance-chosen for the bench workload, 8 otherwise)."""
+    x = make()
+    ref, info = R.tt_round_adaptive(x.cores, tol, seed=2024, block=block, nrmx=x.norm)
+    with B.round_adaptive(dev(x.cores), tol, block, 2024,
+                          B.options(precision=B.TTR_PREC_SLICED, slices=slices, nrmx=x.norm, block_loop_tc=True)) as y:
+        assert y.ranks == info["ranks"]
+        got = y.to_numpy()
+    assert rel_tensor_diff(got, ref) <= bar
+    assert T.tt_dist(got, x.cores) <= tol * x.norm
+
+
 def test_adaptive_adap_r_sliced(B):
     """The Remark 3.2 pass after the sliced rounding (8 slices): ranks and tensor as the oracle's."""
     x = WL.c1()
