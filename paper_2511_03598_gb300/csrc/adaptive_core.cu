@@ -92,13 +92,22 @@ __shared__ unsigned long long* s_barrier_prof;
 
 constexpr int ACC = 8192;                         // doubles per accumulation buffer allocated up front
 
+// generation of the grid barrier this CTA last passed (thread 0; read once at the kernel's start,
+// before any CTA can pass a barrier, then advanced by one per barrier)
+__shared__ unsigned s_gen;
+
+__device__ __forceinline__ void grid_sync_init(unsigned* bar) {
+  if (threadIdx.x == 0) s_gen = *(volatile unsigned*)(bar + 1);
+}
+
 __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
   __syncthreads();
   __shared__ int ok_s;
   if (threadIdx.x == 0) {
     ok_s = 1;
     volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
+    const unsigned gen = s_gen;
+    s_gen = gen + 1u;
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u);
     if (arrived == gridDim.x - 1) {
@@ -131,23 +140,43 @@ __device__ __forceinline__ void my_rows(int64_t m, int64_t& lo, int64_t& hi) {
 
 // Cross-CTA sums go through three rotating accumulation buffers in global memory: for reduction i
 // every CTA adds its partial sums into buffer i%3 with FP64 atomics, passes the grid barrier and
-// reads the totals (through L2).  Right after barrier i, CTA 0 zeroes buffer (i+2)%3: its last
-// readers (reduction i-1) finished before barrier i, and its next writers (reduction i+2) start
-// only after barrier i+1.  The totals are the same in every CTA, so all CTAs take the same branch.
+// reads the totals (through L2).  On grids of at least RCOPY_FROM CTAs each buffer holds RCOPY
+// copies, CTA c adding into copy c % RCOPY (fewer atomics per address: the barrier's fence waits
+// for them to drain) and readers summing the copies; smaller grids use one copy.  Right after barrier i, the CTAs zero buffer (i+2)%3 between them: its last readers
+// (reduction i-1) finished before barrier i, and its next writers (reduction i+2) start only after
+// barrier i+1.  The totals are the same in every CTA, so all CTAs take the same branch.
+constexpr int RCOPY = 4;
+constexpr int RCOPY_FROM = 128;
+__device__ __forceinline__ int red_copies() { return gridDim.x >= RCOPY_FROM ? RCOPY : 1; }
 struct Red {
-  double* base;     // 3 x used doubles, zero on entry
+  double* base;     // 3 x RCOPY x used doubles, zero on entry
   int i;            // index of the next reduction
-  int used;         // entries to clear per buffer
+  int used;         // entries of one copy (the distance between copies)
 };
 
-__device__ __forceinline__ double* red_buf(const Red& r) { return r.base + (int64_t)(r.i % 3) * r.used; }
+// copy 0 of the current buffer (readers), and this CTA's copy (writers)
+__device__ __forceinline__ double* red_buf(const Red& r) {
+  return r.base + (int64_t)(r.i % 3) * red_copies() * r.used;
+}
+__device__ __forceinline__ double* red_out(const Red& r) {
+  return red_buf(r) + (int64_t)(blockIdx.x % red_copies()) * r.used;
+}
+
+// the total at p (a location in copy 0) over the copies, `stride` doubles apart
+__device__ __forceinline__ double rtot(const double* p, int stride) {
+  double t = __ldcg(p);
+  if (red_copies() > 1) {
+#pragma unroll
+    for (int q = 1; q < RCOPY; ++q) t += __ldcg(p + (int64_t)q * stride);
+  }
+  return t;
+}
 
 // after the barrier of the current reduction: clear the buffer two reductions ahead, advance
 __device__ __forceinline__ void red_advance(Red& r) {
-  if (blockIdx.x == 0) {
-    double* z = r.base + (int64_t)((r.i + 2) % 3) * r.used;
-    for (int o = threadIdx.x; o < r.used; o += NT) z[o] = 0.0;
-  }
+  double* z = r.base + (int64_t)((r.i + 2) % 3) * red_copies() * r.used;
+  const int n = red_copies() * r.used;
+  for (int o = blockIdx.x * NT + threadIdx.x; o < n; o += gridDim.x * NT) z[o] = 0.0;
   r.i++;
 }
 
@@ -423,13 +452,13 @@ __device__ void sumsq_acc(const typename A::T* X, int ldx, int b, int nr, double
 }
 
 // shared-memory copy of the first n totals of buf (written by other CTAs: read through L2)
-__device__ void read_totals(const double* buf, int n, double* dst) {
-  for (int o = threadIdx.x; o < n; o += NT) dst[o] = __ldcg(buf + o);
+__device__ void read_totals(const double* buf, int n, double* dst, int stride) {
+  for (int o = threadIdx.x; o < n; o += NT) dst[o] = rtot(buf + o, stride);
   __syncthreads();
 }
 template <class A>
-__device__ void read_totals_t(const double* buf, int n, typename A::T* dst) {
-  for (int o = threadIdx.x; o < n; o += NT) dst[o] = A::from(__ldcg(buf + o));
+__device__ void read_totals_t(const double* buf, int n, typename A::T* dst, int stride) {
+  for (int o = threadIdx.x; o < n; o += NT) dst[o] = A::from(rtot(buf + o, stride));
   __syncthreads();
 }
 
@@ -573,19 +602,26 @@ __device__ bool factor_small_df(const double* G, int b, double* Ri, double* M, d
     if (threadIdx.x == 0) {
       sigma_s = e >> 1;
       fail = 0;
-      sc[0] = 1.0;
+      reinterpret_cast<dfl*>(sc)[0] = {1.f, 0.f};
     }
   }
   __syncthreads();
   const int sigma = sigma_s;
+  dfl* scd = reinterpret_cast<dfl*>(sc);                     // s_j in double-float (8 bytes, as sc)
   dfl v[FKMAX];
   int pp[FKMAX], qq[FKMAX];
 #pragma unroll
   for (int k = 0; k < FKMAX; ++k) {
-    const int e = threadIdx.x + k * NT;
     pp[k] = -1;
     qq[k] = 0;
     v[k] = {0.f, 0.f};
+  }
+  // the conversions only for the slots that hold elements (the bound is the same for the whole CTA:
+  // FP64 instructions with all lanes masked off still take FP64 pipe time on this part)
+#pragma unroll
+  for (int k = 0; k < FKMAX; ++k) {
+    if (k * NT >= tot) break;
+    const int e = threadIdx.x + k * NT;
     if (e < tot) {
       pp[k] = e / w2;
       qq[k] = e % w2;
@@ -613,7 +649,7 @@ __device__ bool factor_small_df(const double* G, int b, double* Ri, double* M, d
     const dfl dp = df_scale(d, inv2);
     if (threadIdx.x == 0) {
       scp = df_mul(scp, dp);
-      sc[j + 1] = df_to(scp);
+      scd[j + 1] = scp;                                       // no FP64 operation on the critical path
     }
 #pragma unroll
     for (int k = 0; k < FKMAX; ++k) {
@@ -628,16 +664,25 @@ __device__ bool factor_small_df(const double* G, int b, double* Ri, double* M, d
   }
   __syncthreads();
   if (fail) return false;
+  dfl* Md = reinterpret_cast<dfl*>(M);                       // [G | I] after the elimination, double-float
 #pragma unroll
   for (int k = 0; k < FKMAX; ++k)
-    if (pp[k] >= 0 && (qq[k] == pp[k] || (qq[k] >= b && qq[k] - b <= pp[k]))) M[pp[k] * w2 + qq[k]] = df_to(v[k]);
+    if (pp[k] >= 0 && (qq[k] == pp[k] || (qq[k] >= b && qq[k] - b <= pp[k]))) Md[pp[k] * w2 + qq[k]] = v[k];
   __syncthreads();
+  // R^{-1}(i, j) = M(j, b + i) / sqrt(M(j, j) s_j) in double-float (the reciprocal square root from a
+  // binary32 seed and one Newton step, ~2^-45 relative), one conversion to FP64 per entry
   for (int e = threadIdx.x; e < b * b; e += NT) {
     const int i = e / b, j = e % b;
     double r = 0.0;
     if (i <= j) {
-      const double y = M[j * w2 + j] * sc[j];
-      r = (y > 0.0 && isfinite(y)) ? mul_pow2(M[j * w2 + b + i] * rsqrt_full(y), -sigma) : 0.0;
+      const dfl y = df_mul(Md[j * w2 + j], scd[j]);
+      const int yb = __float_as_int(y.h), ye = (yb >> 23) & 0xFF;
+      if (yb > 0 && ye != 0 && ye != 0xFF) {
+        const float r0 = rsqrtf(y.h);
+        const dfl t = df_sub(dfl{1.f, 0.f}, df_mul(df_mul(y, dfl{r0, 0.f}), dfl{r0, 0.f}));   // 1 - y r0^2
+        const dfl rs = df_add(dfl{r0, 0.f}, dfl{0.5f * r0 * t.h, 0.f});
+        r = mul_pow2(df_to(df_mul(Md[j * w2 + b + i], rs)), -sigma);
+      }
     }
     Ri[e] = r;
   }
@@ -735,11 +780,11 @@ __device__ void sub_qp(typename A::T* X, int ldx, const typename A::T* Q, int ld
 // out (b x n, ld n, shared) = Ri^T (b x b lower) C (b x n, ld n, global totals): the coefficients
 // of the new basis block (X R^{-1})^T Y from X^T Y
 template <class A>
-__device__ void mul_rinv_t_left(const double* C, int b, int n, const double* Ri, typename A::T* out) {
+__device__ void mul_rinv_t_left(const double* C, int b, int n, const double* Ri, typename A::T* out, int stride) {
   for (int e = threadIdx.x; e < b * n; e += NT) {
     const int i = e / n, j = e % n;
     double v = 0.0;
-    for (int k = 0; k <= i; ++k) v = fma(Ri[k * b + i], __ldcg(C + k * n + j), v);
+    for (int k = 0; k <= i; ++k) v = fma(Ri[k * b + i], rtot(C + k * n + j, stride), v);
     out[e] = A::from(v);
   }
   __syncthreads();
@@ -759,6 +804,8 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   __shared__ dfl colbuf_df[2 * BMAX];
   __shared__ double sc[BMAX + 1];
   __shared__ double est_s;
+  __shared__ double wred[NT / 32];
+  __shared__ double c2_s;
   // first CholeskyQR pass: double-float elimination; second pass: near-identity series, else the
   // FP64 elimination
   auto factor1 = [&](int bb) { return factor_small_df(G, bb, Ri, M, rowbuf_df, colbuf_df, sc); };
@@ -784,6 +831,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
   Red rd{a.acc, 0, a.acc_used};
   Timer tmr{a.prof, clock64()};
   if (threadIdx.x == 0) s_barrier_prof = (blockIdx.x == 0) ? a.prof : nullptr;
+  grid_sync_init(a.bar);
   // tensor-core products: TMEM, the completion barrier and the scales
   __shared__ uint32_t tmem_slot;
   __shared__ __align__(8) uint64_t tc_bar;
@@ -860,23 +908,23 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     const int b0 = a.b0;
     for (int e = threadIdx.x; e < nr * b0; e += NT) Qs[(e / b0) * ldq + e % b0] = Ss[(e / b0) * ldw + e % b0];
     __syncthreads();
-    gram_acc<A>(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
+    gram_acc<A>(Qs, ldq, Qs, ldq, b0, b0, nr, red_out(rd));
     double* buf = reduce();
     if (!buf) return finish(ST_TIMEOUT);
-    read_totals(buf, b0 * b0, G);
+    read_totals(buf, b0 * b0, G, rd.used);
     if (!factor1(b0)) return finish(ST_BREAKDOWN);
     to_arith<A>(Ri, b0 * b0, RiT);
     apply_rinv<A>(Qs, ldq, b0, RiT, nr, Tb);
     const bool want = b0 < a.rbar && b0 + bi <= a.width;
-    gram_acc<A>(Qs, ldq, Qs, ldq, b0, b0, nr, red_buf(rd));
-    if (want) gram_acc<A>(Qs, ldq, Ss + b0, ldw, b0, bi, nr, red_buf(rd) + b0 * b0);
+    gram_acc<A>(Qs, ldq, Qs, ldq, b0, b0, nr, red_out(rd));
+    if (want) gram_acc<A>(Qs, ldq, Ss + b0, ldw, b0, bi, nr, red_out(rd) + b0 * b0);
     buf = reduce();
     if (!buf) return finish(ST_TIMEOUT);
-    read_totals(buf, b0 * b0, G);
+    read_totals(buf, b0 * b0, G, rd.used);
     if (!factor2(b0)) return finish(ST_BREAKDOWN);
     to_arith<A>(Ri, b0 * b0, RiT);
     apply_rinv<A>(Qs, ldq, b0, RiT, nr, Tb);
-    if (want) mul_rinv_t_left<A>(buf + b0 * b0, b0, bi, Ri, Ps);      // (Q1 R2^{-1})^T S = R2^{-T} Q1^T S
+    if (want) mul_rinv_t_left<A>(buf + b0 * b0, b0, bi, Ri, Ps, rd.used);      // (Q1 R2^{-1})^T S = R2^{-T} Q1^T S
     have_p = want;
     cc = b0;
     tmr.mark(PH_FIRST_QR);
@@ -885,7 +933,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     if (cc + bi > a.width) return finish(ST_EXTEND);
     if (!have_p) {
       if (TCP && nr > 0) {
-        double* eb = red_buf(rd);
+        double* eb = red_out(rd);
         const T* sc_ = Ss + cc;
         if (!tc_product(
                 tcx, cc, bi, nr, [&](int m, int k) { return A::to(Qs[k * ldq + m]); },
@@ -895,11 +943,11 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
           return finish(ST_TIMEOUT);
         }
       } else {
-        gram_acc<A>(Qs, ldq, Ss + cc, ldw, cc, bi, nr, red_buf(rd));
+        gram_acc<A>(Qs, ldq, Ss + cc, ldw, cc, bi, nr, red_out(rd));
       }
       double* buf = reduce();
       if (!buf) return finish(ST_TIMEOUT);
-      read_totals_t<A>(buf, cc * bi, Ps);
+      read_totals_t<A>(buf, cc * bi, Ps, rd.used);
     }
     tmr.mark(PH_COEFF);
     // residual sketch of the next block (Eqs. (3.4)-(3.5)): S = S_all(:, cc:cc+bi) - Q P
@@ -920,14 +968,14 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     // reduction B: ||S||_F^2 and the Gram matrix of the candidate block S(:, 0:bb)
     const int bb = min(a.ba, a.rbar - cc);
     {
-      double* eb = red_buf(rd);
+      double* eb = red_out(rd);
       sumsq_acc<A>(Rs, bi, bi, nr, eb);
       gram_acc<A>(Rs, bi, Rs, bi, bb, bb, nr, eb + 1);
     }
     tmr.mark(PH_B_LOCAL);
     double* bufB = reduce();
     if (!bufB) return finish(ST_TIMEOUT);
-    if (threadIdx.x == 0) est_s = __ldcg(bufB);
+    if (threadIdx.x == 0) est_s = rtot(bufB, rd.used);
     __syncthreads();
     const double ss = est_s;                               // ||S||_F^2
     if (blockIdx.x == 0 && threadIdx.x == 0) a.est_out[nest] = mul_pow2(ss, -2 * a.sshift);   // host: sqrt(ss / b_e)
@@ -939,7 +987,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     // new directions (Algorithm 6): Q_new = qr(S(:, 0:bb)); Q_new -= Q (Q^T Q_new); Q_new = qr(Q_new).
     // Each qr is one CholeskyQR pass (CholeskyQR2 with the block Gram-Schmidt step in between:
     // the first pass leaves Q_new orthonormal to ~u cond(S)^2, the second to ~u).
-    read_totals(bufB + 1, bb * bb, G);
+    read_totals(bufB + 1, bb * bb, G, rd.used);
     if (!factor1(bb)) return finish(ST_BREAKDOWN);
     tmr.mark(PH_QR1_FACTOR);
     T* Qn = Qs + cc;
@@ -957,7 +1005,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     const int nxt = cc + bb;
     const bool want = nxt < a.rbar && nxt + bi <= a.width;
     {
-      double* eb = red_buf(rd);
+      double* eb = red_out(rd);
       if (TCP && nr > 0) {
         const T* sn = Ss + nxt;
         const int nb = bb + (want ? bi : 0);
@@ -979,13 +1027,39 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     tmr.mark(PH_RO_LOCAL);
     double* bufA = reduce();
     if (!bufA) return finish(ST_TIMEOUT);
-    if (cc > 0) read_totals_t<A>(bufA, cc * bb, Cs);
+    // C = Q^T Q_new (cc x bb) and ||C||_F^2: when that is at most 2^-54, every entry of C^T C lies
+    // below half an ulp of the unit diagonal of G (Q_new is orthonormal to ~u after the first pass)
+    // and the correction G - C^T C is G to FP64 accuracy
+    {
+      double part = 0.0;
+      for (int o = threadIdx.x; o < cc * bb; o += NT) {
+        const double v = rtot(bufA + o, rd.used);
+        Cs[o] = A::from(v);
+        part = fma(v, v, part);
+      }
+      for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = part;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += wred[w];
+        c2_s = t;
+      }
+      __syncthreads();
+    }
     tmr.mark(PH_RO_REDUCE);
-    for (int o = threadIdx.x; o < bb * bb; o += NT) {
-      const int i = o / bb, j = o % bb;
+    const bool c_tiny = !(c2_s > 0x1p-54);
+    // G - C^T C, two threads per output (each the sum over every other row of C)
+    for (int base = 0; base < 2 * bb * bb; base += NT) {
+      const int o2 = base + threadIdx.x, o = o2 >> 1, h = o2 & 1;
+      const bool live = o < bb * bb;
       T t = A::zero();
-      for (int k = 0; k < cc; ++k) t = A::fma(Cs[k * bb + i], Cs[k * bb + j], t);
-      G[o] = __ldcg(bufA + (cc + i) * bb + j) - A::to(t);
+      if (live && !c_tiny) {
+        const int i = o / bb, j = o % bb;
+        for (int k = h; k < cc; k += 2) t = A::fma(Cs[k * bb + i], Cs[k * bb + j], t);
+      }
+      t = A::add(t, A::shfl_xor(t, 1));
+      if (live && h == 0) G[o] = rtot(bufA + (cc + o / bb) * bb + o % bb, rd.used) - A::to(t);
     }
     __syncthreads();
     tmr.mark(PH_RO_FIX);
@@ -1006,12 +1080,17 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     if (want) {
       // P = [Q^T S_next; R2^{-T} (Q_new^T S_next - C^T Q^T S_next)]; the middle term goes through M
       const double* pb = bufA + nxt * bb;
-      read_totals_t<A>(pb, cc * bi, Ps);
-      for (int o = threadIdx.x; o < bb * bi; o += NT) {
-        const int i = o / bi, j = o % bi;
+      read_totals_t<A>(pb, cc * bi, Ps, rd.used);
+      for (int base = 0; base < 2 * bb * bi; base += NT) {
+        const int o2 = base + threadIdx.x, o = o2 >> 1, h = o2 & 1;
+        const bool live = o < bb * bi;
         T t = A::zero();
-        for (int k = 0; k < cc; ++k) t = A::fma(Cs[k * bb + i], Ps[k * bi + j], t);
-        M[o] = __ldcg(pb + (cc + i) * bi + j) - A::to(t);
+        if (live) {
+          const int i = o / bi, j = o % bi;
+          for (int k = h; k < cc; k += 2) t = A::fma(Cs[k * bb + i], Ps[k * bi + j], t);
+        }
+        t = A::add(t, A::shfl_xor(t, 1));
+        if (live && h == 0) M[o] = rtot(pb + (cc + o / bi) * bi + o % bi, rd.used) - A::to(t);
       }
       __syncthreads();
       for (int o = threadIdx.x; o < bb * bi; o += NT) {
@@ -1157,7 +1236,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
   }
   if (c.ac_part_cap < used) {
     const int cap = std::max(used, ac::ACC + 64);
-    TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * cap));   // 3 rotating accumulation buffers
+    TTR_CHECK(c.alloc_t(&c.ac_part, (size_t)3 * ac::RCOPY * cap));   // 3 rotating accumulation buffers
     c.ac_part_cap = cap;
   }
   // status words and the estimates share one device buffer, read back by a single copy:
@@ -1173,7 +1252,7 @@ int adaptive_core(Ctx& c, const double* Sall, int64_t lds, double* Q, int64_t ld
     TTR_CHECK(c.alloc_t(&c.d_flags, 4));
     TTR_CUDA(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), c.stream));
   }
-  TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * used, c.stream));
+  TTR_CUDA(cudaMemsetAsync(c.ac_part, 0, sizeof(double) * 3 * ac::RCOPY * used, c.stream));
   ac::Args a{};
   a.Sall = Sall; a.lds = lds; a.Q = Q; a.ldq = ldq; a.S = S; a.acc = c.ac_part; a.acc_used = used;
   a.m = m; a.qcols = qcols; a.rpc = rpc; a.b0 = b0; a.bi = bi; a.ba = ba; a.rbar = rbar; a.width = width; a.cc0 = cc0;
