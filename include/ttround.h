@@ -130,6 +130,13 @@ typedef struct {
                              with K <= 256 per CTA these products are short, and the FMA form is
                              the faster one on the measured workloads).  The small factorizations,
                              the residual norms and every decision stay FP64 either way. */
+  int32_t autotune;       /* TTR_PREC_SLICED: 1 = the tensor-core launches (partial contractions,
+                             sketches, projections, tall products) choose their tile width, K split
+                             and slabs per tile from a table of measured shapes: the first call of a
+                             shape in the process times the candidates (each twice, on the call's
+                             stream) and keeps the fastest; the choices leave the stated error of
+                             the sliced form unchanged.  0 = the fixed rule (default) or a shape
+                             already measured. */
 } ttr_options;
 
 typedef struct {
@@ -161,7 +168,7 @@ typedef struct {
 
 /* Fill `opts` with defaults: FP64, adap_r off, scale 1, nrmx 0 (estimate), f_init 0.1,
  * f_inc 0.05 (the values of Sec. 4.2), width_hint 0, kernel_timing 0, max_sms 0, est_min 0,
- * est_safety 1, rl_percore 0, block_loop_df 0, block_loop_tc 0. */
+ * est_safety 1, rl_percore 0, block_loop_df 0, block_loop_tc 0, autotune 0. */
 void ttr_default_options(ttr_options* opts);
 
 /* Algorithm 4 (Sec. 3.2): fixed-rank randomize-then-orthogonalize with a KRP sketch.

@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
                 ("f_inc", ctypes.c_double), ("width_hint", ctypes.c_int64), ("kernel_timing", ctypes.c_int32),
                 ("max_sms", ctypes.c_int32), ("est_min", ctypes.c_int32), ("est_safety", ctypes.c_double),
                 ("rl_percore", ctypes.c_int32), ("block_loop_df", ctypes.c_int32),
-                ("block_loop_tc", ctypes.c_int32)]
+                ("block_loop_tc", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -145,7 +145,8 @@ def _tt_args(cores):
 def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = False, adap_r_tau_scale: float = 1.0,
             nrmx: float = 0.0, f_init: float = 0.1, f_inc: float = 0.05, width_hint: int = 0,
             kernel_timing: bool = False, max_sms: int = 0, est_min: int = 0, est_safety: float = 1.0,
-            rl_percore: int = 0, block_loop_df: bool = False, block_loop_tc: bool = False) -> Options:
+            rl_percore: int = 0, block_loop_df: bool = False, block_loop_tc: bool = False,
+            autotune: bool = False) -> Options:
     o = Options()
     lib().ttr_default_options(ctypes.byref(o))
     o.precision, o.slices, o.adap_r = precision, slices, int(adap_r)
@@ -156,6 +157,7 @@ def options(precision: int = TTR_PREC_FP64, slices: int = 0, adap_r: bool = Fals
     o.rl_percore = int(rl_percore)
     o.block_loop_df = int(block_loop_df)
     o.block_loop_tc = int(block_loop_tc)
+    o.autotune = int(autotune)
     return o
 
 

@@ -904,6 +904,7 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   c.stream = stream;
   c.prof_begin();
   c.timing = o.kernel_timing != 0;
+  c.autotune = o.autotune != 0;
   Timer tm;
   tm.rec(0, stream);
   Engine E;
@@ -983,6 +984,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   c.stream = stream;
   c.prof_begin();
   c.timing = o.kernel_timing != 0;
+  c.autotune = o.autotune != 0;
   Timer tm;
   tm.rec(0, stream);
   const int d = X.d;
@@ -1585,6 +1587,7 @@ void ttr_default_options(ttr_options* o) {
   o->rl_percore = 0;
   o->block_loop_df = 0;
   o->block_loop_tc = 0;
+  o->autotune = 0;
 }
 
 static int finish(int st, ttr_result* out, cudaStream_t s) {

@@ -40,7 +40,9 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <vector>
 
 #include "engine.cuh"
 #include "sliced_mma.cuh"
@@ -811,8 +813,8 @@ static int ensure_err(Ctx& c) {
 }
 
 static int prep_b(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int s, BPrep& p,
-                  BPlanes* keep = nullptr) {
-  const int tmax = tile_width(s);
+                  BPlanes* keep = nullptr, int tmax_in = 0) {
+  const int tmax = tmax_in > 0 ? std::min(tmax_in, tile_width(s)) : tile_width(s);
   p.nchunks = (int)((N + tmax - 1) / tmax);
   // balance the chunks: the narrowest multiple of 16 that still needs only nchunks tiles
   const int64_t per = (N + p.nchunks - 1) / p.nchunks;
@@ -925,6 +927,106 @@ static int kseg_for(int64_t tiles, int64_t K) {
 }
 
 
+// ---- tile-shape autotuner.  The tensor-core launches have three free parameters that change the
+// work split but not the product's error bound: the widest tile (UMMA N) the B digit planes are cut
+// for, the K per CTA (K-split CTAs add their partial results atomically in FP64, as the default
+// split does), and, for the partial contractions, the mode slabs per 128-row tile.  With
+// ttr_options::autotune set, the first call of each shape (kind of launch, slices, M, K, N, n_k)
+// times every candidate on its stream (each run twice, the second timed between two events, the
+// whole call: B preparation and product) and keeps the fastest for the rest of the process; every
+// later call of that shape, tuned or not, uses the table.
+struct TuneKey {
+  int kind, s;
+  int64_t M, K, N, n;
+  bool operator<(const TuneKey& o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (s != o.s) return s < o.s;
+    if (M != o.M) return M < o.M;
+    if (K != o.K) return K < o.K;
+    if (N != o.N) return N < o.N;
+    return n < o.n;
+  }
+};
+struct TuneVal {
+  int tmax;   // widest tile the B planes are cut for (0: tile_width(s))
+  int kseg;   // K per CTA (a multiple of KC, at most KSEG)
+  int g;      // mode slabs per tile (partial contractions; 0 elsewhere)
+};
+enum TuneKind { TK_GEMM_TN = 0, TK_ROWMAJOR, TK_PROJECT, TK_RL };
+
+static std::mutex tune_mu;
+static std::map<TuneKey, TuneVal>& tune_table() {
+  static std::map<TuneKey, TuneVal> t;
+  return t;
+}
+
+// K-per-CTA candidates: the default first, then every power-of-two number of chunks up to KSEG
+static std::vector<int> kseg_candidates(int dflt, int64_t K) {
+  std::vector<int> v{dflt};
+  for (int k = KC; k <= KSEG; k *= 2)
+    if (k != dflt && (k < K || k == KC)) v.push_back(k);
+  return v;
+}
+
+// Shapes share a table entry by bucket: 128-row tiles and K rounded up to powers of two, N to a
+// multiple of 16 (the host-driven block loop grows its products by a few columns per block).
+static int64_t pow2_at_least(int64_t x) {
+  int64_t b = 1;
+  while (b < x) b <<= 1;
+  return b;
+}
+static TuneKey bucketed(const TuneKey& k) {
+  TuneKey b = k;
+  b.M = pow2_at_least((k.M + TM - 1) / TM);
+  b.K = pow2_at_least(k.K);
+  b.N = (k.N + 15) / 16;
+  return b;
+}
+
+// the configuration for `key_exact`: from the table (by bucket), else (autotune) the fastest of
+// `cands` measured with `run`, else cands[0]
+template <class F>
+static int tuned(Ctx& c, const TuneKey& key_exact, const std::vector<TuneVal>& cands, F run, TuneVal& out) {
+  const TuneKey key = bucketed(key_exact);
+  {
+    std::lock_guard<std::mutex> lock(tune_mu);
+    auto it = tune_table().find(key);
+    if (it != tune_table().end()) {
+      out = it->second;
+      return TTR_OK;
+    }
+  }
+  out = cands[0];
+  if (!c.autotune || cands.size() < 2) return TTR_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TTR_CUDA(cudaEventCreate(&e0));
+  TTR_CUDA(cudaEventCreate(&e1));
+  float best = 3.0e38f;
+  int st = TTR_OK;
+  for (const TuneVal& v : cands) {
+    if ((st = run(v)) != TTR_OK) break;
+    cudaEventRecord(e0, c.stream);
+    if ((st = run(v)) != TTR_OK) break;
+    cudaEventRecord(e1, c.stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = (set_error("autotune: event wait failed"), TTR_ERR_CUDA);
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      out = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TTR_OK) return st;
+  std::lock_guard<std::mutex> lock(tune_mu);
+  tune_table().emplace(key, out);
+  return TTR_OK;
+}
+
 // Zero the a x b region C(i, j) = C[i*scm + j*scn] where one of the strides is 1.
 static int zero_region(Ctx& c, double* C, int64_t a, int64_t b, int64_t scm, int64_t scn) {
   if (scn == 1) {
@@ -938,6 +1040,22 @@ static int zero_region(Ctx& c, double* C, int64_t a, int64_t b, int64_t scm, int
 }  // namespace tc
 
 using namespace tc;
+
+// candidates of a plain product (M rows in 128-row tiles, K, N columns): the default split first,
+// then the other K splits, then half-width tiles (two column chunks) with their default split
+static void add_plain_candidates(std::vector<TuneVal>& cands, int s, int64_t M, int64_t K, int64_t N) {
+  const int tw = tile_width(s);
+  auto tiles_for = [&](int tmax) {
+    const int64_t nch = (N + tmax - 1) / tmax;
+    return (M + TM - 1) / TM * nch;
+  };
+  const int kd = kseg_for(tiles_for(tw), K);
+  for (int k : kseg_candidates(kd, K)) cands.push_back({tw, k, 0});
+  if (N > 32) {
+    const int half = (int)std::min<int64_t>(tw, std::max<int64_t>(16, ((N + 1) / 2 + 15) / 16 * 16));
+    if (half < tw) cands.push_back({half, kseg_for(tiles_for(half), K), 0});
+  }
+}
 
 // Widest UMMA N whose s per-diagonal accumulators fit the 512 TMEM columns.
 int tile_width(int s) {
@@ -953,44 +1071,67 @@ int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int6
   if (slices < 3 || slices > MAXS || m <= 0 || a_cols <= 0 || b_cols <= 0) return TTR_ERR_UNSUPPORTED;
   if (scm != 1 && scn != 1) return TTR_ERR_UNSUPPORTED;
   TTR_CHECK(ensure_err(c));
-  BPrep bp;
-  TTR_CHECK(prep_b(c, Y, ldy, 1, m, b_cols, slices, bp));
-  Args a{};
-  a.A = X; a.M = a_cols; a.K = m; a.sam = 1; a.sak = ldx;
-  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = b_cols; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
-  a.C = C; a.scm = scm; a.scn = scn; a.err = c.d_flags;
-  const int64_t tiles = (a_cols + TM - 1) / TM * bp.nchunks;
-  a.kseg = kseg_for(tiles, m);
-  const unsigned ksplit = (unsigned)((m + a.kseg - 1) / a.kseg);
-  dim3 grid((unsigned)((a_cols + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
-  if (ksplit > 1) {
-    TTR_CHECK(zero_region(c, C, a_cols, b_cols, scm, scn));
-    return launch<ATOMIC, false>(c, a, grid, "tc_gemm_tn");
-  }
-  return launch<PLAIN, false>(c, a, grid, "tc_gemm_tn");
+  auto run = [&](const TuneVal& v) -> int {
+    BPrep bp;
+    TTR_CHECK(prep_b(c, Y, ldy, 1, m, b_cols, slices, bp, nullptr, v.tmax));
+    Args a{};
+    a.A = X; a.M = a_cols; a.K = m; a.sam = 1; a.sak = ldx;
+    a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = b_cols; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
+    a.C = C; a.scm = scm; a.scn = scn; a.err = c.d_flags;
+    a.kseg = v.kseg;
+    const unsigned ksplit = (unsigned)((m + a.kseg - 1) / a.kseg);
+    dim3 grid((unsigned)((a_cols + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
+    if (ksplit > 1) {
+      TTR_CHECK(zero_region(c, C, a_cols, b_cols, scm, scn));
+      return launch<ATOMIC, false>(c, a, grid, "tc_gemm_tn");
+    }
+    return launch<PLAIN, false>(c, a, grid, "tc_gemm_tn");
+  };
+  std::vector<TuneVal> cands;
+  add_plain_candidates(cands, slices, a_cols, m, b_cols);
+  TuneVal v;
+  TTR_CHECK(tuned(c, TuneKey{TK_GEMM_TN, slices, a_cols, m, b_cols, 0}, cands, run, v));
+  return run(v);
 }
 
 int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int64_t r1, const double* Wn, int64_t ldw,
                const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo, BPlanes* keep) {
   if (n > TM || slices < 3 || slices > MAXS || !Omi) return TTR_ERR_UNSUPPORTED;
   TTR_CHECK(ensure_err(c));
-  BPrep bp;
-  TTR_CHECK(prep_b(c, Wn, ldw, 1, r1, w, slices, bp, keep));
-  Args a{};
-  a.A = Xk; a.M = r0 * n; a.K = r1; a.sam = r1; a.sak = 1;
-  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = w; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
-  a.Omint = Omi; a.ldo = ldoi; a.nmode = n; a.g = (int)(TM / n); a.slabs = r0; a.W = Wout; a.ldw = ldwo;
-  a.err = c.d_flags;
-  const int64_t tiles = (r0 + a.g - 1) / a.g * bp.nchunks;
-  a.kseg = kseg_for(tiles, r1);
-  const unsigned ksplit = (unsigned)((r1 + a.kseg - 1) / a.kseg);
-  if (ksplit > 1) {
-    a.watomic = 1;
-    TTR_CUDA(cudaMemset2DAsync(Wout, ldwo * sizeof(double), 0, w * sizeof(double), r0, c.stream));
+  auto run_with = [&](const TuneVal& v, BPlanes* kp) -> int {
+    BPrep bp;
+    TTR_CHECK(prep_b(c, Wn, ldw, 1, r1, w, slices, bp, kp, v.tmax));
+    Args a{};
+    a.A = Xk; a.M = r0 * n; a.K = r1; a.sam = r1; a.sak = 1;
+    a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = w; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
+    a.Omint = Omi; a.ldo = ldoi; a.nmode = n; a.g = v.g; a.slabs = r0; a.W = Wout; a.ldw = ldwo;
+    a.err = c.d_flags;
+    a.kseg = v.kseg;
+    const unsigned ksplit = (unsigned)((r1 + a.kseg - 1) / a.kseg);
+    if (ksplit > 1) {
+      a.watomic = 1;
+      TTR_CUDA(cudaMemset2DAsync(Wout, ldwo * sizeof(double), 0, w * sizeof(double), r0, c.stream));
+    }
+    dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, ksplit);
+    return launch<RLM, true>(c, a, grid, "tc_rl_step");
+  };
+  // candidates: the default (all slabs of a 128-row tile, the split that fills one wave), the other
+  // K splits, and tiles of half as many slabs
+  const int tw = tile_width(slices);
+  const int g0 = (int)(TM / n);
+  const int64_t nch = (w + tw - 1) / tw;
+  std::vector<TuneVal> cands;
+  const int kd = kseg_for((r0 + g0 - 1) / g0 * nch, r1);
+  for (int k : kseg_candidates(kd, r1)) cands.push_back({tw, k, g0});
+  if (g0 >= 2) {
+    const int g1 = g0 / 2;
+    cands.push_back({tw, kseg_for((r0 + g1 - 1) / g1 * nch, r1), g1});
   }
-  dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, ksplit);
+  TuneVal v;
+  TTR_CHECK(tuned(c, TuneKey{TK_RL, slices, r0, r1, w, n}, cands, [&](const TuneVal& t) { return run_with(t, nullptr); },
+                  v));
   c.time_begin(Ctx::KT_RL);
-  TTR_CHECK((launch<RLM, true>(c, a, grid, "tc_rl_step")));
+  TTR_CHECK(run_with(v, keep));
   c.time_end(8.0 * ((double)r0 * n * r1 + (double)r1 * w + (double)r0 * w));
   return TTR_OK;
 }
@@ -1034,30 +1175,43 @@ int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M
                      int64_t ldb, int64_t N, double* C, int64_t ldc, const BPlanes* reuse) {
   if (slices < 3 || slices > MAXS || M <= 0 || N <= 0 || K <= 0) return TTR_ERR_UNSUPPORTED;
   TTR_CHECK(ensure_err(c));
-  BPrep bp;
-  if (reuse && reuse->planes && reuse->src == B && reuse->ld == ldb && reuse->K == K && reuse->N == N &&
-      reuse->s == slices) {
-    bp.planes = reuse->planes;                 // the digit planes of this operand are already made
-    bp.Fmax = reuse->Fmax;
-    bp.nchunks = reuse->nchunks;
-    bp.kchunks = reuse->kchunks;
-    bp.tn = reuse->tn;
+  const bool reused = reuse && reuse->planes && reuse->src == B && reuse->ld == ldb && reuse->K == K &&
+                      reuse->N == N && reuse->s == slices;
+  auto run = [&](const TuneVal& v) -> int {
+    BPrep bp;
+    if (reused) {
+      bp.planes = reuse->planes;                 // the digit planes of this operand are already made
+      bp.Fmax = reuse->Fmax;
+      bp.nchunks = reuse->nchunks;
+      bp.kchunks = reuse->kchunks;
+      bp.tn = reuse->tn;
+    } else {
+      TTR_CHECK(prep_b(c, B, ldb, 1, K, N, slices, bp, nullptr, v.tmax));
+    }
+    Args a{};
+    a.A = A; a.M = M; a.K = K; a.sam = lda; a.sak = 1;
+    a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = N; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
+    a.C = C; a.scm = ldc; a.scn = 1; a.err = c.d_flags;
+    a.kseg = v.kseg;
+    const unsigned ksplit = (unsigned)((K + a.kseg - 1) / a.kseg);
+    dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
+    if (ksplit > 1) {
+      TTR_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, N * sizeof(double), M, c.stream));
+      return launch<ATOMIC, true>(c, a, grid, "tc_sketch");
+    }
+    return launch<PLAIN, true>(c, a, grid, "tc_sketch");
+  };
+  std::vector<TuneVal> cands;
+  if (reused) {
+    // the planes fix the tile width: only the K split is free
+    const int64_t tiles = (M + TM - 1) / TM * reuse->nchunks;
+    for (int k : kseg_candidates(kseg_for(tiles, K), K)) cands.push_back({reuse->tn, k, 0});
   } else {
-    TTR_CHECK(prep_b(c, B, ldb, 1, K, N, slices, bp));
+    add_plain_candidates(cands, slices, M, K, N);
   }
-  Args a{};
-  a.A = A; a.M = M; a.K = K; a.sam = lda; a.sak = 1;
-  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = N; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
-  a.C = C; a.scm = ldc; a.scn = 1; a.err = c.d_flags;
-  const int64_t tiles = (M + TM - 1) / TM * bp.nchunks;
-  a.kseg = kseg_for(tiles, K);
-  const unsigned ksplit = (unsigned)((K + a.kseg - 1) / a.kseg);
-  dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
-  if (ksplit > 1) {
-    TTR_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, N * sizeof(double), M, c.stream));
-    return launch<ATOMIC, true>(c, a, grid, "tc_sketch");
-  }
-  return launch<PLAIN, true>(c, a, grid, "tc_sketch");
+  TuneVal v;
+  TTR_CHECK(tuned(c, TuneKey{TK_ROWMAJOR, slices, M, K, N, reused ? reuse->tn : 0}, cands, run, v));
+  return run(v);
 }
 
 // Y = Mk (L x K, row-major ldm) @ H(X_{k+1}) (K x ncol, row-major), computed as
@@ -1066,21 +1220,27 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
                double* Y) {
   if (slices < 3 || slices > MAXS || L <= 0 || ncol <= 0 || K <= 0) return TTR_ERR_UNSUPPORTED;
   TTR_CHECK(ensure_err(c));
-  BPrep bp;
-  TTR_CHECK(prep_b(c, Mk, 1, ldm, K, L, slices, bp));
-  Args a{};
-  a.A = Xn; a.M = ncol; a.K = K; a.sam = 1; a.sak = ncol;
-  a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = L; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
-  a.C = Y; a.scm = 1; a.scn = ncol; a.err = c.d_flags;
-  const int64_t tiles = (ncol + TM - 1) / TM * bp.nchunks;
-  a.kseg = kseg_for(tiles, K);
-  const unsigned ksplit = (unsigned)((K + a.kseg - 1) / a.kseg);
-  dim3 grid((unsigned)((ncol + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
-  if (ksplit > 1) {
-    TTR_CUDA(cudaMemsetAsync(Y, 0, (size_t)L * ncol * sizeof(double), c.stream));
-    return launch<ATOMIC, false>(c, a, grid, "tc_project");
-  }
-  return launch<PLAIN, false>(c, a, grid, "tc_project");
+  auto run = [&](const TuneVal& v) -> int {
+    BPrep bp;
+    TTR_CHECK(prep_b(c, Mk, 1, ldm, K, L, slices, bp, nullptr, v.tmax));
+    Args a{};
+    a.A = Xn; a.M = ncol; a.K = K; a.sam = 1; a.sak = ncol;
+    a.Bp = bp.planes; a.Fmax = bp.Fmax; a.N = L; a.kchunks = bp.kchunks; a.s = slices; a.tn = bp.tn;
+    a.C = Y; a.scm = 1; a.scn = ncol; a.err = c.d_flags;
+    a.kseg = v.kseg;
+    const unsigned ksplit = (unsigned)((K + a.kseg - 1) / a.kseg);
+    dim3 grid((unsigned)((ncol + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
+    if (ksplit > 1) {
+      TTR_CUDA(cudaMemsetAsync(Y, 0, (size_t)L * ncol * sizeof(double), c.stream));
+      return launch<ATOMIC, false>(c, a, grid, "tc_project");
+    }
+    return launch<PLAIN, false>(c, a, grid, "tc_project");
+  };
+  std::vector<TuneVal> cands;
+  add_plain_candidates(cands, slices, ncol, K, L);
+  TuneVal v;
+  TTR_CHECK(tuned(c, TuneKey{TK_PROJECT, slices, ncol, K, L, 0}, cands, run, v));
+  return run(v);
 }
 
 // C_g = A_g B for up to MAXG row-major A_g (M[g] x K, leading dimension lda[g]) sharing one row-major

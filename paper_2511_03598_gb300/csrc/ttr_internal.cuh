@@ -63,6 +63,7 @@ struct Ctx {
   // between consecutive events is charged to the later launch (so it includes GPU idle time)
   std::vector<std::pair<const char*, cudaEvent_t>> prof;
   bool profiling = false;
+  bool autotune = false;           // tensor-core launches: measure tile shapes on first use (ttr_options::autotune)
   cudaEvent_t prof_start = nullptr;
   void prof_begin();
   void prof_report();

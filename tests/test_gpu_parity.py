@@ -358,6 +358,21 @@ def test_adaptive_block_loop_tensor_core_products(B, name, make, tol, block, sli
     assert T.tt_dist(got, x.cores) <= tol * x.norm
 
 
+def test_adaptive_sliced_autotuned(B):
+    """The bench configuration with the tile-shape autotuner on (each new shape times its candidate
+    launches once per process): the oracle's ranks and the sliced form's bars, on the call that tunes
+    and on a later call that reads the table."""
+    x = WL.c2()
+    ref, info = R.tt_round_adaptive(x.cores, 1e-6, seed=2024, block=10, nrmx=x.norm)
+    for _ in range(2):
+        with B.round_adaptive(dev(x.cores), 1e-6, 10, 2024,
+                              B.options(precision=B.TTR_PREC_SLICED, nrmx=x.norm, autotune=True)) as y:
+            assert y.ranks == info["ranks"]
+            got = y.to_numpy()
+        assert rel_tensor_diff(got, ref) <= 1e-8
+        assert T.tt_dist(got, x.cores) <= 1e-6 * x.norm
+
+
 def test_adaptive_adap_r_sliced(B):
     """The Remark 3.2 pass after the sliced rounding (8 slices): ranks and tensor as the oracle's."""
     x = WL.c1()
