@@ -1098,7 +1098,8 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
                const int* Omi, int64_t ldoi, int64_t w, double* Wout, int64_t ldwo, BPlanes* keep) {
   if (n > TM || slices < 3 || slices > MAXS || !Omi) return TTR_ERR_UNSUPPORTED;
   TTR_CHECK(ensure_err(c));
-  auto run_with = [&](const TuneVal& v, BPlanes* kp) -> int {
+  // timed: the library's kernel events around the contraction launch (not the B preparation)
+  auto run_with = [&](const TuneVal& v, BPlanes* kp, bool timed) -> int {
     BPrep bp;
     TTR_CHECK(prep_b(c, Wn, ldw, 1, r1, w, slices, bp, kp, v.tmax));
     Args a{};
@@ -1113,7 +1114,10 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
       TTR_CUDA(cudaMemset2DAsync(Wout, ldwo * sizeof(double), 0, w * sizeof(double), r0, c.stream));
     }
     dim3 grid((unsigned)((r0 + a.g - 1) / a.g), (unsigned)bp.nchunks, ksplit);
-    return launch<RLM, true>(c, a, grid, "tc_rl_step");
+    if (timed) c.time_begin(Ctx::KT_RL);
+    TTR_CHECK((launch<RLM, true>(c, a, grid, "tc_rl_step")));
+    if (timed) c.time_end(8.0 * ((double)r0 * n * r1 + (double)r1 * w + (double)r0 * w));
+    return TTR_OK;
   };
   // candidates: the default (all slabs of a 128-row tile, the split that fills one wave), the other
   // K splits, and tiles of half as many slabs
@@ -1128,12 +1132,9 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
     cands.push_back({tw, kseg_for((r0 + g1 - 1) / g1 * nch, r1), g1});
   }
   TuneVal v;
-  TTR_CHECK(tuned(c, TuneKey{TK_RL, slices, r0, r1, w, n}, cands, [&](const TuneVal& t) { return run_with(t, nullptr); },
-                  v));
-  c.time_begin(Ctx::KT_RL);
-  TTR_CHECK(run_with(v, keep));
-  c.time_end(8.0 * ((double)r0 * n * r1 + (double)r1 * w + (double)r0 * w));
-  return TTR_OK;
+  TTR_CHECK(tuned(c, TuneKey{TK_RL, slices, r0, r1, w, n}, cands,
+                  [&](const TuneVal& t) { return run_with(t, nullptr, false); }, v));
+  return run_with(v, keep, true);
 }
 
 int tc_rl_step_grouped(Ctx& c, int slices, int ng, const double* const* Xk, const int64_t* r0, int64_t n,
