@@ -388,7 +388,44 @@ def configs_table(B, reps: int) -> dict:
                  "gpu_krp_fp64_ms": g_fp, "gpu_krp_sliced_ms": g_sl, "ranks_krp_middle": sl_ranks[len(sl_ranks) // 2],
                  "ranks_equal_fp64": sl_ranks == fp_ranks, "err_sliced_vs_x": err,
                  "note": "no oracle or deterministic columns: the formal sum is 25 GB"})
-    return {"configs": rows}
+    return {"configs": rows, "oracle_single_thread": oracle_single_thread()}
+
+
+def oracle_single_thread() -> dict:
+    """The oracle's times for C1-C3 with one BLAS thread (a child process: the thread count of the
+    BLAS is fixed when NumPy loads), median of 3 after a warm-up."""
+    code = r'''
+import json, time, numpy as np, workloads as WL
+from oracle import rounding as R
+out = {}
+for name, x, tol, mode, block, est in (("c1", WL.c1(), 1e-6, "fixed", 0, {}), ("c2", WL.c2(), 1e-6, "adaptive", 10, {}),
+                                        ("c3", WL.c3(), 1e-8, "adaptive", 0, {"est_min": 10, "est_safety": 10.0})):
+    def krp():
+        if mode == "fixed":
+            return R.svd_pass_rl(R.tt_round_fixed(x.cores, 13, 2024)[0], max_rank=8)
+        return R.tt_round_adaptive(x.cores, tol, 2024, block=block, nrmx=x.norm, **est)
+    det = lambda: R.tt_round_deterministic(x.cores, tol)
+    row = {}
+    for key, fn in (("det_ms", det), ("krp_ms", krp)):
+        fn()
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(1e3 * (time.perf_counter() - t0))
+        row[key] = float(np.median(ts))
+    out[name] = row
+print(json.dumps(out))
+'''
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=600)
+        if r.returncode != 0:
+            return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else f"exit {r.returncode}"}
+        return {"threads": 1, **json.loads(r.stdout.strip().splitlines()[-1])}
+    except Exception as e:  # noqa: BLE001 - reported in the table
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def tt_sum_norm(terms) -> float:
@@ -711,6 +748,27 @@ def main():
                    "ms_per_launch": kt["ms_rl_kernel"] / kt["n_rl_kernel"],
                    "measured": "single-stream part of the timed run (kernel alone on the GPU)",
                    "share_of_step": kt["ms_rl_kernel"] / single_total}
+        if args.precision == "sliced" and pk.get("bf16_tflops"):
+            # the same launches against the tensor pipe: the BF16 MMA work the sliced products issue
+            # (s(s+1)/2 digit products of 128 x tn x K_pad per 128-row tile, K padded to chunks of 32)
+            s_sl = min(8, max(4, math.ceil((-math.log2(TOL) + 16) / 7)))
+            tw = (512 // s_sl) // 16 * 16
+            nch = -(-w // tw)
+            per = -(-w // nch)
+            tn = min(tw, max(16, -(-per // 16) * 16))
+            g = 128 // x.modes[0]
+            mma = 0.0
+            for k in range(2, x.d):                       # the RL launches: W_k for k = d-1 .. 2
+                r0, r1 = x.ranks[k - 1], x.ranks[k]
+                tiles = -(-r0 // g) * nch
+                mma += 2.0 * 128 * tn * (-(-r1 // 32) * 32) * (s_sl * (s_sl + 1) // 2) * tiles
+            per_launch = mma / (x.d - 2)
+            tach = per_launch / (kt["ms_rl_kernel"] / kt["n_rl_kernel"] / 1e3) / 1e12
+            roof_rl["tensor_pipe"] = {"achieved": tach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                                      "frac": tach / pk["bf16_tflops"],
+                                      "per_unit": f"{per_launch:.3e} BF16 MMA flop per launch ({s_sl} slices: "
+                                                  f"{s_sl * (s_sl + 1) // 2} digit products, tile width {tn})",
+                                      "peak_source": f"bf16_tflops {pk_kind}"}
     cand = [r for r in (roof_bl, roof_rl) if r]
     roof = max(cand, key=lambda r: r["share_of_step"]) if cand else None
     roof_other = [r for r in cand if r is not roof]
