@@ -3,6 +3,7 @@
 // descriptor, bounded mbarrier waits, the cut of FP64 values into base-128 digits exact in BF16,
 // the digit layout of B operands, and the integer-only conversion of the recombined results.
 #pragma once
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace ttr {
@@ -39,11 +40,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
 // s base-128 digits (BF16 bit patterns, sign attached) of 8 values sharing the biased exponent
 // scale E: each value becomes the 7s-bit integer floor(|v| 2^(7s - E + 1022)), cut into s digits,
 // most significant first.
-// The slice count is fixed at compile time (constant digit offsets), and each pair of
-// BF16 digits is packed by one byte permute of the two binary32 images (a digit d < 128 is the
-// binary32 0x4B000000 | d minus 2^23, exactly; BF16 is its upper half).
+// The slice count is fixed at compile time (constant digit offsets).  The two digits d0, d1 < 128 of
+// a pair of values are packed as the BF16 bit patterns of 128 + d0 and 128 + d1 (0x4300 | d), and
+// one packed BF16 subtraction of (128, 128) leaves d0 and d1 exactly; the signs are then ORed in.
 template <int S>
 __device__ __forceinline__ void slice8_t(const double* v, int E, uint32_t (&w)[S][4]) {
+  const __nv_bfloat162 c128 = __floats2bfloat162_rn(128.f, 128.f);
 #pragma unroll
   for (int h = 0; h < 4; ++h) {
     uint64_t fx[2];
@@ -57,13 +59,15 @@ __device__ __forceinline__ void slice8_t(const double* v, int E, uint32_t (&w)[S
       const int sh = 53 - 7 * S + (E - (ef ? ef : 1));
       fx[u] = (sh >= 64) ? 0ull : (sh >= 0 ? (mant >> sh) : (mant << (-sh)));
     }
+    const uint32_t sgn = (sg[0] >> 16) | sg[1];               // sign bits of the low and high halves
 #pragma unroll
     for (int p = 0; p < S; ++p) {
       const int off = 7 * (S - 1 - p);
       const uint32_t d0 = (uint32_t)(fx[0] >> off) & 127u, d1 = (uint32_t)(fx[1] >> off) & 127u;
-      const uint32_t f0 = __float_as_uint(__uint_as_float(0x4B000000u | d0) - 8388608.0f) | sg[0];
-      const uint32_t f1 = __float_as_uint(__uint_as_float(0x4B000000u | d1) - 8388608.0f) | sg[1];
-      w[p][h] = __byte_perm(f0, f1, 0x7632);
+      const uint32_t packed = __byte_perm(d0, d1, 0x5410) | 0x43004300u;
+      __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&packed);
+      b = __hsub2(b, c128);
+      w[p][h] = *reinterpret_cast<const uint32_t*>(&b) | sgn;
     }
   }
 }
