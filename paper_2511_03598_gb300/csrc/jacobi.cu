@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "engine.cuh"
+#include "rsqrt.cuh"
 
 namespace ttr {
 namespace jc {
@@ -136,13 +137,8 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(Args a) {
             B2 += red[NW + w];
             G += red[2 * NW + w];
           }
-          double cs = 1.0, sn = 0.0;
-          if (G != 0.0 && fabs(G) > 1e-15 * sqrt(A2) * sqrt(B2) && !(A2 <= tiny && B2 <= tiny)) {
-            const double zeta = (B2 - A2) / (2.0 * G);
-            const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-            cs = 1.0 / sqrt(1.0 + t * t);
-            sn = cs * t;
-          }
+          double cs, sn;
+          jacobi_rotation(A2, B2, G, tiny, cs, sn);
           rot[0] = cs;
           rot[1] = sn;
         }

@@ -783,10 +783,9 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(double* A, int64_t b, 
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al) * sqrt(be) && !(al <= tiny && be <= tiny)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        double cs, sn;
+        jacobi_rotation(al, be, ga, tiny, cs, sn);
+        if (sn != 0.0) {
           double* vp = Vt + p * ld;
           double* vq = Vt + q * ld;
           for (int64_t i = lane; i < b; i += 32) {

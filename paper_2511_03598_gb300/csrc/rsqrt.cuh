@@ -28,4 +28,42 @@ static __device__ __forceinline__ double rsqrt_full(double y) {
   return __longlong_as_double(__double_as_longlong(r1) - (long long)h * (1LL << 52));
 }
 
+// Rotation (cs, sn) of one-sided Jacobi for a column pair with squared norms A2, B2 and inner product
+// G: none (cs = 1, sn = 0) when |G| <= 1e-15 sqrt(A2 B2) or both columns lie below `tiny`; else
+// zeta = (B2 - A2) / (2 G), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), cs = 1 / sqrt(1 + t^2),
+// sn = cs t.  The square roots and reciprocals come from rsqrt_full (1 / x = rsqrt(x)^2, sqrt(x) =
+// x rsqrt(x)), a few dependent FP64 operations each instead of the FP64 square root and division;
+// cs^2 + sn^2 = 1 to a few ulps, as with them.  Inputs whose products leave the normal range take
+// the library square root and division.
+static __device__ __forceinline__ void jacobi_rotation(double A2, double B2, double G, double tiny, double& cs,
+                                                       double& sn) {
+  cs = 1.0;
+  sn = 0.0;
+  if (G == 0.0 || (A2 <= tiny && B2 <= tiny)) return;
+  const double ab = A2 * B2, g2 = 2.0 * G;
+  if (!(ab > 2.3e-308) || !(ab < 1.7e308) || !(fabs(g2) > 2.3e-308)) {
+    if (!(fabs(G) > 1e-15 * sqrt(A2) * sqrt(B2))) return;
+    const double zeta = (B2 - A2) / g2;
+    const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+    cs = 1.0 / sqrt(1.0 + t * t);
+    sn = cs * t;
+    return;
+  }
+  if (!(fabs(G) > 1e-15 * (ab * rsqrt_full(ab)))) return;
+  const double rg = rsqrt_full(fabs(g2));
+  const double zeta = (B2 - A2) * copysign(rg * rg, g2);     // (B2 - A2) / (2 G)
+  const double az = fabs(zeta);
+  double t;
+  if (az < 0x1p500) {
+    const double y = fma(zeta, zeta, 1.0);
+    const double rd = rsqrt_full(az + y * rsqrt_full(y));
+    t = copysign(rd * rd, zeta);
+  } else {
+    const double rz = rsqrt_full(az);
+    t = copysign(0.5 * rz * rz, zeta);
+  }
+  cs = rsqrt_full(fma(t, t, 1.0));
+  sn = cs * t;
+}
+
 }  // namespace ttr
