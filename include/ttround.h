@@ -349,6 +349,16 @@ int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r,
  * counterpart in the paper; for tests of that arithmetic against a correctly rounded reference. */
 int ttr_selftest_rsqrt(const double* x, double* out, int64_t count, void* stream);
 
+/* Self-test of the plane rotation of the one-sided Jacobi SVD (Sec. 2.3: the SVD of the small
+ * triangular factor in the deterministic rounding and in the Remark 3.2 pass).  For each i < count,
+ * abg[3i..3i+2] = (A2, B2, G): the squared norms of a column pair and their inner product; the
+ * result cs_sn[2i..2i+1] = (cs, sn) with zeta = (B2 - A2) / (2 G), t = sign(zeta) / (|zeta| +
+ * sqrt(1 + zeta^2)), cs = 1 / sqrt(1 + t^2), sn = cs t, or (1, 0) when G = 0, when
+ * |G| <= 1e-15 sqrt(A2 B2) or when A2 and B2 both lie at or below `tiny` (>= 0).  Both arrays are
+ * DEVICE buffers (3 count and 2 count doubles); the call returns once the results are written.
+ * Returns TTR_ERR_ARG for null pointers, a negative count or tiny. */
+int ttr_selftest_jacobi_rotation(const double* abg, double tiny, double* cs_sn, int64_t count, void* stream);
+
 /* The partial contractions of ttr_partial_contractions (arguments, layout of W and results alike,
  * FP64) in the per-core-parallel form of the Conclusion (Sec. 5; ttr_options::rl_percore = 1):
  * all G_k(:, :, j) = sum_i X_k(:, i, :) Omega_k(i, j) for k = t..d in one launch, then

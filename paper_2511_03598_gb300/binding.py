@@ -93,6 +93,7 @@ def lib():
         L.ttr_partial_contractions.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, i32, i32, PP, vp]
         L.ttr_partial_contractions_noalloc.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, PP, vp]
         L.ttr_selftest_rsqrt.argtypes = [vp, vp, i64, vp]
+        L.ttr_selftest_jacobi_rotation.argtypes = [vp, ctypes.c_double, vp, i64, vp]
         L.ttr_partial_contractions_percore.argtypes = [i32, P64, P64, PP, u64, i64, i64, i32, PP, vp]
         L.tt_round_adaptive_matvec.argtypes = [i32, P64, P64, P64, PP, P64, PP, dbl, i64, u64,
                                                ctypes.POINTER(Options), vp, ctypes.POINTER(Result)]
@@ -417,6 +418,19 @@ def partial_contractions_noalloc(cores, seed: int, col0: int, col1: int, t: int 
     _check(lib().ttr_partial_contractions_noalloc(d, n, r, p, ctypes.c_uint64(seed), col0, col1, t, ptrs,
                                                   _stream_handle(stream)))
     return bufs
+
+
+def selftest_jacobi_rotation(abg, tiny=0.0, stream=None):
+    """The one-sided Jacobi rotation (cs, sn) for each row (A2, B2, G) of the CUDA float64 tensor abg
+    of shape (count, 3); returns a (count, 2) tensor (ttr_selftest_jacobi_rotation)."""
+    import torch
+    if not (isinstance(abg, torch.Tensor) and abg.is_cuda and abg.dtype == torch.float64 and abg.is_contiguous()
+            and abg.dim() == 2 and abg.shape[1] == 3):
+        raise ValueError("abg must be a contiguous CUDA float64 tensor of shape (count, 3)")
+    out = torch.empty((abg.shape[0], 2), dtype=torch.float64, device=abg.device)
+    _check(lib().ttr_selftest_jacobi_rotation(ctypes.c_void_p(abg.data_ptr()), float(tiny),
+                                              ctypes.c_void_p(out.data_ptr()), abg.shape[0], _stream_handle(stream)))
+    return out
 
 
 def selftest_rsqrt(x, stream=None):

@@ -1116,6 +1116,15 @@ __global__ void rsqrt_selftest_kernel(const double* x, double* out, int64_t n) {
     out[i] = rsqrt_full(x[i]);
 }
 
+__global__ void jacobi_rotation_selftest_kernel(const double* abg, double tiny, double* cs_sn, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double cs, sn;
+    jacobi_rotation(abg[3 * i], abg[3 * i + 1], abg[3 * i + 2], tiny, cs, sn);
+    cs_sn[2 * i] = cs;
+    cs_sn[2 * i + 1] = sn;
+  }
+}
+
 }  // namespace ac
 
 int rsqrt_selftest(Ctx& c, const double* x, double* out, int64_t n) {
@@ -1123,6 +1132,13 @@ int rsqrt_selftest(Ctx& c, const double* x, double* out, int64_t n) {
   const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
   ac::rsqrt_selftest_kernel<<<blocks, 256, 0, c.stream>>>(x, out, n);
   return c.check_launch("rsqrt_selftest");
+}
+
+int jacobi_rotation_selftest(Ctx& c, const double* abg, double tiny, double* cs_sn, int64_t n) {
+  if (n <= 0) return TTR_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  ac::jacobi_rotation_selftest_kernel<<<blocks, 256, 0, c.stream>>>(abg, tiny, cs_sn, n);
+  return c.check_launch("jacobi_rotation_selftest");
 }
 
 // Whether the block loop's rows for these sizes fit in shared memory (else they would live in

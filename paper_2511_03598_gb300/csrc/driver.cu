@@ -1760,6 +1760,16 @@ int ttr_selftest_rsqrt(const double* x, double* out, int64_t count, void* stream
   return TTR_OK;
 }
 
+int ttr_selftest_jacobi_rotation(const double* abg, double tiny, double* cs_sn, int64_t count, void* stream) {
+  if (!abg || !cs_sn || count < 0 || !(tiny >= 0.0)) return set_error("bad self-test arguments"), TTR_ERR_ARG;
+  Ctx c;
+  c.stream = (cudaStream_t)stream;
+  TTR_CHECK(jacobi_rotation_selftest(c, abg, tiny, cs_sn, count));
+  const cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return set_error(cudaGetErrorString(e)), TTR_ERR_CUDA;
+  return TTR_OK;
+}
+
 int ttr_partial_contractions(int32_t d, const int64_t* n, const int64_t* r, const double* const* cores,
                              uint64_t seed, int64_t col0, int64_t col1, int32_t t, int32_t precision,
                              int32_t slices, double* const* W, void* stream) {

@@ -121,6 +121,8 @@ int mv_ahat(Ctx& c, const double* A, int64_t p0, int64_t n, int64_t m, int64_t p
 
 // out[i] = the block loop's reciprocal square root of x[i] (positive, finite), for its self-test.
 int rsqrt_selftest(Ctx& c, const double* x, double* out, int64_t n);
+// the one-sided Jacobi rotation (cs, sn) for each triple (A2, B2, G) of abg, into cs_sn
+int jacobi_rotation_selftest(Ctx& c, const double* abg, double tiny, double* cs_sn, int64_t n);
 
 // Widest tensor-core tile (UMMA N) usable with s slices.
 int tile_width(int s);

@@ -373,14 +373,18 @@ __global__ void __launch_bounds__(NT, 1) sliced_kernel(const Args a0, const Grou
     __syncwarp();
   } else {
     // A digits: 128 rows x 4 groups of 8 consecutive k = 512 tasks, TASKS per thread; the values of
-    // chunk c + 1 are loaded into registers while chunk c is being sliced
+    // chunk c + 1 are loaded into registers while chunk c is being sliced.  Row-major A: a warp
+    // takes 8 rows x 4 groups (its loads cover 32 consecutive k of each row), lane l row l % 8 and
+    // group l / 8, so that the 8 lanes of each quarter-warp store phase write 8 different rows:
+    // 8 different 16-byte bank groups of the digit plane.  Column-major A: lanes take consecutive
+    // rows of one group (coalesced loads, and stores 16 bytes apart).
     constexpr int TASKS = (TM * (KC / 8)) / NP;
     int trow[TASKS], tgrp[TASKS];
 #pragma unroll
     for (int i = 0; i < TASKS; ++i) {
       const int u = tid + NP * i;
-      trow[i] = AKFAST ? (u >> 2) : (u % TM);
-      tgrp[i] = AKFAST ? (u & 3) : (u / TM);
+      trow[i] = AKFAST ? ((u >> 5) * 8 + (u & 7)) : (u % TM);
+      tgrp[i] = AKFAST ? ((u & 31) >> 3) : (u / TM);
     }
     auto load_chunk = [&](int c, double (&v)[TASKS][8]) {
 #pragma unroll
