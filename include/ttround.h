@@ -102,7 +102,9 @@ typedef struct {
                              events on `stream` (fields ms_block_loop ... of ttr_result) */
   int32_t max_sms;        /* largest number of SMs the persistent block-loop kernel (one CTA per
                              SM, all resident at once) may take; 0 = all.  Lets calls on different
-                             streams run side by side: e.g. two calls with half the SMs each */
+                             streams run side by side: e.g. two calls with half the SMs each.  The
+                             tensor-core launches that split K over CTAs size the split for the
+                             same number of SMs (their CTAs may still run on any SM) */
   int32_t est_min;        /* adaptive only: the residual estimate of each block uses
                              max(b_inc, est_min) sketch columns, while b_inc columns are appended
                              (0 = b_inc, Algorithm 6 as printed; 0..4096) */

@@ -905,6 +905,7 @@ static int round_fixed(const TT& X, int64_t ell, int64_t target, uint64_t seed, 
   c.prof_begin();
   c.timing = o.kernel_timing != 0;
   c.autotune = o.autotune != 0;
+  c.sm_share = o.max_sms;
   Timer tm;
   tm.rec(0, stream);
   Engine E;
@@ -985,6 +986,7 @@ static int round_adaptive(const SumTT& X, double tol, int64_t block, uint64_t se
   c.prof_begin();
   c.timing = o.kernel_timing != 0;
   c.autotune = o.autotune != 0;
+  c.sm_share = o.max_sms;
   Timer tm;
   tm.rec(0, stream);
   const int d = X.d;

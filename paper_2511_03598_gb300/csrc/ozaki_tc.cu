@@ -921,9 +921,14 @@ static int prep_b_float(Ctx& c, const double* B, int64_t sbk, int64_t sbn, int64
 
 // K per CTA for `tiles` output tiles: the fewest K-chunks per CTA that keep the grid within one
 // wave (one CTA per SM: the shared memory and TMEM of a CTA fill an SM), at most KSEG.
-static int kseg_for(int64_t tiles, int64_t K) {
+// K per CTA: the fewest 32-deep chunks per CTA with which the tiles' K segments fit in one wave of
+// the SMs the call is sized for (all of them, or its share ttr_options::max_sms when several calls
+// share the GPU: fewer, longer CTAs then spend less SM time on the per-CTA exponent scans, TMEM
+// set-up and the atomic epilogues of partial results).
+static int kseg_for(const Ctx& c, int64_t tiles, int64_t K) {
   int dev = 0, nsm = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (c.sm_share > 0 && c.sm_share < nsm) nsm = c.sm_share;
   const int64_t kch = (K + KC - 1) / KC;
   for (int cp = 1; cp < KSEG / KC; ++cp)
     if (cp >= kch || tiles * ((kch + cp - 1) / cp) <= nsm) return cp * KC;
@@ -1047,17 +1052,17 @@ using namespace tc;
 
 // candidates of a plain product (M rows in 128-row tiles, K, N columns): the default split first,
 // then the other K splits, then half-width tiles (two column chunks) with their default split
-static void add_plain_candidates(std::vector<TuneVal>& cands, int s, int64_t M, int64_t K, int64_t N) {
+static void add_plain_candidates(const Ctx& c, std::vector<TuneVal>& cands, int s, int64_t M, int64_t K, int64_t N) {
   const int tw = tile_width(s);
   auto tiles_for = [&](int tmax) {
     const int64_t nch = (N + tmax - 1) / tmax;
     return (M + TM - 1) / TM * nch;
   };
-  const int kd = kseg_for(tiles_for(tw), K);
+  const int kd = kseg_for(c, tiles_for(tw), K);
   for (int k : kseg_candidates(kd, K)) cands.push_back({tw, k, 0});
   if (N > 32) {
     const int half = (int)std::min<int64_t>(tw, std::max<int64_t>(16, ((N + 1) / 2 + 15) / 16 * 16));
-    if (half < tw) cands.push_back({half, kseg_for(tiles_for(half), K), 0});
+    if (half < tw) cands.push_back({half, kseg_for(c, tiles_for(half), K), 0});
   }
 }
 
@@ -1092,7 +1097,7 @@ int tc_gemm_tn(Ctx& c, int slices, const double* X, int64_t ldx, int64_t m, int6
     return launch<PLAIN, false>(c, a, grid, "tc_gemm_tn");
   };
   std::vector<TuneVal> cands;
-  add_plain_candidates(cands, slices, a_cols, m, b_cols);
+  add_plain_candidates(c, cands, slices, a_cols, m, b_cols);
   TuneVal v;
   TTR_CHECK(tuned(c, TuneKey{TK_GEMM_TN, slices, a_cols, m, b_cols, 0}, cands, run, v));
   return run(v);
@@ -1129,11 +1134,11 @@ int tc_rl_step(Ctx& c, int slices, const double* Xk, int64_t r0, int64_t n, int6
   const int g0 = (int)(TM / n);
   const int64_t nch = (w + tw - 1) / tw;
   std::vector<TuneVal> cands;
-  const int kd = kseg_for((r0 + g0 - 1) / g0 * nch, r1);
+  const int kd = kseg_for(c, (r0 + g0 - 1) / g0 * nch, r1);
   for (int k : kseg_candidates(kd, r1)) cands.push_back({tw, k, g0});
   if (g0 >= 2) {
     const int g1 = g0 / 2;
-    cands.push_back({tw, kseg_for((r0 + g1 - 1) / g1 * nch, r1), g1});
+    cands.push_back({tw, kseg_for(c, (r0 + g1 - 1) / g1 * nch, r1), g1});
   }
   TuneVal v;
   TTR_CHECK(tuned(c, TuneKey{TK_RL, slices, r0, r1, w, n}, cands,
@@ -1210,9 +1215,9 @@ int tc_gemm_rowmajor(Ctx& c, int slices, const double* A, int64_t lda, int64_t M
   if (reused) {
     // the planes fix the tile width: only the K split is free
     const int64_t tiles = (M + TM - 1) / TM * reuse->nchunks;
-    for (int k : kseg_candidates(kseg_for(tiles, K), K)) cands.push_back({reuse->tn, k, 0});
+    for (int k : kseg_candidates(kseg_for(c, tiles, K), K)) cands.push_back({reuse->tn, k, 0});
   } else {
-    add_plain_candidates(cands, slices, M, K, N);
+    add_plain_candidates(c, cands, slices, M, K, N);
   }
   TuneVal v;
   TTR_CHECK(tuned(c, TuneKey{TK_ROWMAJOR, slices, M, K, N, reused ? reuse->tn : 0}, cands, run, v));
@@ -1242,7 +1247,7 @@ int tc_project(Ctx& c, int slices, const double* Mk, int64_t ldm, int64_t L, int
     return launch<PLAIN, false>(c, a, grid, "tc_project");
   };
   std::vector<TuneVal> cands;
-  add_plain_candidates(cands, slices, ncol, K, L);
+  add_plain_candidates(c, cands, slices, ncol, K, L);
   TuneVal v;
   TTR_CHECK(tuned(c, TuneKey{TK_PROJECT, slices, ncol, K, L, 0}, cands, run, v));
   return run(v);
@@ -1321,7 +1326,7 @@ int tc_rl_step_flt(Ctx& c, int fs, const double* Xk, int64_t r0, int64_t n, int6
   a.Omd = Om; a.ldo = ldo; a.nmode = n; a.g = (int)(TM / n); a.slabs = r0; a.W = Wout; a.ldw = ldwo;
   a.err = c.d_flags; a.flt = 1;
   const int64_t tiles = (r0 + a.g - 1) / a.g * bp.nchunks;
-  a.kseg = kseg_for(tiles, r1);
+  a.kseg = kseg_for(c, tiles, r1);
   const unsigned ksplit = (unsigned)((r1 + a.kseg - 1) / a.kseg);
   if (ksplit > 1) {
     a.watomic = 1;
@@ -1345,7 +1350,7 @@ int tc_gemm_rowmajor_flt(Ctx& c, int fs, const double* A, int64_t lda, int64_t M
   a.Bp = bp.planes; a.Fmax = nullptr; a.N = N; a.kchunks = bp.kchunks; a.s = fs; a.tn = bp.tn;
   a.C = C; a.scm = ldc; a.scn = 1; a.err = c.d_flags; a.flt = 1;
   const int64_t tiles = (M + TM - 1) / TM * bp.nchunks;
-  a.kseg = kseg_for(tiles, K);
+  a.kseg = kseg_for(c, tiles, K);
   const unsigned ksplit = (unsigned)((K + a.kseg - 1) / a.kseg);
   dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)bp.nchunks, ksplit);
   if (ksplit > 1) {

@@ -64,6 +64,7 @@ struct Ctx {
   std::vector<std::pair<const char*, cudaEvent_t>> prof;
   bool profiling = false;
   bool autotune = false;           // tensor-core launches: measure tile shapes on first use (ttr_options::autotune)
+  int sm_share = 0;                // SMs this call's K-split launches are sized for (ttr_options::max_sms; 0: all)
   cudaEvent_t prof_start = nullptr;
   void prof_begin();
   void prof_report();
