@@ -940,16 +940,18 @@ static int kseg_for(const Ctx& c, int64_t tiles, int64_t K) {
 // work split but not the product's error bound: the widest tile (UMMA N) the B digit planes are cut
 // for, the K per CTA (K-split CTAs add their partial results atomically in FP64, as the default
 // split does), and, for the partial contractions, the mode slabs per 128-row tile.  With
-// ttr_options::autotune set, the first call of each shape (kind of launch, slices, M, K, N, n_k)
+// ttr_options::autotune set, the first call of each shape (kind of launch, slices, M, K, N, n_k, SM share)
 // times every candidate on its stream (each run twice, the second timed between two events, the
 // whole call: B preparation and product) and keeps the fastest for the rest of the process; every
 // later call of that shape, tuned or not, uses the table.
 struct TuneKey {
   int kind, s;
   int64_t M, K, N, n;
+  int share = 0;   // the call's SM share (Ctx::sm_share): the default split and candidates depend on it
   bool operator<(const TuneKey& o) const {
     if (kind != o.kind) return kind < o.kind;
     if (s != o.s) return s < o.s;
+    if (share != o.share) return share < o.share;
     if (M != o.M) return M < o.M;
     if (K != o.K) return K < o.K;
     if (N != o.N) return N < o.N;
@@ -996,7 +998,8 @@ static TuneKey bucketed(const TuneKey& k) {
 // `cands` measured with `run`, else cands[0]
 template <class F>
 static int tuned(Ctx& c, const TuneKey& key_exact, const std::vector<TuneVal>& cands, F run, TuneVal& out) {
-  const TuneKey key = bucketed(key_exact);
+  TuneKey key = bucketed(key_exact);
+  key.share = c.sm_share;
   {
     std::lock_guard<std::mutex> lock(tune_mu);
     auto it = tune_table().find(key);
