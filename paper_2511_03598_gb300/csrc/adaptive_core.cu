@@ -430,6 +430,47 @@ __device__ void gram_acc(const typename A::T* X, int ldx, const typename A::T* Y
   }
 }
 
+// buf[i b + j] and buf[j b + i] += sum over the own rows of X(r, i) X(r, j) for i <= j < b: the
+// upper triangle of a symmetric Gram matrix, the rows of each entry split over ks lanes (ks a power
+// of two, at most 8, at least 4 rows a part) so that the few entries of a narrow block still spread
+// over the warps; the ks partial sums meet by xor shuffles.  Warp-uniform trip counts.
+template <class A>
+__device__ void gram_sym_acc(const typename A::T* X, int ldx, int b, int nr, double* buf) {
+  using T = typename A::T;
+  const int nout = b * (b + 1) / 2;
+  int ks = 1;
+  while (ks < 8 && nout * ks * 2 <= NT && nr >= 8 * ks) ks *= 2;
+  const int per = (nr + ks - 1) / ks;
+  const int total = nout * ks;
+  const int lane = threadIdx.x & 31;
+  for (int base = threadIdx.x - lane; base < total; base += NT) {
+    const int o = base + lane;
+    const bool live = o < total;
+    const int u = live ? o / ks : 0, p = o % ks;
+    int i = 0, rem = u;                                     // u -> (i, j): triangle row i holds b - i entries
+    while (rem >= b - i) {
+      rem -= b - i;
+      ++i;
+    }
+    const int j = i + rem;
+    const int r0 = live ? p * per : 0, r1 = live ? min(nr, r0 + per) : 0;
+    T s0 = A::zero(), s1 = A::zero();
+    int r = r0;
+    for (; r + 1 < r1; r += 2) {
+      s0 = A::fma(X[r * ldx + i], X[r * ldx + j], s0);
+      s1 = A::fma(X[(r + 1) * ldx + i], X[(r + 1) * ldx + j], s1);
+    }
+    if (r < r1) s0 = A::fma(X[r * ldx + i], X[r * ldx + j], s0);
+    T t = A::add(s0, s1);
+    for (int m = 1; m < ks; m <<= 1) t = A::add(t, A::shfl_xor(t, m));
+    if (live && p == 0 && nr > 0) {
+      const double v = A::to(t);
+      atomicAdd(buf + i * b + j, v);
+      if (i != j) atomicAdd(buf + j * b + i, v);
+    }
+  }
+}
+
 // buf[0] += sum of squares of the own rows of X (b columns, shared memory)
 template <class A>
 __device__ void sumsq_acc(const typename A::T* X, int ldx, int b, int nr, double* buf) {
@@ -729,17 +770,24 @@ __device__ bool rinv_near_identity(const double* G, int b, double* Ri, double* N
 template <class A>
 __device__ void apply_rinv(typename A::T* X, int ldx, int b, const typename A::T* Ri, int nr, typename A::T* T) {
   using V = typename A::T;
-  for (int e = threadIdx.x; e < nr * b; e += NT) {
-    const int r = e / b, j = e % b;
+  // a task is row r and the column pair j, b - 1 - j (j < ceil(b / 2)): column j takes j + 1 terms
+  // and column b - 1 - j takes b - j, so every task makes b + 1 multiply-adds in one loop.  A warp
+  // issues each FP64 instruction for all its lanes, masked or not, so equal trip counts keep the
+  // lanes of the triangular product busy.
+  const int hb = (b + 1) / 2;
+  for (int e = threadIdx.x; e < nr * hb; e += NT) {
+    const int r = e / hb, j = e % hb, j2 = b - 1 - j;
     const V* xr = X + r * ldx;
-    V v0 = A::zero(), v1 = A::zero();
-    int i = 0;
-    for (; i + 1 <= j; i += 2) {
-      v0 = A::fma(xr[i], Ri[i * b + j], v0);
-      v1 = A::fma(xr[i + 1], Ri[(i + 1) * b + j], v1);
+    V v = A::zero(), w = A::zero();
+    for (int t = 0; t <= b; ++t) {
+      const bool first = t <= j;
+      const int i = first ? t : t - j - 1;
+      const V res = A::fma(xr[i], Ri[i * b + (first ? j : j2)], first ? v : w);
+      if (first) v = res;
+      else w = res;
     }
-    if (i <= j) v0 = A::fma(xr[i], Ri[i * b + j], v0);
-    T[e] = A::add(v0, v1);
+    T[r * b + j] = v;
+    if (j2 != j) T[r * b + j2] = w;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * b; e += NT) X[(e / b) * ldx + e % b] = T[e];
@@ -908,7 +956,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     const int b0 = a.b0;
     for (int e = threadIdx.x; e < nr * b0; e += NT) Qs[(e / b0) * ldq + e % b0] = Ss[(e / b0) * ldw + e % b0];
     __syncthreads();
-    gram_acc<A>(Qs, ldq, Qs, ldq, b0, b0, nr, red_out(rd));
+    gram_sym_acc<A>(Qs, ldq, b0, nr, red_out(rd));
     double* buf = reduce();
     if (!buf) return finish(ST_TIMEOUT);
     read_totals(buf, b0 * b0, G, rd.used);
@@ -916,7 +964,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     to_arith<A>(Ri, b0 * b0, RiT);
     apply_rinv<A>(Qs, ldq, b0, RiT, nr, Tb);
     const bool want = b0 < a.rbar && b0 + bi <= a.width;
-    gram_acc<A>(Qs, ldq, Qs, ldq, b0, b0, nr, red_out(rd));
+    gram_sym_acc<A>(Qs, ldq, b0, nr, red_out(rd));
     if (want) gram_acc<A>(Qs, ldq, Ss + b0, ldw, b0, bi, nr, red_out(rd) + b0 * b0);
     buf = reduce();
     if (!buf) return finish(ST_TIMEOUT);
@@ -970,7 +1018,7 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
     {
       double* eb = red_out(rd);
       sumsq_acc<A>(Rs, bi, bi, nr, eb);
-      gram_acc<A>(Rs, bi, Rs, bi, bb, bb, nr, eb + 1);
+      gram_sym_acc<A>(Rs, bi, bb, nr, eb + 1);
     }
     tmr.mark(PH_B_LOCAL);
     double* bufB = reduce();
