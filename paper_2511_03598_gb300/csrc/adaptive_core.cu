@@ -801,8 +801,7 @@ __device__ void to_arith(const double* src, int n, typename A::T* dst) {
   __syncthreads();
 }
 
-// own rows: X(:, 0:b) -= Q(:, 0:c) P, P (c x b, leading dimension ldp) in shared memory;
-// four independent FMA chains per element
+// own rows: X(:, 0:b) -= Q(:, 0:c) P, P (c x b, leading dimension ldp) in shared memory
 template <class A>
 __device__ void sub_qp(typename A::T* X, int ldx, const typename A::T* Q, int ldq, int c, const typename A::T* P,
                        int ldp, int b, int nr) {
@@ -811,16 +810,16 @@ __device__ void sub_qp(typename A::T* X, int ldx, const typename A::T* Q, int ld
   for (int e = threadIdx.x; e < nr * b; e += NT) {
     const int r = e / b, j = e % b;
     const V* qr = Q + r * ldq;
-    V s0 = A::zero(), s1 = A::zero(), s2 = A::zero(), s3 = A::zero();
+    // two chains, the first starting from X(r, j): one FP64 addition per element to join them
+    // (each FP64 warp instruction holds this part's FP64 unit for 64 cycles, so the joins count)
+    V s0 = X[r * ldx + j], s1 = A::zero();
     int i = 0;
-    for (; i + 3 < c; i += 4) {
-      s0 = A::fma(qr[i], P[i * ldp + j], s0);
-      s1 = A::fma(qr[i + 1], P[(i + 1) * ldp + j], s1);
-      s2 = A::fma(qr[i + 2], P[(i + 2) * ldp + j], s2);
-      s3 = A::fma(qr[i + 3], P[(i + 3) * ldp + j], s3);
+    for (; i + 1 < c; i += 2) {
+      s0 = A::fma(A::neg(qr[i]), P[i * ldp + j], s0);
+      s1 = A::fma(A::neg(qr[i + 1]), P[(i + 1) * ldp + j], s1);
     }
-    for (; i < c; ++i) s0 = A::fma(qr[i], P[i * ldp + j], s0);
-    X[r * ldx + j] = A::add(X[r * ldx + j], A::neg(A::add(A::add(s0, s1), A::add(s2, s3))));
+    if (i < c) s0 = A::fma(A::neg(qr[i]), P[i * ldp + j], s0);
+    X[r * ldx + j] = A::add(s0, s1);
   }
   __syncthreads();
 }
