@@ -127,7 +127,7 @@ def probe_peaks() -> dict:
 # this workload in sliced precision, for the kernels as they stand (the capture command is in
 # profiles/): the FP64 block loop's figure is the median over full-rank cores, the partial
 # contraction's the mean over all 18 launches of one pass.  Other precisions run other kernels.
-TRAFFIC_SLICED = {"block_loop": 2.456e6, "rl_kernel": 17.98e6}
+TRAFFIC_SLICED = {"block_loop": 2.454e6, "rl_kernel": 17.98e6}
 
 
 def serving_run(B, nreq: int, workers: int, budget: int, nreq_open: int | None = None) -> dict:
