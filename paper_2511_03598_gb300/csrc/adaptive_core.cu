@@ -430,31 +430,6 @@ __device__ void gram_acc(const typename A::T* X, int ldx, const typename A::T* Y
   }
 }
 
-// gram_acc of X against the columns of Y1 (b1) and of Y2 (b2) in one pass: buf1[i b1 + j] and
-// buf2[i b2 + j] (i < a), so that the two products share one tail of partly filled warps
-template <class A>
-__device__ void gram_acc2(const typename A::T* X, int ldx, const typename A::T* Y1, int ldy1, int b1,
-                          const typename A::T* Y2, int ldy2, int b2, int a, int nr, double* buf1, double* buf2) {
-  using T = typename A::T;
-  const int bt = b1 + b2;
-  for (int o = threadIdx.x; o < a * bt; o += NT) {
-    const int i = o / bt, jj = o % bt;
-    const bool one = jj < b1;
-    const T* Y = one ? Y1 + jj : Y2 + (jj - b1);
-    const int ldy = one ? ldy1 : ldy2;
-    T s0 = A::zero(), s1 = A::zero(), s2 = A::zero(), s3 = A::zero();      // four independent chains
-    int r = 0;
-    for (; r + 3 < nr; r += 4) {
-      s0 = A::fma(X[r * ldx + i], Y[r * ldy], s0);
-      s1 = A::fma(X[(r + 1) * ldx + i], Y[(r + 1) * ldy], s1);
-      s2 = A::fma(X[(r + 2) * ldx + i], Y[(r + 2) * ldy], s2);
-      s3 = A::fma(X[(r + 3) * ldx + i], Y[(r + 3) * ldy], s3);
-    }
-    for (; r < nr; ++r) s0 = A::fma(X[r * ldx + i], Y[r * ldy], s0);
-    if (nr > 0) atomicAdd(one ? buf1 + i * b1 + jj : buf2 + i * b2 + (jj - b1), A::to(A::add(A::add(s0, s1), A::add(s2, s3))));
-  }
-}
-
 // buf[i b + j] and buf[j b + i] += sum over the own rows of X(r, i) X(r, j) for i <= j < b: the
 // upper triangle of a symmetric Gram matrix, the rows of each entry split over ks lanes (ks a power
 // of two, at most 8, at least 4 rows a part) so that the few entries of a narrow block still spread
@@ -1092,8 +1067,8 @@ __global__ void __launch_bounds__(NT, 1) adaptive_core_kernel(Args a) {
           return finish(ST_TIMEOUT);
         }
       } else {
-        // (cc + bb) x bb and, when wanted, (cc + bb) x bi
-        gram_acc2<A>(Qs, ldq, Qn, ldq, bb, Ss + nxt, ldw, want ? bi : 0, nxt, nr, eb, eb + nxt * bb);
+        gram_acc<A>(Qs, ldq, Qn, ldq, nxt, bb, nr, eb);                                  // (cc + bb) x bb
+        if (want) gram_acc<A>(Qs, ldq, Ss + nxt, ldw, nxt, bi, nr, eb + nxt * bb);      // (cc + bb) x bi
       }
     }
     tmr.mark(PH_RO_LOCAL);
